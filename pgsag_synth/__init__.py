@@ -1,0 +1,414 @@
+"""Seeded synthetic inputs for the masked Gaussian-splat path.
+
+This module only *draws* inputs: Gaussian parameters, pinhole cameras, binary
+building masks and photometric targets.  It holds none of the method's
+arithmetic (no projection, blending, loss or mask morphology), so both the
+FP64 oracle and the CUDA path may use it.
+
+Shapes and distributions follow the paper's workloads: aerial oblique views of
+building clusters at the original GauU-Scene resolution (Sec. 5.1, 5468x3636
+images, 120 m flight height) with building masks (Sec. 4.1).  The datasets
+themselves are not available, so seeded stand-ins are drawn here.
+
+All arrays are float32 (the kernels' input precision); the oracle upcasts the
+same float32 values to float64.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+BASE_SEED = 2025_0103
+SH_COEFFS = 16  # degree 3
+
+
+@dataclasses.dataclass
+class Camera:
+    """Pinhole camera, OpenCV axes (x right, y down, z forward).
+
+    x_cam = R @ x_world + t.  Pixel (u, v) has its centre at (u+0.5, v+0.5).
+    """
+    R: np.ndarray          # float32 [3,3] world -> camera rotation
+    t: np.ndarray          # float32 [3]
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+    znear: float = 0.2
+
+    def __post_init__(self):
+        self.R = np.asarray(self.R, dtype=np.float32).reshape(3, 3)
+        self.t = np.asarray(self.t, dtype=np.float32).reshape(3)
+        self.fx = float(np.float32(self.fx))
+        self.fy = float(np.float32(self.fy))
+        self.cx = float(np.float32(self.cx))
+        self.cy = float(np.float32(self.cy))
+        self.znear = float(np.float32(self.znear))
+
+
+@dataclasses.dataclass
+class Gaussians:
+    """Raw (pre-activation) Gaussian parameters, SoA float32."""
+    means: np.ndarray          # [N,3]
+    log_scales: np.ndarray     # [N,3]
+    quats: np.ndarray          # [N,4]  (w, x, y, z), not necessarily unit
+    opacity_logit: np.ndarray  # [N]
+    sh: np.ndarray             # [N,16,3]  coefficient-major, channel-minor
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    def subset(self, idx) -> "Gaussians":
+        return Gaussians(self.means[idx], self.log_scales[idx], self.quats[idx],
+                         self.opacity_logit[idx], self.sh[idx])
+
+    @staticmethod
+    def concat(parts: Sequence["Gaussians"]) -> "Gaussians":
+        return Gaussians(*(np.ascontiguousarray(np.concatenate([getattr(p, f.name) for p in parts], 0))
+                           for f in dataclasses.fields(Gaussians)))
+
+
+@dataclasses.dataclass
+class View:
+    """One rendered view: camera, building mask (u8 0/1, [H,W]) and target RGB [H,W,3]."""
+    cam: Camera
+    mask: np.ndarray
+    target: np.ndarray
+
+
+def streams(config_index: int, n: int = 4) -> List[np.random.Generator]:
+    """Independent PCG64 streams (scene, cameras, mask, target) for one config."""
+    ss = np.random.SeedSequence(BASE_SEED + config_index)
+    return [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(n)]
+
+
+# --------------------------------------------------------------------------
+# cameras
+# --------------------------------------------------------------------------
+
+def look_at_camera(campos, target, width, height, fx, fy=None, up=(0.0, 0.0, 1.0), znear=0.2) -> Camera:
+    """Camera at `campos` looking at `target`; image principal point at the centre."""
+    campos = np.asarray(campos, np.float64)
+    fwd = np.asarray(target, np.float64) - campos
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, np.asarray(up, np.float64))
+    if np.linalg.norm(right) < 1e-9:
+        right = np.cross(fwd, np.array([0.0, 1.0, 0.0]))
+    right /= np.linalg.norm(right)
+    down = np.cross(fwd, right)
+    R = np.stack([right, down, fwd], 0)
+    t = -R @ campos
+    fy = fx if fy is None else fy
+    return Camera(R, t, fx, fy, width / 2.0, height / 2.0, width, height, znear)
+
+
+def identity_camera(width, height, fx, fy=None, znear=0.2) -> Camera:
+    fy = fx if fy is None else fy
+    return Camera(np.eye(3), np.zeros(3), fx, fy, width / 2.0, height / 2.0, width, height, znear)
+
+
+# --------------------------------------------------------------------------
+# Gaussian attributes
+# --------------------------------------------------------------------------
+
+def random_quats(rng, n) -> np.ndarray:
+    q = rng.standard_normal((n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return q.astype(np.float32)
+
+
+def _rotmat_to_quat(M: np.ndarray) -> np.ndarray:
+    """Rotation matrices [n,3,3] -> quaternions (w,x,y,z) (input drawing only)."""
+    from scipy.spatial.transform import Rotation
+    xyzw = Rotation.from_matrix(M).as_quat()
+    return np.concatenate([xyzw[:, 3:4], xyzw[:, :3]], 1)
+
+
+def cube_scene(rng, n, cube=10.0, zmin=5.0, zmax=15.0) -> Gaussians:
+    """Means uniform in a cube (side `cube`) spanning depth [zmin, zmax] in front of
+    an identity camera; log-scales N(-3, 0.5); uniform unit quaternions; opacity
+    logits N(0,1); SH degree-3 coefficients N(0, 0.2)."""
+    means = np.empty((n, 3), np.float64)
+    means[:, 0] = rng.uniform(-cube / 2, cube / 2, n)
+    means[:, 1] = rng.uniform(-cube / 2, cube / 2, n)
+    means[:, 2] = rng.uniform(zmin, zmax, n)
+    log_scales = rng.normal(-3.0, 0.5, (n, 3))
+    quats = random_quats(rng, n)
+    opac = rng.normal(0.0, 1.0, n)
+    sh = rng.normal(0.0, 0.2, (n, SH_COEFFS, 3))
+    return Gaussians(means.astype(np.float32), log_scales.astype(np.float32), quats,
+                     opac.astype(np.float32), sh.astype(np.float32))
+
+
+# --------------------------------------------------------------------------
+# masks and targets
+# --------------------------------------------------------------------------
+
+def rect_mask(rng, height, width, coverage=0.40, tol=0.03, nmin=3, nmax=6, max_tries=10000) -> np.ndarray:
+    """Union of nmin..nmax random axis-aligned rectangles, rejection-sampled until the
+    covered fraction is within coverage +- tol."""
+    for _ in range(max_tries):
+        m = np.zeros((height, width), np.uint8)
+        k = int(rng.integers(nmin, nmax + 1))
+        for _ in range(k):
+            w = int(rng.integers(max(1, width // 8), max(2, (width * 3) // 4)))
+            h = int(rng.integers(max(1, height // 8), max(2, (height * 3) // 4)))
+            x0 = int(rng.integers(0, max(1, width - w + 1)))
+            y0 = int(rng.integers(0, max(1, height - h + 1)))
+            m[y0:y0 + h, x0:x0 + w] = 1
+        if abs(m.mean() - coverage) <= tol:
+            return m
+    raise RuntimeError("rect_mask: coverage target not reached")
+
+
+def random_target(rng, height, width) -> np.ndarray:
+    return rng.random((height, width, 3), dtype=np.float32)
+
+
+# --------------------------------------------------------------------------
+# aerial building scenes
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Box:
+    x0: float
+    y0: float
+    x1: float
+    y1: float
+    h: float
+
+
+def random_boxes(rng, n, area=160.0, fmin=8.0, fmax=30.0, hmin=8.0, hmax=45.0, gap=2.0,
+                 footprint_scale=1.0, max_tries=200000) -> List[Box]:
+    """n non-overlapping box 'buildings' with footprints U(fmin,fmax)*scale and heights
+    U(hmin,hmax) inside an area x area square centred at the origin."""
+    boxes: List[Box] = []
+    tries = 0
+    while len(boxes) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("random_boxes: could not place boxes")
+        w = rng.uniform(fmin, fmax) * footprint_scale
+        d = rng.uniform(fmin, fmax) * footprint_scale
+        h = rng.uniform(hmin, hmax)
+        if w >= area or d >= area:
+            continue
+        x0 = rng.uniform(-area / 2, area / 2 - w)
+        y0 = rng.uniform(-area / 2, area / 2 - d)
+        ok = all(x0 + w + gap <= b.x0 or b.x1 + gap <= x0 or y0 + d + gap <= b.y0 or b.y1 + gap <= y0
+                 for b in boxes)
+        if ok:
+            boxes.append(Box(x0, y0, x0 + w, y0 + d, h))
+    return boxes
+
+
+def _surfaces(boxes: Sequence[Box], ground: float):
+    """Rectangular surfaces (origin, edge u, edge v, outward normal)."""
+    S = []
+    g = ground / 2
+    S.append((np.array([-g, -g, 0.0]), np.array([ground, 0, 0.0]), np.array([0, ground, 0.0]), np.array([0, 0, 1.0])))
+    for b in boxes:
+        w, d, h = b.x1 - b.x0, b.y1 - b.y0, b.h
+        S.append((np.array([b.x0, b.y0, h]), np.array([w, 0, 0.0]), np.array([0, d, 0.0]), np.array([0, 0, 1.0])))
+        S.append((np.array([b.x0, b.y0, 0.0]), np.array([w, 0, 0.0]), np.array([0, 0, h]), np.array([0, -1.0, 0])))
+        S.append((np.array([b.x0, b.y1, 0.0]), np.array([w, 0, 0.0]), np.array([0, 0, h]), np.array([0, 1.0, 0])))
+        S.append((np.array([b.x0, b.y0, 0.0]), np.array([0, d, 0.0]), np.array([0, 0, h]), np.array([-1.0, 0, 0])))
+        S.append((np.array([b.x1, b.y0, 0.0]), np.array([0, d, 0.0]), np.array([0, 0, h]), np.array([1.0, 0, 0])))
+    return S
+
+
+def surface_gaussians(rng, boxes: Sequence[Box], n: int, ground: float = 200.0) -> Gaussians:
+    """n flat, surface-hugging Gaussians on the box surfaces and the ground plane,
+    placed proportionally to area; tangent log-scales N(-3,0.5), the normal axis
+    ten times thinner; random in-plane twist; other attributes as cube_scene."""
+    S = _surfaces(boxes, ground)
+    areas = np.array([np.linalg.norm(np.cross(u, v)) for _, u, v, _ in S])
+    counts = rng.multinomial(n, areas / areas.sum())
+    means, rots = [], []
+    for (o, u, v, nrm), c in zip(S, counts):
+        if c == 0:
+            continue
+        a = rng.random((c, 1))
+        b = rng.random((c, 1))
+        means.append(o[None] + a * u[None] + b * v[None] + 1e-3 * nrm[None])
+        tu = u / np.linalg.norm(u)
+        tv = np.cross(nrm, tu)
+        th = rng.uniform(0, 2 * np.pi, c)
+        t1 = np.cos(th)[:, None] * tu[None] + np.sin(th)[:, None] * tv[None]
+        t2 = np.cross(np.broadcast_to(nrm, t1.shape), t1)
+        M = np.stack([t1, t2, np.broadcast_to(nrm, t1.shape)], axis=2)  # columns = axes
+        rots.append(M)
+    means = np.concatenate(means, 0)
+    M = np.concatenate(rots, 0)
+    perm = rng.permutation(n)
+    means, M = means[perm], M[perm]
+    quats = _rotmat_to_quat(M)
+    ls = rng.normal(-3.0, 0.5, (n, 3))
+    ls[:, 2] = rng.normal(-3.0, 0.5, n) - math.log(10.0)
+    opac = rng.normal(0.0, 1.0, n)
+    sh = rng.normal(0.0, 0.2, (n, SH_COEFFS, 3))
+    return Gaussians(means.astype(np.float32), ls.astype(np.float32), quats.astype(np.float32),
+                     opac.astype(np.float32), sh.astype(np.float32))
+
+
+def raycast_box_mask(boxes: Sequence[Box], cam: Camera, step: int = 1) -> np.ndarray:
+    """Binary mask of the pixels whose ray hits a box (boxes stand on the ground, so a
+    box hit is always in front of the ground hit).  `step` > 1 casts a subsampled grid."""
+    H, W = cam.height, cam.width
+    R = cam.R.astype(np.float64)
+    t = cam.t.astype(np.float64)
+    C = -R.T @ t
+    us = np.arange(0, W, step) + 0.5
+    vs = np.arange(0, H, step) + 0.5
+    m = np.zeros((len(vs), len(us)), np.uint8)
+    for b in boxes:
+        corners = np.array([[x, y, z] for x in (b.x0, b.x1) for y in (b.y0, b.y1) for z in (0.0, b.h)])
+        pc = corners @ R.T + t
+        if np.all(pc[:, 2] <= 1e-6):
+            continue
+        if np.any(pc[:, 2] <= 1e-6):
+            ub = (0, W)
+            vb = (0, H)
+        else:
+            px = cam.fx * pc[:, 0] / pc[:, 2] + cam.cx
+            py = cam.fy * pc[:, 1] / pc[:, 2] + cam.cy
+            ub = (max(0.0, px.min() - 2), min(float(W), px.max() + 2))
+            vb = (max(0.0, py.min() - 2), min(float(H), py.max() + 2))
+        iu = np.nonzero((us >= ub[0]) & (us <= ub[1]))[0]
+        iv = np.nonzero((vs >= vb[0]) & (vs <= vb[1]))[0]
+        if len(iu) == 0 or len(iv) == 0:
+            continue
+        uu, vv = np.meshgrid(us[iu], vs[iv])
+        dcam = np.stack([(uu - cam.cx) / cam.fx, (vv - cam.cy) / cam.fy, np.ones_like(uu)], -1)
+        dw = dcam @ R  # R^T d
+        lo = np.array([b.x0, b.y0, 0.0])
+        hi = np.array([b.x1, b.y1, b.h])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / dw
+            t0 = (lo - C) * inv
+            t1 = (hi - C) * inv
+        tmin = np.nanmax(np.minimum(t0, t1), axis=-1)
+        tmax = np.nanmin(np.maximum(t0, t1), axis=-1)
+        hit = (tmax >= np.maximum(tmin, 0.0)).astype(np.uint8)
+        sub = m[np.ix_(iv, iu)]
+        m[np.ix_(iv, iu)] = np.maximum(sub, hit)
+    return m
+
+
+def aerial_views(rng_scene, rng_cam, n_gauss, n_boxes, area, cams_fn, coverage=None, cov_tol=0.05,
+                 ground=None, max_iter=6):
+    """Boxes + surface Gaussians + cameras + ray-cast masks.  If `coverage` is given,
+    footprints are rescaled until the first view's mask covers coverage +- cov_tol."""
+    ground = ground if ground is not None else area * 1.25
+    scale = 1.0
+    state = rng_scene.bit_generator.state
+    for _ in range(max_iter):
+        rng_scene.bit_generator.state = state
+        boxes = random_boxes(rng_scene, n_boxes, area=area, footprint_scale=scale)
+        cams = cams_fn(rng_cam)
+        if coverage is None:
+            break
+        cov = raycast_box_mask(boxes, cams[0], step=8).mean()
+        if abs(cov - coverage) <= cov_tol:
+            break
+        scale *= math.sqrt(coverage / max(cov, 1e-3))
+    g = surface_gaussians(rng_scene, boxes, n_gauss, ground=ground)
+    masks = [raycast_box_mask(boxes, c) for c in cams]
+    return g, boxes, cams, masks
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+
+def config0() -> Tuple[Gaussians, List[View]]:
+    """20k Gaussians in a 10 m cube 5-15 m in front of a 256x256 pinhole camera
+    (fx = fy = 300), rectangle mask ~40%, uniform random target."""
+    rs, rc, rm, rt = streams(0)
+    g = cube_scene(rs, 20000)
+    cam = identity_camera(256, 256, 300.0)
+    mask = rect_mask(rm, 256, 256, 0.40, 0.03)
+    return g, [View(cam, mask, random_target(rt, 256, 256))]
+
+
+def aerial_camera(width, height, altitude=120.0, pitch_deg=45.0, azimuth_deg=0.0, look_at=(0.0, 0.0, 0.0),
+                  fx_factor=1.2) -> Camera:
+    """Oblique camera at `altitude` m, looking down at `pitch_deg` towards `look_at`."""
+    dist = altitude / math.tan(math.radians(pitch_deg))
+    az = math.radians(azimuth_deg)
+    campos = np.array(look_at, np.float64) + np.array([-dist * math.cos(az), -dist * math.sin(az), altitude])
+    return look_at_camera(campos, look_at, width, height, fx_factor * width)
+
+
+def config1(n_gauss=1_500_000, width=5472, height=3648):
+    """Single oblique aerial view at 5472x3648 of 40 box buildings (1.5M surface
+    Gaussians over a ground plane), fx = 1.2 W, 120 m altitude, 45 deg pitch; the
+    building mask (ray-cast) covers ~35% of the pixels."""
+    rs, rc, rm, rt = streams(1)
+    g, boxes, cams, masks = aerial_views(
+        rs, rc, n_gauss, 40, 160.0,
+        lambda r: [aerial_camera(width, height, 120.0, 45.0)], coverage=0.35, cov_tol=0.05, ground=200.0)
+    return g, [View(cams[0], masks[0], random_target(rt, height, width))], boxes
+
+
+def config2(n_gauss=300_000, width=1920, height=1080, n_views=4):
+    """300k Gaussians on 8 buildings, 4 views at 1920x1080 (fx = 2304) around the block."""
+    rs, rc, rm, rt = streams(2)
+    area = 160.0 * math.sqrt(8 / 40)
+
+    def cams_fn(r):
+        return [aerial_camera(width, height, 60.0, 45.0, azimuth_deg=90.0 * j) for j in range(n_views)]
+    g, boxes, cams, masks = aerial_views(rs, rc, n_gauss, 8, area, cams_fn, ground=area * 1.25)
+    return g, [View(c, m, random_target(rt, height, width)) for c, m in zip(cams, masks)], boxes
+
+
+CONFIG3_SIZES = (200_000, 400_000, 600_000, 900_000, 1_200_000, 1_800_000, 2_400_000, 3_000_000)
+CONFIG3_RES = ((1920, 1080), (4000, 3000), (5472, 3648))
+
+
+def config3(sizes=CONFIG3_SIZES, views_per_region=4, res=CONFIG3_RES, scale=1.0):
+    """Uneven sub-regions: region s has sizes[s] Gaussians on its own building scene;
+    its view j is at resolution res[(s+j) % 3], fx = 1.2 W; rectangle masks with
+    coverage U(0.2, 0.6).  Returns (gaussians concatenated, per-region ranges, views,
+    view -> region)."""
+    rs, rc, rm, rt = streams(3)
+    parts, ranges, views, owner = [], [], [], []
+    start = 0
+    for s, n in enumerate(sizes):
+        n = max(1, int(n * scale))
+        nb = max(2, int(round(40 * n / 1_500_000)))
+        area = 160.0 * math.sqrt(nb / 40)
+        boxes = random_boxes(rs, nb, area=area)
+        g = surface_gaussians(rs, boxes, n, ground=area * 1.25)
+        parts.append(g)
+        ranges.append((start, start + n))
+        start += n
+        for j in range(views_per_region):
+            w, h = res[(s + j) % len(res)]
+            if scale < 1.0:
+                w = max(64, int(w * math.sqrt(scale)))
+                h = max(64, int(h * math.sqrt(scale)))
+            alt = 120.0 * math.sqrt(nb / 40)
+            cam = aerial_camera(w, h, alt, 45.0, azimuth_deg=90.0 * j + float(rc.uniform(-20, 20)))
+            cov = float(rm.uniform(0.2, 0.6))
+            mask = rect_mask(rm, h, w, cov, 0.03)
+            views.append(View(cam, mask, random_target(rt, h, w)))
+            owner.append(s)
+    return Gaussians.concat(parts), ranges, views, owner
+
+
+def tiny_scene(seed, n=48, width=32, height=32, fx=40.0, coverage=0.5, zmin=3.0, zmax=8.0, log_scale_mu=-1.5):
+    """Small random scene for brute-force checks."""
+    ss = np.random.SeedSequence([BASE_SEED, 7, seed])
+    r1, r2, r3 = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(3)]
+    g = cube_scene(r1, n, cube=3.0, zmin=zmin, zmax=zmax)
+    g.log_scales[:] = r1.normal(log_scale_mu, 0.4, (n, 3)).astype(np.float32)
+    cam = identity_camera(width, height, fx)
+    mask = rect_mask(r2, height, width, coverage, 0.1, nmin=1, nmax=3)
+    return g, View(cam, mask, random_target(r3, height, width))

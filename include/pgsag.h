@@ -1,0 +1,336 @@
+/*
+ * pgsag.h -- C ABI of libpgsag.so: masked, tile-based differentiable
+ * Gaussian-splat rasterisation (forward and backward) for PG-SAG's per-sub-region
+ * optimisation (arXiv 2501.01677), hand-written CUDA for sm_103a (B300).
+ *
+ * What the library computes (paper passages):
+ *   - Sec. 3.1, Eq. 1: each 3D Gaussian is projected to a 2D Gaussian (EWA,
+ *     3DGS by citation), binned to image tiles, depth-sorted and alpha-blended
+ *     front to back: C = sum_i c_i a_i T_i, T_i = prod_{j<i} (1 - a_j).
+ *   - Sec. 3.1, Eq. 2-3: the same weights blend the camera-frame normal of each
+ *     flattened Gaussian (N) and its camera-to-plane distance d_i (D).
+ *   - Sec. 3.1, Eq. 4: unbiased depth Depth(p) = D / (-N(p) . K^-1 p~).
+ *   - Sec. 4.1 / 4.2 / Sec. 5.3: only building-mask pixels are rendered and
+ *     optimised, at the original image resolution.
+ *   - Sec. 4.2, Eq. 8: boundary-aware normal loss (w = 0.1 on mask boundaries).
+ *   - Sec. 4.3, Eq. 9: per-pixel / per-tile Gaussian counts for the
+ *     gradient-constrained balance-load loss.
+ *
+ * Conventions (all entry points):
+ *   - Every array argument is DEVICE memory owned by the caller, unless marked
+ *     "host".  The library never allocates device memory and never synchronises
+ *     the host inside a step call; work is enqueued on `stream`.
+ *   - Floating-point arrays are float32, row-major, contiguous; float4 / uint2 /
+ *     uint4 arrays must be 16-byte (uint2: 8-byte) aligned.
+ *   - Return value: PGSAG_OK, or a negative status detected on the host
+ *     (bad argument, launch failure).  Errors found on the device (capacity
+ *     overflow, a bounded wait that ran out) are OR-ed as bit flags into the
+ *     caller's `int32_t* status` (device); kernels that see a nonzero status
+ *     return without work.  Nothing traps.
+ *   - Views.  A step may render several views at once (sub-regions of uneven
+ *     size, mixed resolutions).  Each view renders the Gaussian index range
+ *     [g_begin, g_end) of the shared parameter arrays; a (view, Gaussian) pair has
+ *     index pair_base + (g - g_begin).  Per-pixel arrays of all views are
+ *     concatenated: pixel (x, y) of view v lives at pix_base + y * width + x.
+ *     Per-tile arrays are concatenated with tile_base / sat_base; active tiles
+ *     (tiles holding at least one rendered pixel) are numbered globally from
+ *     act_base.
+ *   - Pixel (x, y) has its centre at (x + 0.5, y + 0.5).  Camera axes follow
+ *     OpenCV (x right, y down, z forward); x_cam = R x_world + t.
+ */
+#ifndef PGSAG_H
+#define PGSAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* host-side status codes */
+#define PGSAG_OK 0
+#define PGSAG_ERR_ARG (-1)         /* null pointer, bad size, misalignment      */
+#define PGSAG_ERR_CAPACITY (-2)    /* host-visible capacity/workspace too small */
+#define PGSAG_ERR_CUDA (-3)        /* a CUDA launch or API call failed          */
+#define PGSAG_ERR_TIMEOUT (-4)     /* reserved for bounded device waits         */
+#define PGSAG_ERR_UNSUPPORTED (-5) /* parameter outside the supported range     */
+
+/* device status bit flags (OR-ed into *status) */
+#define PGSAG_DEV_CAPACITY 1u      /* duplicate count K exceeded the capacity   */
+#define PGSAG_DEV_TIMEOUT 2u       /* a bounded spin-wait ran out               */
+#define PGSAG_DEV_BOUNDS 4u        /* an index failed a bounds check            */
+
+#define PGSAG_MAX_VIEWS 256
+#define PGSAG_CHUNK 32             /* rendered pixels per warp work item        */
+#define PGSAG_SH_COEFFS 16         /* SH degree 3, coefficient-major [N,16,3]   */
+#define PGSAG_REC_FLOATS 16        /* projected record per (view, Gaussian)     */
+#define PGSAG_GRAD2D_FLOATS 16     /* 2D gradient record per (view, Gaussian)   */
+
+/* pixel flag bits (uint8 per pixel) */
+#define PGSAG_PIX_MASK 1u          /* M: building mask pixel                     */
+#define PGSAG_PIX_EDGE 2u          /* E: mask boundary (3x3 dilation - erosion)  */
+#define PGSAG_PIX_RENDER 4u        /* R: rendered (3x3 dilation of M)            */
+
+/*
+ * One view.  Filled by the caller (host), uploaded as an array of
+ * pgsag_view (device) for the step calls.  Fields marked (prep) are results of
+ * pgsag_prep_flags / pgsag_prep_lists that the caller copies in.
+ */
+typedef struct pgsag_view {
+  float R[9];                 /* world -> camera rotation, row-major            */
+  float t[3];                 /* world -> camera translation                    */
+  float fx, fy, cx, cy;       /* pinhole intrinsics (pixels)                    */
+  float znear;                /* near plane; Gaussians with z <= znear culled   */
+  float reserved0[3];         /* unused (the camera centre is computed from R, t) */
+  int32_t width, height;      /* image size (pixels)                            */
+  int32_t tile_w, tile_h;     /* tile size: each in {8,16,32}, tile_w*tile_h<=1024 */
+  int32_t tiles_x, tiles_y;   /* ceil(width/tile_w), ceil(height/tile_h)        */
+  uint32_t g_begin, g_end;    /* Gaussian index range rendered in this view     */
+  uint32_t pair_base;         /* first (view, Gaussian) pair index              */
+  uint32_t tile_base;         /* offset of this view in per-tile arrays         */
+  uint32_t sat_base;          /* offset in the summed-area table of active tiles*/
+  uint32_t act_base;          /* global index of this view's first active tile  */
+  uint32_t n_active;          /* (prep) active tiles of this view               */
+  uint32_t n_mask;            /* (prep) |M|, building-mask pixels               */
+  uint64_t pix_base;          /* offset of this view in per-pixel arrays        */
+} pgsag_view;
+
+/* Optional work scheduling for the render kernels. */
+typedef struct pgsag_sched {
+  const uint32_t* order;      /* device, n_chunks chunk ids in processing order, or NULL */
+  uint32_t* counter;          /* device uint32 work counter for a persistent launch, or NULL */
+  int32_t ctas_per_sm;        /* persistent launch: CTAs per SM (used when counter != NULL) */
+  int32_t reserved;
+} pgsag_sched;
+
+/* Human-readable name of a host status code. */
+const char* pgsag_status_str(int status);
+
+/* Library / build information string (architecture, version). */
+const char* pgsag_build_info(void);
+
+/* --------------------------------------------------------------------------
+ * Mask preparation (once per view; not part of the timed step).
+ * Sec. 4.1 (refined building masks RBM), Sec. 4.2 (mask boundaries MB).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * pgsag_prep_flags: per-pixel sets and per-tile counts of one view.
+ *   view   host, one view (size, tiling, pix_base, tile_base are used)
+ *   mask   device uint8 [height*width], nonzero = building pixel (M)
+ *   flags  device uint8 [per-pixel array], written at pix_base:
+ *          PGSAG_PIX_MASK (M), PGSAG_PIX_EDGE (E = 3x3 dilation minus 3x3
+ *          erosion of M), PGSAG_PIX_RENDER (R = 3x3 dilation of M); neighbours
+ *          outside the image are ignored.
+ *   tile_npix  device uint32 [per-tile array], written at tile_base: number of R
+ *          pixels in each tile.
+ *   totals device uint32 [4], overwritten: {active tiles, |R|, chunks, |M|} of
+ *          this view (chunks = sum over tiles of ceil(npix / 32)).
+ * Errors: PGSAG_ERR_ARG on null pointers or a bad tiling.
+ */
+int pgsag_prep_flags(const pgsag_view* view, const uint8_t* mask, uint8_t* flags,
+                     uint32_t* tile_npix, uint32_t* totals, void* stream);
+
+/*
+ * pgsag_prep_lists: active-tile numbering, compacted pixel lists and chunk list
+ * of one view, given its tile counts.
+ *   view        host; act_base, tile_base, sat_base, pix_base set
+ *   view_index  index of this view in the step's view array
+ *   flags, tile_npix   from pgsag_prep_flags
+ *   px_base     global offset of this view's first rendered pixel in px_list
+ *   chunk_base  global offset of this view's first chunk in chunks
+ *   tile_act    device int32 [per-tile]: global active index of each tile, -1 if
+ *               the tile renders no pixel
+ *   sat         device uint32 [(tiles_y+1)*(tiles_x+1) at sat_base]: summed-area
+ *               table of the active-tile indicator, S[y][x] = #active in [0,y)x[0,x)
+ *   act_tiles   device uint4 [active tiles at act_base]: {view_index,
+ *               tile_x | tile_y << 16, first px_list entry, pixel count}
+ *   px_list     device uint32 [|R| at px_base]: linear pixel index y*width+x of
+ *               every R pixel, grouped by active tile, row-major inside a tile
+ *   chunks      device uint2 [chunks at chunk_base]: {global active tile, first
+ *               px_list entry}; a chunk covers up to 32 consecutive entries of one
+ *               tile
+ * Errors: PGSAG_ERR_ARG on null pointers; PGSAG_ERR_UNSUPPORTED for tiles of
+ * more than 1024 pixels.
+ */
+int pgsag_prep_lists(const pgsag_view* view, uint32_t view_index, const uint8_t* flags,
+                     const uint32_t* tile_npix, uint32_t px_base, uint32_t chunk_base,
+                     int32_t* tile_act, uint32_t* sat, void* act_tiles, uint32_t* px_list,
+                     void* chunks, void* stream);
+
+/*
+ * pgsag_prep_gc_weight: w_i of Eq. 9 (Sec. 4.3), read as 1 + |Sobel(Y)| of the
+ * target luminance Y = 0.299 R + 0.587 G + 0.114 B, replicated borders.
+ *   target  device float [height*width*3] at 3*pix_base (RGB interleaved)
+ *   weight  device float [height*width] at pix_base
+ */
+int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* weight, void* stream);
+
+/* --------------------------------------------------------------------------
+ * Step calls (the timed hot path).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * pgsag_preprocess (Sec. 3.1, Eq. 2-3; EWA projection and SH colour of 3DGS by
+ * citation).  For every (view, Gaussian) pair:
+ *   s = exp(log_scale), q^ = q/|q| (w,x,y,z), o = sigmoid(opacity_logit);
+ *   mu_c = R mu + t; the pair is culled if any input is non-finite or the depth
+ *   key z (camera z in float32, ((R20 x + R21 y) + R22 z) + t2 without FMA) is
+ *   <= znear, or o < 1/255;
+ *   Sigma = R(q^) diag(s^2) R(q^)^T; Sigma' = J R Sigma R^T J^T + 0.3 I with J the
+ *   pinhole Jacobian at mu_c (x/z, y/z clamped to 1.3 x half-FOV);
+ *   conic Q = Sigma'^-1; mean2d = (fx x/z + cx, fy y/z + cy);
+ *   rgb = max(0, SH3(normalize(mu - c)) + 0.5), c = -R^T t the camera centre;
+ *   normal n_c = R * (column of R(q^) for the smallest log-scale, ties to the
+ *   lowest axis), negated if n_c . mu_c > 0; d = -n_c . mu_c;
+ *   tile rectangle = tiles overlapping the axis-aligned box of the alpha >= 1/255
+ *   ellipse (half-extents sqrt(2 ln(255 o) Sigma'_xx), ... plus 1 px), and
+ *   `touched` = number of ACTIVE tiles in it (from the summed-area table).
+ * Inputs: means [N,3], log_scales [N,3], quats [N,4], opacity_logit [N],
+ *   sh [N,16,3]; views (device, n_views <= PGSAG_MAX_VIEWS); tile_act, sat.
+ * Outputs per pair p:
+ *   rec [p*16 .. p*16+15] float (16-byte aligned):
+ *     {mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz, z, 0, 0}
+ *   depth_key [p]: float bits of z, 0xFFFFFFFF for culled pairs
+ *   bininfo [p] uint4: {x0 | y0 << 16, x1 | y1 << 16 (inclusive tile rect),
+ *     view index, touched}
+ * n_pairs = sum over views of (g_end - g_begin).
+ * This call begins a step: it clears *status before its kernel runs.
+ */
+int pgsag_preprocess(uint32_t n_gauss, const float* means, const float* log_scales,
+                     const float* quats, const float* opacity_logit, const float* sh,
+                     uint32_t n_views, const pgsag_view* views, const int32_t* tile_act,
+                     const uint32_t* sat, float* rec, uint32_t* depth_key, void* bininfo,
+                     int32_t* status, void* stream);
+
+/*
+ * pgsag_bin (Sec. 3.1: projected to tiles, sorted).  Duplicates every visible
+ * pair once per active tile of its rectangle and orders each tile's list by
+ * (depth key, Gaussian index):
+ *   1. stable LSD radix sort of all pairs by depth key (pair index order breaks
+ *      ties, i.e. ascending Gaussian index within a view);
+ *   2. exclusive scan of `touched` in that order -> K (written to *k_out);
+ *   3. emission of (global active tile, pair) in that order;
+ *   4. stable LSD radix sort of the K entries by active tile;
+ *   5. per-active-tile ranges [begin, end) into dup_pairs.
+ * The result equals a sort of K keys (tile, depth, index) and is bit-exact.
+ *   capacity   maximum K; if K > capacity, PGSAG_DEV_CAPACITY is set in *status,
+ *              nothing is emitted, and later step kernels return without work.
+ *   ws         device workspace of pgsag_bin_workspace_size(n_pairs, capacity) bytes
+ *   dup_pairs  device uint32 [capacity]: pair index of each duplicate, sorted
+ *   ranges     device uint2 [n_active_total]: {begin, end} per active tile
+ *   k_out      device uint64 [1]: K
+ */
+size_t pgsag_bin_workspace_size(uint32_t n_pairs, uint64_t capacity);
+int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
+              uint32_t n_active_total, const int32_t* tile_act, const void* bininfo,
+              const uint32_t* depth_key, uint64_t capacity, void* ws, size_t ws_bytes,
+              uint32_t* dup_pairs, void* ranges, uint64_t* k_out, int32_t* status,
+              void* stream);
+
+/*
+ * pgsag_render_fwd (Sec. 3.1, Eq. 1-4).  One warp per chunk of up to 32 rendered
+ * pixels of one active tile; the tile's sorted Gaussians are staged through
+ * shared memory in batches of 32.  Per pixel, front to back:
+ *   alpha = min(0.99, o exp(-1/2 d^T Q d)); skipped if alpha < 1/255; if
+ *   T (1 - alpha) < 1e-4 the pixel stops before this Gaussian; otherwise
+ *   w = alpha T, C += w c, N += w n_c, D += w d, T *= 1 - alpha.
+ *   Depth = D / (-N . K^-1 (x+1/2, y+1/2, 1)) if something was blended,
+ *   -N.r > 1e-8 and D > 0 (the pixel is then "valid"), else 0.
+ * Outputs (per-pixel arrays, only R pixels written):
+ *   out8  float [8 per pixel]: {C_r, C_g, C_b, D, N_x, N_y, N_z, A = 1 - T}
+ *   depth float [1 per pixel]
+ *   aux   uint4 [1 per pixel]: {float bits of final T, index (into dup_pairs) of the
+ *         last blended Gaussian, number blended n_contrib, 0}
+ * sched may be NULL (one warp per chunk in chunk order).
+ */
+int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec,
+                     const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
+                     uint32_t n_chunks, const void* chunks, const uint32_t* px_list,
+                     const pgsag_sched* sched, float* out8, float* depth, void* aux,
+                     int32_t* status, void* stream);
+
+/*
+ * pgsag_loss_ban (Sec. 4.2, Eq. 8; photometric L1 term of Eq. 10).  Per view v:
+ *   L_rgb = 1/(3|M|) sum_{i in M} |C_i - C*_i|_1
+ *   L_ban = 1/|V| sum_{i in V} w_i || n_depth,i - N_i/|N_i| ||^2,
+ *     n_depth = normalize((P[y+1]-P[y-1]) x (P[x+1]-P[x-1])), P = Depth r,
+ *     w = 0.1 on E, 1 elsewhere; V = mask pixels off the image border that are
+ *     valid, whose 4 neighbours are in R and valid, with a non-zero cross product.
+ *   L = L_rgb + lambda_ban L_ban.
+ * Writes dL/d(out8) for every R pixel (gradient through both n_depth -- into D
+ * and N of the 4 neighbours via Eq. 4 -- and the rendered normal; dL/dA = 0).
+ *   target   float [3 per pixel] (RGB interleaved, at 3*pix_base)
+ *   scratch  float [6 per pixel] (only M pixels touched)
+ *   acc      double [4 per view] scratch accumulators
+ *   loss     float [3 per view + 1]: {L_rgb, L_ban, L} per view, then sum_v L
+ *   dout8    float [8 per pixel]
+ */
+int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
+                   const void* chunks, const void* act_tiles, const uint32_t* px_list,
+                   const uint8_t* flags, const float* out8, const float* depth,
+                   const void* aux, const float* target, float lambda_ban, float* scratch,
+                   double* acc, float* loss, float* dout8, int32_t* status, void* stream);
+
+/*
+ * pgsag_render_bwd (Sec. 3.1: "optimized ... using differentiable rendering").
+ * Adjoint of pgsag_render_fwd: each warp re-traverses its tile's list back to
+ * front from the last blended Gaussian, recovering T by division
+ * (T_i = T_{i+1} / (1 - alpha_i)), and accumulates per pair
+ *   grad2d[p*16 + {0..12}] = dL/d{mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz}
+ * (warp shuffle reduction, then one atomic add per warp and value).  grad2d is
+ * zeroed by this call.  ddepth (nullable) adds a gradient on the depth output,
+ * folded into dD and dN through Eq. 4.  dout_scale (nullable, device float[1])
+ * multiplies the whole upstream gradient (chain rule from a scalar loss).
+ */
+int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec,
+                     const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
+                     uint32_t n_chunks, const void* chunks, const uint32_t* px_list,
+                     const pgsag_sched* sched, const float* out8, const void* aux,
+                     const float* dout8, const float* ddepth, const float* dout_scale,
+                     uint32_t n_pairs, float* grad2d, int32_t* status, void* stream);
+
+/*
+ * pgsag_preprocess_bwd: chain rule from grad2d to the raw parameters (the
+ * adjoint of pgsag_preprocess), summed over the views that render each Gaussian
+ * (no atomics: one thread per Gaussian loops over its views).  The argmin axis,
+ * the normal flip, the Jacobian clamp and the colour clamp are locally constant.
+ * accumulate = 0 overwrites the outputs, 1 adds to them.
+ * Outputs: d_means [N,3], d_log_scales [N,3], d_quats [N,4], d_opacity_logit [N],
+ * d_sh [N,16,3].
+ */
+int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const float* log_scales,
+                         const float* quats, const float* opacity_logit, const float* sh,
+                         uint32_t n_views, const pgsag_view* views, const void* bininfo,
+                         const float* grad2d, int accumulate, float* d_means,
+                         float* d_log_scales, float* d_quats, float* d_opacity_logit,
+                         float* d_sh, int32_t* status, void* stream);
+
+/*
+ * pgsag_tile_stats (Sec. 4.3, Eq. 9).
+ *   tile_counts [n_active_total] uint32: Gaussians binned to each active tile
+ *     (length of its range);
+ *   per view, GC-load = population std over R pixels of g_i / w_i with
+ *     g_i = n_contrib (from aux) and w_i from pgsag_prep_gc_weight;
+ *   acc   double [3 per view] scratch; gc_load float [1 per view].
+ */
+int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint32_t n_active_total,
+                     const void* ranges, uint32_t n_chunks, const void* chunks,
+                     const void* act_tiles, const uint32_t* px_list, const void* aux,
+                     const float* gc_weight, uint32_t* tile_counts, double* acc,
+                     float* gc_load, int32_t* status, void* stream);
+
+/*
+ * pgsag_adam: fused Adam update of n parameters (p, g, m, v float32):
+ *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *   p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * The paper does not name its optimiser; this is the 3DGS convention.
+ */
+int pgsag_adam(uint64_t n, float* p, const float* g, float* m, float* v, float lr, float beta1,
+               float beta2, float eps, int32_t step, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGSAG_H */

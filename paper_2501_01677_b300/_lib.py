@@ -1,0 +1,94 @@
+"""ctypes binding of libpgsag.so (include/pgsag.h): argument marshalling only.
+
+The shared library is built in-tree by paper_2501_01677_b300.build.  Loading
+fails loudly if it is missing; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_float, c_int, c_int32, c_size_t, c_uint32, c_uint64, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpgsag.so")
+
+PGSAG_OK = 0
+PGSAG_DEV_CAPACITY = 1
+PGSAG_DEV_TIMEOUT = 2
+PGSAG_DEV_BOUNDS = 4
+MAX_VIEWS = 256
+CHUNK = 32
+PIX_MASK, PIX_EDGE, PIX_RENDER = 1, 2, 4
+
+# Every entry point declared in include/pgsag.h
+EXPORTS = (
+    "pgsag_status_str", "pgsag_build_info", "pgsag_prep_flags", "pgsag_prep_lists", "pgsag_prep_gc_weight",
+    "pgsag_preprocess", "pgsag_bin_workspace_size", "pgsag_bin", "pgsag_render_fwd", "pgsag_loss_ban",
+    "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_adam",
+)
+
+
+class PgsagView(ctypes.Structure):
+    _fields_ = [
+        ("R", c_float * 9), ("t", c_float * 3),
+        ("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float),
+        ("znear", c_float), ("reserved0", c_float * 3),
+        ("width", c_int32), ("height", c_int32), ("tile_w", c_int32), ("tile_h", c_int32),
+        ("tiles_x", c_int32), ("tiles_y", c_int32),
+        ("g_begin", c_uint32), ("g_end", c_uint32), ("pair_base", c_uint32), ("tile_base", c_uint32),
+        ("sat_base", c_uint32), ("act_base", c_uint32), ("n_active", c_uint32), ("n_mask", c_uint32),
+        ("pix_base", c_uint64),
+    ]
+
+
+assert ctypes.sizeof(PgsagView) == 144
+
+
+class PgsagSched(ctypes.Structure):
+    _fields_ = [("order", c_void_p), ("counter", c_void_p), ("ctas_per_sm", c_int32), ("reserved", c_int32)]
+
+
+_lib = None
+
+
+def _sig(lib, name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+
+
+def load(path: str = LIB_PATH):
+    """Load libpgsag.so (raises if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libpgsag.so not built at {path}; run `python -m paper_2501_01677_b300.build`")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    _sig(lib, "pgsag_status_str", ctypes.c_char_p, [c_int])
+    _sig(lib, "pgsag_build_info", ctypes.c_char_p, [])
+    _sig(lib, "pgsag_prep_flags", c_int, [POINTER(PgsagView), P, P, P, P, P])
+    _sig(lib, "pgsag_prep_lists", c_int, [POINTER(PgsagView), c_uint32, P, P, c_uint32, c_uint32, P, P, P, P, P, P])
+    _sig(lib, "pgsag_prep_gc_weight", c_int, [POINTER(PgsagView), P, P, P])
+    _sig(lib, "pgsag_preprocess", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_bin_workspace_size", c_size_t, [c_uint32, c_uint64])
+    _sig(lib, "pgsag_bin", c_int, [c_uint32, c_uint32, P, c_uint32, P, P, P, c_uint64, P, c_size_t, P, P, P, P, P])
+    _sig(lib, "pgsag_render_fwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, POINTER(PgsagSched), P, P, P, P, P])
+    _sig(lib, "pgsag_loss_ban", c_int, [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, c_float, P, P, P, P, P, P])
+    _sig(lib, "pgsag_render_bwd", c_int,
+         [c_uint32, P, P, P, P, P, c_uint32, P, P, POINTER(PgsagSched), P, P, P, P, P, c_uint32, P, P, P])
+    _sig(lib, "pgsag_preprocess_bwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_adam", c_int, [c_uint64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P])
+    _lib = lib
+    return lib
+
+
+class PgsagError(RuntimeError):
+    pass
+
+
+def check(rc: int, what: str):
+    if rc != PGSAG_OK:
+        msg = load().pgsag_status_str(rc).decode()
+        raise PgsagError(f"{what} failed: {rc} ({msg})")

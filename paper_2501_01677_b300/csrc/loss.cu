@@ -1,0 +1,366 @@
+// Photometric L1 term and boundary-aware normal loss (Sec. 4.2, Eq. 8) with
+// their gradient on the rendered channels; per-tile / per-pixel Gaussian
+// counts and the GC-load statistic (Sec. 4.3, Eq. 9).
+//
+// The loss needs the unbiased depth (Eq. 4) of each pixel's 4 neighbours, so the
+// per-pixel arrays are dense per view (only rendered pixels are touched) and the
+// kernels walk the compacted pixel lists chunk by chunk (one warp, one pixel per
+// lane).
+#include "common.cuh"
+
+namespace pgsag {
+
+constexpr int kLossThreads = 256;
+constexpr float kWBoundary = 0.1f;  // Eq. 8: boundary weight
+
+struct PixCtx {
+  bool has;
+  uint32_t view;
+  ViewLite V;
+  int x, y;
+  uint64_t gp;
+};
+
+__device__ __forceinline__ PixCtx pix_ctx(uint32_t c, int lane, const uint2* __restrict__ chunks,
+                                          const uint4* __restrict__ act_tiles,
+                                          const uint32_t* __restrict__ px_list,
+                                          const pgsag_view* __restrict__ views) {
+  PixCtx P;
+  const uint2 ch = __ldg(chunks + c);
+  const uint4 at = __ldg(act_tiles + ch.x);
+  const uint32_t cnt = min(32u, at.z + at.w - ch.y);
+  P.view = at.x;
+  P.V = load_view_lite(views + at.x);
+  P.has = (uint32_t)lane < cnt;
+  const uint32_t pix = P.has ? __ldg(px_list + ch.y + lane) : 0u;
+  P.y = (int)(pix / (uint32_t)P.V.width);
+  P.x = (int)(pix - (uint32_t)P.y * (uint32_t)P.V.width);
+  P.gp = P.V.pix_base + pix;
+  return P;
+}
+
+__device__ __forceinline__ void ray(const ViewLite& V, int x, int y, float r[3]) {
+  r[0] = ((float)x + 0.5f - V.cx) / V.fx;
+  r[1] = ((float)y + 0.5f - V.cy) / V.fy;
+  r[2] = 1.f;
+}
+
+// Pass A: per rendered pixel.  L1 term and its gradient; for interior valid
+// mask pixels with valid neighbours, the Eq. 8 term, the gradient on the own
+// rendered normal (unscaled) and dL/da, dL/db of the two central differences
+// (stored in `scratch` for the neighbours to gather).
+__global__ void __launch_bounds__(kLossThreads) k_loss_a(
+    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
+    const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
+    const uint8_t* __restrict__ flags, const float4* __restrict__ out8, const float* __restrict__ depth,
+    const float* __restrict__ target, float* __restrict__ scratch, double* __restrict__ acc,
+    float4* __restrict__ dout8, const int32_t* status) {
+  if (status_bad(status)) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
+  if (c >= n_chunks) return;
+  const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
+  float l1 = 0.f, lb = 0.f, nv = 0.f;
+  if (P.has) {
+    const uint8_t f = __ldg(flags + P.gp);
+    const float4 o0 = __ldg(out8 + 2 * P.gp), o1 = __ldg(out8 + 2 * P.gp + 1);
+    float dC[3] = {0.f, 0.f, 0.f}, dNo[3] = {0.f, 0.f, 0.f};
+    if (f & PGSAG_PIX_MASK) {
+      const uint32_t nm = __ldg(&views[P.view].n_mask);
+      const float inv3m = nm ? 1.f / (3.f * (float)nm) : 0.f;
+      const float C[3] = {o0.x, o0.y, o0.z};
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float d = C[ch] - __ldg(target + 3 * P.gp + ch);
+        l1 += fabsf(d);
+        dC[ch] = d > 0.f ? inv3m : (d < 0.f ? -inv3m : 0.f);
+      }
+      float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
+      const int W = P.V.width, H = P.V.height;
+      const float dep = __ldg(depth + P.gp);
+      bool inV = P.x >= 1 && P.x <= W - 2 && P.y >= 1 && P.y <= H - 2 && dep > 0.f;
+      float Pn[4][3];  // y-1, y+1, x-1, x+1
+      if (inV) {
+        const int nx[4] = {P.x, P.x, P.x - 1, P.x + 1};
+        const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t q = P.V.pix_base + (uint64_t)ny[k] * W + nx[k];
+          const uint8_t fq = __ldg(flags + q);
+          float dq = 0.f;
+          if (fq & PGSAG_PIX_RENDER) dq = __ldg(depth + q);
+          inV = inV && (fq & PGSAG_PIX_RENDER) && dq > 0.f;
+          float r[3];
+          ray(P.V, nx[k], ny[k], r);
+          Pn[k][0] = dq * r[0];
+          Pn[k][1] = dq * r[1];
+          Pn[k][2] = dq * r[2];
+        }
+      }
+      if (inV) {
+        const float a[3] = {Pn[1][0] - Pn[0][0], Pn[1][1] - Pn[0][1], Pn[1][2] - Pn[0][2]};
+        const float b[3] = {Pn[3][0] - Pn[2][0], Pn[3][1] - Pn[2][1], Pn[3][2] - Pn[2][2]};
+        const float cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        const float cn = sqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        const float Nn = sqrtf(o1.x * o1.x + o1.y * o1.y + o1.z * o1.z);
+        if (cn > 0.f && Nn > 0.f) {
+          const float icn = 1.f / cn, iNn = 1.f / Nn;
+          const float nd[3] = {cr[0] * icn, cr[1] * icn, cr[2] * icn};
+          const float nr[3] = {o1.x * iNn, o1.y * iNn, o1.z * iNn};
+          const float w = (f & PGSAG_PIX_EDGE) ? kWBoundary : 1.f;
+          const float df[3] = {nd[0] - nr[0], nd[1] - nr[1], nd[2] - nr[2]};
+          lb = w * (df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+          nv = 1.f;
+          // d/d nd = 2 w df, d/d nr = -2 w df
+          const float gnd[3] = {2.f * w * df[0], 2.f * w * df[1], 2.f * w * df[2]};
+          const float pnd = nd[0] * gnd[0] + nd[1] * gnd[1] + nd[2] * gnd[2];
+          const float gc[3] = {(gnd[0] - nd[0] * pnd) * icn, (gnd[1] - nd[1] * pnd) * icn,
+                               (gnd[2] - nd[2] * pnd) * icn};
+          const float pnr = -(nr[0] * gnd[0] + nr[1] * gnd[1] + nr[2] * gnd[2]);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) dNo[k] = (-gnd[k] - nr[k] * pnr) * iNn;
+          // c = a x b: dL/da = b x gc, dL/db = gc x a
+          ga[0] = b[1] * gc[2] - b[2] * gc[1];
+          ga[1] = b[2] * gc[0] - b[0] * gc[2];
+          ga[2] = b[0] * gc[1] - b[1] * gc[0];
+          gb[0] = gc[1] * a[2] - gc[2] * a[1];
+          gb[1] = gc[2] * a[0] - gc[0] * a[2];
+          gb[2] = gc[0] * a[1] - gc[1] * a[0];
+        }
+      }
+      float* sc = scratch + 6 * P.gp;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sc[k] = ga[k];
+        sc[3 + k] = gb[k];
+      }
+    }
+    dout8[2 * P.gp] = make_float4(dC[0], dC[1], dC[2], 0.f);
+    dout8[2 * P.gp + 1] = make_float4(dNo[0], dNo[1], dNo[2], 0.f);
+  }
+  // a chunk belongs to one view: warp-reduce then one atomic per value
+  const float s1 = warp_sum(l1), s2 = warp_sum(lb), s3 = warp_sum(nv);
+  if (lane == 0) {
+    double* A = acc + 4 * P.view;
+    if (s1 != 0.f) atomicAdd(A + 0, (double)s1);
+    if (s2 != 0.f) atomicAdd(A + 1, (double)s2);
+    if (s3 != 0.f) atomicAdd(A + 2, (double)s3);
+  }
+}
+
+// Pass B: per rendered pixel, gather dL/dP from the neighbours whose central
+// differences used this pixel, map it to D and N through Eq. 4, scale.
+__global__ void __launch_bounds__(kLossThreads) k_loss_b(
+    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
+    const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
+    const uint8_t* __restrict__ flags, const float4* __restrict__ out8, const float* __restrict__ depth,
+    const float* __restrict__ scratch, const double* __restrict__ acc, float lambda_ban,
+    float4* __restrict__ dout8, const int32_t* status) {
+  if (status_bad(status)) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
+  if (c >= n_chunks) return;
+  const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
+  if (!P.has) return;
+  const double nV = acc[4 * P.view + 2];
+  const float scale = nV > 0.0 ? (float)(lambda_ban / nV) : 0.f;
+  const int W = P.V.width, H = P.V.height;
+  float dP[3] = {0.f, 0.f, 0.f};
+  // this pixel is P[y+1] of (x, y-1), P[y-1] of (x, y+1), P[x+1] of (x-1, y), P[x-1] of (x+1, y)
+  const int nx[4] = {P.x, P.x, P.x - 1, P.x + 1};
+  const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
+  const float sg[4] = {1.f, -1.f, 1.f, -1.f};
+  const int off[4] = {0, 0, 3, 3};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (nx[k] < 0 || nx[k] >= W || ny[k] < 0 || ny[k] >= H) continue;
+    const uint64_t q = P.V.pix_base + (uint64_t)ny[k] * W + nx[k];
+    if (!(__ldg(flags + q) & PGSAG_PIX_MASK)) continue;
+    const float* sc = scratch + 6 * q + off[k];
+    dP[0] += sg[k] * __ldg(sc + 0);
+    dP[1] += sg[k] * __ldg(sc + 1);
+    dP[2] += sg[k] * __ldg(sc + 2);
+  }
+  float4 g1 = dout8[2 * P.gp + 1];
+  float dD = 0.f, dN[3] = {0.f, 0.f, 0.f};
+  const float dep = __ldg(depth + P.gp);
+  if (dep > 0.f && (dP[0] != 0.f || dP[1] != 0.f || dP[2] != 0.f)) {
+    const float4 o0 = __ldg(out8 + 2 * P.gp), o1 = __ldg(out8 + 2 * P.gp + 1);
+    float r[3];
+    ray(P.V, P.x, P.y, r);
+    const float sdot = -(o1.x * r[0] + o1.y * r[1] + o1.z * r[2]);
+    const float gdep = dP[0] * r[0] + dP[1] * r[1] + dP[2] * r[2];  // P = Depth r
+    const float is = 1.f / sdot;
+    dD = gdep * is;
+    const float k = gdep * o0.w * is * is;
+    dN[0] = k * r[0];
+    dN[1] = k * r[1];
+    dN[2] = k * r[2];
+  }
+  float4 g0 = dout8[2 * P.gp];
+  g0.w = scale * dD;
+  g1.x = scale * (g1.x + dN[0]);
+  g1.y = scale * (g1.y + dN[1]);
+  g1.z = scale * (g1.z + dN[2]);
+  g1.w = 0.f;
+  dout8[2 * P.gp] = g0;
+  dout8[2 * P.gp + 1] = g1;
+}
+
+// One thread: per-view losses and their sum (views are few).
+__global__ void k_loss_final(const pgsag_view* __restrict__ views, uint32_t n_views,
+                             const double* __restrict__ acc, float lambda_ban, float* __restrict__ loss,
+                             const int32_t* status) {
+  if (status_bad(status)) return;
+  if (threadIdx.x != 0) return;
+  double total = 0.0;
+  for (uint32_t v = 0; v < n_views; ++v) {
+    const uint32_t nm = views[v].n_mask;
+    const double lr = nm ? acc[4 * v + 0] / (3.0 * nm) : 0.0;
+    const double lb = acc[4 * v + 2] > 0.0 ? acc[4 * v + 1] / acc[4 * v + 2] : 0.0;
+    loss[3 * v + 0] = (float)lr;
+    loss[3 * v + 1] = (float)lb;
+    loss[3 * v + 2] = (float)(lr + (double)lambda_ban * lb);
+    total += lr + (double)lambda_ban * lb;
+  }
+  loss[3 * n_views] = (float)total;
+}
+
+// ------------------------------------------------------------------ Eq. 9
+
+__global__ void k_tile_counts(uint32_t n_active, const uint2* __restrict__ ranges,
+                              uint32_t* __restrict__ counts, const int32_t* status) {
+  if (status_bad(status)) return;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_active) return;
+  const uint2 r = __ldg(ranges + t);
+  counts[t] = r.y - r.x;
+}
+
+__global__ void __launch_bounds__(kLossThreads) k_gc_accum(
+    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
+    const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
+    const uint4* __restrict__ aux, const float* __restrict__ weight, double* __restrict__ acc,
+    const int32_t* status) {
+  if (status_bad(status)) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
+  if (c >= n_chunks) return;
+  const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
+  double x = 0.0, n = 0.0;
+  if (P.has) {
+    const uint32_t g = __ldg(&aux[P.gp].z);
+    x = (double)g / (double)__ldg(weight + P.gp);
+    n = 1.0;
+  }
+  const double s0 = warp_sum_d(n), s1 = warp_sum_d(x), s2 = warp_sum_d(x * x);
+  if (lane == 0) {
+    double* A = acc + 3 * P.view;
+    atomicAdd(A + 0, s0);
+    atomicAdd(A + 1, s1);
+    atomicAdd(A + 2, s2);
+  }
+}
+
+__global__ void k_gc_final(uint32_t n_views, const double* __restrict__ acc, float* __restrict__ out,
+                           const int32_t* status) {
+  if (status_bad(status)) return;
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n_views) return;
+  const double n = acc[3 * v], s = acc[3 * v + 1], q = acc[3 * v + 2];
+  double var = 0.0;
+  if (n > 0.0) {
+    const double m = s / n;
+    var = q / n - m * m;
+  }
+  out[v] = (float)sqrt(var > 0.0 ? var : 0.0);
+}
+
+// w = 1 + |Sobel(Y)|, replicated borders
+__global__ void k_gc_weight(int W, int H, const float* __restrict__ target, float* __restrict__ weight) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= W || y >= H) return;
+  float Y[3][3];
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int xx = min(max(x + dx, 0), W - 1), yy = min(max(y + dy, 0), H - 1);
+      const float* t = target + 3 * ((size_t)yy * W + xx);
+      Y[dy + 1][dx + 1] = 0.299f * t[0] + 0.587f * t[1] + 0.114f * t[2];
+    }
+  const float gx = (Y[0][2] + 2.f * Y[1][2] + Y[2][2]) - (Y[0][0] + 2.f * Y[1][0] + Y[2][0]);
+  const float gy = (Y[2][0] + 2.f * Y[2][1] + Y[2][2]) - (Y[0][0] + 2.f * Y[0][1] + Y[0][2]);
+  weight[(size_t)y * W + x] = 1.f + sqrtf(gx * gx + gy * gy);
+}
+
+}  // namespace pgsag
+
+using namespace pgsag;
+
+extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
+                              const void* chunks, const void* act_tiles, const uint32_t* px_list,
+                              const uint8_t* flags, const float* out8, const float* depth,
+                              const void* aux, const float* target, float lambda_ban, float* scratch,
+                              double* acc, float* loss, float* dout8, int32_t* status, void* stream) {
+  (void)aux;
+  if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
+  if (!views || !status || !acc || !loss) return PGSAG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 4 * sizeof(double), s));
+  if (n_chunks) {
+    if (!chunks || !act_tiles || !px_list || !flags || !out8 || !depth || !target || !scratch || !dout8)
+      return PGSAG_ERR_ARG;
+    if (((uintptr_t)out8 | (uintptr_t)dout8 | (uintptr_t)act_tiles) & 15u) return PGSAG_ERR_ARG;
+    const unsigned blocks = pgsag_div_up(n_chunks, kLossThreads / 32);
+    k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
+                                             px_list, flags, (const float4*)out8, depth, target, scratch, acc,
+                                             (float4*)dout8, status);
+    PGSAG_CHECK_LAUNCH();
+    k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
+                                             px_list, flags, (const float4*)out8, depth, scratch, acc,
+                                             lambda_ban, (float4*)dout8, status);
+    PGSAG_CHECK_LAUNCH();
+  }
+  k_loss_final<<<1, 32, 0, s>>>(views, n_views, acc, lambda_ban, loss, status);
+  PGSAG_CHECK_LAUNCH();
+  return PGSAG_OK;
+}
+
+extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint32_t n_active_total,
+                                const void* ranges, uint32_t n_chunks, const void* chunks,
+                                const void* act_tiles, const uint32_t* px_list, const void* aux,
+                                const float* gc_weight, uint32_t* tile_counts, double* acc,
+                                float* gc_load, int32_t* status, void* stream) {
+  if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
+  if (!views || !status || !acc || !gc_load) return PGSAG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 3 * sizeof(double), s));
+  if (n_active_total) {
+    if (!ranges || !tile_counts) return PGSAG_ERR_ARG;
+    k_tile_counts<<<pgsag_div_up(n_active_total, 256), 256, 0, s>>>(n_active_total, (const uint2*)ranges,
+                                                                    tile_counts, status);
+    PGSAG_CHECK_LAUNCH();
+  }
+  if (n_chunks) {
+    if (!chunks || !act_tiles || !px_list || !aux || !gc_weight) return PGSAG_ERR_ARG;
+    k_gc_accum<<<pgsag_div_up(n_chunks, kLossThreads / 32), kLossThreads, 0, s>>>(
+        views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles, px_list, (const uint4*)aux, gc_weight,
+        acc, status);
+    PGSAG_CHECK_LAUNCH();
+  }
+  k_gc_final<<<pgsag_div_up(n_views, 128), 128, 0, s>>>(n_views, acc, gc_load, status);
+  PGSAG_CHECK_LAUNCH();
+  return PGSAG_OK;
+}
+
+extern "C" int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* weight, void* stream) {
+  if (!view || !target || !weight) return PGSAG_ERR_ARG;
+  if (view->width <= 0 || view->height <= 0) return PGSAG_ERR_ARG;
+  dim3 grid(pgsag_div_up(view->width, 256), view->height);
+  k_gc_weight<<<grid, 256, 0, (cudaStream_t)stream>>>(view->width, view->height, target + 3 * view->pix_base,
+                                                      weight + view->pix_base);
+  PGSAG_CHECK_LAUNCH();
+  return PGSAG_OK;
+}

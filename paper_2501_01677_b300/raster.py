@@ -1,0 +1,404 @@
+"""Python layer over libpgsag: a Plan owns the device buffers of one set of views,
+and two autograd Functions expose the differentiable renderer and the fused
+render + loss step.  PyTorch supplies device memory and the stream only; every
+step of the computation runs in the library's CUDA kernels.
+
+Paper passages: Sec. 3.1 (Eq. 1-4, rendering), Sec. 4.2 (Eq. 8, boundary-aware
+normal loss), Sec. 4.3 (Eq. 9, GC-load statistic; Eq. 10-11 weights).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+LAMBDA_BAN = 0.01  # Eq. 10-11: lambda_4
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class GaussianParams:
+    """Raw Gaussian parameters on the GPU (float32, contiguous)."""
+    means: torch.Tensor          # [N,3]
+    log_scales: torch.Tensor     # [N,3]
+    quats: torch.Tensor          # [N,4] (w,x,y,z)
+    opacity_logit: torch.Tensor  # [N]
+    sh: torch.Tensor             # [N,16,3]
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    def tensors(self):
+        return (self.means, self.log_scales, self.quats, self.opacity_logit, self.sh)
+
+    @staticmethod
+    def from_numpy(g, device="cuda", requires_grad=False) -> "GaussianParams":
+        ts = [torch.from_numpy(np.ascontiguousarray(getattr(g, k), np.float32)).to(device)
+              for k in ("means", "log_scales", "quats", "opacity_logit", "sh")]
+        if requires_grad:
+            for t in ts:
+                t.requires_grad_(True)
+        return GaussianParams(*ts)
+
+
+class Plan:
+    """Device state for rendering a fixed set of views.
+
+    cams: objects with R [3,3], t [3], fx, fy, cx, cy, width, height, znear
+    masks: uint8 [H,W] building masks (host numpy or device tensors)
+    targets: float32 [H,W,3] photometric targets
+    g_ranges: per view (g_begin, g_end) into the shared Gaussian arrays; default
+      every view renders all n_gauss Gaussians
+    tile: (tile_w, tile_h), each in {8, 16, 32}
+    capacity: maximum number of (tile, Gaussian) duplicates; None sizes it on the
+      first forward (one host synchronisation) and grows it on overflow.
+
+    Outputs of forward() live in this plan's buffers and stay valid until the
+    next forward on the same plan; backward must run before that.
+    """
+
+    def __init__(self, cams, masks, targets, n_gauss: int, g_ranges: Optional[Sequence[Tuple[int, int]]] = None,
+                 tile=(16, 16), capacity: Optional[int] = None, device="cuda"):
+        self.lib = L.load()
+        self.device = torch.device(device)
+        V = len(cams)
+        if V == 0 or V > L.MAX_VIEWS:
+            raise ValueError("number of views must be in [1, 256]")
+        self.n_views = V
+        self.n_gauss = int(n_gauss)
+        self.tile = (int(tile[0]), int(tile[1]))
+        tw, th = self.tile
+        views = (L.PgsagView * V)()
+        pix_base = tile_base = sat_base = pair_base = 0
+        self.shapes = []
+        for v, cam in enumerate(cams):
+            vw = views[v]
+            R = np.asarray(cam.R, np.float32).reshape(9)
+            t = np.asarray(cam.t, np.float32).reshape(3)
+            for i in range(9):
+                vw.R[i] = float(R[i])
+            for i in range(3):
+                vw.t[i] = float(t[i])
+            vw.fx, vw.fy, vw.cx, vw.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+            vw.znear = float(cam.znear)
+            W, H = int(cam.width), int(cam.height)
+            vw.width, vw.height, vw.tile_w, vw.tile_h = W, H, tw, th
+            vw.tiles_x, vw.tiles_y = (W + tw - 1) // tw, (H + th - 1) // th
+            gb, ge = g_ranges[v] if g_ranges is not None else (0, self.n_gauss)
+            if not (0 <= gb <= ge <= self.n_gauss):
+                raise ValueError("bad Gaussian range")
+            vw.g_begin, vw.g_end = gb, ge
+            vw.pair_base = pair_base
+            vw.tile_base = tile_base
+            vw.sat_base = sat_base
+            vw.pix_base = pix_base
+            pair_base += ge - gb
+            tile_base += vw.tiles_x * vw.tiles_y
+            sat_base += (vw.tiles_x + 1) * (vw.tiles_y + 1)
+            pix_base += W * H
+            self.shapes.append((H, W))
+        self.views_host = views
+        self.n_pairs, self.n_tiles, self.n_sat, self.n_pix = pair_base, tile_base, sat_base, pix_base
+        if self.n_pairs >= 2 ** 32 or self.n_pix >= 2 ** 40:
+            raise ValueError("problem too large")
+        dev = self.device
+        s = _stream_ptr()
+        u8, i32, f32 = torch.uint8, torch.int32, torch.float32
+
+        # ---- mask preparation (outside the timed step)
+        self.flags = torch.zeros(self.n_pix, dtype=u8, device=dev)
+        self.tile_npix = torch.zeros(max(self.n_tiles, 1), dtype=i32, device=dev)
+        totals = torch.zeros((V, 4), dtype=i32, device=dev)
+        for v in range(V):
+            m = masks[v]
+            m = m if torch.is_tensor(m) else torch.from_numpy(np.ascontiguousarray(m, np.uint8))
+            m = m.to(dev, torch.uint8).contiguous()
+            L.check(self.lib.pgsag_prep_flags(ctypes.byref(views[v]), _ptr(m), _ptr(self.flags), _ptr(self.tile_npix),
+                                              _ptr(totals[v]), s), "pgsag_prep_flags")
+        tot = totals.cpu().numpy().astype(np.int64)
+        self.n_active_v = tot[:, 0].copy()
+        self.n_render_v = tot[:, 1].copy()
+        self.n_chunks_v = tot[:, 2].copy()
+        self.n_mask_v = tot[:, 3].copy()
+        self.n_active = int(tot[:, 0].sum())
+        self.n_render = int(tot[:, 1].sum())
+        self.n_chunks = int(tot[:, 2].sum())
+        self.n_mask = int(tot[:, 3].sum())
+        self.tile_act = torch.empty(max(self.n_tiles, 1), dtype=i32, device=dev)
+        self.sat = torch.empty(max(self.n_sat, 1), dtype=i32, device=dev)
+        self.act_tiles = torch.empty((max(self.n_active, 1), 4), dtype=i32, device=dev)
+        self.px_list = torch.empty(max(self.n_render, 1), dtype=i32, device=dev)
+        self.chunks = torch.empty((max(self.n_chunks, 1), 2), dtype=i32, device=dev)
+        act_base = px_base = chunk_base = 0
+        for v in range(V):
+            views[v].act_base = act_base
+            views[v].n_active = int(self.n_active_v[v])
+            views[v].n_mask = int(self.n_mask_v[v])
+            L.check(self.lib.pgsag_prep_lists(ctypes.byref(views[v]), v, _ptr(self.flags), _ptr(self.tile_npix),
+                                              px_base, chunk_base, _ptr(self.tile_act), _ptr(self.sat),
+                                              _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.chunks), s),
+                    "pgsag_prep_lists")
+            act_base += int(self.n_active_v[v])
+            px_base += int(self.n_render_v[v])
+            chunk_base += int(self.n_chunks_v[v])
+        self.target = torch.zeros(self.n_pix * 3, dtype=f32, device=dev)
+        self.gc_weight = torch.ones(self.n_pix, dtype=f32, device=dev)
+        for v in range(V):
+            tg = targets[v]
+            tg = tg if torch.is_tensor(tg) else torch.from_numpy(np.ascontiguousarray(tg, np.float32))
+            H, W = self.shapes[v]
+            pb = int(views[v].pix_base)
+            self.target[3 * pb:3 * (pb + H * W)].copy_(tg.reshape(-1).to(dev, f32))
+            L.check(self.lib.pgsag_prep_gc_weight(ctypes.byref(views[v]), _ptr(self.target), _ptr(self.gc_weight), s),
+                    "pgsag_prep_gc_weight")
+        raw = bytes(views)
+        self.views_dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
+
+        # ---- per-pixel buffers (dense per view; only rendered pixels are touched)
+        self.out8 = torch.zeros((self.n_pix, 8), dtype=f32, device=dev)
+        self.depth = torch.zeros(self.n_pix, dtype=f32, device=dev)
+        self.aux = torch.zeros((self.n_pix, 4), dtype=i32, device=dev)
+        self.dout8 = torch.zeros((self.n_pix, 8), dtype=f32, device=dev)
+        self.scratch = torch.zeros((self.n_pix, 6), dtype=f32, device=dev)
+        # ---- per-pair buffers
+        npairs = max(self.n_pairs, 1)
+        self.rec = torch.empty((npairs, 16), dtype=f32, device=dev)
+        self.dkey = torch.empty(npairs, dtype=i32, device=dev)
+        self.bininfo = torch.empty((npairs, 4), dtype=i32, device=dev)
+        self.grad2d = torch.empty((npairs, 16), dtype=f32, device=dev)
+        # ---- per-tile / per-view
+        self.ranges = torch.zeros((max(self.n_active, 1), 2), dtype=i32, device=dev)
+        self.tile_counts = torch.zeros(max(self.n_active, 1), dtype=i32, device=dev)
+        self.k_out = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=i32, device=dev)
+        self.acc_loss = torch.zeros(4 * V, dtype=torch.float64, device=dev)
+        self.acc_gc = torch.zeros(3 * V, dtype=torch.float64, device=dev)
+        self.gc_load = torch.zeros(V, dtype=f32, device=dev)
+        self.loss_buf = torch.zeros(3 * V + 1, dtype=f32, device=dev)
+        self.sched = None
+        self.sched_order = None
+        self.sched_counter = torch.zeros(1, dtype=i32, device=dev)
+        self._auto_capacity = capacity is None
+        self._alloc_capacity(int(capacity) if capacity is not None else max(4 * self.n_pairs, 1 << 16))
+
+    # ------------------------------------------------------------------ buffers
+    def _alloc_capacity(self, cap: int):
+        self.capacity = int(max(cap, 1))
+        self.dup_pairs = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
+        nbytes = int(self.lib.pgsag_bin_workspace_size(self.n_pairs, self.capacity))
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def use_persistent_schedule(self, ctas_per_sm: int = 8, order: Optional[torch.Tensor] = None):
+        """Render with a persistent grid pulling chunks from a device work counter,
+        optionally in the given chunk order."""
+        self.sched_order = order
+        self.sched = L.PgsagSched(order.data_ptr() if order is not None else None, self.sched_counter.data_ptr(),
+                                  int(ctas_per_sm), 0)
+
+    def use_plain_schedule(self):
+        self.sched = None
+        self.sched_order = None
+
+    def _sched_arg(self):
+        return ctypes.byref(self.sched) if self.sched is not None else None
+
+    # ------------------------------------------------------------------ step calls
+    def status_value(self) -> int:
+        return int(self.status.item())
+
+    def k_value(self) -> int:
+        return int(self.k_out.item())
+
+    def preprocess(self, P: GaussianParams, stream=None):
+        s = _stream_ptr(stream)
+        L.check(self.lib.pgsag_preprocess(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats), _ptr(P.opacity_logit),
+                                          _ptr(P.sh), self.n_views, _ptr(self.views_dev), _ptr(self.tile_act),
+                                          _ptr(self.sat), _ptr(self.rec), _ptr(self.dkey), _ptr(self.bininfo),
+                                          _ptr(self.status), s), "pgsag_preprocess")
+
+    def bin(self, stream=None):
+        s = _stream_ptr(stream)
+        L.check(self.lib.pgsag_bin(self.n_pairs, self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.tile_act),
+                                   _ptr(self.bininfo), _ptr(self.dkey), self.capacity, _ptr(self.ws), self.ws.numel(),
+                                   _ptr(self.dup_pairs), _ptr(self.ranges), _ptr(self.k_out), _ptr(self.status), s),
+                "pgsag_bin")
+
+    def render_fwd(self, stream=None):
+        s = _stream_ptr(stream)
+        L.check(self.lib.pgsag_render_fwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
+                                          _ptr(self.ranges), _ptr(self.act_tiles), self.n_chunks, _ptr(self.chunks),
+                                          _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.depth),
+                                          _ptr(self.aux), _ptr(self.status), s), "pgsag_render_fwd")
+
+    def loss(self, lambda_ban=LAMBDA_BAN, loss_out: Optional[torch.Tensor] = None, stream=None):
+        s = _stream_ptr(stream)
+        out = self.loss_buf if loss_out is None else loss_out
+        L.check(self.lib.pgsag_loss_ban(self.n_views, _ptr(self.views_dev), self.n_chunks, _ptr(self.chunks),
+                                        _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags), _ptr(self.out8),
+                                        _ptr(self.depth), _ptr(self.aux), _ptr(self.target), float(lambda_ban),
+                                        _ptr(self.scratch), _ptr(self.acc_loss), _ptr(out), _ptr(self.dout8),
+                                        _ptr(self.status), s), "pgsag_loss_ban")
+        return out
+
+    def tile_stats(self, stream=None):
+        s = _stream_ptr(stream)
+        L.check(self.lib.pgsag_tile_stats(self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.ranges),
+                                          self.n_chunks, _ptr(self.chunks), _ptr(self.act_tiles), _ptr(self.px_list),
+                                          _ptr(self.aux), _ptr(self.gc_weight), _ptr(self.tile_counts),
+                                          _ptr(self.acc_gc), _ptr(self.gc_load), _ptr(self.status), s),
+                "pgsag_tile_stats")
+
+    def render_bwd(self, dout8: torch.Tensor, ddepth: Optional[torch.Tensor] = None,
+                   dout_scale: Optional[torch.Tensor] = None, stream=None):
+        s = _stream_ptr(stream)
+        L.check(self.lib.pgsag_render_bwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
+                                          _ptr(self.ranges), _ptr(self.act_tiles), self.n_chunks, _ptr(self.chunks),
+                                          _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.aux),
+                                          _ptr(dout8), _ptr(ddepth), _ptr(dout_scale), self.n_pairs, _ptr(self.grad2d),
+                                          _ptr(self.status), s), "pgsag_render_bwd")
+
+    def preprocess_bwd(self, P: GaussianParams, grads: Sequence[torch.Tensor], accumulate=False, stream=None):
+        s = _stream_ptr(stream)
+        gm, gl, gq, go, gs = grads
+        L.check(self.lib.pgsag_preprocess_bwd(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats),
+                                              _ptr(P.opacity_logit), _ptr(P.sh), self.n_views, _ptr(self.views_dev),
+                                              _ptr(self.bininfo), _ptr(self.grad2d), 1 if accumulate else 0, _ptr(gm),
+                                              _ptr(gl), _ptr(gq), _ptr(go), _ptr(gs), _ptr(self.status), s),
+                "pgsag_preprocess_bwd")
+
+    def forward(self, P: GaussianParams, check: bool = True, stream=None):
+        """preprocess -> bin -> render_fwd.  With check=True (or while the capacity
+        is being sized) the host synchronises once to read the device status and
+        grows the duplicate capacity if it overflowed."""
+        for _ in range(3):
+            self.preprocess(P, stream)
+            self.bin(stream)
+            if not (check or self._auto_capacity):
+                break
+            st = self.status_value()
+            if st & L.PGSAG_DEV_CAPACITY:
+                self._alloc_capacity(int(self.k_value() * 1.25) + 1024)
+                continue
+            if st:
+                raise L.PgsagError(f"device status {st} after binning")
+            if self._auto_capacity:
+                self._auto_capacity = False
+            break
+        self.render_fwd(stream)
+
+    def check_status(self):
+        st = self.status_value()
+        if st:
+            raise L.PgsagError(f"device status {st}")
+
+    # ------------------------------------------------------------------ views of outputs
+    def pix_slice(self, v: int):
+        pb = int(self.views_host[v].pix_base)
+        H, W = self.shapes[v]
+        return slice(pb, pb + H * W)
+
+    def images(self, v: int):
+        """Dense images of view v: rgb [H,W,3], dist [H,W], normal [H,W,3], alpha
+        [H,W], depth [H,W], n_contrib [H,W] (zero outside the rendered set)."""
+        H, W = self.shapes[v]
+        sl = self.pix_slice(v)
+        o = self.out8[sl].view(H, W, 8)
+        return dict(rgb=o[..., 0:3], dist=o[..., 3], normal=o[..., 4:7], alpha=o[..., 7],
+                    depth=self.depth[sl].view(H, W), n_contrib=self.aux[sl, 2].view(H, W),
+                    final_T=self.aux[sl, 0].view(H, W).view(torch.float32))
+
+    def flags_image(self, v: int):
+        H, W = self.shapes[v]
+        return self.flags[self.pix_slice(v)].view(H, W)
+
+
+def new_param_grads(P: GaussianParams):
+    return [torch.empty_like(t) for t in P.tensors()]
+
+
+class RenderLossFn(torch.autograd.Function):
+    """Fused masked render + loss:  params -> sum over views of
+    L_rgb + lambda_4 L_ban  (Eq. 8, Eq. 10 restricted to the L1 photometric and
+    boundary-aware normal terms).  Backward runs the adjoint renderer on the
+    gradient the loss kernel produced and the preprocess adjoint."""
+
+    @staticmethod
+    def forward(ctx, plan: Plan, lambda_ban: float, check: bool, means, log_scales, quats, opacity_logit, sh):
+        P = GaussianParams(means, log_scales, quats, opacity_logit, sh)
+        plan.forward(P, check=check)
+        out = torch.empty(3 * plan.n_views + 1, dtype=torch.float32, device=plan.device)
+        plan.loss(lambda_ban, loss_out=out)
+        plan.tile_stats()
+        ctx.plan = plan
+        ctx.P = P
+        ctx.per_view = out
+        return out[3 * plan.n_views]
+
+    @staticmethod
+    def backward(ctx, g):
+        plan, P = ctx.plan, ctx.P
+        g = g.contiguous().to(torch.float32)
+        plan.render_bwd(plan.dout8, None, g)
+        grads = new_param_grads(P)
+        plan.preprocess_bwd(P, grads)
+        return (None, None, None) + tuple(grads)
+
+
+class RenderFn(torch.autograd.Function):
+    """Differentiable masked renderer: params -> (out8 [n_pix, 8] = {rgb, dist,
+    normal, alpha}, depth [n_pix]) for all views' rendered pixels (Eq. 1-4)."""
+
+    @staticmethod
+    def forward(ctx, plan: Plan, check: bool, means, log_scales, quats, opacity_logit, sh):
+        P = GaussianParams(means, log_scales, quats, opacity_logit, sh)
+        plan.forward(P, check=check)
+        ctx.plan = plan
+        ctx.P = P
+        return plan.out8.detach(), plan.depth.detach()
+
+    @staticmethod
+    def backward(ctx, g_out8, g_depth):
+        plan, P = ctx.plan, ctx.P
+        if g_out8 is None:
+            g_out8 = torch.zeros_like(plan.out8)
+        g_out8 = g_out8.contiguous()
+        if g_depth is not None:
+            g_depth = g_depth.contiguous()
+        plan.render_bwd(g_out8, g_depth, None)
+        grads = new_param_grads(P)
+        plan.preprocess_bwd(P, grads)
+        return (None, None) + tuple(grads)
+
+
+def render_loss(plan: Plan, P: GaussianParams, lambda_ban: float = LAMBDA_BAN, check: bool = True):
+    return RenderLossFn.apply(plan, lambda_ban, check, *P.tensors())
+
+
+def render(plan: Plan, P: GaussianParams, check: bool = True):
+    return RenderFn.apply(plan, check, *P.tensors())
+
+
+def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: Sequence[torch.Tensor],
+              v: Sequence[torch.Tensor], lr, step: int, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """Fused Adam over each parameter tensor (per-tensor learning rates allowed)."""
+    lib = L.load()
+    s = _stream_ptr(stream)
+    lrs = lr if isinstance(lr, (list, tuple)) else [lr] * len(params)
+    for p, g, mm, vv, l in zip(params, grads, m, v, lrs):
+        L.check(lib.pgsag_adam(p.numel(), _ptr(p), _ptr(g), _ptr(mm), _ptr(vv), float(l), float(beta1), float(beta2),
+                               float(eps), int(step), s), "pgsag_adam")

@@ -1,0 +1,257 @@
+"""CUDA path vs the FP64 oracle, through the C-ABI (ctypes binding)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import pgsag_synth as syn
+from oracle import pgsag_oracle as O
+from tests._helpers import (FWD_TOL, GRAD_TOL, compare_forward, compare_grads, gpu_run, oracle_run, rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def config0():
+    g, views = syn.config0()
+    res = oracle_run(g, views[0])
+    return g, views, res
+
+
+def test_config0_forward_parity(config0):
+    g, views, res = config0
+    plan, P = gpu_run(g, views)
+    errs = compare_forward(plan, 0, res)
+    print("config0 forward errors", errs)
+
+
+def test_config0_loss_and_gradients(config0):
+    g, views, res = config0
+    plan, P = gpu_run(g, views)
+    lv = res["loss"]
+    # per-view loss values from the loss kernel
+    plan2, P2 = gpu_run(g, views, grad=False)
+    lb = plan2.loss_buf.cpu().numpy()
+    assert lb[0] == pytest.approx(float(lv["l_rgb"]), rel=1e-4)
+    assert lb[1] == pytest.approx(float(lv["l_ban"]), rel=1e-3)
+    assert lb[3] == pytest.approx(float(lv["total"]), rel=1e-4)
+    errs = compare_grads(P, res)
+    print("config0 gradient rel-L2", errs)
+
+
+def test_config0_preprocess_parity(config0):
+    g, views, res = config0
+    plan, P = gpu_run(g, views, grad=False)
+    pr = res["proj"]
+    rec = plan.rec.cpu().numpy()
+    bi = plan.bininfo.cpu().numpy()
+    vis = pr["visible"].numpy() & (bi[:, 3] > 0)
+    assert vis.sum() > 1000
+    m2 = pr["mean2d"].detach().numpy()
+    q = pr["conic"].detach().numpy()
+    np.testing.assert_allclose(rec[vis, 0:2], m2[vis], rtol=1e-5, atol=1e-3)
+    for j, k in ((2, 0), (3, 1), (4, 2)):
+        scale = np.maximum(np.abs(q[vis]).max(1), 1e-12)
+        assert (np.abs(rec[vis, j] - q[vis, k]) / scale).max() < 1e-4
+    np.testing.assert_allclose(rec[vis, 5], pr["opacity"].detach().numpy()[vis], rtol=1e-5)
+    np.testing.assert_allclose(rec[vis, 6:9], pr["rgb"].detach().numpy()[vis], rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(rec[vis, 9], pr["dist"].detach().numpy()[vis], rtol=1e-4, atol=1e-5)
+    amb = pr["flip_ambiguous"].numpy()
+    ok = vis & ~amb
+    np.testing.assert_allclose(rec[ok, 10:13], pr["normal"].detach().numpy()[ok], atol=1e-5)
+    # depth key is bit-identical to the oracle's float32 key
+    assert (plan.dkey.cpu().numpy().view(np.float32)[vis] == pr["key"].numpy()[vis]).all()
+
+
+def test_config0_rect_is_conservative(config0):
+    """Every pixel where the oracle finds alpha >= 1/255 lies in the GPU tile rect."""
+    g, views, res = config0
+    plan, P = gpu_run(g, views, grad=False)
+    pr = res["proj"]
+    bi = plan.bininfo.cpu().numpy().astype(np.int64)
+    lin, gid = O.candidate_pairs(pr, 256, 256)
+    u = (lin % 256).numpy()
+    v = (lin // 256).numpy()
+    gid = gid.numpy()
+    m2 = pr["mean2d"].detach().numpy()
+    q = pr["conic"].detach().numpy()
+    o = pr["opacity"].detach().numpy()
+    dx = u + 0.5 - m2[gid, 0]
+    dy = v + 0.5 - m2[gid, 1]
+    a = o[gid] * np.exp(-0.5 * (q[gid, 0] * dx * dx + 2 * q[gid, 1] * dx * dy + q[gid, 2] * dy * dy))
+    ent = a >= 1 / 255
+    tx, ty = u[ent] // 16, v[ent] // 16
+    gg = gid[ent]
+    x0, y0 = bi[gg, 0] & 0xFFFF, bi[gg, 0] >> 16
+    x1, y1 = bi[gg, 1] & 0xFFFF, bi[gg, 1] >> 16
+    assert (bi[gg, 3] > 0).all() or not ent.any()
+    inside = (tx >= x0) & (tx <= x1) & (ty >= y0) & (ty <= y1)
+    assert inside.all()
+
+
+def _dup_reference(plan):
+    """(active tile, pair) multiset implied by the GPU's own rects and active-tile
+    map, in (tile, depth key, pair) order -- a check of the sort, not of the rects."""
+    bi = plan.bininfo.cpu().numpy().astype(np.int64)
+    ta = plan.tile_act.cpu().numpy()
+    key = plan.dkey.cpu().numpy().view(np.uint32)
+    vh = plan.views_host
+    tiles, pairs = [], []
+    for p in np.nonzero(bi[:, 3] > 0)[0]:
+        v = int(bi[p, 2])
+        x0, y0, x1, y1 = bi[p, 0] & 0xFFFF, bi[p, 0] >> 16, bi[p, 1] & 0xFFFF, bi[p, 1] >> 16
+        base, tx = vh[v].tile_base, vh[v].tiles_x
+        for yy in range(y0, y1 + 1):
+            a = ta[base + yy * tx + x0: base + yy * tx + x1 + 1]
+            a = a[a >= 0]
+            tiles.extend(a.tolist())
+            pairs.extend([p] * len(a))
+    tiles = np.array(tiles, np.int64)
+    pairs = np.array(pairs, np.int64)
+    order = np.lexsort((pairs, key[pairs], tiles))
+    return tiles[order], pairs[order]
+
+
+def test_config0_bin_is_exact_sort(config0):
+    g, views, res = config0
+    plan, P = gpu_run(g, views, grad=False)
+    K = plan.k_value()
+    dup = plan.dup_pairs[:K].cpu().numpy().astype(np.int64)
+    tiles_ref, pairs_ref = _dup_reference(plan)
+    assert K == len(pairs_ref)
+    assert (dup == pairs_ref).all()
+    rg = plan.ranges.cpu().numpy().astype(np.int64)[:plan.n_active]
+    cnt = np.bincount(tiles_ref, minlength=plan.n_active)
+    assert (rg[:, 1] - rg[:, 0] == cnt).all()
+    nz = cnt > 0
+    assert (rg[nz, 0] == np.concatenate([[0], np.cumsum(cnt)[:-1]])[nz]).all()
+    assert (plan.tile_counts.cpu().numpy()[:plan.n_active] == cnt).all()
+
+
+def test_config0_gc_load(config0):
+    g, views, res = config0
+    plan, P = gpu_run(g, views, grad=False)
+    M, E, R = res["sets"]
+    nc = O.to_dense_np(res["out"]["n_contrib"].double(), res["pix"], 256, 256).astype(np.int64)
+    w = O.luminance_gradient_weight(views[0].target)
+    ref = O.gc_load(nc, w, R)
+    assert float(plan.gc_load[0]) == pytest.approx(ref, rel=1e-4)
+    np.testing.assert_allclose(plan.gc_weight[:256 * 256].cpu().numpy(), w.reshape(-1), rtol=1e-5, atol=1e-6)
+    fl = plan.flags_image(0).cpu().numpy()
+    assert ((fl & 1) != 0).sum() == M.sum() and (((fl & 2) != 0) == E).all() and (((fl & 4) != 0) == R).all()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_scenes_forward_and_grad(seed):
+    g, v = syn.tiny_scene(seed, n=64, width=37, height=29)
+    res = oracle_run(g, v)
+    plan, P = gpu_run(g, [v], tile=(8, 8))
+    compare_forward(plan, 0, res)
+    compare_grads(P, res)
+
+
+def test_results_independent_of_tile_size(config0):
+    g, views, res = config0
+    outs = []
+    for tile in ((8, 8), (16, 16), (16, 32), (32, 32), (32, 8)):
+        plan, P = gpu_run(g, views, tile=tile, grad=False)
+        outs.append((plan.out8.cpu().numpy(), plan.aux[:, 2].cpu().numpy(), plan.depth.cpu().numpy()))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        assert np.array_equal(o[1], outs[0][1])
+        assert np.array_equal(o[2], outs[0][2])
+
+
+def test_batched_views_equal_plain_views():
+    """Several views (different resolutions, Gaussian subsets) in one plan give the
+    same per-view results as one plan per view; the sort is bit-identical."""
+    g, ranges, views, owner = syn.config3(sizes=(3000, 5000, 2000), views_per_region=2, scale=0.2)
+    g_ranges = [ranges[o] for o in owner]
+    planb, Pb = gpu_run(g, views, g_ranges=g_ranges)
+    for v in range(len(views)):
+        plan1, P1 = gpu_run(g, [views[v]], g_ranges=[g_ranges[v]])
+        sl = planb.pix_slice(v)
+        assert np.array_equal(planb.out8[sl].cpu().numpy(), plan1.out8.cpu().numpy())
+        assert np.array_equal(planb.aux[sl, 2].cpu().numpy(), plan1.aux[:, 2].cpu().numpy())
+    # gradients of the batch = sum of per-view gradients
+    acc = [torch.zeros_like(t) for t in Pb.tensors()]
+    for v in range(len(views)):
+        plan1, P1 = gpu_run(g, [views[v]], g_ranges=[g_ranges[v]])
+        for a, t in zip(acc, P1.tensors()):
+            a += t.grad
+    for a, t in zip(acc, Pb.tensors()):
+        assert rel_l2(t.grad.cpu().numpy().ravel(), a.cpu().numpy().ravel()) < 1e-5
+
+
+def test_empty_mask_and_no_gaussians():
+    g, v = syn.tiny_scene(3, n=20, width=24, height=24)
+    v.mask[:] = 0
+    plan, P = gpu_run(g, [v])
+    assert plan.n_render == 0 and plan.n_chunks == 0
+    for t in P.tensors():
+        assert float(t.grad.abs().max()) == 0.0
+    g0, v0 = syn.tiny_scene(4, n=10)
+    g0 = g0.subset(np.arange(0))
+    plan, P = gpu_run(g0, [v0], grad=False)
+    assert plan.k_value() == 0
+    assert float(plan.out8.abs().max()) == 0.0
+
+
+def test_culled_and_nonfinite_gaussians():
+    g, v = syn.tiny_scene(6, n=40, width=32, height=32)
+    g.means[:10, 2] = -3.0                 # behind the camera
+    g.means[10, 0] = np.nan                # non-finite
+    g.opacity_logit[11] = np.inf
+    g.opacity_logit[12] = -20.0            # o < 1/255
+    plan, P = gpu_run(g, [v], grad=False)
+    bi = plan.bininfo.cpu().numpy()
+    assert (bi[:13, 3] == 0).all()
+    assert (plan.dkey.cpu().numpy().view(np.uint32)[:13] == 0xFFFFFFFF).all()
+    assert np.isfinite(plan.out8.cpu().numpy()).all()
+
+
+def test_capacity_overflow_reports_status_then_grows():
+    g, views = syn.config0()
+    from paper_2501_01677_b300 import raster
+    P = raster.GaussianParams.from_numpy(g)
+    plan = raster.Plan([views[0].cam], [views[0].mask], [views[0].target], g.n, capacity=1000)
+    plan.preprocess(P)
+    plan.bin()
+    plan.render_fwd()
+    torch.cuda.synchronize()
+    assert plan.status_value() & 1
+    assert plan.k_value() > 1000
+    plan._auto_capacity = True
+    plan.forward(P)
+    torch.cuda.synchronize()
+    assert plan.status_value() == 0 and plan.capacity >= plan.k_value()
+
+
+def test_render_fn_upstream_gradient_matches_oracle():
+    """Differentiable renderer with an arbitrary upstream gradient on the outputs
+    (RGB, D, N, A and depth): gradient of <G, outputs> vs oracle autograd."""
+    g, v = syn.tiny_scene(9, n=50, width=30, height=26)
+    from paper_2501_01677_b300 import raster
+    rng = np.random.default_rng(0)
+    H, W = 26, 30
+    G8 = rng.standard_normal((H * W, 8)).astype(np.float32)
+    Gd = rng.standard_normal(H * W).astype(np.float32)
+    P = raster.GaussianParams.from_numpy(g, requires_grad=True)
+    plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, tile=(16, 16))
+    out8, depth = raster.render(plan, P)
+    (out8 * torch.from_numpy(G8).cuda()).sum().add_((depth * torch.from_numpy(Gd).cuda()).sum()).backward()
+    # oracle
+    cam = O.Cam.from_synth(v.cam)
+    p = O.params_from_synth(g, requires_grad=True)
+    pr, out, dep, valid, pix, sets = O.render_view(p, cam, v.mask, g.means)
+    pu, pv = pix
+    lin = (pv * W + pu).numpy()
+    G8t = torch.from_numpy(G8.astype(np.float64))[lin]
+    Gdt = torch.from_numpy(Gd.astype(np.float64))[lin]
+    obj = (out["rgb"] * G8t[:, 0:3]).sum() + (out["dist"] * G8t[:, 3]).sum() + (out["normal"] * G8t[:, 4:7]).sum() \
+        + (out["alpha"] * G8t[:, 7]).sum() + (dep * Gdt).sum()
+    obj.backward()
+    for name, t in zip(("means", "log_scales", "quats", "opacity_logit", "sh"), P.tensors()):
+        e = rel_l2(t.grad.cpu().numpy().astype(np.float64).ravel(), p[name].grad.numpy().ravel())
+        assert e < GRAD_TOL, (name, e)

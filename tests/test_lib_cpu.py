@@ -1,0 +1,61 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every entry
+point declared in include/pgsag.h, its struct layout matches the binding and
+its host-only queries answer."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2501_01677_b300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "pgsag.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pgsag_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(L.LIB_PATH):
+        from paper_2501_01677_b300 import build
+        build.build()
+    return L.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(L.EXPORTS) == names
+
+
+def test_view_struct_layout(lib):
+    assert ctypes.sizeof(L.PgsagView) == 144
+    assert b"144" in lib.pgsag_build_info()
+
+
+def test_status_strings(lib):
+    assert lib.pgsag_status_str(0) == b"ok"
+    assert b"argument" in lib.pgsag_status_str(-1)
+    assert b"unknown" in lib.pgsag_status_str(17)
+
+
+def test_bin_workspace_size_grows_with_sizes(lib):
+    a = lib.pgsag_bin_workspace_size(1000, 4000)
+    b = lib.pgsag_bin_workspace_size(2000, 4000)
+    c = lib.pgsag_bin_workspace_size(2000, 8000)
+    assert 0 < a < b < c
+    assert b - a >= 4 * 1000 * 4
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    # argument errors are detected before any device work
+    assert lib.pgsag_preprocess(10, None, None, None, None, None, 0, None, None, None, None, None, None, None,
+                                None) == -5
+    assert lib.pgsag_bin(10, 1, None, 0, None, None, None, 0, None, 0, None, None, None, None, None) == -1
+    assert lib.pgsag_adam(10, None, None, None, None, 0.1, 0.9, 0.999, 1e-8, 1, None) == -1

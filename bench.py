@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Masked forward+backward throughput of the differentiable Gaussian-splat step.
+
+Workload (default): one oblique aerial view at 5472x3648 of 40 box buildings
+covered by 1.5M flat Gaussians (synthetic stand-in for a GauU-Scene building
+group at the original resolution), building mask ~37% of the pixels.  One
+step = preprocess -> bin -> masked render -> L1 + boundary-aware normal loss ->
+per-tile / per-pixel Gaussian statistics -> render adjoint -> preprocess
+adjoint, through the fused autograd Function.  Metric: building-mask pixels
+per second (Mpix/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the workload (independent
+sub-regions; weak scaling); the value is the total over ranks divided by the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "masked fwd+bwd Mpix/s @5472x3648, 1.5M Gaussians; % HBM roofline; batched vs plain"
+UNIT = "Mpix/s"
+WORKLOAD = "aerial view 5472x3648, 1.5M Gaussians on 40 box buildings, building mask ~37%"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- workload
+
+def workload():
+    import pgsag_synth as syn
+    g, views, boxes = syn.config1()
+    return g, views
+
+
+def cpu_crop_sample(views):
+    import pgsag_synth as syn
+    v = views[0]
+    w = 128
+    x0, y0 = syn.densest_window(v.mask, w, w)
+    return syn.crop_view(v, x0, y0, w, w), f"{w}x{w} window (densest mask) of the 5472x3648 view, all 1.5M Gaussians projected"
+
+
+def run_oracle_steps(g, cv, n):
+    import torch
+    from oracle import pgsag_oracle as O
+    times = []
+    for _ in range(n):
+        t = time.perf_counter()
+        O.step(g, cv)
+        times.append(time.perf_counter() - t)
+    return times, torch.get_num_threads()
+
+
+# ---------------------------------------------------------------------------- algorithmic bytes
+
+def algorithmic_bytes(plan, K):
+    """Compulsory DRAM bytes per stage of one step (each item read / written once
+    by the stage that needs it), from the measured sizes N, pairs, K and pixels."""
+    N, NP, P, A = plan.n_gauss, plan.n_pairs, plan.n_render, plan.n_active
+    M = plan.n_mask
+    tile_passes = (int(A - 1).bit_length() + 7) // 8 if A > 1 else 0
+    return {
+        # params 236 B/G; per pair: rec 64 + key 4 + bininfo 16
+        "preprocess": 236 * N + 84 * NP,
+        # 4 depth passes (hist read 4 + scatter read 8 + write 8); scan read order + bininfo twice;
+        # emission write 8/dup; tile passes 20/dup; ranges read 4/dup + write 8/tile
+        "bin": NP * (4 * 20 + 2 * 20) + K * (8 + 20 * tile_passes + 4) + 8 * A,
+        # per pixel: list 4 + out8 32 + depth 4 + aux 16; per duplicate: id 4 + record 64
+        "render_fwd": 56 * P + 68 * K,
+        # pass A: flags 1 + out8 32 + depth 4 + dout8 32 (+ target 12 + scratch 24 on M);
+        # pass B: out8 32 + depth 4 + dout8 64 + scratch 24
+        "loss": P * (1 + 32 + 4 + 32 + 32 + 4 + 64) + M * (12 + 24 + 24),
+        "tile_stats": P * (4 + 16 + 4) + 8 * A,
+        # per pixel: list 4 + aux 16 + dout8 32; per duplicate: id 4 + record 64; grad2d zero + write-back 2x64/pair
+        "render_bwd": 52 * P + 68 * K + 128 * NP,
+        # params read 236 + grads write 236 per G; per pair grad2d 64 + bininfo 16
+        "preprocess_bwd": 472 * N + 80 * NP,
+    }
+
+
+def read_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 2 and parts[0] == kernel:
+            try:
+                return float(parts[1])
+            except ValueError:
+                return None
+    return None
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------- arms
+
+def ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2501_01677_b300 import raster
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    tw, th = (int(x) for x in args.tile.split("x"))
+    g, views = workload()
+    v = views[0]
+    P = raster.GaussianParams.from_numpy(g, requires_grad=True)
+    plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, tile=(tw, th))
+
+    def step(check=False):
+        for t in P.tensors():
+            t.grad = None
+        loss = raster.render_loss(plan, P, check=check)
+        loss.backward()
+        return loss
+
+    step(check=True)
+    for _ in range(max(args.warmup - 1, 0)):
+        step()
+    torch.cuda.synchronize()
+    plan.check_status()
+    K_dup = plan.k_value()
+
+    # timed region (device time, CUDA events on the launching stream)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    plan.stage_events = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    stage_ms = {}
+    for name, a, b in plan.stage_events:
+        stage_ms[name] = stage_ms.get(name, 0.0) + a.elapsed_time(b)
+    plan.stage_events = None
+    stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
+    plan.check_status()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    mpix = plan.n_mask / 1e6
+    value = ws * mpix * args.steps / (ms / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [t.detach().cpu().pin_memory() for t in P.tensors()]
+        ghost = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in P.tensors()]
+        loss_host = torch.empty((), dtype=torch.float32, pin_memory=True)
+        h2d = sum(t.numel() * t.element_size() for t in host)
+        d2h = 4 + h2d
+        n_e2e = max(3, args.steps // 2)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_e2e):
+            with torch.no_grad():
+                for d, h in zip(P.tensors(), host):
+                    d.copy_(h, non_blocking=True)
+            loss = step()
+            loss_host.copy_(loss.detach(), non_blocking=True)
+            for h, d in zip(ghost, P.tensors()):
+                h.copy_(d.grad, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = a.elapsed_time(b)
+        if ws > 1:
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": ws * mpix * n_e2e / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / n_e2e}
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant single-kernel stage
+    pk, pk_src = peaks()
+    ab = algorithmic_bytes(plan, K_dup)
+    single = ("preprocess", "render_fwd", "render_bwd", "preprocess_bwd")
+    dom = max(single, key=lambda k: stage_ms.get(k, 0.0))
+    kernel_name = {"preprocess": "k_preprocess", "render_fwd": "k_render_fwd", "render_bwd": "k_render_bwd",
+                   "preprocess_bwd": "k_preprocess_bwd"}[dom]
+    achieved = ab[dom] / (stage_ms[dom] / 1e3) / 1e9
+    traffic = read_traffic(kernel_name)
+    roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "peak_source": pk_src, "traffic": traffic,
+                "algorithmic_bytes": ab[dom]}
+    step_bytes = sum(ab.values())
+    whole = {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9,
+             "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / pk["hbm_gbs"]}
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cv, sample = cpu_crop_sample(views)
+        times, cores = run_oracle_steps(g, cv, 2)
+        t = min(times)
+        cpu = {"value": float(cv.mask.sum()) / 1e6 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": sample, "s_per_step": t}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": v.cam.width, "height": v.cam.height, "n_gaussians": g.n,
+                   "mask_pixels": plan.n_mask, "rendered_pixels": plan.n_render, "active_tiles": plan.n_active,
+                   "duplicates_K": K_dup, "tile": args.tile, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (params 354 MB, per-pixel buffers > 2 GB)"},
+        "roofline": roofline, "step_roofline": whole,
+        "stages_ms": stage_ms, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": plan.kernel_launches_per_step() * args.steps,
+        "clocks": ck,
+    }
+    print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    g, views = workload()
+    cv, sample = cpu_crop_sample(views)
+    run_oracle_steps(g, cv, args.warmup)
+    times, cores = run_oracle_steps(g, cv, args.steps)
+    t = sum(times)
+    value = float(cv.mask.sum()) * args.steps / 1e6 / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference(a)
+    else:
+        ours(a)

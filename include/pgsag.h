@@ -93,12 +93,14 @@ typedef struct pgsag_view {
   uint32_t act_base;          /* global index of this view's first active tile  */
   uint32_t n_active;          /* (prep) active tiles of this view               */
   uint32_t n_mask;            /* (prep) |M|, building-mask pixels               */
+  uint32_t chunk_base;        /* (prep) global index of this view's first chunk */
+  uint32_t n_chunks;          /* (prep) chunks of this view                     */
   uint64_t pix_base;          /* offset of this view in per-pixel arrays        */
 } pgsag_view;
 
 /* Optional work scheduling for the render kernels. */
 typedef struct pgsag_sched {
-  const uint32_t* order;      /* device, n_chunks chunk ids in processing order, or NULL */
+  const uint32_t* order;      /* device, active-tile ids in processing order, or NULL */
   uint32_t* counter;          /* device uint32 work counter for a persistent launch, or NULL */
   int32_t ctas_per_sm;        /* persistent launch: CTAs per SM (used when counter != NULL) */
   int32_t reserved;
@@ -191,7 +193,8 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* wei
  *   sh [N,16,3]; views (device, n_views <= PGSAG_MAX_VIEWS); tile_act, sat.
  * Outputs per pair p:
  *   rec [p*16 .. p*16+15] float (16-byte aligned):
- *     {mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz, z, 0, 0}
+ *     {mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz, z, ex, ey}
+ *     (ex, ey: half-extents of the alpha >= 1/255 box, 1 px margin included)
  *   depth_key [p]: float bits of z, 0xFFFFFFFF for culled pairs
  *   bininfo [p] uint4: {x0 | y0 << 16, x1 | y1 << 16 (inclusive tile rect),
  *     view index, touched}
@@ -230,9 +233,10 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
               void* stream);
 
 /*
- * pgsag_render_fwd (Sec. 3.1, Eq. 1-4).  One warp per chunk of up to 32 rendered
- * pixels of one active tile; the tile's sorted Gaussians are staged through
- * shared memory in batches of 32.  Per pixel, front to back:
+ * pgsag_render_fwd (Sec. 3.1, Eq. 1-4).  One CTA (8 warps) per active tile, one
+ * warp per 32 compacted rendered pixels of the tile; the tile's sorted Gaussians
+ * are staged through shared memory in batches of 256 and each warp skips the
+ * Gaussians whose alpha >= 1/255 box misses its pixels.  Per pixel, front to back:
  *   alpha = min(0.99, o exp(-1/2 d^T Q d)); skipped if alpha < 1/255; if
  *   T (1 - alpha) < 1e-4 the pixel stops before this Gaussian; otherwise
  *   w = alpha T, C += w c, N += w n_c, D += w d, T *= 1 - alpha.
@@ -243,13 +247,13 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
  *   depth float [1 per pixel]
  *   aux   uint4 [1 per pixel]: {float bits of final T, index (into dup_pairs) of the
  *         last blended Gaussian, number blended n_contrib, 0}
- * sched may be NULL (one warp per chunk in chunk order).
+ * sched may be NULL (one CTA per active tile in index order); with a counter the
+ * launch is persistent (ctas_per_sm x SMs CTAs pulling tiles, in `order` if given).
  */
 int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec,
                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
-                     uint32_t n_chunks, const void* chunks, const uint32_t* px_list,
-                     const pgsag_sched* sched, float* out8, float* depth, void* aux,
-                     int32_t* status, void* stream);
+                     uint32_t n_active_total, const uint32_t* px_list, const pgsag_sched* sched,
+                     float* out8, float* depth, void* aux, int32_t* status, void* stream);
 
 /*
  * pgsag_loss_ban (Sec. 4.2, Eq. 8; photometric L1 term of Eq. 10).  Per view v:
@@ -264,6 +268,8 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
  *   target   float [3 per pixel] (RGB interleaved, at 3*pix_base)
  *   scratch  float [6 per pixel] (only M pixels touched)
  *   acc      double [4 per view] scratch accumulators
+ *   chunk_scratch  float [4 per chunk] scratch (per-chunk partial sums, reduced
+ *            per view without contended atomics)
  *   loss     float [3 per view + 1]: {L_rgb, L_ban, L} per view, then sum_v L
  *   dout8    float [8 per pixel]
  */
@@ -271,25 +277,27 @@ int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                    const void* chunks, const void* act_tiles, const uint32_t* px_list,
                    const uint8_t* flags, const float* out8, const float* depth,
                    const void* aux, const float* target, float lambda_ban, float* scratch,
-                   double* acc, float* loss, float* dout8, int32_t* status, void* stream);
+                   double* acc, float* chunk_scratch, float* loss, float* dout8, int32_t* status,
+                   void* stream);
 
 /*
  * pgsag_render_bwd (Sec. 3.1: "optimized ... using differentiable rendering").
- * Adjoint of pgsag_render_fwd: each warp re-traverses its tile's list back to
+ * Adjoint of pgsag_render_fwd: each CTA re-traverses its tile's list back to
  * front from the last blended Gaussian, recovering T by division
  * (T_i = T_{i+1} / (1 - alpha_i)), and accumulates per pair
  *   grad2d[p*16 + {0..12}] = dL/d{mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz}
- * (warp shuffle reduction, then one atomic add per warp and value).  grad2d is
- * zeroed by this call.  ddepth (nullable) adds a gradient on the depth output,
+ * (warp shuffle reduction, shared-memory sum over the CTA's warps, then one
+ * float4 atomic add per 4 values per tile).  grad2d (16-byte aligned) is zeroed
+ * by this call.  ddepth (nullable) adds a gradient on the depth output,
  * folded into dD and dN through Eq. 4.  dout_scale (nullable, device float[1])
  * multiplies the whole upstream gradient (chain rule from a scalar loss).
  */
 int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec,
                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
-                     uint32_t n_chunks, const void* chunks, const uint32_t* px_list,
-                     const pgsag_sched* sched, const float* out8, const void* aux,
-                     const float* dout8, const float* ddepth, const float* dout_scale,
-                     uint32_t n_pairs, float* grad2d, int32_t* status, void* stream);
+                     uint32_t n_active_total, const uint32_t* px_list, const pgsag_sched* sched,
+                     const float* out8, const void* aux, const float* dout8, const float* ddepth,
+                     const float* dout_scale, uint32_t n_pairs, float* grad2d, int32_t* status,
+                     void* stream);
 
 /*
  * pgsag_preprocess_bwd: chain rule from grad2d to the raw parameters (the
@@ -313,13 +321,14 @@ int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const float* log_
  *     (length of its range);
  *   per view, GC-load = population std over R pixels of g_i / w_i with
  *     g_i = n_contrib (from aux) and w_i from pgsag_prep_gc_weight;
- *   acc   double [3 per view] scratch; gc_load float [1 per view].
+ *   acc   double [3 per view] scratch; chunk_scratch float [4 per chunk] scratch;
+ *   gc_load float [1 per view].
  */
 int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint32_t n_active_total,
                      const void* ranges, uint32_t n_chunks, const void* chunks,
                      const void* act_tiles, const uint32_t* px_list, const void* aux,
                      const float* gc_weight, uint32_t* tile_counts, double* acc,
-                     float* gc_load, int32_t* status, void* stream);
+                     float* chunk_scratch, float* gc_load, int32_t* status, void* stream);
 
 /*
  * pgsag_adam: fused Adam update of n parameters (p, g, m, v float32):

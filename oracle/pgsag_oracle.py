@@ -316,7 +316,8 @@ def composite(pr, pu: torch.Tensor, pv: torch.Tensor, pair_pix: torch.Tensor, pa
 
     pair_pix indexes into (pu, pv).  Returns dict with rgb [P,3], dist D [P],
     normal N [P,3], alpha A [P], n_contrib [P] (long), ambiguous [P] (bool),
-    final_T [P]."""
+    final_T [P], and mag: the magnitude sums sum_i w_i |x_i| of each channel,
+    which bound the rounding error of any evaluation of these sums."""
     Pn = pu.shape[0]
     key = pr["key"].numpy()
     # order: pixel, then (depth key, gaussian index)
@@ -349,6 +350,10 @@ def composite(pr, pu: torch.Tensor, pv: torch.Tensor, pair_pix: torch.Tensor, pa
     C = torch.zeros(Pn, 3, dtype=DT)
     N = torch.zeros(Pn, 3, dtype=DT)
     D = torch.zeros(Pn, dtype=DT)
+    # magnitude sums sum_i w_i |x_i| of each blended channel (condition of the sums)
+    magC = torch.zeros(Pn, 3, dtype=DT)
+    magN = torch.zeros(Pn, 3, dtype=DT)
+    magD = torch.zeros(Pn, dtype=DT)
     ncon = torch.zeros(Pn, dtype=torch.long)
     done = torch.zeros(Pn, dtype=torch.bool)
     col = pr["rgb"][gi]
@@ -367,9 +372,14 @@ def composite(pr, pu: torch.Tensor, pv: torch.Tensor, pair_pix: torch.Tensor, pa
         C = C + w[:, None] * col[:, j]
         N = N + w[:, None] * nor[:, j]
         D = D + w * dst[:, j]
+        wd = w.detach()
+        magC = magC + wd[:, None] * col[:, j].detach().abs()
+        magN = magN + wd[:, None] * nor[:, j].detach().abs()
+        magD = magD + wd * dst[:, j].detach().abs()
         T = torch.where(blend, test, T)
         ncon = ncon + blend.long()
-    return dict(rgb=C, normal=N, dist=D, alpha=1.0 - T, final_T=T, n_contrib=ncon, ambiguous=amb)
+    return dict(rgb=C, normal=N, dist=D, alpha=1.0 - T, final_T=T, n_contrib=ncon, ambiguous=amb,
+                mag=dict(rgb=magC, normal=magN, dist=magD, alpha=(1.0 - T).detach()))
 
 
 def pixel_rays(cam: Cam, pu: torch.Tensor, pv: torch.Tensor) -> torch.Tensor:

@@ -36,11 +36,11 @@ class PgsagView(ctypes.Structure):
         ("tiles_x", c_int32), ("tiles_y", c_int32),
         ("g_begin", c_uint32), ("g_end", c_uint32), ("pair_base", c_uint32), ("tile_base", c_uint32),
         ("sat_base", c_uint32), ("act_base", c_uint32), ("n_active", c_uint32), ("n_mask", c_uint32),
-        ("pix_base", c_uint64),
+        ("chunk_base", c_uint32), ("n_chunks", c_uint32), ("pix_base", c_uint64),
     ]
 
 
-assert ctypes.sizeof(PgsagView) == 144
+assert ctypes.sizeof(PgsagView) == 152
 
 
 class PgsagSched(ctypes.Structure):
@@ -73,12 +73,12 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_preprocess", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_bin_workspace_size", c_size_t, [c_uint32, c_uint64])
     _sig(lib, "pgsag_bin", c_int, [c_uint32, c_uint32, P, c_uint32, P, P, P, c_uint64, P, c_size_t, P, P, P, P, P])
-    _sig(lib, "pgsag_render_fwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, POINTER(PgsagSched), P, P, P, P, P])
-    _sig(lib, "pgsag_loss_ban", c_int, [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, c_float, P, P, P, P, P, P])
+    _sig(lib, "pgsag_render_fwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P])
+    _sig(lib, "pgsag_loss_ban", c_int, [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, c_float, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_render_bwd", c_int,
-         [c_uint32, P, P, P, P, P, c_uint32, P, P, POINTER(PgsagSched), P, P, P, P, P, c_uint32, P, P, P])
+         [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P, c_uint32, P, P, P])
     _sig(lib, "pgsag_preprocess_bwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, P])
-    _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_adam", c_int, [c_uint64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P])
     _lib = lib
     return lib

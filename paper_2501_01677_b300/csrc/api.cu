@@ -3,7 +3,7 @@
 
 #define PGSAG_STR2(x) #x
 #define PGSAG_STR(x) PGSAG_STR2(x)
-#define PGSAG_VIEW_BYTES 144
+#define PGSAG_VIEW_BYTES 152
 static_assert(sizeof(pgsag_view) == PGSAG_VIEW_BYTES, "pgsag_view layout");
 
 extern "C" const char* pgsag_status_str(int status) {

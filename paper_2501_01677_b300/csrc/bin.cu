@@ -6,9 +6,10 @@
 // keys, with N-sized instead of K-sized depth passes.
 //
 // The radix sort is a reduce-then-scan design with no inter-block waits:
-// per pass (8-bit digit) one histogram kernel, one single-block scan of the
-// digit-major histogram table, and one scatter kernel that ranks keys stably
-// inside each block with warp match/popc.
+// per pass (8-bit digit) one histogram kernel, one row-parallel scan of the
+// digit-major histogram table (a block per digit), and one scatter kernel that
+// scans the 256 digit totals, then ranks keys stably inside each block with
+// warp match/popc.
 #include "common.cuh"
 
 namespace pgsag {
@@ -65,48 +66,52 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint32_t* __res
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan in place of `count` uint32 values by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_scan_flat(uint32_t* __restrict__ data, uint32_t count,
-                                                    const int32_t* status) {
+// One block per digit d: exclusive scan (in place) of row d of the digit-major
+// histogram table (the counts of digit d in blocks 0..G-1) and the row total.
+__global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t* __restrict__ hist, uint32_t G,
+                                                        uint32_t* __restrict__ dtot, const int32_t* status) {
   __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
   if (status_bad(status)) return;
-  const uint32_t per = (count + 1023) / 1024;
-  const uint32_t lo = min(count, threadIdx.x * per), hi = min(count, lo + per);
-  uint32_t s = 0;
-  for (uint32_t i = lo; i < hi; ++i) s += data[i];
-  // block exclusive scan of s
+  uint32_t* row = hist + (size_t)blockIdx.x * G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[warp] = x;
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = wsum[lane];
+  for (uint32_t base = 0; base < G; base += 1024) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t s = i < G ? row[i] : 0u;
+    uint32_t x = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, w, o);
-      if (lane >= o) w += y;
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
     }
-    wsum[lane] = w;
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t c = carry;
+    if (i < G) row[i] = c + x - s + (warp > 0 ? wsum[warp - 1] : 0u);
+    __syncthreads();
+    if (threadIdx.x == 0) carry = c + wsum[31];
+    __syncthreads();
   }
-  __syncthreads();
-  uint32_t run = x - s + (warp > 0 ? wsum[warp - 1] : 0u);
-  for (uint32_t i = lo; i < hi; ++i) {
-    const uint32_t t = data[i];
-    data[i] = run;
-    run += t;
-  }
+  if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
 }
 
 __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const uint64_t* n_dev,
     uint64_t n_const, uint64_t cap, int shift, const uint32_t* __restrict__ hist,
-    const int32_t* status) {
+    const uint32_t* __restrict__ dtot, const int32_t* status) {
   __shared__ uint32_t run[256];
   __shared__ uint32_t tot[256];
   __shared__ uint32_t wcnt[kRsWarps][256];
@@ -114,8 +119,23 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(
   const uint32_t n = load_n(n_dev, n_const, cap);
   uint32_t lo, hi;
   block_range(n, blockIdx.x, gridDim.x, lo, hi);
-  run[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    // digit bases: exclusive scan of the 256 digit totals
+    const uint32_t t = dtot[threadIdx.x];
+    uint32_t x = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) tot[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre += tot[w];
+    run[threadIdx.x] = pre + x - t + hist[threadIdx.x * gridDim.x + blockIdx.x];
+    __syncthreads();
+  }
   const uint32_t lt = lanemask_lt();
   for (uint32_t tile = lo; tile < hi; tile += kRsTile) {
 #pragma unroll
@@ -315,7 +335,7 @@ namespace {
 struct BinWs {
   uint32_t *kA, *kB, *vA, *vB;  // depth sort (n_pairs)
   uint32_t *dkA, *dkB, *dvW;    // tile sort (capacity)
-  uint32_t* hist;               // 256 * kRsBlocks
+  uint32_t* hist;               // 256 * kRsBlocks counts, then 256 digit totals
   uint64_t* partial;            // kScanBlocks + 1
   size_t bytes;
 };
@@ -337,7 +357,7 @@ BinWs carve(void* base, uint32_t np, uint64_t cap) {
   w.dkA = (uint32_t*)take(capb);
   w.dkB = (uint32_t*)take(capb);
   w.dvW = (uint32_t*)take(capb);
-  w.hist = (uint32_t*)take((size_t)256 * kRsBlocks * 4);
+  w.hist = (uint32_t*)take((size_t)256 * (kRsBlocks + 1) * 4);
   w.partial = (uint64_t*)take((size_t)(kScanBlocks + 1) * 8);
   w.bytes = o;
   return w;
@@ -348,10 +368,10 @@ int radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_
                int32_t* status, cudaStream_t s) {
   k_radix_hist<<<kRsBlocks, kRsThreads, 0, s>>>(kin, n_dev, n_const, cap, shift, hist, status);
   PGSAG_CHECK_LAUNCH();
-  k_scan_flat<<<1, 1024, 0, s>>>(hist, 256u * kRsBlocks, status);
+  k_radix_rowscan<<<256, 1024, 0, s>>>(hist, kRsBlocks, hist + 256 * kRsBlocks, status);
   PGSAG_CHECK_LAUNCH();
   k_radix_scatter<<<kRsBlocks, kRsThreads, 0, s>>>(kin, vin, kout, vout, n_dev, n_const, cap, shift, hist,
-                                                   status);
+                                                   hist + 256 * kRsBlocks, status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
     const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
     const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
     const uint8_t* __restrict__ flags, const float4* __restrict__ out8, const float* __restrict__ depth,
-    const float* __restrict__ target, float* __restrict__ scratch, double* __restrict__ acc,
+    const float* __restrict__ target, float* __restrict__ scratch, float4* __restrict__ partial,
     float4* __restrict__ dout8, const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
@@ -138,13 +138,42 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
     dout8[2 * P.gp] = make_float4(dC[0], dC[1], dC[2], 0.f);
     dout8[2 * P.gp + 1] = make_float4(dNo[0], dNo[1], dNo[2], 0.f);
   }
-  // a chunk belongs to one view: warp-reduce then one atomic per value
+  // per-chunk partial sums, reduced per view by k_view_reduce
   const float s1 = warp_sum(l1), s2 = warp_sum(lb), s3 = warp_sum(nv);
+  if (lane == 0) partial[c] = make_float4(s1, s2, s3, 0.f);
+}
+
+// One block per view: sum the per-chunk partials of the view's chunk range in
+// double into acc[stride * v + 0 .. ncomp).
+__global__ void __launch_bounds__(256) k_view_reduce(const pgsag_view* __restrict__ views,
+                                                     const float4* __restrict__ partial, int ncomp,
+                                                     int stride, double* __restrict__ acc,
+                                                     const int32_t* status) {
+  __shared__ double sh[8][3];
+  if (status_bad(status)) return;
+  const pgsag_view* V = views + blockIdx.x;
+  const uint32_t b = __ldg(&V->chunk_base), n = __ldg(&V->n_chunks);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float4 p = __ldg(partial + b + i);
+    a0 += p.x;
+    a1 += p.y;
+    a2 += p.z;
+  }
+  a0 = warp_sum_d(a0);
+  a1 = warp_sum_d(a1);
+  a2 = warp_sum_d(a2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    double* A = acc + 4 * P.view;
-    if (s1 != 0.f) atomicAdd(A + 0, (double)s1);
-    if (s2 != 0.f) atomicAdd(A + 1, (double)s2);
-    if (s3 != 0.f) atomicAdd(A + 2, (double)s3);
+    sh[warp][0] = a0;
+    sh[warp][1] = a1;
+    sh[warp][2] = a2;
+  }
+  __syncthreads();
+  if (threadIdx.x < ncomp) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w][threadIdx.x];
+    acc[stride * blockIdx.x + threadIdx.x] = t;
   }
 }
 
@@ -240,26 +269,21 @@ __global__ void k_tile_counts(uint32_t n_active, const uint2* __restrict__ range
 __global__ void __launch_bounds__(kLossThreads) k_gc_accum(
     const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
     const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
-    const uint4* __restrict__ aux, const float* __restrict__ weight, double* __restrict__ acc,
+    const uint4* __restrict__ aux, const float* __restrict__ weight, float4* __restrict__ partial,
     const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
   if (c >= n_chunks) return;
   const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
-  double x = 0.0, n = 0.0;
+  float x = 0.f, n = 0.f;
   if (P.has) {
     const uint32_t g = __ldg(&aux[P.gp].z);
-    x = (double)g / (double)__ldg(weight + P.gp);
-    n = 1.0;
+    x = (float)g / __ldg(weight + P.gp);
+    n = 1.f;
   }
-  const double s0 = warp_sum_d(n), s1 = warp_sum_d(x), s2 = warp_sum_d(x * x);
-  if (lane == 0) {
-    double* A = acc + 3 * P.view;
-    atomicAdd(A + 0, s0);
-    atomicAdd(A + 1, s1);
-    atomicAdd(A + 2, s2);
-  }
+  const float s0 = warp_sum(n), s1 = warp_sum(x), s2 = warp_sum(x * x);
+  if (lane == 0) partial[c] = make_float4(s0, s1, s2, 0.f);
 }
 
 __global__ void k_gc_final(uint32_t n_views, const double* __restrict__ acc, float* __restrict__ out,
@@ -303,20 +327,25 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
                               const void* chunks, const void* act_tiles, const uint32_t* px_list,
                               const uint8_t* flags, const float* out8, const float* depth,
                               const void* aux, const float* target, float lambda_ban, float* scratch,
-                              double* acc, float* loss, float* dout8, int32_t* status, void* stream) {
+                              double* acc, float* chunk_scratch, float* loss, float* dout8, int32_t* status,
+                              void* stream) {
   (void)aux;
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status || !acc || !loss) return PGSAG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 4 * sizeof(double), s));
   if (n_chunks) {
-    if (!chunks || !act_tiles || !px_list || !flags || !out8 || !depth || !target || !scratch || !dout8)
+    if (!chunks || !act_tiles || !px_list || !flags || !out8 || !depth || !target || !scratch || !dout8 ||
+        !chunk_scratch)
       return PGSAG_ERR_ARG;
-    if (((uintptr_t)out8 | (uintptr_t)dout8 | (uintptr_t)act_tiles) & 15u) return PGSAG_ERR_ARG;
+    if (((uintptr_t)out8 | (uintptr_t)dout8 | (uintptr_t)act_tiles | (uintptr_t)chunk_scratch) & 15u)
+      return PGSAG_ERR_ARG;
     const unsigned blocks = pgsag_div_up(n_chunks, kLossThreads / 32);
     k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
-                                             px_list, flags, (const float4*)out8, depth, target, scratch, acc,
-                                             (float4*)dout8, status);
+                                             px_list, flags, (const float4*)out8, depth, target, scratch,
+                                             (float4*)chunk_scratch, (float4*)dout8, status);
+    PGSAG_CHECK_LAUNCH();
+    k_view_reduce<<<n_views, 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 4, acc, status);
     PGSAG_CHECK_LAUNCH();
     k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
                                              px_list, flags, (const float4*)out8, depth, scratch, acc,
@@ -332,7 +361,7 @@ extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint3
                                 const void* ranges, uint32_t n_chunks, const void* chunks,
                                 const void* act_tiles, const uint32_t* px_list, const void* aux,
                                 const float* gc_weight, uint32_t* tile_counts, double* acc,
-                                float* gc_load, int32_t* status, void* stream) {
+                                float* chunk_scratch, float* gc_load, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status || !acc || !gc_load) return PGSAG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -344,10 +373,13 @@ extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint3
     PGSAG_CHECK_LAUNCH();
   }
   if (n_chunks) {
-    if (!chunks || !act_tiles || !px_list || !aux || !gc_weight) return PGSAG_ERR_ARG;
+    if (!chunks || !act_tiles || !px_list || !aux || !gc_weight || !chunk_scratch) return PGSAG_ERR_ARG;
+    if (((uintptr_t)chunk_scratch | (uintptr_t)aux) & 15u) return PGSAG_ERR_ARG;
     k_gc_accum<<<pgsag_div_up(n_chunks, kLossThreads / 32), kLossThreads, 0, s>>>(
         views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles, px_list, (const uint4*)aux, gc_weight,
-        acc, status);
+        (float4*)chunk_scratch, status);
+    PGSAG_CHECK_LAUNCH();
+    k_view_reduce<<<n_views, 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 3, acc, status);
     PGSAG_CHECK_LAUNCH();
   }
   k_gc_final<<<pgsag_div_up(n_views, 128), 128, 0, s>>>(n_views, acc, gc_load, status);

@@ -129,7 +129,7 @@ class Plan:
             m = m if torch.is_tensor(m) else torch.from_numpy(np.ascontiguousarray(m, np.uint8))
             m = m.to(dev, torch.uint8).contiguous()
             L.check(self.lib.pgsag_prep_flags(ctypes.byref(views[v]), _ptr(m), _ptr(self.flags), _ptr(self.tile_npix),
-                                              _ptr(totals[v]), s), "pgsag_prep_flags")
+                                                  _ptr(totals[v]), s), "pgsag_prep_flags")
         tot = totals.cpu().numpy().astype(np.int64)
         self.n_active_v = tot[:, 0].copy()
         self.n_render_v = tot[:, 1].copy()
@@ -149,10 +149,12 @@ class Plan:
             views[v].act_base = act_base
             views[v].n_active = int(self.n_active_v[v])
             views[v].n_mask = int(self.n_mask_v[v])
+            views[v].chunk_base = chunk_base
+            views[v].n_chunks = int(self.n_chunks_v[v])
             L.check(self.lib.pgsag_prep_lists(ctypes.byref(views[v]), v, _ptr(self.flags), _ptr(self.tile_npix),
-                                              px_base, chunk_base, _ptr(self.tile_act), _ptr(self.sat),
-                                              _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.chunks), s),
-                    "pgsag_prep_lists")
+                                                  px_base, chunk_base, _ptr(self.tile_act), _ptr(self.sat),
+                                                  _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.chunks), s),
+                        "pgsag_prep_lists")
             act_base += int(self.n_active_v[v])
             px_base += int(self.n_render_v[v])
             chunk_base += int(self.n_chunks_v[v])
@@ -165,7 +167,7 @@ class Plan:
             pb = int(views[v].pix_base)
             self.target[3 * pb:3 * (pb + H * W)].copy_(tg.reshape(-1).to(dev, f32))
             L.check(self.lib.pgsag_prep_gc_weight(ctypes.byref(views[v]), _ptr(self.target), _ptr(self.gc_weight), s),
-                    "pgsag_prep_gc_weight")
+                        "pgsag_prep_gc_weight")
         raw = bytes(views)
         self.views_dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
 
@@ -188,11 +190,13 @@ class Plan:
         self.status = torch.zeros(1, dtype=i32, device=dev)
         self.acc_loss = torch.zeros(4 * V, dtype=torch.float64, device=dev)
         self.acc_gc = torch.zeros(3 * V, dtype=torch.float64, device=dev)
+        self.chunk_scratch = torch.zeros((max(self.n_chunks, 1), 4), dtype=f32, device=dev)
         self.gc_load = torch.zeros(V, dtype=f32, device=dev)
         self.loss_buf = torch.zeros(3 * V + 1, dtype=f32, device=dev)
         self.sched = None
         self.sched_order = None
         self.sched_counter = torch.zeros(1, dtype=i32, device=dev)
+        self.stage_events = None  # list -> (name, start event, end event) per step call
         self._auto_capacity = capacity is None
         self._alloc_capacity(int(capacity) if capacity is not None else max(4 * self.n_pairs, 1 << 16))
 
@@ -203,9 +207,9 @@ class Plan:
         nbytes = int(self.lib.pgsag_bin_workspace_size(self.n_pairs, self.capacity))
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
 
-    def use_persistent_schedule(self, ctas_per_sm: int = 8, order: Optional[torch.Tensor] = None):
-        """Render with a persistent grid pulling chunks from a device work counter,
-        optionally in the given chunk order."""
+    def use_persistent_schedule(self, ctas_per_sm: int = 4, order: Optional[torch.Tensor] = None):
+        """Render with a persistent grid pulling active tiles from a device work
+        counter, optionally in the given tile order."""
         self.sched_order = order
         self.sched = L.PgsagSched(order.data_ptr() if order is not None else None, self.sched_counter.data_ptr(),
                                   int(ctas_per_sm), 0)
@@ -218,6 +222,40 @@ class Plan:
         return ctypes.byref(self.sched) if self.sched is not None else None
 
     # ------------------------------------------------------------------ step calls
+    def _ev(self, name):
+        """Record CUDA events around a step call on the current stream when
+        stage_events is a list (profiling); a no-op otherwise."""
+        plan = self
+
+        class _Ctx:
+            def __enter__(self_):
+                if plan.stage_events is not None:
+                    self_.a = torch.cuda.Event(enable_timing=True)
+                    self_.a.record()
+
+            def __exit__(self_, *exc):
+                if plan.stage_events is not None:
+                    b = torch.cuda.Event(enable_timing=True)
+                    b.record()
+                    plan.stage_events.append((name, self_.a, b))
+        return _Ctx()
+
+    def kernel_launches_per_step(self, with_stats=True) -> int:
+        """Number of library kernels one render + loss + backward step launches."""
+        tile_passes = 0
+        if self.n_active > 1:
+            tile_passes = (int(self.n_active - 1).bit_length() + 7) // 8
+        n = 1  # preprocess
+        if self.n_pairs:
+            n += 4 * 3 + 3 + 3 * tile_passes + (1 if self.n_active else 0)
+        n += 1 if self.n_active else 0          # render_fwd
+        n += (3 if self.n_chunks else 0) + 1    # loss
+        if with_stats:
+            n += (1 if self.n_active else 0) + (2 if self.n_chunks else 0) + 1
+        n += 1 if self.n_active else 0          # render_bwd
+        n += 1 if self.n_gauss else 0           # preprocess_bwd
+        return n
+
     def status_value(self) -> int:
         return int(self.status.item())
 
@@ -226,60 +264,67 @@ class Plan:
 
     def preprocess(self, P: GaussianParams, stream=None):
         s = _stream_ptr(stream)
-        L.check(self.lib.pgsag_preprocess(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats), _ptr(P.opacity_logit),
-                                          _ptr(P.sh), self.n_views, _ptr(self.views_dev), _ptr(self.tile_act),
-                                          _ptr(self.sat), _ptr(self.rec), _ptr(self.dkey), _ptr(self.bininfo),
-                                          _ptr(self.status), s), "pgsag_preprocess")
+        with self._ev('preprocess'):
+            L.check(self.lib.pgsag_preprocess(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats), _ptr(P.opacity_logit),
+                                              _ptr(P.sh), self.n_views, _ptr(self.views_dev), _ptr(self.tile_act),
+                                              _ptr(self.sat), _ptr(self.rec), _ptr(self.dkey), _ptr(self.bininfo),
+                                              _ptr(self.status), s), "pgsag_preprocess")
 
     def bin(self, stream=None):
         s = _stream_ptr(stream)
-        L.check(self.lib.pgsag_bin(self.n_pairs, self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.tile_act),
-                                   _ptr(self.bininfo), _ptr(self.dkey), self.capacity, _ptr(self.ws), self.ws.numel(),
-                                   _ptr(self.dup_pairs), _ptr(self.ranges), _ptr(self.k_out), _ptr(self.status), s),
-                "pgsag_bin")
+        with self._ev('bin'):
+            L.check(self.lib.pgsag_bin(self.n_pairs, self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.tile_act),
+                                       _ptr(self.bininfo), _ptr(self.dkey), self.capacity, _ptr(self.ws), self.ws.numel(),
+                                       _ptr(self.dup_pairs), _ptr(self.ranges), _ptr(self.k_out), _ptr(self.status), s),
+                    "pgsag_bin")
 
     def render_fwd(self, stream=None):
         s = _stream_ptr(stream)
-        L.check(self.lib.pgsag_render_fwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
-                                          _ptr(self.ranges), _ptr(self.act_tiles), self.n_chunks, _ptr(self.chunks),
-                                          _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.depth),
-                                          _ptr(self.aux), _ptr(self.status), s), "pgsag_render_fwd")
+        with self._ev('render_fwd'):
+            L.check(self.lib.pgsag_render_fwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
+                                              _ptr(self.ranges), _ptr(self.act_tiles), self.n_active,
+                                              _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.depth),
+                                              _ptr(self.aux), _ptr(self.status), s), "pgsag_render_fwd")
 
     def loss(self, lambda_ban=LAMBDA_BAN, loss_out: Optional[torch.Tensor] = None, stream=None):
         s = _stream_ptr(stream)
         out = self.loss_buf if loss_out is None else loss_out
-        L.check(self.lib.pgsag_loss_ban(self.n_views, _ptr(self.views_dev), self.n_chunks, _ptr(self.chunks),
-                                        _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags), _ptr(self.out8),
-                                        _ptr(self.depth), _ptr(self.aux), _ptr(self.target), float(lambda_ban),
-                                        _ptr(self.scratch), _ptr(self.acc_loss), _ptr(out), _ptr(self.dout8),
-                                        _ptr(self.status), s), "pgsag_loss_ban")
+        with self._ev('loss'):
+            L.check(self.lib.pgsag_loss_ban(self.n_views, _ptr(self.views_dev), self.n_chunks, _ptr(self.chunks),
+                                            _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags), _ptr(self.out8),
+                                            _ptr(self.depth), _ptr(self.aux), _ptr(self.target), float(lambda_ban),
+                                            _ptr(self.scratch), _ptr(self.acc_loss), _ptr(self.chunk_scratch), _ptr(out), _ptr(self.dout8),
+                                            _ptr(self.status), s), "pgsag_loss_ban")
         return out
 
     def tile_stats(self, stream=None):
         s = _stream_ptr(stream)
-        L.check(self.lib.pgsag_tile_stats(self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.ranges),
-                                          self.n_chunks, _ptr(self.chunks), _ptr(self.act_tiles), _ptr(self.px_list),
-                                          _ptr(self.aux), _ptr(self.gc_weight), _ptr(self.tile_counts),
-                                          _ptr(self.acc_gc), _ptr(self.gc_load), _ptr(self.status), s),
-                "pgsag_tile_stats")
+        with self._ev('tile_stats'):
+            L.check(self.lib.pgsag_tile_stats(self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.ranges),
+                                              self.n_chunks, _ptr(self.chunks), _ptr(self.act_tiles), _ptr(self.px_list),
+                                              _ptr(self.aux), _ptr(self.gc_weight), _ptr(self.tile_counts),
+                                              _ptr(self.acc_gc), _ptr(self.chunk_scratch), _ptr(self.gc_load), _ptr(self.status), s),
+                    "pgsag_tile_stats")
 
     def render_bwd(self, dout8: torch.Tensor, ddepth: Optional[torch.Tensor] = None,
                    dout_scale: Optional[torch.Tensor] = None, stream=None):
         s = _stream_ptr(stream)
-        L.check(self.lib.pgsag_render_bwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
-                                          _ptr(self.ranges), _ptr(self.act_tiles), self.n_chunks, _ptr(self.chunks),
-                                          _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.aux),
-                                          _ptr(dout8), _ptr(ddepth), _ptr(dout_scale), self.n_pairs, _ptr(self.grad2d),
-                                          _ptr(self.status), s), "pgsag_render_bwd")
+        with self._ev('render_bwd'):
+            L.check(self.lib.pgsag_render_bwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
+                                              _ptr(self.ranges), _ptr(self.act_tiles), self.n_active,
+                                              _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.aux),
+                                              _ptr(dout8), _ptr(ddepth), _ptr(dout_scale), self.n_pairs, _ptr(self.grad2d),
+                                              _ptr(self.status), s), "pgsag_render_bwd")
 
     def preprocess_bwd(self, P: GaussianParams, grads: Sequence[torch.Tensor], accumulate=False, stream=None):
         s = _stream_ptr(stream)
         gm, gl, gq, go, gs = grads
-        L.check(self.lib.pgsag_preprocess_bwd(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats),
-                                              _ptr(P.opacity_logit), _ptr(P.sh), self.n_views, _ptr(self.views_dev),
-                                              _ptr(self.bininfo), _ptr(self.grad2d), 1 if accumulate else 0, _ptr(gm),
-                                              _ptr(gl), _ptr(gq), _ptr(go), _ptr(gs), _ptr(self.status), s),
-                "pgsag_preprocess_bwd")
+        with self._ev('preprocess_bwd'):
+            L.check(self.lib.pgsag_preprocess_bwd(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats),
+                                                  _ptr(P.opacity_logit), _ptr(P.sh), self.n_views, _ptr(self.views_dev),
+                                                  _ptr(self.bininfo), _ptr(self.grad2d), 1 if accumulate else 0, _ptr(gm),
+                                                  _ptr(gl), _ptr(gq), _ptr(go), _ptr(gs), _ptr(self.status), s),
+                    "pgsag_preprocess_bwd")
 
     def forward(self, P: GaussianParams, check: bool = True, stream=None):
         """preprocess -> bin -> render_fwd.  With check=True (or while the capacity

@@ -412,3 +412,26 @@ def tiny_scene(seed, n=48, width=32, height=32, fx=40.0, coverage=0.5, zmin=3.0,
     cam = identity_camera(width, height, fx)
     mask = rect_mask(r2, height, width, coverage, 0.1, nmin=1, nmax=3)
     return g, View(cam, mask, random_target(r3, height, width))
+
+
+def crop_view(view: View, x0: int, y0: int, w: int, h: int) -> View:
+    """The w x h window at (x0, y0) of a view, as a view of its own: the same
+    camera with the principal point shifted by the window origin."""
+    c = view.cam
+    cam = Camera(c.R, c.t, c.fx, c.fy, c.cx - x0, c.cy - y0, w, h, c.znear)
+    return View(cam, np.ascontiguousarray(view.mask[y0:y0 + h, x0:x0 + w]),
+                np.ascontiguousarray(view.target[y0:y0 + h, x0:x0 + w]))
+
+
+def densest_window(mask: np.ndarray, w: int, h: int, step: int = 64):
+    """Top-left corner of the w x h window (on a `step` grid) with the most mask pixels."""
+    H, W = mask.shape
+    S = np.zeros((H + 1, W + 1), np.int64)
+    S[1:, 1:] = np.cumsum(np.cumsum(mask.astype(np.int64), 0), 1)
+    best, arg = -1, (0, 0)
+    for y in range(0, max(1, H - h + 1), step):
+        for x in range(0, max(1, W - w + 1), step):
+            c = S[y + h, x + w] - S[y, x + w] - S[y + h, x] + S[y, x]
+            if c > best:
+                best, arg = c, (x, y)
+    return arg

@@ -35,8 +35,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_view_struct_layout(lib):
-    assert ctypes.sizeof(L.PgsagView) == 144
-    assert b"144" in lib.pgsag_build_info()
+    assert ctypes.sizeof(L.PgsagView) == 152
+    assert b"152" in lib.pgsag_build_info()
 
 
 def test_status_strings(lib):

@@ -193,8 +193,9 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* wei
  *   sh [N,16,3]; views (device, n_views <= PGSAG_MAX_VIEWS); tile_act, sat.
  * Outputs per pair p:
  *   rec [p*16 .. p*16+15] float (16-byte aligned):
- *     {mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz, z, ex, ey}
- *     (ex, ey: half-extents of the alpha >= 1/255 box, 1 px margin included)
+ *     {mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz, thr, ex, ey}
+ *     (thr = -ln(255 o): the pair enters a pixel iff -1/2 d^T Q d >= thr, i.e.
+ *     alpha >= 1/255; ex, ey: half-extents of that region's box, 1 px margin)
  *   depth_key [p]: float bits of z, 0xFFFFFFFF for culled pairs
  *   bininfo [p] uint4: {x0 | y0 << 16, x1 | y1 << 16 (inclusive tile rect),
  *     view index, touched}
@@ -237,7 +238,8 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
  * warp per 32 compacted rendered pixels of the tile; the tile's sorted Gaussians
  * are staged through shared memory in batches of 256 and each warp skips the
  * Gaussians whose alpha >= 1/255 box misses its pixels.  Per pixel, front to back:
- *   alpha = min(0.99, o exp(-1/2 d^T Q d)); skipped if alpha < 1/255; if
+ *   alpha = min(0.99, o exp(-1/2 d^T Q d)); skipped if alpha < 1/255 (tested as
+ *   -1/2 d^T Q d < thr, identically in the forward and the adjoint); if
  *   T (1 - alpha) < 1e-4 the pixel stops before this Gaussian; otherwise
  *   w = alpha T, C += w c, N += w n_c, D += w d, T *= 1 - alpha.
  *   Depth = D / (-N . K^-1 (x+1/2, y+1/2, 1)) if something was blended,

@@ -12,6 +12,7 @@ namespace pgsag {
 
 constexpr int kLossThreads = 256;
 constexpr float kWBoundary = 0.1f;  // Eq. 8: boundary weight
+constexpr int kReduceBlocks = 64;   // blocks per view for the per-view sums
 
 struct PixCtx {
   bool has;
@@ -143,18 +144,21 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
   if (lane == 0) partial[c] = make_float4(s1, s2, s3, 0.f);
 }
 
-// One block per view: sum the per-chunk partials of the view's chunk range in
-// double into acc[stride * v + 0 .. ncomp).
+// Grid (blocks, views): each block sums a slice of the view's per-chunk partials
+// in double and adds it into acc[stride * v + 0 .. ncomp) (acc zeroed before).
 __global__ void __launch_bounds__(256) k_view_reduce(const pgsag_view* __restrict__ views,
                                                      const float4* __restrict__ partial, int ncomp,
                                                      int stride, double* __restrict__ acc,
                                                      const int32_t* status) {
   __shared__ double sh[8][3];
   if (status_bad(status)) return;
-  const pgsag_view* V = views + blockIdx.x;
+  const pgsag_view* V = views + blockIdx.y;
   const uint32_t b = __ldg(&V->chunk_base), n = __ldg(&V->n_chunks);
+  const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
+  if (lo >= hi) return;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const float4 p = __ldg(partial + b + i);
     a0 += p.x;
     a1 += p.y;
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(256) k_view_reduce(const pgsag_view* __restric
   if (threadIdx.x < ncomp) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += sh[w][threadIdx.x];
-    acc[stride * blockIdx.x + threadIdx.x] = t;
+    atomicAdd(acc + stride * blockIdx.y + threadIdx.x, t);
   }
 }
 
@@ -345,7 +349,8 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
                                              px_list, flags, (const float4*)out8, depth, target, scratch,
                                              (float4*)chunk_scratch, (float4*)dout8, status);
     PGSAG_CHECK_LAUNCH();
-    k_view_reduce<<<n_views, 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 4, acc, status);
+    k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 4, acc,
+                                                                status);
     PGSAG_CHECK_LAUNCH();
     k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
                                              px_list, flags, (const float4*)out8, depth, scratch, acc,
@@ -379,7 +384,8 @@ extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint3
         views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles, px_list, (const uint4*)aux, gc_weight,
         (float4*)chunk_scratch, status);
     PGSAG_CHECK_LAUNCH();
-    k_view_reduce<<<n_views, 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 3, acc, status);
+    k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 3, acc,
+                                                                status);
     PGSAG_CHECK_LAUNCH();
   }
   k_gc_final<<<pgsag_div_up(n_views, 128), 128, 0, s>>>(n_views, acc, gc_load, status);

@@ -325,7 +325,7 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
     R4[0] = make_float4(mx, my, P.c * inv, -P.b * inv);
     R4[1] = make_float4(P.a * inv, P.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
     R4[2] = make_float4(fmaxf(col[2], 0.f), P.dist, P.nc[0], P.nc[1]);
-    R4[3] = make_float4(P.nc[2], P.mc[2], ex, ey);
+    R4[3] = make_float4(P.nc[2], -logf(255.f * P.o), ex, ey);
     dkey[p] = __float_as_uint(P.mc[2]);
     bininfo[p] = make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16), vi,
                             touched);

@@ -1,13 +1,13 @@
 // Masked tile rendering, forward (Sec. 3.1 Eq. 1-4) and adjoint.
 //
-// Work item = one active tile, handled by one CTA of 8 warps.  The tile's
-// rendered (mask-dilated) pixels are compacted: warp w takes pixels
-// [32 w, 32 w + 32) of the tile's pixel list (more rounds for tiles larger than
-// 256 pixels), one pixel per lane.  The tile's depth-sorted Gaussians are staged
-// through shared memory in batches of 256 (one 64-byte record per thread,
+// Work item = one active tile, handled by one CTA of 4 warps.  The tile's
+// rendered (mask-dilated) pixels are compacted; each lane takes 2 of them (more
+// rounds for tiles larger than 256 pixels).  The tile's depth-sorted Gaussians
+// are staged through shared memory in batches of 256 (64-byte records,
 // coalesced), then each warp walks the batch, skipping -- as a warp-uniform
 // branch -- every Gaussian whose alpha >= 1/255 box misses the bounding box of
-// the warp's 32 pixels.  The forward stops a batch loop when every warp of the
+// the warp's pixels.  A pair is rejected before the exponential when the
+// exponent is below the Gaussian's threshold -ln(255 o) (alpha < 1/255).  The forward stops a batch loop when every warp of the
 // CTA has terminated (__syncthreads_or).  The adjoint re-walks the list back to
 // front from the CTA's last blended Gaussian, recovers T by division, reduces
 // each Gaussian's 13 gradient values across the warp with 16 shuffles, sums the
@@ -16,9 +16,12 @@
 
 namespace pgsag {
 
-constexpr int kRenderWarps = 8;
+constexpr int kRenderWarps = 4;                   // warps per CTA (one CTA per active tile)
 constexpr int kRenderThreads = kRenderWarps * 32;
-constexpr int kBatch = kRenderThreads;
+constexpr int kPPT = 2;                           // pixels per lane
+constexpr int kTilePix = kRenderThreads * kPPT;   // pixels per CTA round
+constexpr int kBatch = 256;                       // Gaussians staged per batch
+constexpr int kStagePerThread = kBatch / kRenderThreads;
 
 struct TileInfo {
   uint32_t view, px_first, npix, rbeg, rend;
@@ -63,10 +66,42 @@ __device__ __forceinline__ uint32_t next_tile(const Sched& s, uint32_t& iter, ui
   return c;
 }
 
-// Bounding box of the valid lanes' pixel centres (warp-uniform result).
-__device__ __forceinline__ float4 warp_pixel_box(bool has, float px, float py) {
-  float x0 = has ? px : 3.0e38f, x1 = has ? px : -3.0e38f;
-  float y0 = has ? py : 3.0e38f, y1 = has ? py : -3.0e38f;
+// Pixels of lane `lane` in warp `warp` for the round starting at r0: entries
+// r0 + (warp * kPPT + k) * 32 + lane of the tile's compacted pixel list, so a
+// warp covers kPPT consecutive 32-pixel runs.
+struct Pix {
+  bool has[kPPT];
+  uint32_t pix[kPPT];
+  float px[kPPT], py[kPPT];
+};
+
+__device__ __forceinline__ Pix load_pixels(const TileInfo& ti, uint32_t r0, int warp, int lane, int width,
+                                           const uint32_t* __restrict__ px_list) {
+  Pix P;
+#pragma unroll
+  for (int k = 0; k < kPPT; ++k) {
+    const uint32_t li = r0 + (uint32_t)((warp * kPPT + k) * 32 + lane);
+    P.has[k] = li < ti.npix;
+    P.pix[k] = P.has[k] ? __ldg(px_list + ti.px_first + li) : 0u;
+    const uint32_t yy = P.pix[k] / (uint32_t)width;
+    P.px[k] = (float)(P.pix[k] - yy * (uint32_t)width) + 0.5f;
+    P.py[k] = (float)yy + 0.5f;
+  }
+  return P;
+}
+
+// Bounding box of the warp's valid pixel centres (warp-uniform result).
+__device__ __forceinline__ float4 warp_pixel_box(const Pix& P) {
+  float x0 = 3.0e38f, x1 = -3.0e38f, y0 = 3.0e38f, y1 = -3.0e38f;
+#pragma unroll
+  for (int k = 0; k < kPPT; ++k) {
+    if (P.has[k]) {
+      x0 = fminf(x0, P.px[k]);
+      x1 = fmaxf(x1, P.px[k]);
+      y0 = fminf(y0, P.py[k]);
+      y1 = fmaxf(y1, P.py[k]);
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     x0 = fminf(x0, __shfl_xor_sync(kFull, x0, o));
@@ -107,70 +142,92 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
   __shared__ float4 sbox[kBatch];
   __shared__ uint32_t s_item;
   if (status_bad(status)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t iter = 0;
   for (;;) {
     const uint32_t t = next_tile(sched, iter, n_items, &s_item);
     if (t >= n_items) break;
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
-    for (uint32_t r0i = 0; r0i < ti.npix; r0i += kRenderThreads) {
-      const uint32_t li = r0i + threadIdx.x;
-      const bool has = li < ti.npix;
-      const uint32_t pix = has ? __ldg(px_list + ti.px_first + li) : 0u;
-      const uint32_t py_i = pix / (uint32_t)V.width;
-      const float px = (float)(pix - py_i * (uint32_t)V.width) + 0.5f;
-      const float py = (float)py_i + 0.5f;
-      const float4 cbox = warp_pixel_box(has, px, py);
-
-      float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
-      uint32_t last = 0, cnt = 0;
-      bool done = !has;
+    for (uint32_t r0 = 0; r0 < ti.npix; r0 += kTilePix) {
+      const Pix P = load_pixels(ti, r0, warp, lane, V.width, px_list);
+      const float4 cbox = warp_pixel_box(P);
+      float T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT], N0[kPPT], N1[kPPT], N2[kPPT];
+      uint32_t last[kPPT], cnt[kPPT];
+      bool done[kPPT];
+      bool all_done = true;
+#pragma unroll
+      for (int k = 0; k < kPPT; ++k) {
+        T[k] = 1.f;
+        C0[k] = C1[k] = C2[k] = D[k] = N0[k] = N1[k] = N2[k] = 0.f;
+        last[k] = 0;
+        cnt[k] = 0;
+        done[k] = !P.has[k];
+        all_done = all_done && done[k];
+      }
       for (uint32_t base = ti.rbeg; base < ti.rend; base += kBatch) {
-        if (!__syncthreads_or(!done)) break;
+        if (!__syncthreads_or(!all_done)) break;
         const uint32_t nb = min((uint32_t)kBatch, ti.rend - base);
-        if (threadIdx.x < nb) stage(base + threadIdx.x, threadIdx.x, dup_pairs, rec, srec, sbox, nullptr);
+#pragma unroll
+        for (int u = 0; u < kStagePerThread; ++u) {
+          const uint32_t slot = threadIdx.x + u * kRenderThreads;
+          if (slot < nb) stage(base + slot, slot, dup_pairs, rec, srec, sbox, nullptr);
+        }
         __syncthreads();
-        if (!done) {
+        if (!all_done) {
           for (uint32_t j = 0; j < nb; ++j) {
             if (box_miss(sbox[j], cbox)) continue;
             const float4 q0 = srec[j][0];
             const float4 q1 = srec[j][1];
-            float dx, dy;
-            const float pw = gauss_power(px, py, q0, q1.x, dx, dy);
-            const float raw = __fmul_rn(q1.y, __expf(pw));
-            if (raw < kAlphaMin) continue;
-            const float alpha = fminf(raw, kAlphaMax);
-            const float test = __fmul_rn(T, __fsub_rn(1.f, alpha));
-            if (test < kTMin) {
-              done = true;
+            const float thr = srec[j][3].y;
+#pragma unroll
+            for (int k = 0; k < kPPT; ++k) {
+              if (done[k]) continue;
+              float dx, dy;
+              const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy);
+              if (!(pw >= thr)) continue;  // alpha < 1/255
+              const float alpha = fminf(__fmul_rn(q1.y, __expf(pw)), kAlphaMax);
+              const float test = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+              if (test < kTMin) {
+                done[k] = true;
+                continue;
+              }
+              const float4 q2 = srec[j][2];
+              const float nz = srec[j][3].x;
+              const float w = __fmul_rn(alpha, T[k]);
+              C0[k] = fmaf(w, q1.z, C0[k]);
+              C1[k] = fmaf(w, q1.w, C1[k]);
+              C2[k] = fmaf(w, q2.x, C2[k]);
+              D[k] = fmaf(w, q2.y, D[k]);
+              N0[k] = fmaf(w, q2.z, N0[k]);
+              N1[k] = fmaf(w, q2.w, N1[k]);
+              N2[k] = fmaf(w, nz, N2[k]);
+              T[k] = test;
+              last[k] = base + j;
+              ++cnt[k];
+            }
+            bool ad = true;
+#pragma unroll
+            for (int k = 0; k < kPPT; ++k) ad = ad && done[k];
+            if (ad) {
+              all_done = true;
               break;
             }
-            const float4 q2 = srec[j][2];
-            const float4 q3 = srec[j][3];
-            const float w = __fmul_rn(alpha, T);
-            C0 = fmaf(w, q1.z, C0);
-            C1 = fmaf(w, q1.w, C1);
-            C2 = fmaf(w, q2.x, C2);
-            D = fmaf(w, q2.y, D);
-            N0 = fmaf(w, q2.z, N0);
-            N1 = fmaf(w, q2.w, N1);
-            N2 = fmaf(w, q3.x, N2);
-            T = test;
-            last = base + j;
-            ++cnt;
           }
         }
       }
-      if (has) {
-        const uint64_t gp = V.pix_base + pix;
-        out8[2 * gp + 0] = make_float4(C0, C1, C2, D);
-        out8[2 * gp + 1] = make_float4(N0, N1, N2, 1.f - T);
+#pragma unroll
+      for (int k = 0; k < kPPT; ++k) {
+        if (!P.has[k]) continue;
+        const uint64_t gp = V.pix_base + P.pix[k];
+        out8[2 * gp + 0] = make_float4(C0[k], C1[k], C2[k], D[k]);
+        out8[2 * gp + 1] = make_float4(N0[k], N1[k], N2[k], 1.f - T[k]);
         // Eq. 4: ray-plane depth
-        const float rx = (px - V.cx) / V.fx, ry = (py - V.cy) / V.fy;
-        const float sdot = -(N0 * rx + N1 * ry + N2);
-        const bool valid = cnt > 0 && sdot > kRayDotMin && D > 0.f;
-        depth[gp] = valid ? D / sdot : 0.f;
-        aux[gp] = make_uint4(__float_as_uint(T), last, cnt, 0u);
+        const float rx = (P.px[k] - V.cx) / V.fx, ry = (P.py[k] - V.cy) / V.fy;
+        const float sdot = -(N0[k] * rx + N1[k] * ry + N2[k]);
+        const bool valid = cnt[k] > 0 && sdot > kRayDotMin && D[k] > 0.f;
+        depth[gp] = valid ? D[k] / sdot : 0.f;
+        aux[gp] = make_uint4(__float_as_uint(T[k]), last[k], cnt[k], 0u);
       }
     }
   }
@@ -219,6 +276,15 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float v[16], int la
   return a1 + __shfl_xor_sync(kFull, a1, 1);
 }
 
+// Per-pixel adjoint state.
+struct BwdPix {
+  float T, Tfin;
+  int last;
+  float dC0, dC1, dC2, dD, dN0, dN1, dN2, dA;
+  float SC0, SC1, SC2, SN0, SN1, SN2, SD;                  // suffix sums behind the current Gaussian
+  float pa, pc0, pc1, pc2, pn0, pn1, pn2, pd;              // previous (next in front-to-back order)
+};
+
 __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
     const pgsag_view* __restrict__ views, const float4* __restrict__ rec,
     const uint32_t* __restrict__ dup_pairs, const uint2* __restrict__ ranges,
@@ -233,60 +299,62 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
   __shared__ uint32_t s_item;
   __shared__ int s_max;
   if (status_bad(status)) return;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float gscale = dout_scale ? __ldg(dout_scale) : 1.f;
-  sacc[threadIdx.x][0] = sacc[threadIdx.x][1] = sacc[threadIdx.x][2] = sacc[threadIdx.x][3] =
-      make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = threadIdx.x; i < kBatch; i += kRenderThreads)
+    sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t iter = 0;
   for (;;) {
     const uint32_t t = next_tile(sched, iter, n_items, &s_item);
     if (t >= n_items) break;
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
-    for (uint32_t r0i = 0; r0i < ti.npix; r0i += kRenderThreads) {
-      const uint32_t li = r0i + threadIdx.x;
-      const bool has = li < ti.npix;
-      const uint32_t pix = has ? __ldg(px_list + ti.px_first + li) : 0u;
-      const uint32_t py_i = pix / (uint32_t)V.width;
-      const float px = (float)(pix - py_i * (uint32_t)V.width) + 0.5f;
-      const float py = (float)py_i + 0.5f;
-      const uint64_t gp = V.pix_base + pix;
-      const float4 cbox = warp_pixel_box(has, px, py);
-
-      float T = 1.f, Tfin = 1.f;
+    for (uint32_t r0 = 0; r0 < ti.npix; r0 += kTilePix) {
+      const Pix P = load_pixels(ti, r0, warp, lane, V.width, px_list);
+      const float4 cbox = warp_pixel_box(P);
+      BwdPix B[kPPT];
       int lane_last = -1;
-      float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, dN0 = 0.f, dN1 = 0.f, dN2 = 0.f, dA = 0.f;
-      if (has) {
+#pragma unroll
+      for (int k = 0; k < kPPT; ++k) {
+        BwdPix& b = B[k];
+        b.T = b.Tfin = 1.f;
+        b.last = -1;
+        b.dC0 = b.dC1 = b.dC2 = b.dD = b.dN0 = b.dN1 = b.dN2 = b.dA = 0.f;
+        b.SC0 = b.SC1 = b.SC2 = b.SN0 = b.SN1 = b.SN2 = b.SD = 0.f;
+        b.pa = b.pc0 = b.pc1 = b.pc2 = b.pn0 = b.pn1 = b.pn2 = b.pd = 0.f;
+        if (!P.has[k]) continue;
+        const uint64_t gp = V.pix_base + P.pix[k];
         const uint4 ax = __ldg(aux + gp);
-        Tfin = __uint_as_float(ax.x);
-        T = Tfin;
-        lane_last = ax.z > 0 ? (int)ax.y : -1;
+        b.Tfin = __uint_as_float(ax.x);
+        b.T = b.Tfin;
+        b.last = ax.z > 0 ? (int)ax.y : -1;
         const float4 g0 = __ldg(dout8 + 2 * gp), g1 = __ldg(dout8 + 2 * gp + 1);
-        dC0 = gscale * g0.x;
-        dC1 = gscale * g0.y;
-        dC2 = gscale * g0.z;
-        dD = gscale * g0.w;
-        dN0 = gscale * g1.x;
-        dN1 = gscale * g1.y;
-        dN2 = gscale * g1.z;
-        dA = gscale * g1.w;
+        b.dC0 = gscale * g0.x;
+        b.dC1 = gscale * g0.y;
+        b.dC2 = gscale * g0.z;
+        b.dD = gscale * g0.w;
+        b.dN0 = gscale * g1.x;
+        b.dN1 = gscale * g1.y;
+        b.dN2 = gscale * g1.z;
+        b.dA = gscale * g1.w;
         if (ddepth != nullptr && ax.z > 0) {
           // Eq. 4: Depth = D / s, s = -N . r
           const float gd = gscale * __ldg(ddepth + gp);
           if (gd != 0.f) {
             const float4 o0 = __ldg(out8 + 2 * gp), o1 = __ldg(out8 + 2 * gp + 1);
-            const float rx = (px - V.cx) / V.fx, ry = (py - V.cy) / V.fy;
+            const float rx = (P.px[k] - V.cx) / V.fx, ry = (P.py[k] - V.cy) / V.fy;
             const float sdot = -(o1.x * rx + o1.y * ry + o1.z);
             if (sdot > kRayDotMin && o0.w > 0.f) {
               const float is = 1.f / sdot;
-              dD += gd * is;
-              const float k = gd * o0.w * is * is;
-              dN0 += k * rx;
-              dN1 += k * ry;
-              dN2 += k;
+              b.dD += gd * is;
+              const float kk = gd * o0.w * is * is;
+              b.dN0 += kk * rx;
+              b.dN1 += kk * ry;
+              b.dN2 += kk;
             }
           }
         }
+        lane_last = max(lane_last, b.last);
       }
       const int warp_last = warp_max_i(lane_last);
       if (threadIdx.x == 0) s_max = -1;
@@ -295,73 +363,79 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
       __syncthreads();
       const int cta_last = s_max;
       __syncthreads();
-      // suffix accumulators (colour, normal, distance behind the current Gaussian)
-      float SC0 = 0.f, SC1 = 0.f, SC2 = 0.f, SN0 = 0.f, SN1 = 0.f, SN2 = 0.f, SD = 0.f;
-      float pa = 0.f, pc0 = 0.f, pc1 = 0.f, pc2 = 0.f, pn0 = 0.f, pn1 = 0.f, pn2 = 0.f, pd = 0.f;
       for (int hi = cta_last; hi >= (int)ti.rbeg; hi -= kBatch) {
         const int lo = max((int)ti.rbeg, hi - kBatch + 1);
         const int nb = hi - lo + 1;
-        if ((int)threadIdx.x < nb) stage(lo + threadIdx.x, threadIdx.x, dup_pairs, rec, srec, sbox, spair);
+#pragma unroll
+        for (int u = 0; u < kStagePerThread; ++u) {
+          const int slot = threadIdx.x + u * kRenderThreads;
+          if (slot < nb) stage(lo + slot, slot, dup_pairs, rec, srec, sbox, spair);
+        }
         __syncthreads();
         const int jtop = min(nb - 1, warp_last - lo);
         for (int j = jtop; j >= 0; --j) {
           if (box_miss(sbox[j], cbox)) continue;
           const int idx = lo + j;
+          const float4 q0 = srec[j][0];
+          const float4 q1 = srec[j][1];
+          const float thr = srec[j][3].y;
           float g[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) g[k] = 0.f;
           bool contrib = false;
-          if (idx <= lane_last) {
-            const float4 q0 = srec[j][0];
-            const float4 q1 = srec[j][1];
+#pragma unroll
+          for (int k = 0; k < kPPT; ++k) {
+            BwdPix& b = B[k];
+            if (idx > b.last) continue;
             float dx, dy;
-            const float pw = gauss_power(px, py, q0, q1.x, dx, dy);
+            const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy);
+            if (!(pw >= thr)) continue;  // alpha < 1/255: not blended
+            contrib = true;
+            const float4 q2 = srec[j][2];
+            const float n2 = srec[j][3].x;
             const float G = __expf(pw);
             const float raw = __fmul_rn(q1.y, G);
-            if (raw >= kAlphaMin) {
-              contrib = true;
-              const float4 q2 = srec[j][2];
-              const float4 q3 = srec[j][3];
-              const float alpha = fminf(raw, kAlphaMax);
-              const float oma = 1.f - alpha;
-              T = T / oma;  // transmittance in front of this Gaussian
-              const float w = alpha * T;
-              // S_i = a_{i+1} x_{i+1} + (1 - a_{i+1}) S_{i+1}
-              SC0 = pa * pc0 + (1.f - pa) * SC0;
-              SC1 = pa * pc1 + (1.f - pa) * SC1;
-              SC2 = pa * pc2 + (1.f - pa) * SC2;
-              SN0 = pa * pn0 + (1.f - pa) * SN0;
-              SN1 = pa * pn1 + (1.f - pa) * SN1;
-              SN2 = pa * pn2 + (1.f - pa) * SN2;
-              SD = pa * pd + (1.f - pa) * SD;
-              const float c0 = q1.z, c1 = q1.w, c2 = q2.x, d = q2.y, n0 = q2.z, n1 = q2.w, n2 = q3.x;
-              float dalpha = T * ((c0 - SC0) * dC0 + (c1 - SC1) * dC1 + (c2 - SC2) * dC2 + (d - SD) * dD +
-                                  (n0 - SN0) * dN0 + (n1 - SN1) * dN1 + (n2 - SN2) * dN2);
-              dalpha += dA * Tfin / oma;
-              pa = alpha;
-              pc0 = c0;
-              pc1 = c1;
-              pc2 = c2;
-              pd = d;
-              pn0 = n0;
-              pn1 = n1;
-              pn2 = n2;
-              g[6] = w * dC0;
-              g[7] = w * dC1;
-              g[8] = w * dC2;
-              g[9] = w * dD;
-              g[10] = w * dN0;
-              g[11] = w * dN1;
-              g[12] = w * dN2;
-              if (raw < kAlphaMax) {
-                g[5] = dalpha * G;                // d alpha / d o
-                const float dp = dalpha * alpha;  // d alpha / d power
-                g[0] = dp * (q0.z * dx + q0.w * dy);
-                g[1] = dp * (q0.w * dx + q1.x * dy);
-                g[2] = -0.5f * dp * dx * dx;
-                g[3] = -dp * dx * dy;
-                g[4] = -0.5f * dp * dy * dy;
-              }
+            const float alpha = fminf(raw, kAlphaMax);
+            const float oma = 1.f - alpha;
+            b.T = b.T / oma;  // transmittance in front of this Gaussian
+            const float w = alpha * b.T;
+            // S_i = a_{i+1} x_{i+1} + (1 - a_{i+1}) S_{i+1}
+            const float om = 1.f - b.pa;
+            b.SC0 = b.pa * b.pc0 + om * b.SC0;
+            b.SC1 = b.pa * b.pc1 + om * b.SC1;
+            b.SC2 = b.pa * b.pc2 + om * b.SC2;
+            b.SN0 = b.pa * b.pn0 + om * b.SN0;
+            b.SN1 = b.pa * b.pn1 + om * b.SN1;
+            b.SN2 = b.pa * b.pn2 + om * b.SN2;
+            b.SD = b.pa * b.pd + om * b.SD;
+            const float c0 = q1.z, c1 = q1.w, c2 = q2.x, d = q2.y, n0 = q2.z, n1 = q2.w;
+            float dalpha = b.T * ((c0 - b.SC0) * b.dC0 + (c1 - b.SC1) * b.dC1 + (c2 - b.SC2) * b.dC2 +
+                                  (d - b.SD) * b.dD + (n0 - b.SN0) * b.dN0 + (n1 - b.SN1) * b.dN1 +
+                                  (n2 - b.SN2) * b.dN2);
+            dalpha += b.dA * b.Tfin / oma;
+            b.pa = alpha;
+            b.pc0 = c0;
+            b.pc1 = c1;
+            b.pc2 = c2;
+            b.pd = d;
+            b.pn0 = n0;
+            b.pn1 = n1;
+            b.pn2 = n2;
+            g[6] += w * b.dC0;
+            g[7] += w * b.dC1;
+            g[8] += w * b.dC2;
+            g[9] += w * b.dD;
+            g[10] += w * b.dN0;
+            g[11] += w * b.dN1;
+            g[12] += w * b.dN2;
+            if (raw < kAlphaMax) {
+              g[5] += dalpha * G;                // d alpha / d o
+              const float dp = dalpha * alpha;   // d alpha / d power
+              g[0] += dp * (q0.z * dx + q0.w * dy);
+              g[1] += dp * (q0.w * dx + q1.x * dy);
+              g[2] -= 0.5f * dp * dx * dx;
+              g[3] -= dp * dx * dy;
+              g[4] -= 0.5f * dp * dy * dy;
             }
           }
           if (__any_sync(kFull, contrib)) {
@@ -372,14 +446,18 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
         }
         __syncthreads();
         // one float4 atomic per 4 gradient values per Gaussian for the whole tile
-        if ((int)threadIdx.x < nb) {
-          float* gdst = grad2d + 16ull * spair[threadIdx.x];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 a = sacc[threadIdx.x][q];
-            if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f) {
-              atomicAdd(reinterpret_cast<float4*>(gdst) + q, a);
-              sacc[threadIdx.x][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < kStagePerThread; ++u) {
+          const int slot = threadIdx.x + u * kRenderThreads;
+          if (slot < nb) {
+            float* gdst = grad2d + 16ull * spair[slot];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 a = sacc[slot][q];
+              if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f) {
+                atomicAdd(reinterpret_cast<float4*>(gdst) + q, a);
+                sacc[slot][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+              }
             }
           }
         }

@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="aerial", choices=["aerial", "aerial-crop2048"],
+                    help="aerial: the 5472x3648 view; aerial-crop2048: its 2048x2048 window with the most "
+                         "mask pixels, all 1.5M Gaussians (a smaller case for profiler captures)")
     return ap.parse_args()
 
 
@@ -112,9 +115,12 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------- workload
 
-def workload():
+def workload(name="aerial"):
     import pgsag_synth as syn
     g, views, boxes = syn.config1()
+    if name == "aerial-crop2048":
+        x0, y0 = syn.densest_window(views[0].mask, 2048, 2048, step=256)
+        views = [syn.crop_view(views[0], x0, y0, 2048, 2048)]
     return g, views
 
 
@@ -199,7 +205,7 @@ def ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     tw, th = (int(x) for x in args.tile.split("x"))
-    g, views = workload()
+    g, views = workload(args.workload)
     v = views[0]
     P = raster.GaussianParams.from_numpy(g, requires_grad=True)
     plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, tile=(tw, th))
@@ -304,7 +310,7 @@ def ours(args):
              "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / pk["hbm_gbs"]}
 
     cpu = None
-    if not args.no_cpu_baseline and ws == 1:
+    if not args.no_cpu_baseline and ws == 1 and args.workload == "aerial":
         cv, sample = cpu_crop_sample(views)
         times, cores = run_oracle_steps(g, cv, 2)
         t = min(times)
@@ -315,7 +321,7 @@ def ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "width": v.cam.width, "height": v.cam.height, "n_gaussians": g.n,
+        "config": {"workload": WORKLOAD if args.workload == "aerial" else args.workload, "width": v.cam.width, "height": v.cam.height, "n_gaussians": g.n,
                    "mask_pixels": plan.n_mask, "rendered_pixels": plan.n_render, "active_tiles": plan.n_active,
                    "duplicates_K": K_dup, "tile": args.tile, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (params 354 MB, per-pixel buffers > 2 GB)"},

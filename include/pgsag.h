@@ -188,7 +188,10 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* wei
  *   lowest axis), negated if n_c . mu_c > 0; d = -n_c . mu_c;
  *   tile rectangle = tiles overlapping the axis-aligned box of the alpha >= 1/255
  *   ellipse (half-extents sqrt(2 ln(255 o) Sigma'_xx), ... plus 1 px), and
- *   `touched` = number of ACTIVE tiles in it (from the summed-area table).
+ *   `touched` = number of ACTIVE tiles the pair is binned to: if the rectangle
+ *   spans at most 64 tiles, the active tiles whose pixel centres the ellipse
+ *   meets (exact ellipse-rectangle test, widened by its float32 error bound);
+ *   otherwise every active tile of the rectangle (summed-area table).
  * Inputs: means [N,3], log_scales [N,3], quats [N,4], opacity_logit [N],
  *   sh [N,16,3]; views (device, n_views <= PGSAG_MAX_VIEWS); tile_act, sat.
  * Outputs per pair p:
@@ -210,8 +213,9 @@ int pgsag_preprocess(uint32_t n_gauss, const float* means, const float* log_scal
 
 /*
  * pgsag_bin (Sec. 3.1: projected to tiles, sorted).  Duplicates every visible
- * pair once per active tile of its rectangle and orders each tile's list by
- * (depth key, Gaussian index):
+ * pair once per tile it is binned to (the rule of pgsag_preprocess, reading the
+ * pair's record `rec`) and orders each tile's list by (depth key, Gaussian
+ * index):
  *   1. stable LSD radix sort of all pairs by depth key (pair index order breaks
  *      ties, i.e. ascending Gaussian index within a view);
  *   2. exclusive scan of `touched` in that order -> K (written to *k_out);
@@ -228,7 +232,7 @@ int pgsag_preprocess(uint32_t n_gauss, const float* means, const float* log_scal
  */
 size_t pgsag_bin_workspace_size(uint32_t n_pairs, uint64_t capacity);
 int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
-              uint32_t n_active_total, const int32_t* tile_act, const void* bininfo,
+              uint32_t n_active_total, const int32_t* tile_act, const float* rec, const void* bininfo,
               const uint32_t* depth_key, uint64_t capacity, void* ws, size_t ws_bytes,
               uint32_t* dup_pairs, void* ranges, uint64_t* k_out, int32_t* status,
               void* stream);

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint64_t* __restrict__ p
 __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
     const uint32_t* __restrict__ order, const uint4* __restrict__ bininfo, uint32_t n,
     const uint64_t* __restrict__ partial, const pgsag_view* __restrict__ views,
-    const int32_t* __restrict__ tile_act, uint32_t* __restrict__ keys_out,
+    const int32_t* __restrict__ tile_act, const float4* __restrict__ rec, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int32_t* status) {
   __shared__ uint32_t sh[kScanThreads / 32];
   if (status_bad(status)) return;
@@ -291,13 +291,26 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
       const int tiles_x = __ldg(&V->tiles_x);
       const int32_t* ta = tile_act + __ldg(&V->tile_base);
       const uint32_t x0 = bi.x & 0xffffu, y0 = bi.x >> 16, x1 = bi.y & 0xffffu, y1 = bi.y >> 16;
+      const bool exact = (x1 - x0 + 1) * (y1 - y0 + 1) <= (uint32_t)kExactTileMax;
+      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float qc = 0.f, thr = 0.f;
+      int tw = 0, th = 0, W = 0, H = 0;
+      if (exact) {
+        r0 = __ldg(rec + 4ull * p);
+        qc = __ldg(&rec[4ull * p + 1].x);
+        thr = __ldg(&rec[4ull * p + 3].y);
+        tw = __ldg(&V->tile_w);
+        th = __ldg(&V->tile_h);
+        W = __ldg(&V->width);
+        H = __ldg(&V->height);
+      }
       uint32_t o = carry + off;
       const uint32_t oend = o + bi.w;
       for (uint32_t ty = y0; ty <= y1; ++ty) {
         const int32_t* row = ta + (size_t)ty * tiles_x;
         for (uint32_t tx = x0; tx <= x1; ++tx) {
           const int32_t a = __ldg(row + tx);
-          if (a >= 0) {
+          if (a >= 0 && (!exact || tile_hit(r0, qc, thr, (int)tx, (int)ty, tw, th, W, H))) {
             if (o < oend) {
               keys_out[o] = (uint32_t)a;
               vals_out[o] = p;
@@ -382,14 +395,15 @@ extern "C" size_t pgsag_bin_workspace_size(uint32_t n_pairs, uint64_t capacity) 
 }
 
 extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
-                         uint32_t n_active_total, const int32_t* tile_act, const void* bininfo,
+                         uint32_t n_active_total, const int32_t* tile_act, const float* rec, const void* bininfo,
                          const uint32_t* depth_key, uint64_t capacity, void* ws, size_t ws_bytes,
                          uint32_t* dup_pairs, void* ranges, uint64_t* k_out, int32_t* status,
                          void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !k_out || !status || !ws) return PGSAG_ERR_ARG;
   if (capacity > 0xffffffffull) return PGSAG_ERR_UNSUPPORTED;
-  if (n_pairs && (!bininfo || !depth_key || !tile_act)) return PGSAG_ERR_ARG;
+  if (n_pairs && (!bininfo || !depth_key || !tile_act || !rec)) return PGSAG_ERR_ARG;
+  if (((uintptr_t)rec | (uintptr_t)bininfo) & 15u) return PGSAG_ERR_ARG;
   if (n_active_total && !ranges) return PGSAG_ERR_ARG;
   if (capacity && !dup_pairs) return PGSAG_ERR_ARG;
   const BinWs w = carve(ws, n_pairs, capacity);
@@ -433,7 +447,7 @@ extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* v
   k_scan_partials<<<1, 1024, 0, s>>>(w.partial, nsb, k_out, capacity, status);
   PGSAG_CHECK_LAUNCH();
   k_scan_emit<<<nsb, kScanThreads, 0, s>>>(order, (const uint4*)bininfo, n_pairs, w.partial, views, tile_act,
-                                           keysX[0], valsX[0], status);
+                                           (const float4*)rec, keysX[0], valsX[0], status);
   PGSAG_CHECK_LAUNCH();
 
   // 4. stable sort of the duplicates by active tile

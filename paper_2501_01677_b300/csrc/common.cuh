@@ -55,6 +55,56 @@ __device__ __forceinline__ float gauss_power(float px, float py, float4 r0, floa
   return __fmaf_rn(-r0.w, __fmul_rn(dx, dy), t);
 }
 
+// Does the region {d : -1/2 d^T Q d >= thr} of a 2D Gaussian (centre m, conic
+// Q = [[qa, qb], [qb, qc]]) meet the axis-aligned rectangle [x0, x1] x [y0, y1]
+// of pixel centres?  Minimises the quadratic over the rectangle (centre inside,
+// else each edge's 1D minimum clamped to the edge).  Conservative: the bound is
+// widened by the float32 error of evaluating the quadratic at any pixel, which
+// grows with the conic's condition number, so every pixel whose float32 exponent
+// passes the threshold lies in a rectangle this test accepts.
+__device__ __forceinline__ bool ellipse_rect_hit(float mx, float my, float qa, float qb, float qc, float thr,
+                                                 float x0, float x1, float y0, float y1) {
+  const float dx0 = x0 - mx, dx1 = x1 - mx, dy0 = y0 - my, dy1 = y1 - my;
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
+  const float h2 = -2.f * thr;  // d^T Q d <= h2
+  float f = 3.0e38f;
+  {
+    const float ex[2] = {dx0, dx1};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float dx = ex[i];
+      const float dy = fminf(fmaxf(-qb * dx / qc, dy0), dy1);
+      f = fminf(f, qa * dx * dx + 2.f * qb * dx * dy + qc * dy * dy);
+    }
+    const float ey[2] = {dy0, dy1};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float dy = ey[i];
+      const float dx = fminf(fmaxf(-qb * dy / qa, dx0), dx1);
+      f = fminf(f, qa * dx * dx + 2.f * qb * dx * dy + qc * dy * dy);
+    }
+  }
+  // condition number of Q bounds the relative rounding error of the quadratic
+  const float hm = 0.5f * (qa + qc);
+  const float rt = sqrtf(0.25f * (qa - qc) * (qa - qc) + qb * qb);
+  const float lmin = fmaxf(hm - rt, 1e-30f);
+  const float kappa = (hm + rt) / lmin;
+  return f <= h2 * (1.001f + 1e-6f * kappa) + 1e-3f;
+}
+
+// Tile binning rule shared by the count (preprocess) and the emission (bin):
+// a pair whose tile rectangle spans at most kExactTileMax tiles is duplicated to
+// the active tiles its alpha >= 1/255 region meets (ellipse_rect_hit on the
+// tile's pixel centres); a larger rectangle goes to all its active tiles.
+constexpr int kExactTileMax = 64;
+
+__device__ __forceinline__ bool tile_hit(float4 r0, float qc, float thr, int tx, int ty, int tw, int th, int W,
+                                         int H) {
+  const float x0 = (float)(tx * tw) + 0.5f, x1 = (float)min((tx + 1) * tw, W) - 0.5f;
+  const float y0 = (float)(ty * th) + 0.5f, y1 = (float)min((ty + 1) * th, H) - 0.5f;
+  return ellipse_rect_hit(r0.x, r0.y, r0.z, r0.w, qc, thr, x0, x1, y0, y1);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);

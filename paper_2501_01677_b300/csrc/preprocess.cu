@@ -292,6 +292,19 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
         touched = __ldg(S + (uint32_t)(y1 + 1) * sw + (uint32_t)(x1 + 1)) -
                   __ldg(S + (uint32_t)y0 * sw + (uint32_t)(x1 + 1)) -
                   __ldg(S + (uint32_t)(y1 + 1) * sw + (uint32_t)x0) + __ldg(S + (uint32_t)y0 * sw + (uint32_t)x0);
+        if (touched && (x1 - x0 + 1) * (y1 - y0 + 1) <= kExactTileMax) {
+          const float inv = 1.f / P.det;
+          const float4 r0 = make_float4(mx, my, P.c * inv, -P.b * inv);
+          const float qc = P.a * inv, thr = -logf(255.f * P.o);
+          const int32_t* ta = tile_act + V.tile_base;
+          uint32_t cnt = 0;
+          for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx)
+              if (__ldg(ta + ty * V.tiles_x + tx) >= 0 &&
+                  tile_hit(r0, qc, thr, tx, ty, V.tile_w, V.tile_h, V.width, V.height))
+                ++cnt;
+          touched = cnt;
+        }
       } else {
         vis = false;
       }
@@ -581,9 +594,8 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
                                 uint32_t n_views, const pgsag_view* views, const int32_t* tile_act,
                                 const uint32_t* sat, float* rec, uint32_t* depth_key, void* bininfo,
                                 int32_t* status, void* stream) {
-  (void)tile_act;
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
-  if (!views || !sat || !status) return PGSAG_ERR_ARG;
+  if (!views || !sat || !tile_act || !status) return PGSAG_ERR_ARG;
   if (n_gauss == 0) return cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream) == cudaSuccess ? PGSAG_OK : PGSAG_ERR_CUDA;
   if (!means || !log_scales || !quats || !opacity_logit || !sh || !rec || !depth_key || !bininfo)
     return PGSAG_ERR_ARG;

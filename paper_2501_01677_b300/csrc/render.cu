@@ -112,24 +112,40 @@ __device__ __forceinline__ float4 warp_pixel_box(const Pix& P) {
   return make_float4(x0, x1, y0, y1);
 }
 
-// Stage the record of duplicate `i` into slot `slot`: record, its pair id and
-// the box {mx-ex, mx+ex, my-ey, my+ey} outside which its alpha < 1/255.
+// Shared-memory image of a batch of staged Gaussians, packed by use:
+// g0 = {mx, my, Qxx, Qxy}, g1 = {Qyy, o, thr, -}, g2 = {r, g, b, d}, g3 = {nx, ny, nz, -}.
+struct Stage {
+  float4 g0[kBatch], g1[kBatch], g2[kBatch], g3[kBatch];
+};
+
 __device__ __forceinline__ void stage(uint32_t i, int slot, const uint32_t* __restrict__ dup_pairs,
-                                      const float4* __restrict__ rec, float4 (*srec)[4], float4* sbox,
-                                      uint32_t* spair) {
+                                      const float4* __restrict__ rec, Stage& S, uint32_t* spair) {
   const uint32_t p = __ldg(dup_pairs + i);
   const float4* r = rec + 4ull * p;
   const float4 r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
-  srec[slot][0] = r0;
-  srec[slot][1] = r1;
-  srec[slot][2] = r2;
-  srec[slot][3] = r3;
-  sbox[slot] = make_float4(r0.x - r3.z, r0.x + r3.z, r0.y - r3.w, r0.y + r3.w);
+  S.g0[slot] = r0;
+  S.g1[slot] = make_float4(r1.x, r1.y, r3.y, 0.f);
+  S.g2[slot] = make_float4(r1.z, r1.w, r2.x, r2.y);
+  S.g3[slot] = make_float4(r2.z, r2.w, r3.x, 0.f);
   if (spair) spair[slot] = p;
 }
 
-__device__ __forceinline__ bool box_miss(float4 g, float4 c) {
-  return g.x > c.y || g.y < c.x || g.z > c.w || g.w < c.z;
+// Relevance of staged Gaussians c*32 + lane (c < kBatch/32) to the warp's pixel
+// rectangle: one ellipse-rectangle test per lane, one ballot per 32 Gaussians.
+// Bits beyond `limit` (exclusive) are cleared.
+__device__ __forceinline__ void warp_relevance(const Stage& S, int limit, float4 cbox, int lane,
+                                               uint32_t rel[kBatch / 32]) {
+#pragma unroll
+  for (int c = 0; c < kBatch / 32; ++c) {
+    const int j = c * 32 + lane;
+    bool hit = false;
+    if (j < limit) {
+      const float4 a = S.g0[j];
+      const float4 b = S.g1[j];
+      hit = ellipse_rect_hit(a.x, a.y, a.z, a.w, b.x, b.z, cbox.x, cbox.y, cbox.z, cbox.w);
+    }
+    rel[c] = __ballot_sync(kFull, hit);
+  }
 }
 
 __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
@@ -138,8 +154,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
     const uint4* __restrict__ act_tiles, uint32_t n_items, const uint32_t* __restrict__ px_list,
     Sched sched, float4* __restrict__ out8, float* __restrict__ depth, uint4* __restrict__ aux,
     const int32_t* status) {
-  __shared__ float4 srec[kBatch][4];
-  __shared__ float4 sbox[kBatch];
+  __shared__ Stage S;
   __shared__ uint32_t s_item;
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -171,37 +186,43 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
 #pragma unroll
         for (int u = 0; u < kStagePerThread; ++u) {
           const uint32_t slot = threadIdx.x + u * kRenderThreads;
-          if (slot < nb) stage(base + slot, slot, dup_pairs, rec, srec, sbox, nullptr);
+          if (slot < nb) stage(base + slot, slot, dup_pairs, rec, S, nullptr);
         }
         __syncthreads();
-        if (!all_done) {
-          for (uint32_t j = 0; j < nb; ++j) {
-            if (box_miss(sbox[j], cbox)) continue;
-            const float4 q0 = srec[j][0];
-            const float4 q1 = srec[j][1];
-            const float thr = srec[j][3].y;
+        if (!__any_sync(kFull, !all_done)) continue;
+        uint32_t rel[kBatch / 32];
+        warp_relevance(S, (int)nb, cbox, lane, rel);
+        if (all_done) continue;
+#pragma unroll 1
+        for (int c = 0; c < kBatch / 32; ++c) {
+          uint32_t m = rel[c];
+          while (m) {
+            const int j = c * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            const float4 q0 = S.g0[j];
+            const float4 q1 = S.g1[j];
 #pragma unroll
             for (int k = 0; k < kPPT; ++k) {
               if (done[k]) continue;
               float dx, dy;
               const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy);
-              if (!(pw >= thr)) continue;  // alpha < 1/255
+              if (!(pw >= q1.z)) continue;  // alpha < 1/255
               const float alpha = fminf(__fmul_rn(q1.y, __expf(pw)), kAlphaMax);
               const float test = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
               if (test < kTMin) {
                 done[k] = true;
                 continue;
               }
-              const float4 q2 = srec[j][2];
-              const float nz = srec[j][3].x;
+              const float4 q2 = S.g2[j];
+              const float4 q3 = S.g3[j];
               const float w = __fmul_rn(alpha, T[k]);
-              C0[k] = fmaf(w, q1.z, C0[k]);
-              C1[k] = fmaf(w, q1.w, C1[k]);
-              C2[k] = fmaf(w, q2.x, C2[k]);
-              D[k] = fmaf(w, q2.y, D[k]);
-              N0[k] = fmaf(w, q2.z, N0[k]);
-              N1[k] = fmaf(w, q2.w, N1[k]);
-              N2[k] = fmaf(w, nz, N2[k]);
+              C0[k] = fmaf(w, q2.x, C0[k]);
+              C1[k] = fmaf(w, q2.y, C1[k]);
+              C2[k] = fmaf(w, q2.z, C2[k]);
+              D[k] = fmaf(w, q2.w, D[k]);
+              N0[k] = fmaf(w, q3.x, N0[k]);
+              N1[k] = fmaf(w, q3.y, N1[k]);
+              N2[k] = fmaf(w, q3.z, N2[k]);
               T[k] = test;
               last[k] = base + j;
               ++cnt[k];
@@ -211,6 +232,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
             for (int k = 0; k < kPPT; ++k) ad = ad && done[k];
             if (ad) {
               all_done = true;
+              c = kBatch / 32;
               break;
             }
           }
@@ -292,8 +314,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
     Sched sched, const float4* __restrict__ out8, const uint4* __restrict__ aux,
     const float4* __restrict__ dout8, const float* __restrict__ ddepth, const float* __restrict__ dout_scale,
     float* __restrict__ grad2d, const int32_t* status) {
-  __shared__ float4 srec[kBatch][4];
-  __shared__ float4 sbox[kBatch];
+  __shared__ Stage S;
   __shared__ uint32_t spair[kBatch];
   __shared__ float4 sacc[kBatch][4];
   __shared__ uint32_t s_item;
@@ -369,16 +390,22 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
 #pragma unroll
         for (int u = 0; u < kStagePerThread; ++u) {
           const int slot = threadIdx.x + u * kRenderThreads;
-          if (slot < nb) stage(lo + slot, slot, dup_pairs, rec, srec, sbox, spair);
+          if (slot < nb) stage(lo + slot, slot, dup_pairs, rec, S, spair);
         }
         __syncthreads();
-        const int jtop = min(nb - 1, warp_last - lo);
-        for (int j = jtop; j >= 0; --j) {
-          if (box_miss(sbox[j], cbox)) continue;
+        uint32_t rel[kBatch / 32];
+        warp_relevance(S, min(nb, warp_last - lo + 1), cbox, lane, rel);
+#pragma unroll 1
+        for (int c = kBatch / 32 - 1; c >= 0; --c) {
+         uint32_t m = rel[c];
+         while (m) {
+          const int bit = 31 - __clz(m);
+          m &= ~(1u << bit);
+          const int j = c * 32 + bit;
           const int idx = lo + j;
-          const float4 q0 = srec[j][0];
-          const float4 q1 = srec[j][1];
-          const float thr = srec[j][3].y;
+          const float4 q0 = S.g0[j];
+          const float4 q1 = S.g1[j];
+          const float thr = q1.z;
           float g[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) g[k] = 0.f;
@@ -391,8 +418,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
             const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy);
             if (!(pw >= thr)) continue;  // alpha < 1/255: not blended
             contrib = true;
-            const float4 q2 = srec[j][2];
-            const float n2 = srec[j][3].x;
+            const float4 q2 = S.g2[j];
+            const float4 q3 = S.g3[j];
             const float G = __expf(pw);
             const float raw = __fmul_rn(q1.y, G);
             const float alpha = fminf(raw, kAlphaMax);
@@ -408,7 +435,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
             b.SN1 = b.pa * b.pn1 + om * b.SN1;
             b.SN2 = b.pa * b.pn2 + om * b.SN2;
             b.SD = b.pa * b.pd + om * b.SD;
-            const float c0 = q1.z, c1 = q1.w, c2 = q2.x, d = q2.y, n0 = q2.z, n1 = q2.w;
+            const float c0 = q2.x, c1 = q2.y, c2 = q2.z, d = q2.w, n0 = q3.x, n1 = q3.y, n2 = q3.z;
             float dalpha = b.T * ((c0 - b.SC0) * b.dC0 + (c1 - b.SC1) * b.dC1 + (c2 - b.SC2) * b.dC2 +
                                   (d - b.SD) * b.dD + (n0 - b.SN0) * b.dN0 + (n1 - b.SN1) * b.dN1 +
                                   (n2 - b.SN2) * b.dN2);
@@ -443,6 +470,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
             const int k = lane >> 1;
             if (!(lane & 1) && k < 13) atomicAdd(&reinterpret_cast<float*>(sacc[j])[k], tot);
           }
+         }
         }
         __syncthreads();
         // one float4 atomic per 4 gradient values per Gaussian for the whole tile

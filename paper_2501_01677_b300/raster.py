@@ -274,7 +274,7 @@ class Plan:
         s = _stream_ptr(stream)
         with self._ev('bin'):
             L.check(self.lib.pgsag_bin(self.n_pairs, self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.tile_act),
-                                       _ptr(self.bininfo), _ptr(self.dkey), self.capacity, _ptr(self.ws), self.ws.numel(),
+                                       _ptr(self.rec), _ptr(self.bininfo), _ptr(self.dkey), self.capacity, _ptr(self.ws), self.ws.numel(),
                                        _ptr(self.dup_pairs), _ptr(self.ranges), _ptr(self.k_out), _ptr(self.status), s),
                     "pgsag_bin")
 

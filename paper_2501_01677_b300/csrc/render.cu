@@ -298,13 +298,14 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float v[16], int la
   return a1 + __shfl_xor_sync(kFull, a1, 1);
 }
 
-// Per-pixel adjoint state.
+// Per-pixel adjoint state.  S* hold the suffix sums S_i = sum_{j>i} x_j a_j
+// prod_{i<l<j} (1 - a_l) of the channels behind the Gaussian being processed;
+// they are advanced eagerly (S <- a x + (1 - a) S) after each contributor.
 struct BwdPix {
-  float T, Tfin;
+  float T;
   int last;
-  float dC0, dC1, dC2, dD, dN0, dN1, dN2, dA;
-  float SC0, SC1, SC2, SN0, SN1, SN2, SD;                  // suffix sums behind the current Gaussian
-  float pa, pc0, pc1, pc2, pn0, pn1, pn2, pd;              // previous (next in front-to-back order)
+  float dC0, dC1, dC2, dD, dN0, dN1, dN2, dATf;  // dATf = dL/dA * T_final
+  float SC0, SC1, SC2, SN0, SN1, SN2, SD;
 };
 
 __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
@@ -338,16 +339,14 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
         BwdPix& b = B[k];
-        b.T = b.Tfin = 1.f;
+        b.T = 1.f;
         b.last = -1;
-        b.dC0 = b.dC1 = b.dC2 = b.dD = b.dN0 = b.dN1 = b.dN2 = b.dA = 0.f;
+        b.dC0 = b.dC1 = b.dC2 = b.dD = b.dN0 = b.dN1 = b.dN2 = b.dATf = 0.f;
         b.SC0 = b.SC1 = b.SC2 = b.SN0 = b.SN1 = b.SN2 = b.SD = 0.f;
-        b.pa = b.pc0 = b.pc1 = b.pc2 = b.pn0 = b.pn1 = b.pn2 = b.pd = 0.f;
         if (!P.has[k]) continue;
         const uint64_t gp = V.pix_base + P.pix[k];
         const uint4 ax = __ldg(aux + gp);
-        b.Tfin = __uint_as_float(ax.x);
-        b.T = b.Tfin;
+        b.T = __uint_as_float(ax.x);
         b.last = ax.z > 0 ? (int)ax.y : -1;
         const float4 g0 = __ldg(dout8 + 2 * gp), g1 = __ldg(dout8 + 2 * gp + 1);
         b.dC0 = gscale * g0.x;
@@ -357,7 +356,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
         b.dN0 = gscale * g1.x;
         b.dN1 = gscale * g1.y;
         b.dN2 = gscale * g1.z;
-        b.dA = gscale * g1.w;
+        b.dATf = gscale * g1.w * b.T;
         if (ddepth != nullptr && ax.z > 0) {
           // Eq. 4: Depth = D / s, s = -N . r
           const float gd = gscale * __ldg(ddepth + gp);
@@ -409,7 +408,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
           float g[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) g[k] = 0.f;
-          bool contrib = false;
+          int ncontrib = 0;
 #pragma unroll
           for (int k = 0; k < kPPT; ++k) {
             BwdPix& b = B[k];
@@ -417,37 +416,29 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
             float dx, dy;
             const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy);
             if (!(pw >= thr)) continue;  // alpha < 1/255: not blended
-            contrib = true;
+            ++ncontrib;
             const float4 q2 = S.g2[j];
             const float4 q3 = S.g3[j];
             const float G = __expf(pw);
             const float raw = __fmul_rn(q1.y, G);
             const float alpha = fminf(raw, kAlphaMax);
             const float oma = 1.f - alpha;
-            b.T = b.T / oma;  // transmittance in front of this Gaussian
+            const float roma = __fdividef(1.f, oma);  // 1 <= 1/(1-alpha) <= 100
+            b.T *= roma;                              // transmittance in front of this Gaussian
             const float w = alpha * b.T;
-            // S_i = a_{i+1} x_{i+1} + (1 - a_{i+1}) S_{i+1}
-            const float om = 1.f - b.pa;
-            b.SC0 = b.pa * b.pc0 + om * b.SC0;
-            b.SC1 = b.pa * b.pc1 + om * b.SC1;
-            b.SC2 = b.pa * b.pc2 + om * b.SC2;
-            b.SN0 = b.pa * b.pn0 + om * b.SN0;
-            b.SN1 = b.pa * b.pn1 + om * b.SN1;
-            b.SN2 = b.pa * b.pn2 + om * b.SN2;
-            b.SD = b.pa * b.pd + om * b.SD;
             const float c0 = q2.x, c1 = q2.y, c2 = q2.z, d = q2.w, n0 = q3.x, n1 = q3.y, n2 = q3.z;
             float dalpha = b.T * ((c0 - b.SC0) * b.dC0 + (c1 - b.SC1) * b.dC1 + (c2 - b.SC2) * b.dC2 +
                                   (d - b.SD) * b.dD + (n0 - b.SN0) * b.dN0 + (n1 - b.SN1) * b.dN1 +
                                   (n2 - b.SN2) * b.dN2);
-            dalpha += b.dA * b.Tfin / oma;
-            b.pa = alpha;
-            b.pc0 = c0;
-            b.pc1 = c1;
-            b.pc2 = c2;
-            b.pd = d;
-            b.pn0 = n0;
-            b.pn1 = n1;
-            b.pn2 = n2;
+            dalpha += b.dATf * roma;
+            // advance the suffix sums past this Gaussian: S <- a x + (1 - a) S
+            b.SC0 = fmaf(alpha, c0 - b.SC0, b.SC0);
+            b.SC1 = fmaf(alpha, c1 - b.SC1, b.SC1);
+            b.SC2 = fmaf(alpha, c2 - b.SC2, b.SC2);
+            b.SN0 = fmaf(alpha, n0 - b.SN0, b.SN0);
+            b.SN1 = fmaf(alpha, n1 - b.SN1, b.SN1);
+            b.SN2 = fmaf(alpha, n2 - b.SN2, b.SN2);
+            b.SD = fmaf(alpha, d - b.SD, b.SD);
             g[6] += w * b.dC0;
             g[7] += w * b.dC1;
             g[8] += w * b.dC2;
@@ -465,10 +456,20 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
               g[4] -= 0.5f * dp * dy * dy;
             }
           }
-          if (__any_sync(kFull, contrib)) {
-            const float tot = warp_reduce_scatter16(g, lane);
-            const int k = lane >> 1;
-            if (!(lane & 1) && k < 13) atomicAdd(&reinterpret_cast<float*>(sacc[j])[k], tot);
+          const uint32_t cm = __ballot_sync(kFull, ncontrib > 0);
+          if (cm) {
+            float* acc = reinterpret_cast<float*>(sacc[j]);
+            if (__popc(cm) <= 4) {
+              // few contributing lanes: add their values directly
+              if (ncontrib > 0) {
+#pragma unroll
+                for (int k = 0; k < 13; ++k) atomicAdd(acc + k, g[k]);
+              }
+            } else {
+              const float tot = warp_reduce_scatter16(g, lane);
+              const int k = lane >> 1;
+              if (!(lane & 1) && k < 13) atomicAdd(acc + k, tot);
+            }
           }
          }
         }

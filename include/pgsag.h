@@ -337,6 +337,31 @@ int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint32_t n_activ
                      float* chunk_scratch, float* gc_load, int32_t* status, void* stream);
 
 /*
+ * pgsag_tile_stats_noalloc: pgsag_tile_stats without caller-provided scratch.
+ * The paper has no counterpart; this is an interface for callers that cannot
+ * allocate device memory (an application or plug-in that must take every
+ * device buffer from its own memory manager, or a latency-critical loop where a
+ * cudaMalloc, which can synchronise the device, is not acceptable).  The caller
+ * still passes all inputs and outputs (same meaning as pgsag_tile_stats); the
+ * scratch lives in a fixed device array inside the library (about 16 MiB, held
+ * on every GPU that loads the library until the process exits).
+ *   - At most PGSAG_NOALLOC_MAX_CHUNKS chunks (2^20, i.e. about 33.5M rendered
+ *     pixels); larger inputs return PGSAG_ERR_CAPACITY and enqueue nothing.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (that device must be current); make this first call
+ *     before any stream capture.
+ *   - Calls share the array: calls that overlap on the GPU (other streams or
+ *     host threads on the same device) race and give wrong results.
+ *   - Allocates nothing (no cudaMalloc / cudaFree, no allocating library call).
+ */
+#define PGSAG_NOALLOC_MAX_CHUNKS (1u << 20)
+int pgsag_tile_stats_noalloc(uint32_t n_views, const pgsag_view* views, uint32_t n_active_total,
+                             const void* ranges, uint32_t n_chunks, const void* chunks,
+                             const void* act_tiles, const uint32_t* px_list, const void* aux,
+                             const float* gc_weight, uint32_t* tile_counts, float* gc_load,
+                             int32_t* status, void* stream);
+
+/*
  * pgsag_adam: fused Adam update of n parameters (p, g, m, v float32):
  *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  *   p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).

@@ -18,12 +18,14 @@ PGSAG_DEV_BOUNDS = 4
 MAX_VIEWS = 256
 CHUNK = 32
 PIX_MASK, PIX_EDGE, PIX_RENDER = 1, 2, 4
+NOALLOC_MAX_CHUNKS = 1 << 20
 
 # Every entry point declared in include/pgsag.h
 EXPORTS = (
     "pgsag_status_str", "pgsag_build_info", "pgsag_prep_flags", "pgsag_prep_lists", "pgsag_prep_gc_weight",
     "pgsag_preprocess", "pgsag_bin_workspace_size", "pgsag_bin", "pgsag_render_fwd", "pgsag_loss_ban",
-    "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_adam",
+    "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_tile_stats_noalloc",
+    "pgsag_adam",
 )
 
 
@@ -79,6 +81,7 @@ def load(path: str = LIB_PATH):
          [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P, c_uint32, P, P, P])
     _sig(lib, "pgsag_preprocess_bwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_tile_stats_noalloc", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_adam", c_int, [c_uint64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P])
     _lib = lib
     return lib

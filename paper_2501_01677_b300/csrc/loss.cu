@@ -6,6 +6,8 @@
 // per-pixel arrays are dense per view (only rendered pixels are touched) and the
 // kernels walk the compacted pixel lists chunk by chunk (one warp, one pixel per
 // lane).
+#include <mutex>
+
 #include "common.cuh"
 
 namespace pgsag {
@@ -401,4 +403,68 @@ extern "C" int pgsag_prep_gc_weight(const pgsag_view* view, const float* target,
                                                       weight + view->pix_base);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of pgsag_tile_stats.
+//
+// Some callers cannot allocate device memory: a host application or plug-in
+// that must take every device buffer from its own memory manager, or a
+// latency-critical loop where a cudaMalloc (which can synchronise the device)
+// is not acceptable.  This entry point keeps its scratch -- the per-view double
+// accumulators and the per-chunk partial sums -- in a fixed array below, so it
+// needs no workspace from the caller and allocates nothing.
+//
+// The array is a file-scope __device__ variable: every GPU that loads this
+// library holds it (kNoAllocScratchBytes) until the process exits.  Host code
+// cannot use its name as a device address, so its address is looked up once per
+// device with cudaGetSymbolAddress, on that device's first call (with the device
+// current).  Make that first call before any stream capture.  All calls share
+// the array and it keeps the last call's contents: the accumulators are cleared
+// at the start of every call, and calls that overlap on the GPU (different
+// streams, or host threads on the same device) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr uint32_t kNoAllocMaxChunks = PGSAG_NOALLOC_MAX_CHUNKS;
+constexpr size_t kNoAllocAccBytes = (size_t)PGSAG_MAX_VIEWS * 3 * sizeof(double);
+constexpr size_t kNoAllocScratchBytes = kNoAllocAccBytes + (size_t)kNoAllocMaxChunks * 4 * sizeof(float);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PGSAG_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return PGSAG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return PGSAG_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PGSAG_OK;
+}
+}  // namespace
+
+extern "C" int pgsag_tile_stats_noalloc(uint32_t n_views, const pgsag_view* views, uint32_t n_active_total,
+                                        const void* ranges, uint32_t n_chunks, const void* chunks,
+                                        const void* act_tiles, const uint32_t* px_list, const void* aux,
+                                        const float* gc_weight, uint32_t* tile_counts, float* gc_load,
+                                        int32_t* status, void* stream) {
+  if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
+  if (n_chunks > kNoAllocMaxChunks) return PGSAG_ERR_CAPACITY;
+  void* base = nullptr;
+  const int r = noalloc_scratch(&base);
+  if (r) return r;
+  double* acc = reinterpret_cast<double*>(base);
+  float* chunk_scratch = reinterpret_cast<float*>(static_cast<unsigned char*>(base) + kNoAllocAccBytes);
+  return pgsag_tile_stats(n_views, views, n_active_total, ranges, n_chunks, chunks, act_tiles, px_list, aux,
+                          gc_weight, tile_counts, acc, chunk_scratch, gc_load, status, stream);
 }

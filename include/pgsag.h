@@ -337,6 +337,19 @@ int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint32_t n_activ
                      float* chunk_scratch, float* gc_load, int32_t* status, void* stream);
 
 /*
+ * pgsag_schedule_lpt (batched sub-regions, Sec. 4.1 / Sec. 5.1): order of the
+ * active tiles for a persistent render launch, longest first.  cost_t =
+ * rendered pixels x (list length + 1); tiles are emitted in descending
+ * floor(log2(cost_t)) (counting sort; order inside a bucket unspecified).
+ *   ws     device uint32 [33] scratch
+ *   order  device uint32 [n_active_total]: a permutation of the active tiles;
+ *          pass it as pgsag_sched.order together with a counter.
+ * Run it after pgsag_bin (it reads the ranges).
+ */
+int pgsag_schedule_lpt(uint32_t n_active_total, const void* ranges, const void* act_tiles,
+                       uint32_t* ws, uint32_t* order, int32_t* status, void* stream);
+
+/*
  * pgsag_tile_stats_noalloc: pgsag_tile_stats without caller-provided scratch.
  * The paper has no counterpart; this is an interface for callers that cannot
  * allocate device memory (an application or plug-in that must take every

@@ -25,7 +25,7 @@ EXPORTS = (
     "pgsag_status_str", "pgsag_build_info", "pgsag_prep_flags", "pgsag_prep_lists", "pgsag_prep_gc_weight",
     "pgsag_preprocess", "pgsag_bin_workspace_size", "pgsag_bin", "pgsag_render_fwd", "pgsag_loss_ban",
     "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_tile_stats_noalloc",
-    "pgsag_adam",
+    "pgsag_schedule_lpt", "pgsag_adam",
 )
 
 
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_preprocess_bwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_tile_stats_noalloc", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_schedule_lpt", c_int, [c_uint32, P, P, P, P, P, P])
     _sig(lib, "pgsag_adam", c_int, [c_uint64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P])
     _lib = lib
     return lib

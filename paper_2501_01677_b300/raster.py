@@ -207,16 +207,33 @@ class Plan:
         nbytes = int(self.lib.pgsag_bin_workspace_size(self.n_pairs, self.capacity))
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
 
-    def use_persistent_schedule(self, ctas_per_sm: int = 4, order: Optional[torch.Tensor] = None):
-        """Render with a persistent grid pulling active tiles from a device work
-        counter, optionally in the given tile order."""
-        self.sched_order = order
-        self.sched = L.PgsagSched(order.data_ptr() if order is not None else None, self.sched_counter.data_ptr(),
+    def use_persistent_schedule(self, ctas_per_sm: int = 4, lpt: bool = True):
+        """Render with a persistent grid (ctas_per_sm x SMs CTAs) pulling active
+        tiles from a device work counter; with lpt=True the tiles are handed out
+        longest first (pgsag_schedule_lpt, recomputed after every binning)."""
+        self.lpt = bool(lpt)
+        if self.lpt:
+            self.sched_order = torch.empty(max(self.n_active, 1), dtype=torch.int32, device=self.device)
+            self.lpt_ws = torch.zeros(64, dtype=torch.int32, device=self.device)
+        else:
+            self.sched_order = None
+        self.sched = L.PgsagSched(self.sched_order.data_ptr() if self.lpt else None, self.sched_counter.data_ptr(),
                                   int(ctas_per_sm), 0)
 
     def use_plain_schedule(self):
         self.sched = None
         self.sched_order = None
+        self.lpt = False
+
+    def schedule(self, stream=None):
+        """Longest-first tile order for the persistent render launches."""
+        if self.sched is None or not getattr(self, "lpt", False):
+            return
+        s = _stream_ptr(stream)
+        with self._ev('schedule'):
+            L.check(self.lib.pgsag_schedule_lpt(self.n_active, _ptr(self.ranges), _ptr(self.act_tiles),
+                                                _ptr(self.lpt_ws), _ptr(self.sched_order), _ptr(self.status), s),
+                    "pgsag_schedule_lpt")
 
     def _sched_arg(self):
         return ctypes.byref(self.sched) if self.sched is not None else None
@@ -248,6 +265,8 @@ class Plan:
         n = 1  # preprocess
         if self.n_pairs:
             n += 4 * 3 + 3 + 3 * tile_passes + (1 if self.n_active else 0)
+        if self.sched is not None and getattr(self, "lpt", False) and self.n_active:
+            n += 3                              # schedule
         n += 1 if self.n_active else 0          # render_fwd
         n += (3 if self.n_chunks else 0) + 1    # loss
         if with_stats:
@@ -344,7 +363,36 @@ class Plan:
             if self._auto_capacity:
                 self._auto_capacity = False
             break
+        self.schedule(stream)
         self.render_fwd(stream)
+
+    def step(self, P: GaussianParams, grads: Sequence[torch.Tensor], lambda_ban: float = LAMBDA_BAN,
+             loss_out: Optional[torch.Tensor] = None, accumulate: bool = False, stream=None):
+        """One whole step through the library with no host synchronisation:
+        preprocess, bin, (schedule), render, loss, statistics, render adjoint,
+        preprocess adjoint into `grads`.  The duplicate capacity must already be
+        sized (one forward(check=True) first)."""
+        self.preprocess(P, stream)
+        self.bin(stream)
+        self.schedule(stream)
+        self.render_fwd(stream)
+        self.loss(lambda_ban, loss_out, stream)
+        self.tile_stats(stream)
+        self.render_bwd(self.dout8, None, None, stream)
+        self.preprocess_bwd(P, grads, accumulate, stream)
+
+    def capture(self, P: GaussianParams, grads: Sequence[torch.Tensor], lambda_ban: float = LAMBDA_BAN):
+        """CUDA graph of one whole step (see step); replay() runs it."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.step(P, grads, lambda_ban)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.step(P, grads, lambda_ban)
+        return graph
 
     def check_status(self):
         st = self.status_value()

@@ -276,3 +276,42 @@ def test_render_fn_upstream_gradient_matches_oracle():
     for name, t in zip(("means", "log_scales", "quats", "opacity_logit", "sh"), P.tensors()):
         e = rel_l2(t.grad.cpu().numpy().astype(np.float64).ravel(), p[name].grad.numpy().ravel())
         assert e < GRAD_TOL, (name, e)
+
+
+def test_persistent_lpt_schedule_and_graph_replay_match_plain():
+    """Persistent launches over a longest-first tile queue, and a CUDA-graph replay
+    of the whole step, give the plain launch's outputs (forward bitwise; gradients
+    up to float atomics order)."""
+    from paper_2501_01677_b300 import raster
+    g, ranges, views, owner = syn.config3(sizes=(3000, 5000, 2000), views_per_region=2, scale=0.2)
+    g_ranges = [ranges[o] for o in owner]
+    P = raster.GaussianParams.from_numpy(g)
+
+    def run(mode):
+        plan = raster.Plan([v.cam for v in views], [v.mask for v in views], [v.target for v in views], g.n,
+                           g_ranges=g_ranges)
+        plan.forward(P)  # sizes the capacity
+        if mode != "plain":
+            plan.use_persistent_schedule(ctas_per_sm=2, lpt=True)
+        grads = raster.new_param_grads(P)
+        if mode == "graph":
+            graph = plan.capture(P, grads)
+            graph.replay()
+            graph.replay()
+        else:
+            plan.step(P, grads)
+        torch.cuda.synchronize()
+        plan.check_status()
+        return plan, [t.cpu().numpy() for t in grads]
+
+    plain, gp = run("plain")
+    pers, gq = run("persistent")
+    graph, gg = run("graph")
+    order = pers.sched_order[:pers.n_active].cpu().numpy()
+    assert sorted(order.tolist()) == list(range(pers.n_active))
+    for other, go in ((pers, gq), (graph, gg)):
+        assert np.array_equal(other.out8.cpu().numpy(), plain.out8.cpu().numpy())
+        assert np.array_equal(other.aux.cpu().numpy(), plain.aux.cpu().numpy())
+        assert np.allclose(other.loss_buf.cpu().numpy(), plain.loss_buf.cpu().numpy(), rtol=1e-6)
+        for a, b in zip(go, gp):
+            assert rel_l2(a.ravel().astype(np.float64), b.ravel().astype(np.float64)) < 1e-5

@@ -182,7 +182,7 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* wei
  *   <= znear, or o < 1/255;
  *   Sigma = R(q^) diag(s^2) R(q^)^T; Sigma' = J R Sigma R^T J^T + 0.3 I with J the
  *   pinhole Jacobian at mu_c (x/z, y/z clamped to 1.3 x half-FOV);
- *   conic Q = Sigma'^-1; mean2d = (fx x/z + cx, fy y/z + cy);
+ *   conic Q = Sigma'^-1 (stored as its Cholesky factor); mean2d = (fx x/z + cx, fy y/z + cy);
  *   rgb = max(0, SH3(normalize(mu - c)) + 0.5), c = -R^T t the camera centre;
  *   normal n_c = R * (column of R(q^) for the smallest log-scale, ties to the
  *   lowest axis), negated if n_c . mu_c > 0; d = -n_c . mu_c;
@@ -196,9 +196,14 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* wei
  *   sh [N,16,3]; views (device, n_views <= PGSAG_MAX_VIEWS); tile_act, sat.
  * Outputs per pair p:
  *   rec [p*16 .. p*16+15] float (16-byte aligned):
- *     {mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz, thr, ex, ey}
- *     (thr = -ln(255 o): the pair enters a pixel iff -1/2 d^T Q d >= thr, i.e.
- *     alpha >= 1/255; ex, ey: half-extents of that region's box, 1 px margin)
+ *     {mx, my, l11, l21, l22, o, r, g, b, d, nx, ny, nz, thr, ex, ey}
+ *     (l11, l21, l22: Cholesky factor of the conic, Q = L L^T with
+ *     L = [[l11, 0], [l21, l22]], so -1/2 d^T Q d = -1/2((l11 dx + l21 dy)^2 +
+ *     (l22 dy)^2); det Sigma' is evaluated as |V0 x V1|^2 + 0.3(|V0|^2 + |V1|^2)
+ *     + 0.09 with Sigma' = V V^T + 0.3 I, free of cancellation for elongated
+ *     Gaussians; thr = -ln(255 o): the pair enters a pixel iff the exponent is
+ *     >= thr, i.e. alpha >= 1/255; ex, ey: half-extents of that region's box,
+ *     1 px margin)
  *   depth_key [p]: float bits of z, 0xFFFFFFFF for culled pairs
  *   bininfo [p] uint4: {x0 | y0 << 16, x1 | y1 << 16 (inclusive tile rect),
  *     view index, touched}
@@ -291,7 +296,7 @@ int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
  * Adjoint of pgsag_render_fwd: each CTA re-traverses its tile's list back to
  * front from the last blended Gaussian, recovering T by division
  * (T_i = T_{i+1} / (1 - alpha_i)), and accumulates per pair
- *   grad2d[p*16 + {0..12}] = dL/d{mx, my, Qxx, Qxy, Qyy, o, r, g, b, d, nx, ny, nz}
+ *   grad2d[p*16 + {0..12}] = dL/d{mx, my, l11, l21, l22, o, r, g, b, d, nx, ny, nz}
  * (warp shuffle reduction, shared-memory sum over the CTA's warps, then one
  * float4 atomic add per 4 values per tile).  grad2d (16-byte aligned) is zeroed
  * by this call.  ddepth (nullable) adds a gradient on the depth output,

@@ -41,18 +41,19 @@ __device__ __forceinline__ ViewLite load_view_lite(const pgsag_view* v) {
   return r;
 }
 
-// The Gaussian's exponent at a pixel, -1/2 d^T Q d, evaluated in a fixed
-// sequence of correctly rounded operations so that the forward and the adjoint
-// kernel obtain identical bits (the alpha >= 1/255 and termination decisions
-// must agree between them).  r0 = {mx, my, Qxx, Qxy}, qyy = Qyy.
-__device__ __forceinline__ float gauss_power(float px, float py, float4 r0, float qyy,
-                                             float& dx, float& dy) {
+// The Gaussian's exponent at a pixel, -1/2 d^T Q d, from the Cholesky factor
+// Q = L L^T, L = [[l11, 0], [l21, l22]]:  -1/2 ((l11 dx + l21 dy)^2 + (l22 dy)^2),
+// a sum of squares (no cancellation for elongated Gaussians).  Evaluated in a
+// fixed sequence of correctly rounded operations so that the forward and the
+// adjoint kernel obtain identical bits (the alpha >= 1/255 and termination
+// decisions must agree between them).  r0 = {mx, my, l11, l21}.
+__device__ __forceinline__ float gauss_power(float px, float py, float4 r0, float l22, float& dx, float& dy,
+                                             float& u, float& w) {
   dx = __fsub_rn(px, r0.x);
   dy = __fsub_rn(py, r0.y);
-  float t = __fmul_rn(r0.z, __fmul_rn(dx, dx));
-  t = __fmaf_rn(qyy, __fmul_rn(dy, dy), t);
-  t = __fmul_rn(-0.5f, t);
-  return __fmaf_rn(-r0.w, __fmul_rn(dx, dy), t);
+  u = __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy));
+  w = __fmul_rn(l22, dy);
+  return __fmul_rn(-0.5f, __fmaf_rn(u, u, __fmul_rn(w, w)));
 }
 
 // Does the region {d : -1/2 d^T Q d >= thr} of a 2D Gaussian (centre m, conic
@@ -98,11 +99,17 @@ __device__ __forceinline__ bool ellipse_rect_hit(float mx, float my, float qa, f
 // tile's pixel centres); a larger rectangle goes to all its active tiles.
 constexpr int kExactTileMax = 64;
 
-__device__ __forceinline__ bool tile_hit(float4 r0, float qc, float thr, int tx, int ty, int tw, int th, int W,
+// Same test from the Cholesky factor: Q = [[l11^2, l11 l21], [l11 l21, l21^2 + l22^2]].
+__device__ __forceinline__ bool factor_rect_hit(float4 r0, float l22, float thr, float x0, float x1, float y0,
+                                                float y1) {
+  return ellipse_rect_hit(r0.x, r0.y, r0.z * r0.z, r0.z * r0.w, r0.w * r0.w + l22 * l22, thr, x0, x1, y0, y1);
+}
+
+__device__ __forceinline__ bool tile_hit(float4 r0, float l22, float thr, int tx, int ty, int tw, int th, int W,
                                          int H) {
   const float x0 = (float)(tx * tw) + 0.5f, x1 = (float)min((tx + 1) * tw, W) - 0.5f;
   const float y0 = (float)(ty * th) + 0.5f, y1 = (float)min((ty + 1) * th, H) - 0.5f;
-  return ellipse_rect_hit(r0.x, r0.y, r0.z, r0.w, qc, thr, x0, x1, y0, y1);
+  return factor_rect_hit(r0, l22, thr, x0, x1, y0, y1);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -155,7 +155,8 @@ struct PairFwd {
   float M[9];       // Rq diag(s)
   float V[6];       // T2 M (2x3)
   float a, b, c;    // Sigma' (dilated)
-  float det;
+  float det;        // det Sigma' (Lagrange identity, no cancellation)
+  float l11, l21, l22;  // Cholesky factor of the conic Sigma'^-1
   bool clampx, clampy;
   float txz, tyz;   // clamped x/z, y/z
   float J00, J02, J11, J12;
@@ -213,11 +214,22 @@ __device__ __forceinline__ bool pair_forward(const pgsag_view& V, const GaussIn&
     for (int k = 0; k < 3; ++k)
       P.V[i * 3 + k] = P.T2[i * 3 + 0] * P.M[0 * 3 + k] + P.T2[i * 3 + 1] * P.M[1 * 3 + k] +
                        P.T2[i * 3 + 2] * P.M[2 * 3 + k];
-  P.a = P.V[0] * P.V[0] + P.V[1] * P.V[1] + P.V[2] * P.V[2] + kCovDilation;
+  const float a0 = P.V[0] * P.V[0] + P.V[1] * P.V[1] + P.V[2] * P.V[2];
+  const float c0 = P.V[3] * P.V[3] + P.V[4] * P.V[4] + P.V[5] * P.V[5];
+  P.a = a0 + kCovDilation;
   P.b = P.V[0] * P.V[3] + P.V[1] * P.V[4] + P.V[2] * P.V[5];
-  P.c = P.V[3] * P.V[3] + P.V[4] * P.V[4] + P.V[5] * P.V[5] + kCovDilation;
-  P.det = P.a * P.c - P.b * P.b;
-  if (!(P.det > 0.f)) return false;
+  P.c = c0 + kCovDilation;
+  // det = a c - b^2 = |V0 x V1|^2 + 0.3 (|V0|^2 + |V1|^2) + 0.09 (Lagrange identity)
+  const float x0 = P.V[1] * P.V[5] - P.V[2] * P.V[4];
+  const float x1 = P.V[2] * P.V[3] - P.V[0] * P.V[5];
+  const float x2 = P.V[0] * P.V[4] - P.V[1] * P.V[3];
+  P.det = x0 * x0 + x1 * x1 + x2 * x2 + kCovDilation * (a0 + c0) + kCovDilation * kCovDilation;
+  if (!(P.det > 0.f) || !isfinite(P.det)) return false;
+  // conic Q = Sigma'^-1 = L L^T: l11 = sqrt(c/det), l21 = -b / sqrt(c det), l22 = 1/sqrt(c)
+  const float sq = rsqrtf(P.c * P.det);
+  P.l11 = P.c * sq;
+  P.l21 = -P.b * sq;
+  P.l22 = rsqrtf(P.c);
   // flattened-Gaussian normal: axis of the smallest log-scale (ties -> lowest)
   int k = 0;
   if (G.ls[1] < G.ls[k]) k = 1;
@@ -293,15 +305,14 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
                   __ldg(S + (uint32_t)y0 * sw + (uint32_t)(x1 + 1)) -
                   __ldg(S + (uint32_t)(y1 + 1) * sw + (uint32_t)x0) + __ldg(S + (uint32_t)y0 * sw + (uint32_t)x0);
         if (touched && (x1 - x0 + 1) * (y1 - y0 + 1) <= kExactTileMax) {
-          const float inv = 1.f / P.det;
-          const float4 r0 = make_float4(mx, my, P.c * inv, -P.b * inv);
-          const float qc = P.a * inv, thr = -logf(255.f * P.o);
+          const float4 r0 = make_float4(mx, my, P.l11, P.l21);
+          const float l22 = P.l22, thr = -logf(255.f * P.o);
           const int32_t* ta = tile_act + V.tile_base;
           uint32_t cnt = 0;
           for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx)
               if (__ldg(ta + ty * V.tiles_x + tx) >= 0 &&
-                  tile_hit(r0, qc, thr, tx, ty, V.tile_w, V.tile_h, V.width, V.height))
+                  tile_hit(r0, l22, thr, tx, ty, V.tile_w, V.tile_h, V.width, V.height))
                 ++cnt;
           touched = cnt;
         }
@@ -334,9 +345,8 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
       col[1] += Y[k] * __ldg(shg + 3 * k + 1);
       col[2] += Y[k] * __ldg(shg + 3 * k + 2);
     }
-    const float inv = 1.f / P.det;
-    R4[0] = make_float4(mx, my, P.c * inv, -P.b * inv);
-    R4[1] = make_float4(P.a * inv, P.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
+    R4[0] = make_float4(mx, my, P.l11, P.l21);
+    R4[1] = make_float4(P.l22, P.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
     R4[2] = make_float4(fmaxf(col[2], 0.f), P.dist, P.nc[0], P.nc[1]);
     R4[3] = make_float4(P.nc[2], -logf(255.f * P.o), ex, ey);
     dkey[p] = __float_as_uint(P.mc[2]);
@@ -388,9 +398,9 @@ __global__ void k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
     if (!pair_forward(V, G, P)) continue;
     const float4* G4 = reinterpret_cast<const float4*>(grad2d) + 4ull * p;
     const float4 g0 = __ldg(G4 + 0), g1 = __ldg(G4 + 1), g2 = __ldg(G4 + 2), g3 = __ldg(G4 + 3);
-    // grad2d = {dmx, dmy, dQxx, dQxy, dQyy, do, dr, dg, db, dd, dnx, dny, dnz}
-    const float dmx = g0.x, dmy = g0.y, dqa = g0.z, dqb = g0.w;
-    const float dqc = g1.x, dop = g1.y;
+    // grad2d = {dmx, dmy, dl11, dl21, dl22, do, dr, dg, db, dd, dnx, dny, dnz}
+    const float dmx = g0.x, dmy = g0.y, dl11 = g0.z, dl21 = g0.w;
+    const float dl22 = g1.x, dop = g1.y;
     const float drgb[3] = {g1.z, g1.w, g2.x};
     const float dd = g2.y;
     float dn[3] = {g2.z, g2.w, g3.x};
@@ -467,12 +477,14 @@ __global__ void k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
     dmc[1] += dmy * V.fy * iz;
     dmc[2] -= dmx * V.fx * P.mc[0] * iz2 + dmy * V.fy * P.mc[1] * iz2;
 
-    // conic Q = Sigma'^-1 -> Sigma' = (a, b, c)
+    // Cholesky factor of the conic -> Sigma' = (a, b, c), det = a c - b^2:
+    // l11 = sqrt(c/det), l21 = -b/sqrt(c det), l22 = c^-1/2
     const float a = P.a, b = P.b, c = P.c;
-    const float id2 = 1.f / (P.det * P.det);
-    const float da = (-c * c * dqa + b * c * dqb - b * b * dqc) * id2;
-    const float db = (2.f * b * c * dqa - (a * c + b * b) * dqb + 2.f * a * b * dqc) * id2;
-    const float dcc = (-b * b * dqa + a * b * dqb - a * a * dqc) * id2;
+    const float iD = 1.f / P.det, ic = 1.f / c;
+    const float da = -0.5f * c * iD * (dl11 * P.l11 + dl21 * P.l21);
+    const float db = dl11 * P.l11 * b * iD - dl21 * a * P.l11 * iD;
+    const float dcc = dl11 * P.l11 * 0.5f * (ic - a * iD) - dl21 * P.l21 * 0.5f * (ic + a * iD) -
+                      dl22 * 0.5f * P.l22 * ic;
     // Sigma' = V V^T: dV0 = 2 da V0 + db V1, dV1 = db V0 + 2 dc V1
     float dV[6];
 #pragma unroll

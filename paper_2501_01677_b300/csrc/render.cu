@@ -113,7 +113,8 @@ __device__ __forceinline__ float4 warp_pixel_box(const Pix& P) {
 }
 
 // Shared-memory image of a batch of staged Gaussians, packed by use:
-// g0 = {mx, my, Qxx, Qxy}, g1 = {Qyy, o, thr, -}, g2 = {r, g, b, d}, g3 = {nx, ny, nz, -}.
+// g0 = {mx, my, l11, l21}, g1 = {l22, o, thr, -}, g2 = {r, g, b, d}, g3 = {nx, ny, nz, -}
+// (l11, l21, l22: Cholesky factor of the conic).
 struct Stage {
   float4 g0[kBatch], g1[kBatch], g2[kBatch], g3[kBatch];
 };
@@ -142,7 +143,7 @@ __device__ __forceinline__ void warp_relevance(const Stage& S, int limit, float4
     if (j < limit) {
       const float4 a = S.g0[j];
       const float4 b = S.g1[j];
-      hit = ellipse_rect_hit(a.x, a.y, a.z, a.w, b.x, b.z, cbox.x, cbox.y, cbox.z, cbox.w);
+      hit = factor_rect_hit(a, b.x, b.z, cbox.x, cbox.y, cbox.z, cbox.w);
     }
     rel[c] = __ballot_sync(kFull, hit);
   }
@@ -204,8 +205,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
 #pragma unroll
             for (int k = 0; k < kPPT; ++k) {
               if (done[k]) continue;
-              float dx, dy;
-              const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy);
+              float dx, dy, u, w2;
+              const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy, u, w2);
               if (!(pw >= q1.z)) continue;  // alpha < 1/255
               const float alpha = fminf(__fmul_rn(q1.y, __expf(pw)), kAlphaMax);
               const float test = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
@@ -413,8 +414,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
           for (int k = 0; k < kPPT; ++k) {
             BwdPix& b = B[k];
             if (idx > b.last) continue;
-            float dx, dy;
-            const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy);
+            float dx, dy, u, wq;
+            const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy, u, wq);
             if (!(pw >= thr)) continue;  // alpha < 1/255: not blended
             ++ncontrib;
             const float4 q2 = S.g2[j];
@@ -449,11 +450,12 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
             if (raw < kAlphaMax) {
               g[5] += dalpha * G;                // d alpha / d o
               const float dp = dalpha * alpha;   // d alpha / d power
-              g[0] += dp * (q0.z * dx + q0.w * dy);
-              g[1] += dp * (q0.w * dx + q1.x * dy);
-              g[2] -= 0.5f * dp * dx * dx;
-              g[3] -= dp * dx * dy;
-              g[4] -= 0.5f * dp * dy * dy;
+              // power = -1/2 (u^2 + w^2), u = l11 dx + l21 dy, w = l22 dy, d = p - m
+              g[0] += dp * u * q0.z;
+              g[1] += dp * (u * q0.w + wq * q1.x);
+              g[2] -= dp * u * dx;
+              g[3] -= dp * u * dy;
+              g[4] -= dp * wq * dy;
             }
           }
           const uint32_t cm = __ballot_sync(kFull, ncontrib > 0);

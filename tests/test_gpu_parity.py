@@ -51,9 +51,13 @@ def test_config0_preprocess_parity(config0):
     m2 = pr["mean2d"].detach().numpy()
     q = pr["conic"].detach().numpy()
     np.testing.assert_allclose(rec[vis, 0:2], m2[vis], rtol=1e-5, atol=1e-3)
-    for j, k in ((2, 0), (3, 1), (4, 2)):
-        scale = np.maximum(np.abs(q[vis]).max(1), 1e-12)
-        assert (np.abs(rec[vis, j] - q[vis, k]) / scale).max() < 1e-4
+    # the record holds the Cholesky factor of the conic: Q = L L^T
+    l11 = np.sqrt(q[:, 0])
+    l21 = q[:, 1] / l11
+    l22 = np.sqrt(q[:, 2] - l21 * l21)
+    for j, ref in ((2, l11), (3, l21), (4, l22)):
+        scale = np.maximum(np.maximum(np.abs(l11), np.abs(l22))[vis], 1e-12)
+        assert (np.abs(rec[vis, j] - ref[vis]) / scale).max() < 1e-5
     np.testing.assert_allclose(rec[vis, 5], pr["opacity"].detach().numpy()[vis], rtol=1e-5)
     np.testing.assert_allclose(rec[vis, 6:9], pr["rgb"].detach().numpy()[vis], rtol=1e-4, atol=1e-5)
     np.testing.assert_allclose(rec[vis, 9], pr["dist"].detach().numpy()[vis], rtol=1e-4, atol=1e-5)

@@ -57,9 +57,11 @@ def test_config2_crop_gradients_vs_oracle(config2):
 
 
 def test_config2_gpu_gradient_central_differences(config2):
-    """Central differences (h = 1e-3) of the CUDA loss on 64 parameters with the
-    largest gradients of the 2k crop (float32 forward), samples whose one-sided
-    differences disagree are skipped (a threshold was crossed)."""
+    """Central differences of the CUDA loss (float64 accumulators of the float32
+    forward) on 64 parameters -- the largest gradients of each tensor on the 2k
+    crop -- with h = 1e-3.  The loss jumps where a pixel's alpha crosses 1/255;
+    when a step changes any pixel's blended count, h is divided by 10 (down to
+    1e-5) so that no threshold is crossed."""
     from paper_2501_01677_b300 import raster
     g, views, boxes = config2
     gc = _crop(g, views)
@@ -69,38 +71,32 @@ def test_config2_gpu_gradient_central_differences(config2):
     loss = raster.render_loss(plan, P)
     loss.backward()
     base = [t.detach().clone() for t in P.tensors()]
-
     nm = float(plan.views_host[0].n_mask)
 
     def L(ti, flat, val):
-        """The loss from the kernel's float64 accumulators (the float32 total
-        would quantise the O(g h) differences away)."""
         ts = [b.clone() for b in base]
         ts[ti].view(-1)[flat] = val
-        Q = raster.GaussianParams(*ts)
-        plan.forward(Q)
+        plan.forward(raster.GaussianParams(*ts))
         plan.loss(O.LAMBDA_BAN)
         a = plan.acc_loss.cpu().numpy()
-        return a[0] / (3.0 * nm) + O.LAMBDA_BAN * (a[1] / a[2] if a[2] > 0 else 0.0)
+        return a[0] / (3.0 * nm) + O.LAMBDA_BAN * (a[1] / a[2] if a[2] > 0 else 0.0), plan.aux[:, 2].clone()
 
-    l0 = L(0, 0, base[0].view(-1)[0])
-    h = 1e-3
     cands = []
     for ti, t in enumerate(P.tensors()):
-        gr = t.grad.view(-1).abs()
-        top = torch.topk(gr, 13).indices.tolist()
+        top = torch.topk(t.grad.view(-1).abs(), 13).indices.tolist()
         cands += [(ti, i, float(t.grad.view(-1)[i])) for i in top]
     checked = 0
     for ti, i, gval in cands[:64]:
         x0 = float(base[ti].view(-1)[i])
-        lp, lm = L(ti, i, x0 + h), L(ti, i, x0 - h)
-        fwd, bwd = (lp - l0) / h, (l0 - lm) / h
-        if abs(fwd - bwd) > 0.05 * max(abs(fwd), abs(bwd)):
-            continue
-        fd = (lp - lm) / (2 * h)
-        assert abs(fd - gval) <= 0.03 * abs(gval) + 1e-9 / h, (ti, i, fd, gval)
-        checked += 1
-    assert checked >= 40
+        for h in (1e-3, 1e-4, 1e-5):
+            lp, cp = L(ti, i, x0 + h)
+            lm, cm = L(ti, i, x0 - h)
+            if torch.equal(cp, cm):
+                fd = (lp - lm) / (2 * h)
+                assert abs(fd - gval) <= 0.02 * abs(gval) + 1e-10 / h, (ti, i, h, fd, gval)
+                checked += 1
+                break
+    assert checked >= 48
 
 
 def test_config2_training_step_with_gc_load(config2):
@@ -124,7 +120,7 @@ def test_config2_training_step_with_gc_load(config2):
         total.backward()
         with torch.no_grad():
             raster.adam_step(list(P.tensors()), [t.grad for t in P.tensors()], m, vv, lrs, step)
-        hist.append((float(geo), float(gcl)))
+        hist.append((float(geo.detach()), float(gcl)))
     torch.cuda.synchronize()
     plan.check_status()
     assert all(np.isfinite(hist).ravel())

@@ -196,14 +196,16 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* wei
  *   sh [N,16,3]; views (device, n_views <= PGSAG_MAX_VIEWS); tile_act, sat.
  * Outputs per pair p:
  *   rec [p*16 .. p*16+15] float (16-byte aligned):
- *     {mx, my, l11, l21, l22, o, r, g, b, d, nx, ny, nz, thr, ex, ey}
- *     (l11, l21, l22: Cholesky factor of the conic, Q = L L^T with
+ *     {mi, ni, l11, l21, l22, o, r, g, b, d, nx, ny, nz, thr, mf, nf}
+ *     (2D mean = (mi + mf, ni + nf): integer part + fraction of a compensated
+ *     float32 evaluation of fx x/z + cx, fy y/z + cy, so that pixel offsets
+ *     keep ~1e-7 px accuracy at any image size;
+ *     l11, l21, l22: Cholesky factor of the conic, Q = L L^T with
  *     L = [[l11, 0], [l21, l22]], so -1/2 d^T Q d = -1/2((l11 dx + l21 dy)^2 +
  *     (l22 dy)^2); det Sigma' is evaluated as |V0 x V1|^2 + 0.3(|V0|^2 + |V1|^2)
  *     + 0.09 with Sigma' = V V^T + 0.3 I, free of cancellation for elongated
  *     Gaussians; thr = -ln(255 o): the pair enters a pixel iff the exponent is
- *     >= thr, i.e. alpha >= 1/255; ex, ey: half-extents of that region's box,
- *     1 px margin)
+ *     >= thr, i.e. alpha >= 1/255)
  *   depth_key [p]: float bits of z, 0xFFFFFFFF for culled pairs
  *   bininfo [p] uint4: {x0 | y0 << 16, x1 | y1 << 16 (inclusive tile rect),
  *     view index, touched}

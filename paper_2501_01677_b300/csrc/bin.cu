@@ -292,13 +292,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
       const int32_t* ta = tile_act + __ldg(&V->tile_base);
       const uint32_t x0 = bi.x & 0xffffu, y0 = bi.x >> 16, x1 = bi.y & 0xffffu, y1 = bi.y >> 16;
       const bool exact = (x1 - x0 + 1) * (y1 - y0 + 1) <= (uint32_t)kExactTileMax;
-      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f);
-      float l22 = 0.f, thr = 0.f;
+      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r3 = r0;
+      float l22 = 0.f;
       int tw = 0, th = 0, W = 0, H = 0;
       if (exact) {
         r0 = __ldg(rec + 4ull * p);
         l22 = __ldg(&rec[4ull * p + 1].x);
-        thr = __ldg(&rec[4ull * p + 3].y);
+        r3 = __ldg(rec + 4ull * p + 3);
         tw = __ldg(&V->tile_w);
         th = __ldg(&V->tile_h);
         W = __ldg(&V->width);
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
         const int32_t* row = ta + (size_t)ty * tiles_x;
         for (uint32_t tx = x0; tx <= x1; ++tx) {
           const int32_t a = __ldg(row + tx);
-          if (a >= 0 && (!exact || tile_hit(r0, l22, thr, (int)tx, (int)ty, tw, th, W, H))) {
+          if (a >= 0 && (!exact || tile_hit(r0.x, r0.y, r3.z, r3.w, r0.z, r0.w, l22, r3.y, (int)tx, (int)ty, tw, th, W, H))) {
             if (o < oend) {
               keys_out[o] = (uint32_t)a;
               vals_out[o] = p;

@@ -26,7 +26,7 @@ __device__ __forceinline__ void status_set(int32_t* st, unsigned flag) {
 // Camera / view fields needed per chunk, read from the device view table.
 struct ViewLite {
   float fx, fy, cx, cy;
-  int width, height;
+  int width, height, tile_w, tile_h;
   uint64_t pix_base;
 };
 __device__ __forceinline__ ViewLite load_view_lite(const pgsag_view* v) {
@@ -37,6 +37,8 @@ __device__ __forceinline__ ViewLite load_view_lite(const pgsag_view* v) {
   r.cy = __ldg(&v->cy);
   r.width = __ldg(&v->width);
   r.height = __ldg(&v->height);
+  r.tile_w = __ldg(&v->tile_w);
+  r.tile_h = __ldg(&v->tile_h);
   r.pix_base = __ldg((const unsigned long long*)&v->pix_base);
   return r;
 }
@@ -56,16 +58,16 @@ __device__ __forceinline__ float gauss_power(float px, float py, float4 r0, floa
   return __fmul_rn(-0.5f, __fmaf_rn(u, u, __fmul_rn(w, w)));
 }
 
-// Does the region {d : -1/2 d^T Q d >= thr} of a 2D Gaussian (centre m, conic
-// Q = [[qa, qb], [qb, qc]]) meet the axis-aligned rectangle [x0, x1] x [y0, y1]
-// of pixel centres?  Minimises the quadratic over the rectangle (centre inside,
-// else each edge's 1D minimum clamped to the edge).  Conservative: the bound is
-// widened by the float32 error of evaluating the quadratic at any pixel, which
-// grows with the conic's condition number, so every pixel whose float32 exponent
-// passes the threshold lies in a rectangle this test accepts.
-__device__ __forceinline__ bool ellipse_rect_hit(float mx, float my, float qa, float qb, float qc, float thr,
-                                                 float x0, float x1, float y0, float y1) {
-  const float dx0 = x0 - mx, dx1 = x1 - mx, dy0 = y0 - my, dy1 = y1 - my;
+// Does the region {d : -1/2 d^T Q d >= thr} of a 2D Gaussian (conic
+// Q = [[qa, qb], [qb, qc]]) meet the axis-aligned rectangle [dx0, dx1] x
+// [dy0, dy1] of pixel-centre offsets from its centre?  Minimises the quadratic
+// over the rectangle (centre inside, else each edge's 1D minimum clamped to the
+// edge).  Conservative: the bound is widened by the float32 error of evaluating
+// the quadratic at any pixel, which grows with the conic's condition number, so
+// every pixel whose float32 exponent passes the threshold lies in a rectangle
+// this test accepts.
+__device__ __forceinline__ bool ellipse_rect_hit(float qa, float qb, float qc, float thr, float dx0, float dx1,
+                                                 float dy0, float dy1) {
   if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
   const float h2 = -2.f * thr;  // d^T Q d <= h2
   float f = 3.0e38f;
@@ -93,23 +95,25 @@ __device__ __forceinline__ bool ellipse_rect_hit(float mx, float my, float qa, f
   return f <= h2 * (1.001f + 1e-6f * kappa) + 1e-3f;
 }
 
-// Tile binning rule shared by the count (preprocess) and the emission (bin):
-// a pair whose tile rectangle spans at most kExactTileMax tiles is duplicated to
-// the active tiles its alpha >= 1/255 region meets (ellipse_rect_hit on the
-// tile's pixel centres); a larger rectangle goes to all its active tiles.
-constexpr int kExactTileMax = 64;
-
 // Same test from the Cholesky factor: Q = [[l11^2, l11 l21], [l11 l21, l21^2 + l22^2]].
-__device__ __forceinline__ bool factor_rect_hit(float4 r0, float l22, float thr, float x0, float x1, float y0,
-                                                float y1) {
-  return ellipse_rect_hit(r0.x, r0.y, r0.z * r0.z, r0.z * r0.w, r0.w * r0.w + l22 * l22, thr, x0, x1, y0, y1);
+__device__ __forceinline__ bool factor_rect_hit(float l11, float l21, float l22, float thr, float dx0, float dx1,
+                                                float dy0, float dy1) {
+  return ellipse_rect_hit(l11 * l11, l11 * l21, l21 * l21 + l22 * l22, thr, dx0, dx1, dy0, dy1);
 }
 
-__device__ __forceinline__ bool tile_hit(float4 r0, float l22, float thr, int tx, int ty, int tw, int th, int W,
-                                         int H) {
+// Tile binning rule shared by the count (preprocess) and the emission (bin):
+// a pair whose tile rectangle spans at most kExactTileMax tiles is duplicated to
+// the active tiles its alpha >= 1/255 region meets (on the tile's pixel
+// centres); a larger rectangle goes to all its active tiles.  The 2D mean is
+// given as integer part (mi, ni) + fraction (mf, nf), so the offsets are exact
+// up to one rounding.
+constexpr int kExactTileMax = 64;
+
+__device__ __forceinline__ bool tile_hit(float mi, float ni, float mf, float nf, float l11, float l21, float l22,
+                                         float thr, int tx, int ty, int tw, int th, int W, int H) {
   const float x0 = (float)(tx * tw) + 0.5f, x1 = (float)min((tx + 1) * tw, W) - 0.5f;
   const float y0 = (float)(ty * th) + 0.5f, y1 = (float)min((ty + 1) * th, H) - 0.5f;
-  return factor_rect_hit(r0, l22, thr, x0, x1, y0, y1);
+  return factor_rect_hit(l11, l21, l22, thr, (x0 - mi) - mf, (x1 - mi) - mf, (y0 - ni) - nf, (y1 - ni) - nf);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

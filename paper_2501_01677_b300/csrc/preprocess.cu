@@ -143,6 +143,49 @@ __device__ __forceinline__ float depth_key_z(const pgsag_view& V, const float m[
   return __fadd_rn(__fadd_rn(__fadd_rn(a, b), c), V.t[2]);
 }
 
+// Error-free transformations: a + b = s + e (Knuth), a * b = p + e (FMA).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// Compensated R_row . m + t (hi + lo).
+__device__ __forceinline__ void dot3_comp(const float* R, const float m[3], float t, float& hi, float& lo) {
+  hi = t;
+  lo = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float p, pe, s, se;
+    two_prod(R[i], m[i], p, pe);
+    two_sum(hi, p, s, se);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(pe, se));
+  }
+}
+
+// One pixel coordinate of the 2D mean, f (x/z) + c, in compensated float32
+// (about 1e-10 relative), split into an integer part ip and a fraction fp so
+// that pixel offsets (p - ip) - fp lose nothing to the magnitude of p.
+__device__ __forceinline__ void mean2d_coord(float xh, float xl, float zh, float zl, float f, float c, float& ip,
+                                             float& fp) {
+  const float qh = __fdiv_rn(xh, zh);
+  float p, pe;
+  two_prod(qh, zh, p, pe);
+  const float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(xh, p), pe), xl), __fmul_rn(qh, zl));
+  const float ql = __fdiv_rn(r, zh);
+  float m, me, s, se;
+  two_prod(f, qh, m, me);
+  two_sum(m, c, s, se);
+  const float lo = __fadd_rn(__fadd_rn(me, __fmul_rn(f, ql)), se);
+  ip = rintf(s);
+  fp = __fadd_rn(__fsub_rn(s, ip), lo);
+}
+
 // Everything the forward computes for one pair that the adjoint reuses.
 struct PairFwd {
   float mc[3];      // camera-frame mean
@@ -282,10 +325,18 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
     float mx = 0.f, my = 0.f, ex = 0.f, ey = 0.f;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
     uint32_t touched = 0;
+    float mi = 0.f, mf = 0.f, ni = 0.f, nf = 0.f;
     if (vis) {
-      const float iz = 1.f / P.mc[2];
-      mx = V.fx * P.mc[0] * iz + V.cx;
-      my = V.fy * P.mc[1] * iz + V.cy;
+      {
+        float xh, xl, yh, yl, zh, zl;
+        dot3_comp(V.R + 0, G.m, V.t[0], xh, xl);
+        dot3_comp(V.R + 3, G.m, V.t[1], yh, yl);
+        dot3_comp(V.R + 6, G.m, V.t[2], zh, zl);
+        mean2d_coord(xh, xl, zh, zl, V.fx, V.cx, mi, mf);
+        mean2d_coord(yh, yl, zh, zl, V.fy, V.cy, ni, nf);
+      }
+      mx = mi + mf;
+      my = ni + nf;
       // axis-aligned box of the alpha >= 1/255 ellipse, + 1 px
       const float r2 = 2.f * logf(255.f * P.o);
       ex = sqrtf(fmaxf(r2, 0.f) * P.a) + 1.f;
@@ -305,14 +356,14 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
                   __ldg(S + (uint32_t)y0 * sw + (uint32_t)(x1 + 1)) -
                   __ldg(S + (uint32_t)(y1 + 1) * sw + (uint32_t)x0) + __ldg(S + (uint32_t)y0 * sw + (uint32_t)x0);
         if (touched && (x1 - x0 + 1) * (y1 - y0 + 1) <= kExactTileMax) {
-          const float4 r0 = make_float4(mx, my, P.l11, P.l21);
-          const float l22 = P.l22, thr = -logf(255.f * P.o);
+          const float thr = -logf(255.f * P.o);
           const int32_t* ta = tile_act + V.tile_base;
           uint32_t cnt = 0;
           for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx)
               if (__ldg(ta + ty * V.tiles_x + tx) >= 0 &&
-                  tile_hit(r0, l22, thr, tx, ty, V.tile_w, V.tile_h, V.width, V.height))
+                  tile_hit(mi, ni, mf, nf, P.l11, P.l21, P.l22, thr, tx, ty, V.tile_w, V.tile_h, V.width,
+                           V.height))
                 ++cnt;
           touched = cnt;
         }
@@ -345,10 +396,10 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
       col[1] += Y[k] * __ldg(shg + 3 * k + 1);
       col[2] += Y[k] * __ldg(shg + 3 * k + 2);
     }
-    R4[0] = make_float4(mx, my, P.l11, P.l21);
+    R4[0] = make_float4(mi, ni, P.l11, P.l21);
     R4[1] = make_float4(P.l22, P.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
     R4[2] = make_float4(fmaxf(col[2], 0.f), P.dist, P.nc[0], P.nc[1]);
-    R4[3] = make_float4(P.nc[2], -logf(255.f * P.o), ex, ey);
+    R4[3] = make_float4(P.nc[2], -logf(255.f * P.o), mf, nf);
     dkey[p] = __float_as_uint(P.mc[2]);
     bininfo[p] = make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16), vi,
                             touched);

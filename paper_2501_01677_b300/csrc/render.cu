@@ -24,7 +24,7 @@ constexpr int kBatch = 256;                       // Gaussians staged per batch
 constexpr int kStagePerThread = kBatch / kRenderThreads;
 
 struct TileInfo {
-  uint32_t view, px_first, npix, rbeg, rend;
+  uint32_t view, tx, ty, px_first, npix, rbeg, rend;
 };
 
 __device__ __forceinline__ TileInfo load_tile(uint32_t t, const uint4* __restrict__ act_tiles,
@@ -33,6 +33,8 @@ __device__ __forceinline__ TileInfo load_tile(uint32_t t, const uint4* __restric
   const uint4 at = __ldg(act_tiles + t);
   const uint2 rg = __ldg(ranges + t);
   ti.view = at.x;
+  ti.tx = at.y & 0xffffu;
+  ti.ty = at.y >> 16;
   ti.px_first = at.z;
   ti.npix = at.w;
   ti.rbeg = rg.x;
@@ -68,15 +70,17 @@ __device__ __forceinline__ uint32_t next_tile(const Sched& s, uint32_t& iter, ui
 
 // Pixels of lane `lane` in warp `warp` for the round starting at r0: entries
 // r0 + (warp * kPPT + k) * 32 + lane of the tile's compacted pixel list, so a
-// warp covers kPPT consecutive 32-pixel runs.
+// warp covers kPPT consecutive 32-pixel runs.  Pixel centres are kept relative
+// to the tile origin (ox, oy), exactly, like the staged Gaussian centres, so
+// that offsets do not lose precision to the image size.
 struct Pix {
   bool has[kPPT];
   uint32_t pix[kPPT];
-  float px[kPPT], py[kPPT];
+  float px[kPPT], py[kPPT];  // centre minus tile origin
 };
 
-__device__ __forceinline__ Pix load_pixels(const TileInfo& ti, uint32_t r0, int warp, int lane, int width,
-                                           const uint32_t* __restrict__ px_list) {
+__device__ __forceinline__ Pix load_pixels(const TileInfo& ti, uint32_t r0, int warp, int lane, int width, int ox,
+                                           int oy, const uint32_t* __restrict__ px_list) {
   Pix P;
 #pragma unroll
   for (int k = 0; k < kPPT; ++k) {
@@ -84,8 +88,8 @@ __device__ __forceinline__ Pix load_pixels(const TileInfo& ti, uint32_t r0, int 
     P.has[k] = li < ti.npix;
     P.pix[k] = P.has[k] ? __ldg(px_list + ti.px_first + li) : 0u;
     const uint32_t yy = P.pix[k] / (uint32_t)width;
-    P.px[k] = (float)(P.pix[k] - yy * (uint32_t)width) + 0.5f;
-    P.py[k] = (float)yy + 0.5f;
+    P.px[k] = (float)((int)(P.pix[k] - yy * (uint32_t)width) - ox) + 0.5f;
+    P.py[k] = (float)((int)yy - oy) + 0.5f;
   }
   return P;
 }
@@ -119,12 +123,15 @@ struct Stage {
   float4 g0[kBatch], g1[kBatch], g2[kBatch], g3[kBatch];
 };
 
+// The centre is staged relative to the tile origin: (integer part - origin) is
+// exact, then the fraction is added.
 __device__ __forceinline__ void stage(uint32_t i, int slot, const uint32_t* __restrict__ dup_pairs,
-                                      const float4* __restrict__ rec, Stage& S, uint32_t* spair) {
+                                      const float4* __restrict__ rec, float ox, float oy, Stage& S,
+                                      uint32_t* spair) {
   const uint32_t p = __ldg(dup_pairs + i);
   const float4* r = rec + 4ull * p;
   const float4 r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
-  S.g0[slot] = r0;
+  S.g0[slot] = make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r3.z), __fadd_rn(__fsub_rn(r0.y, oy), r3.w), r0.z, r0.w);
   S.g1[slot] = make_float4(r1.x, r1.y, r3.y, 0.f);
   S.g2[slot] = make_float4(r1.z, r1.w, r2.x, r2.y);
   S.g3[slot] = make_float4(r2.z, r2.w, r3.x, 0.f);
@@ -143,7 +150,7 @@ __device__ __forceinline__ void warp_relevance(const Stage& S, int limit, float4
     if (j < limit) {
       const float4 a = S.g0[j];
       const float4 b = S.g1[j];
-      hit = factor_rect_hit(a, b.x, b.z, cbox.x, cbox.y, cbox.z, cbox.w);
+      hit = factor_rect_hit(a.z, a.w, b.x, b.z, cbox.x - a.x, cbox.y - a.x, cbox.z - a.y, cbox.w - a.y);
     }
     rel[c] = __ballot_sync(kFull, hit);
   }
@@ -166,7 +173,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
     for (uint32_t r0 = 0; r0 < ti.npix; r0 += kTilePix) {
-      const Pix P = load_pixels(ti, r0, warp, lane, V.width, px_list);
+      const int ox = (int)ti.tx * V.tile_w, oy = (int)ti.ty * V.tile_h;
+      const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
       float T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT], N0[kPPT], N1[kPPT], N2[kPPT];
       uint32_t last[kPPT], cnt[kPPT];
@@ -187,7 +195,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
 #pragma unroll
         for (int u = 0; u < kStagePerThread; ++u) {
           const uint32_t slot = threadIdx.x + u * kRenderThreads;
-          if (slot < nb) stage(base + slot, slot, dup_pairs, rec, S, nullptr);
+          if (slot < nb) stage(base + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, nullptr);
         }
         __syncthreads();
         if (!__any_sync(kFull, !all_done)) continue;
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
         out8[2 * gp + 0] = make_float4(C0[k], C1[k], C2[k], D[k]);
         out8[2 * gp + 1] = make_float4(N0[k], N1[k], N2[k], 1.f - T[k]);
         // Eq. 4: ray-plane depth
-        const float rx = (P.px[k] - V.cx) / V.fx, ry = (P.py[k] - V.cy) / V.fy;
+        const float rx = (P.px[k] + (float)ox - V.cx) / V.fx, ry = (P.py[k] + (float)oy - V.cy) / V.fy;
         const float sdot = -(N0[k] * rx + N1[k] * ry + N2[k]);
         const bool valid = cnt[k] > 0 && sdot > kRayDotMin && D[k] > 0.f;
         depth[gp] = valid ? D[k] / sdot : 0.f;
@@ -333,7 +341,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
     for (uint32_t r0 = 0; r0 < ti.npix; r0 += kTilePix) {
-      const Pix P = load_pixels(ti, r0, warp, lane, V.width, px_list);
+      const int ox = (int)ti.tx * V.tile_w, oy = (int)ti.ty * V.tile_h;
+      const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
       BwdPix B[kPPT];
       int lane_last = -1;
@@ -363,7 +372,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
           const float gd = gscale * __ldg(ddepth + gp);
           if (gd != 0.f) {
             const float4 o0 = __ldg(out8 + 2 * gp), o1 = __ldg(out8 + 2 * gp + 1);
-            const float rx = (P.px[k] - V.cx) / V.fx, ry = (P.py[k] - V.cy) / V.fy;
+            const float rx = (P.px[k] + (float)ox - V.cx) / V.fx, ry = (P.py[k] + (float)oy - V.cy) / V.fy;
             const float sdot = -(o1.x * rx + o1.y * ry + o1.z);
             if (sdot > kRayDotMin && o0.w > 0.f) {
               const float is = 1.f / sdot;
@@ -390,7 +399,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
 #pragma unroll
         for (int u = 0; u < kStagePerThread; ++u) {
           const int slot = threadIdx.x + u * kRenderThreads;
-          if (slot < nb) stage(lo + slot, slot, dup_pairs, rec, S, spair);
+          if (slot < nb) stage(lo + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, spair);
         }
         __syncthreads();
         uint32_t rel[kBatch / 32];

@@ -71,8 +71,8 @@ __device__ __forceinline__ uint32_t next_tile(const Sched& s, uint32_t& iter, ui
 // Pixels of lane `lane` in warp `warp` for the round starting at r0: entries
 // r0 + (warp * kPPT + k) * 32 + lane of the tile's compacted pixel list, so a
 // warp covers kPPT consecutive 32-pixel runs.  Pixel centres are kept relative
-// to the tile origin (ox, oy), exactly, like the staged Gaussian centres, so
-// that offsets do not lose precision to the image size.
+// to an origin (ox, oy) near the tile, exactly, like the staged Gaussian
+// centres, so that offsets do not lose precision to the image size.
 struct Pix {
   bool has[kPPT];
   uint32_t pix[kPPT];
@@ -123,8 +123,8 @@ struct Stage {
   float4 g0[kBatch], g1[kBatch], g2[kBatch], g3[kBatch];
 };
 
-// The centre is staged relative to the tile origin: (integer part - origin) is
-// exact, then the fraction is added.
+// The centre is staged relative to the origin (ox, oy): (integer part - origin)
+// is exact, then the fraction is added.
 __device__ __forceinline__ void stage(uint32_t i, int slot, const uint32_t* __restrict__ dup_pairs,
                                       const float4* __restrict__ rec, float ox, float oy, Stage& S,
                                       uint32_t* spair) {
@@ -173,7 +173,10 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
     for (uint32_t r0 = 0; r0 < ti.npix; r0 += kTilePix) {
-      const int ox = (int)ti.tx * V.tile_w, oy = (int)ti.ty * V.tile_h;
+      // coordinate origin: the 32-pixel-aligned corner of the 32x32 cell holding
+      // the tile (every supported tile lies in one cell), so offsets round the
+      // same way whatever the tile size
+      const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
       const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
       float T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT], N0[kPPT], N1[kPPT], N2[kPPT];
@@ -341,7 +344,10 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
     for (uint32_t r0 = 0; r0 < ti.npix; r0 += kTilePix) {
-      const int ox = (int)ti.tx * V.tile_w, oy = (int)ti.ty * V.tile_h;
+      // coordinate origin: the 32-pixel-aligned corner of the 32x32 cell holding
+      // the tile (every supported tile lies in one cell), so offsets round the
+      // same way whatever the tile size
+      const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
       const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
       BwdPix B[kPPT];

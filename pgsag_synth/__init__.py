@@ -435,3 +435,17 @@ def densest_window(mask: np.ndarray, w: int, h: int, step: int = 64):
             if c > best:
                 best, arg = c, (x, y)
     return arg
+
+
+def hashed_uniform(index: np.ndarray, channel: int, seed: int = 0) -> np.ndarray:
+    """Deterministic pseudo-random values in [-1, 1) per (index, channel), from a
+    64-bit integer hash (splitmix64 finaliser) -- an upstream-gradient field that
+    can be evaluated at any subset of pixels."""
+    with np.errstate(over="ignore"):
+        x = (np.asarray(index, np.uint64) * np.uint64(8) + np.uint64(channel)
+             + np.uint64(seed) * np.uint64(0x9E3779B97F4A7C15))
+        x = x + np.uint64(0x9E3779B97F4A7C15)
+        x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        x = x ^ (x >> np.uint64(31))
+    return ((x >> np.uint64(40)).astype(np.float64) / float(1 << 24) * 2.0 - 1.0).astype(np.float32)

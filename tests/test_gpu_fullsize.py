@@ -1,0 +1,159 @@
+"""Parity at the full benchmark size (5472x3648 aerial view, 1.5M Gaussians,
+16x16 tiles, the launch configuration bench.py times): forward on seeded sampled
+rendered pixels against the oracle evaluated pixel by pixel; per-Gaussian
+gradients of <G, outputs> for a hashed upstream field G on sampled Gaussians
+(the oracle differentiates each one over its footprint); and the directional
+derivative of the fused loss along a random SH direction (colour only, so no
+alpha threshold moves) against its float64-accumulated central difference."""
+import numpy as np
+import pytest
+import torch
+
+import pgsag_synth as syn
+from oracle import pgsag_oracle as O
+from tests._helpers import FWD_TOL, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("means", "log_scales", "quats", "opacity_logit", "sh")
+
+
+@pytest.fixture(scope="module")
+def aerial():
+    from paper_2501_01677_b300 import raster
+    g, views, boxes = syn.config1()
+    v = views[0]
+    plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, tile=(16, 16))
+    cam = O.Cam.from_synth(v.cam)
+    pr = O.project(O.params_from_synth(g), cam, g.means)
+    pr = {k: (t.detach() if torch.is_tensor(t) else t) for k, t in pr.items()}
+    return g, v, plan, cam, pr
+
+
+def _oracle_pixels(pr, cam, pu, pv):
+    pi, gi = O.candidate_pairs(pr, cam.width, cam.height, pu, pv)
+    out = O.composite(pr, torch.as_tensor(pu), torch.as_tensor(pv), pi, gi)
+    dep, val = O.unbiased_depth(out, cam, torch.as_tensor(pu), torch.as_tensor(pv))
+    return out, dep, val
+
+
+def test_fullsize_forward_sampled_pixels(aerial):
+    from paper_2501_01677_b300 import raster
+    g, v, plan, cam, pr = aerial
+    P = raster.GaussianParams.from_numpy(g)
+    plan.forward(P)
+    torch.cuda.synchronize()
+    plan.check_status()
+    M, E, R = O.mask_sets(v.mask)
+    rng = np.random.default_rng(1)
+    rv, ru = np.nonzero(R)
+    pick = rng.choice(len(ru), 400, replace=False)
+    pu, pv = ru[pick], rv[pick]
+    out, dep, val = _oracle_pixels(pr, cam, pu, pv)
+    im = {k: t.cpu().numpy() for k, t in plan.images(0).items()}
+    ok = ~out["ambiguous"].numpy()
+    assert ok.mean() > 0.99
+    worst = 0.0
+    for k in ("rgb", "normal", "dist", "alpha"):
+        o = out[k].numpy().reshape(len(pu), -1)
+        gv = im[k][pv, pu].reshape(len(pu), -1)
+        S = out["mag"][k].numpy().reshape(len(pu), -1)
+        den = np.maximum(np.abs(o), S)
+        e = np.where(den > 0, np.abs(gv - o) / np.where(den > 0, den, 1), np.abs(gv - o) * 1e30)[ok]
+        worst = max(worst, float(e.max()))
+    assert worst <= FWD_TOL, worst
+    assert (im["n_contrib"][pv, pu][ok] == out["n_contrib"].numpy()[ok]).all()
+    vg = im["depth"][pv, pu] > 0
+    assert (vg[ok] == val.numpy()[ok]).all()
+    both = ok & vg
+    d_o = dep.numpy()[both]
+    assert (np.abs(im["depth"][pv, pu][both] - d_o) / d_o).max() < 1e-4
+    assert (im["n_contrib"][pv, pu] > 0).mean() > 0.5
+
+
+def test_fullsize_sampled_gaussian_gradients(aerial):
+    """Gradient of <G, out8> + <Gd, depth> w.r.t. sampled Gaussians' raw
+    parameters: CUDA (whole image) vs oracle (the Gaussian's footprint, every
+    Gaussian overlapping it, autograd through the sampled one)."""
+    from paper_2501_01677_b300 import raster
+    g, v, plan, cam, pr = aerial
+    H, W = cam.height, cam.width
+    lin_all = np.arange(H * W, dtype=np.int64)
+    G8 = np.stack([syn.hashed_uniform(lin_all, c, seed=5) for c in range(8)], 1)
+    Gd = syn.hashed_uniform(lin_all, 8, seed=5)
+    P = raster.GaussianParams.from_numpy(g, requires_grad=True)
+    out8, depth = raster.render(plan, P)
+    obj = (out8 * torch.from_numpy(G8).cuda()).sum() + (depth * torch.from_numpy(Gd).cuda()).sum()
+    obj.backward()
+    torch.cuda.synchronize()
+    plan.check_status()
+    gpu = {n: t.grad.cpu().numpy() for n, t in zip(NAMES, P.tensors())}
+    M, E, R = O.mask_sets(v.mask)
+    ok_rect, u0, u1, v0, v1 = O._ellipse_bbox(pr, pr["visible"])
+    u0, u1, v0, v1 = (t.numpy().astype(np.int64) for t in (u0, u1, v0, v1))
+    rng = np.random.default_rng(2)
+    # Gaussians with a moderate footprint inside the rendered set
+    area = (u1 - u0 + 1) * (v1 - v0 + 1)
+    cand = np.nonzero(ok_rect.numpy() & (area > 20) & (area < 400) & (u0 >= 0) & (v0 >= 0) & (u1 < W) & (v1 < H))[0]
+    rng.shuffle(cand)
+    checked = 0
+    for gi in cand:
+        if checked >= 8:
+            break
+        uu, vv = np.meshgrid(np.arange(u0[gi], u1[gi] + 1), np.arange(v0[gi], v1[gi] + 1))
+        uu, vv = uu.ravel(), vv.ravel()
+        inr = R[vv, uu]
+        if inr.sum() < 10:
+            continue
+        uu, vv = uu[inr], vv[inr]
+        # oracle: autograd through Gaussian gi only
+        p1 = {k: torch.tensor(np.asarray(getattr(g, k)[gi:gi + 1], np.float64), requires_grad=True) for k in NAMES}
+        pr1 = O.project(p1, cam, g.means[gi:gi + 1])
+        mix = {}
+        for k in ("mean2d", "conic", "opacity", "rgb", "normal", "dist"):
+            base = pr[k].clone()
+            mix[k] = torch.cat([base[:gi], pr1[k], base[gi + 1:]], 0)
+        for k in ("key", "visible", "flip_ambiguous", "cov2d"):
+            mix[k] = pr[k]
+        pi, gj = O.candidate_pairs(pr, W, H, uu, vv)
+        out = O.composite(mix, torch.as_tensor(uu), torch.as_tensor(vv), pi, gj)
+        if out["ambiguous"].any():
+            continue
+        dep, val = O.unbiased_depth(out, cam, torch.as_tensor(uu), torch.as_tensor(vv))
+        lin = vv * W + uu
+        g8 = torch.from_numpy(G8[lin].astype(np.float64))
+        gd = torch.from_numpy(Gd[lin].astype(np.float64))
+        o = (out["rgb"] * g8[:, 0:3]).sum() + (out["dist"] * g8[:, 3]).sum() + (out["normal"] * g8[:, 4:7]).sum() \
+            + (out["alpha"] * g8[:, 7]).sum() + (dep * gd).sum()
+        o.backward()
+        ref = np.concatenate([p1[k].grad.numpy().ravel() for k in NAMES])
+        got = np.concatenate([gpu[k][gi].ravel().astype(np.float64) for k in NAMES])
+        if np.linalg.norm(ref) == 0:
+            continue
+        assert rel_l2(got, ref) < 2e-3, (gi, rel_l2(got, ref))
+        checked += 1
+    assert checked >= 6
+
+
+def test_fullsize_loss_directional_derivative_sh(aerial):
+    from paper_2501_01677_b300 import raster
+    g, v, plan, cam, pr = aerial
+    P = raster.GaussianParams.from_numpy(g, requires_grad=True)
+    loss = raster.render_loss(plan, P)
+    loss.backward()
+    grad_sh = P.sh.grad.detach().double()
+    d = torch.from_numpy(np.random.default_rng(3).standard_normal(g.sh.shape).astype(np.float32)).cuda()
+    nm = float(plan.views_host[0].n_mask)
+
+    def L(eps):
+        Q = raster.GaussianParams(P.means.detach(), P.log_scales.detach(), P.quats.detach(),
+                                  P.opacity_logit.detach(), (P.sh.detach() + eps * d).contiguous())
+        plan.forward(Q)
+        plan.loss(O.LAMBDA_BAN)
+        a = plan.acc_loss.cpu().numpy()
+        return a[0] / (3.0 * nm) + O.LAMBDA_BAN * a[1] / a[2]
+
+    eps = 1e-5
+    fd = (L(eps) - L(-eps)) / (2 * eps)
+    an = float((grad_sh * d.double()).sum())
+    assert abs(fd - an) <= 1e-3 * abs(an), (fd, an)

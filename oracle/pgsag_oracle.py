@@ -233,7 +233,7 @@ def project(p: Dict[str, torch.Tensor], cam: Cam, means_f32: Optional[np.ndarray
     flip_amb = cosang < 1e-6
     return dict(mean2d=mean2d, conic=conic, cov2d=torch.stack([a, b, c], -1), opacity=o, rgb=rgb,
                 normal=n_c, dist=dist, key=torch.from_numpy(np.asarray(key, np.float32)),
-                visible=visible, flip_ambiguous=flip_amb, z=z)
+                visible=visible, flip_ambiguous=flip_amb, z=z, mc_norm=torch.linalg.norm(mc.detach(), dim=-1))
 
 
 # ---------------------------------------------------------------------------
@@ -316,8 +316,9 @@ def composite(pr, pu: torch.Tensor, pv: torch.Tensor, pair_pix: torch.Tensor, pa
 
     pair_pix indexes into (pu, pv).  Returns dict with rgb [P,3], dist D [P],
     normal N [P,3], alpha A [P], n_contrib [P] (long), ambiguous [P] (bool),
-    final_T [P], and mag: the magnitude sums sum_i w_i |x_i| of each channel,
-    which bound the rounding error of any evaluation of these sums."""
+    final_T [P], and mag: per channel the blended magnitude of the quantity's own
+    rounding scale (|c| for colour, |n| for normal components, |mu_c| for the
+    plane distance), which bounds the rounding error of any evaluation."""
     Pn = pu.shape[0]
     key = pr["key"].numpy()
     # order: pixel, then (depth key, gaussian index)
@@ -350,10 +351,14 @@ def composite(pr, pu: torch.Tensor, pv: torch.Tensor, pair_pix: torch.Tensor, pa
     C = torch.zeros(Pn, 3, dtype=DT)
     N = torch.zeros(Pn, 3, dtype=DT)
     D = torch.zeros(Pn, dtype=DT)
-    # magnitude sums sum_i w_i |x_i| of each blended channel (condition of the sums)
+    # magnitude sums sum_i w_i |x_i| of each blended channel: the scale of the
+    # rounding error of any evaluation of these sums.  A normal component is
+    # computed from a unit vector, so its error scales with |n| = 1; the plane
+    # distance d = -n . mu_c is a dot product, so its error scales with |mu_c|.
     magC = torch.zeros(Pn, 3, dtype=DT)
     magN = torch.zeros(Pn, 3, dtype=DT)
     magD = torch.zeros(Pn, dtype=DT)
+    mcn = pr["mc_norm"][gi]
     ncon = torch.zeros(Pn, dtype=torch.long)
     done = torch.zeros(Pn, dtype=torch.bool)
     col = pr["rgb"][gi]
@@ -374,8 +379,8 @@ def composite(pr, pu: torch.Tensor, pv: torch.Tensor, pair_pix: torch.Tensor, pa
         D = D + w * dst[:, j]
         wd = w.detach()
         magC = magC + wd[:, None] * col[:, j].detach().abs()
-        magN = magN + wd[:, None] * nor[:, j].detach().abs()
-        magD = magD + wd * dst[:, j].detach().abs()
+        magN = magN + wd[:, None] * torch.linalg.norm(nor[:, j].detach(), dim=-1, keepdim=True)
+        magD = magD + wd * mcn[:, j]
         T = torch.where(blend, test, T)
         ncon = ncon + blend.long()
     return dict(rgb=C, normal=N, dist=D, alpha=1.0 - T, final_T=T, n_contrib=ncon, ambiguous=amb,

@@ -2,9 +2,11 @@
 the same seeded inputs and compare with the tolerances the method fixes.
 
 Forward tolerance (per pixel and channel): |g - o| / max(|o|, S) <= 1e-4 with
-S = sum_i w_i |x_i| the magnitude sum of the blended terms (a floating-point sum
-has error bounded relative to S, not to |sum|: the normal channel has sign
-cancellation), over pixels the oracle does not flag as ambiguous (a float32
+S = sum_i w_i s_i the blended rounding scale of the terms (s = |c| for colour,
+|n| = 1 for normal components, |mu_c| for the plane distance d = -n . mu_c): a
+floating-point sum of products has error bounded relative to S, not to |sum|
+(normal components cancel, d cancels for planes seen edge-on), over pixels the
+oracle does not flag as ambiguous (a float32
 threshold decision within 3e-5 relative of alpha = 1/255 or T(1-alpha) = 1e-4,
 or a normal flip within 1e-6 of edge-on).  Gradient tolerance: relative L2 per
 parameter tensor <= 1e-3.

@@ -153,7 +153,10 @@ def test_fullsize_loss_directional_derivative_sh(aerial):
         a = plan.acc_loss.cpu().numpy()
         return a[0] / (3.0 * nm) + O.LAMBDA_BAN * a[1] / a[2]
 
-    eps = 1e-5
+    # eps = 1e-3: the float32 per-chunk partial sums add ~4e-11 noise to L, so the
+    # difference must be well above it; colour-only steps move no alpha threshold
+    # and cross ~2e-4 of the L1 kinks |C - C*| = 0
+    eps = 1e-3
     fd = (L(eps) - L(-eps)) / (2 * eps)
     an = float((grad_sh * d.double()).sum())
     assert abs(fd - an) <= 1e-3 * abs(an), (fd, an)

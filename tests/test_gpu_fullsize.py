@@ -113,7 +113,7 @@ def test_fullsize_sampled_gaussian_gradients(aerial):
         for k in ("mean2d", "conic", "opacity", "rgb", "normal", "dist"):
             base = pr[k].clone()
             mix[k] = torch.cat([base[:gi], pr1[k], base[gi + 1:]], 0)
-        for k in ("key", "visible", "flip_ambiguous", "cov2d"):
+        for k in ("key", "visible", "flip_ambiguous", "cov2d", "mc_norm"):
             mix[k] = pr[k]
         pi, gj = O.candidate_pairs(pr, W, H, uu, vv)
         out = O.composite(mix, torch.as_tensor(uu), torch.as_tensor(vv), pi, gj)
@@ -136,13 +136,18 @@ def test_fullsize_sampled_gaussian_gradients(aerial):
 
 
 def test_fullsize_loss_directional_derivative_sh(aerial):
+    """Central difference of the fused loss along d = sign(dL/dsh) against
+    sum |dL/dsh|.  Colour-only steps move no alpha threshold; the L1 kinks
+    |C - C*| = 0 crossed by the step bias the difference by at most the crossed
+    fraction (~1e-3), and the signal has no cancellation (unlike a random
+    direction, whose derivative is a small residual of random-sign terms)."""
     from paper_2501_01677_b300 import raster
     g, v, plan, cam, pr = aerial
     P = raster.GaussianParams.from_numpy(g, requires_grad=True)
     loss = raster.render_loss(plan, P)
     loss.backward()
-    grad_sh = P.sh.grad.detach().double()
-    d = torch.from_numpy(np.random.default_rng(3).standard_normal(g.sh.shape).astype(np.float32)).cuda()
+    grad_sh = P.sh.grad.detach()
+    d = torch.sign(grad_sh)
     nm = float(plan.views_host[0].n_mask)
 
     def L(eps):
@@ -153,10 +158,7 @@ def test_fullsize_loss_directional_derivative_sh(aerial):
         a = plan.acc_loss.cpu().numpy()
         return a[0] / (3.0 * nm) + O.LAMBDA_BAN * a[1] / a[2]
 
-    # eps = 1e-3: the float32 per-chunk partial sums add ~4e-11 noise to L, so the
-    # difference must be well above it; colour-only steps move no alpha threshold
-    # and cross ~2e-4 of the L1 kinks |C - C*| = 0
-    eps = 1e-3
+    eps = 1e-4
     fd = (L(eps) - L(-eps)) / (2 * eps)
-    an = float((grad_sh * d.double()).sum())
-    assert abs(fd - an) <= 1e-3 * abs(an), (fd, an)
+    an = float(grad_sh.double().abs().sum())
+    assert abs(fd - an) <= 2e-3 * an, (fd, an)

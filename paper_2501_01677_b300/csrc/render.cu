@@ -16,12 +16,35 @@
 
 namespace pgsag {
 
-constexpr int kRenderWarps = 4;                   // warps per CTA (one CTA per active tile)
-constexpr int kRenderThreads = kRenderWarps * 32;
-constexpr int kPPT = 2;                           // pixels per lane
-constexpr int kTilePix = kRenderThreads * kPPT;   // pixels per CTA round
-constexpr int kBatch = 256;                       // Gaussians staged per batch
-constexpr int kStagePerThread = kBatch / kRenderThreads;
+// Launch shape (compile-time; the defaults are the measured best on B300):
+// warps per CTA (one CTA per active tile), pixels per lane, and the largest
+// number of contributing lanes for which the adjoint adds a Gaussian's
+// gradient to shared memory lane by lane instead of reducing across the warp.
+#ifndef PGSAG_FWD_WARPS
+#define PGSAG_FWD_WARPS 4
+#endif
+#ifndef PGSAG_FWD_PPT
+#define PGSAG_FWD_PPT 2
+#endif
+#ifndef PGSAG_BWD_WARPS
+#define PGSAG_BWD_WARPS 4
+#endif
+#ifndef PGSAG_BWD_PPT
+#define PGSAG_BWD_PPT 2
+#endif
+#ifndef PGSAG_BWD_DIRECT
+#define PGSAG_BWD_DIRECT 0
+#endif
+#ifndef PGSAG_BATCH
+#define PGSAG_BATCH 256
+#endif
+#ifndef PGSAG_FWD_MINB
+#define PGSAG_FWD_MINB 1
+#endif
+#ifndef PGSAG_BWD_MINB
+#define PGSAG_BWD_MINB 1
+#endif
+constexpr int kBatch = PGSAG_BATCH;  // Gaussians staged per batch
 
 struct TileInfo {
   uint32_t view, tx, ty, px_first, npix, rbeg, rend;
@@ -73,15 +96,17 @@ __device__ __forceinline__ uint32_t next_tile(const Sched& s, uint32_t& iter, ui
 // warp covers kPPT consecutive 32-pixel runs.  Pixel centres are kept relative
 // to an origin (ox, oy) near the tile, exactly, like the staged Gaussian
 // centres, so that offsets do not lose precision to the image size.
+template <int kPPT>
 struct Pix {
   bool has[kPPT];
   uint32_t pix[kPPT];
   float px[kPPT], py[kPPT];  // centre minus tile origin
 };
 
-__device__ __forceinline__ Pix load_pixels(const TileInfo& ti, uint32_t r0, int warp, int lane, int width, int ox,
-                                           int oy, const uint32_t* __restrict__ px_list) {
-  Pix P;
+template <int kPPT>
+__device__ __forceinline__ Pix<kPPT> load_pixels(const TileInfo& ti, uint32_t r0, int warp, int lane, int width,
+                                                 int ox, int oy, const uint32_t* __restrict__ px_list) {
+  Pix<kPPT> P;
 #pragma unroll
   for (int k = 0; k < kPPT; ++k) {
     const uint32_t li = r0 + (uint32_t)((warp * kPPT + k) * 32 + lane);
@@ -95,7 +120,8 @@ __device__ __forceinline__ Pix load_pixels(const TileInfo& ti, uint32_t r0, int 
 }
 
 // Bounding box of the warp's valid pixel centres (warp-uniform result).
-__device__ __forceinline__ float4 warp_pixel_box(const Pix& P) {
+template <int kPPT>
+__device__ __forceinline__ float4 warp_pixel_box(const Pix<kPPT>& P) {
   float x0 = 3.0e38f, x1 = -3.0e38f, y0 = 3.0e38f, y1 = -3.0e38f;
 #pragma unroll
   for (int k = 0; k < kPPT; ++k) {
@@ -156,12 +182,16 @@ __device__ __forceinline__ void warp_relevance(const Stage& S, int limit, float4
   }
 }
 
-__global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
+template <int kWarps, int kPPT>
+__global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
     const pgsag_view* __restrict__ views, const float4* __restrict__ rec,
     const uint32_t* __restrict__ dup_pairs, const uint2* __restrict__ ranges,
     const uint4* __restrict__ act_tiles, uint32_t n_items, const uint32_t* __restrict__ px_list,
     Sched sched, float4* __restrict__ out8, float* __restrict__ depth, uint4* __restrict__ aux,
     const int32_t* status) {
+  constexpr int kRenderThreads = kWarps * 32;
+  constexpr int kTilePix = kRenderThreads * kPPT;
+  constexpr int kStagePerThread = kBatch / kRenderThreads;
   __shared__ Stage S;
   __shared__ uint32_t s_item;
   if (status_bad(status)) return;
@@ -177,7 +207,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(
       // the tile (every supported tile lies in one cell), so offsets round the
       // same way whatever the tile size
       const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
-      const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
+      const Pix<kPPT> P = load_pixels<kPPT>(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
       float T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT], N0[kPPT], N1[kPPT], N2[kPPT];
       uint32_t last[kPPT], cnt[kPPT];
@@ -320,13 +350,17 @@ struct BwdPix {
   float SC0, SC1, SC2, SN0, SN1, SN2, SD;
 };
 
-__global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
+template <int kWarps, int kPPT, int kDirect>
+__global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     const pgsag_view* __restrict__ views, const float4* __restrict__ rec,
     const uint32_t* __restrict__ dup_pairs, const uint2* __restrict__ ranges,
     const uint4* __restrict__ act_tiles, uint32_t n_items, const uint32_t* __restrict__ px_list,
     Sched sched, const float4* __restrict__ out8, const uint4* __restrict__ aux,
     const float4* __restrict__ dout8, const float* __restrict__ ddepth, const float* __restrict__ dout_scale,
     float* __restrict__ grad2d, const int32_t* status) {
+  constexpr int kRenderThreads = kWarps * 32;
+  constexpr int kTilePix = kRenderThreads * kPPT;
+  constexpr int kStagePerThread = kBatch / kRenderThreads;
   __shared__ Stage S;
   __shared__ uint32_t spair[kBatch];
   __shared__ float4 sacc[kBatch][4];
@@ -348,7 +382,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
       // the tile (every supported tile lies in one cell), so offsets round the
       // same way whatever the tile size
       const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
-      const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
+      const Pix<kPPT> P = load_pixels<kPPT>(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
       BwdPix B[kPPT];
       int lane_last = -1;
@@ -476,7 +510,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_bwd(
           const uint32_t cm = __ballot_sync(kFull, ncontrib > 0);
           if (cm) {
             float* acc = reinterpret_cast<float*>(sacc[j]);
-            if (__popc(cm) <= 4) {
+            if (__popc(cm) <= kDirect) {
               // few contributing lanes: add their values directly
               if (ncontrib > 0) {
 #pragma unroll
@@ -547,7 +581,7 @@ extern "C" int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const
   if (r) return r;
   cudaStream_t st = (cudaStream_t)stream;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
-  k_render_fwd<<<blocks, kRenderThreads, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
+  k_render_fwd<PGSAG_FWD_WARPS, PGSAG_FWD_PPT><<<blocks, PGSAG_FWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
                                                   (const uint4*)act_tiles, n_active, px_list, s, (float4*)out8, depth,
                                                   (uint4*)aux, status);
   PGSAG_CHECK_LAUNCH();
@@ -576,7 +610,7 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
   int r = launch_cfg(sched, n_active, s, blocks);
   if (r) return r;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
-  k_render_bwd<<<blocks, kRenderThreads, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
+  k_render_bwd<PGSAG_BWD_WARPS, PGSAG_BWD_PPT, PGSAG_BWD_DIRECT><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
                                                   (const uint4*)act_tiles, n_active, px_list, s, (const float4*)out8,
                                                   (const uint4*)aux, (const float4*)dout8, ddepth, dout_scale, grad2d,
                                                   status);

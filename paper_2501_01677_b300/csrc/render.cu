@@ -16,10 +16,13 @@
 
 namespace pgsag {
 
-// Launch shape (compile-time; the defaults are the measured best on B300):
-// warps per CTA (one CTA per active tile), pixels per lane, and the largest
-// number of contributing lanes for which the adjoint adds a Gaussian's
-// gradient to shared memory lane by lane instead of reducing across the warp.
+// Launch shape (compile-time; the defaults are the best measured on B300 for the
+// 5472x3648 aerial workload): warps per CTA (one CTA per active tile), pixels
+// per lane, Gaussians staged per batch, the number of resident CTAs per SM the
+// register allocation must allow (forward 10, adjoint 7), and the largest number
+// of contributing lanes for which the adjoint adds a Gaussian's gradient to
+// shared memory lane by lane instead of reducing across the warp (0: always
+// reduce).
 #ifndef PGSAG_FWD_WARPS
 #define PGSAG_FWD_WARPS 4
 #endif
@@ -36,13 +39,13 @@ namespace pgsag {
 #define PGSAG_BWD_DIRECT 0
 #endif
 #ifndef PGSAG_BATCH
-#define PGSAG_BATCH 256
+#define PGSAG_BATCH 128
 #endif
 #ifndef PGSAG_FWD_MINB
-#define PGSAG_FWD_MINB 1
+#define PGSAG_FWD_MINB 10  // resident CTAs per SM the register budget must allow
 #endif
 #ifndef PGSAG_BWD_MINB
-#define PGSAG_BWD_MINB 1
+#define PGSAG_BWD_MINB 7
 #endif
 constexpr int kBatch = PGSAG_BATCH;  // Gaussians staged per batch
 
@@ -192,6 +195,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
   constexpr int kRenderThreads = kWarps * 32;
   constexpr int kTilePix = kRenderThreads * kPPT;
   constexpr int kStagePerThread = kBatch / kRenderThreads;
+  static_assert(kBatch % kRenderThreads == 0 && kStagePerThread >= 1, "batch must be a multiple of the CTA size");
   __shared__ Stage S;
   __shared__ uint32_t s_item;
   if (status_bad(status)) return;
@@ -361,6 +365,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
   constexpr int kRenderThreads = kWarps * 32;
   constexpr int kTilePix = kRenderThreads * kPPT;
   constexpr int kStagePerThread = kBatch / kRenderThreads;
+  static_assert(kBatch % kRenderThreads == 0 && kStagePerThread >= 1, "batch must be a multiple of the CTA size");
   __shared__ Stage S;
   __shared__ uint32_t spair[kBatch];
   __shared__ float4 sacc[kBatch][4];

@@ -86,18 +86,26 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
       if (inV) {
         const int nx[4] = {P.x, P.x, P.x - 1, P.x + 1};
         const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
+        // independent loads (the dense per-view arrays cover every in-image
+        // pixel); a neighbour's depth is used only if it is rendered
+        uint8_t fq[4];
+        float dq[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint64_t q = P.V.pix_base + (uint64_t)ny[k] * W + nx[k];
-          const uint8_t fq = __ldg(flags + q);
-          float dq = 0.f;
-          if (fq & PGSAG_PIX_RENDER) dq = __ldg(depth + q);
-          inV = inV && (fq & PGSAG_PIX_RENDER) && dq > 0.f;
+          fq[k] = __ldg(flags + q);
+          dq[k] = __ldg(depth + q);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool rk = (fq[k] & PGSAG_PIX_RENDER) != 0;
+          const float d = rk ? dq[k] : 0.f;
+          inV = inV && rk && d > 0.f;
           float r[3];
           ray(P.V, nx[k], ny[k], r);
-          Pn[k][0] = dq * r[0];
-          Pn[k][1] = dq * r[1];
-          Pn[k][2] = dq * r[2];
+          Pn[k][0] = d * r[0];
+          Pn[k][1] = d * r[1];
+          Pn[k][2] = d * r[2];
         }
       }
       if (inV) {
@@ -206,15 +214,28 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_b(
   const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
   const float sg[4] = {1.f, -1.f, 1.f, -1.f};
   const int off[4] = {0, 0, 3, 3};
+  // independent loads of the in-image neighbours' flags and scratch; a
+  // neighbour contributes only if it is a mask pixel (its scratch is written)
+  uint8_t fq[4];
+  float sv[4][3];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
+    fq[k] = 0;
+    sv[k][0] = sv[k][1] = sv[k][2] = 0.f;
     if (nx[k] < 0 || nx[k] >= W || ny[k] < 0 || ny[k] >= H) continue;
     const uint64_t q = P.V.pix_base + (uint64_t)ny[k] * W + nx[k];
-    if (!(__ldg(flags + q) & PGSAG_PIX_MASK)) continue;
+    fq[k] = __ldg(flags + q);
     const float* sc = scratch + 6 * q + off[k];
-    dP[0] += sg[k] * __ldg(sc + 0);
-    dP[1] += sg[k] * __ldg(sc + 1);
-    dP[2] += sg[k] * __ldg(sc + 2);
+    sv[k][0] = __ldg(sc + 0);
+    sv[k][1] = __ldg(sc + 1);
+    sv[k][2] = __ldg(sc + 2);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!(fq[k] & PGSAG_PIX_MASK)) continue;
+    dP[0] += sg[k] * sv[k][0];
+    dP[1] += sg[k] * sv[k][1];
+    dP[2] += sg[k] * sv[k][2];
   }
   float4 g1 = dout8[2 * P.gp + 1];
   float dD = 0.f, dN[3] = {0.f, 0.f, 0.f};

@@ -293,7 +293,32 @@ __device__ __forceinline__ bool pair_forward(const pgsag_view& V, const GaussIn&
   return true;
 }
 
-__global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
+// SH coefficients of a block's Gaussians staged in shared memory: coalesced
+// float4 loads of the block's contiguous [nb, 48] slab, stored with a row
+// stride of 49 floats so that thread t reading row t hits distinct banks.
+constexpr int kPreThreads = 128;
+constexpr int kShStride = 49;
+constexpr size_t kShSlabBytes = (size_t)kPreThreads * kShStride * sizeof(float);
+
+__host__ __device__ __forceinline__ size_t views_bytes(uint32_t n_views) {
+  return ((size_t)n_views * sizeof(pgsag_view) + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ void stage_sh(const float* __restrict__ sh, uint32_t g0, uint32_t n, float* s_sh) {
+  const uint32_t nb = min((uint32_t)kPreThreads, n - g0);
+  const float4* src = reinterpret_cast<const float4*>(sh + 48ull * g0);
+  for (uint32_t i = threadIdx.x; i < nb * 12; i += blockDim.x) {
+    const float4 v = __ldg(src + i);
+    const uint32_t e = 4 * i, row = e / 48, col = e - row * 48;
+    float* d = s_sh + row * kShStride + col;
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
+  }
+}
+
+__global__ void __launch_bounds__(kPreThreads) k_preprocess(uint32_t n, const float* __restrict__ means,
                              const float* __restrict__ log_scales, const float* __restrict__ quats,
                              const float* __restrict__ opacity_logit, const float* __restrict__ sh,
                              uint32_t n_views, const pgsag_view* __restrict__ views,
@@ -308,14 +333,16 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
     uint32_t* dst = reinterpret_cast<uint32_t*>(smem_raw);
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   }
+  float* s_sh = reinterpret_cast<float*>(smem_raw + views_bytes(n_views));
+  if (status_bad(status)) return;
+  stage_sh(sh, blockIdx.x * blockDim.x, n, s_sh);
   __syncthreads();
   set_campos(sv, n_views);
   __syncthreads();
-  if (status_bad(status)) return;
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
   const GaussIn G = load_gauss(g, means, log_scales, quats, opacity_logit);
-  const float* shg = sh + 48ull * g;
+  const float* shg = s_sh + threadIdx.x * kShStride;
   for (uint32_t vi = 0; vi < n_views; ++vi) {
     const pgsag_view& V = sv[vi];
     if (g < V.g_begin || g >= V.g_end) continue;
@@ -392,9 +419,9 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
     float col[3] = {kShOffset, kShOffset, kShOffset};
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      col[0] += Y[k] * __ldg(shg + 3 * k + 0);
-      col[1] += Y[k] * __ldg(shg + 3 * k + 1);
-      col[2] += Y[k] * __ldg(shg + 3 * k + 2);
+      col[0] += Y[k] * shg[3 * k + 0];
+      col[1] += Y[k] * shg[3 * k + 1];
+      col[2] += Y[k] * shg[3 * k + 2];
     }
     R4[0] = make_float4(mi, ni, P.l11, P.l21);
     R4[1] = make_float4(P.l22, P.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
@@ -407,7 +434,8 @@ __global__ void k_preprocess(uint32_t n, const float* __restrict__ means,
 }
 
 // Adjoint of pair_forward + colour, accumulating into the raw-parameter gradients.
-__global__ void k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
+// SH coefficients and their gradients live in shared memory (coalesced in and out).
+__global__ void __launch_bounds__(kPreThreads) k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
                                  const float* __restrict__ log_scales,
                                  const float* __restrict__ quats,
                                  const float* __restrict__ opacity_logit,
@@ -426,21 +454,24 @@ __global__ void k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
     uint32_t* dst = reinterpret_cast<uint32_t*>(smem_raw);
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   }
+  // dynamic shared memory: [view table | SH slab | SH gradient slab]
+  float* s_sh = reinterpret_cast<float*>(smem_raw + views_bytes(n_views));
+  float* s_gsh = s_sh + kPreThreads * kShStride;
+  if (status_bad(status)) return;
+  const uint32_t g0 = blockIdx.x * blockDim.x;
+  stage_sh(sh, g0, n, s_sh);
+  for (int i = threadIdx.x; i < kPreThreads * kShStride; i += blockDim.x) s_gsh[i] = 0.f;
   __syncthreads();
   set_campos(sv, n_views);
   __syncthreads();
-  if (status_bad(status)) return;
-  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  const GaussIn G = load_gauss(g, means, log_scales, quats, opacity_logit);
-  const float* shg = sh + 48ull * g;
-
+  const uint32_t g = g0 + threadIdx.x;
   float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gol = 0.f;
-  float gsh[48];
-#pragma unroll
-  for (int i = 0; i < 48; ++i) gsh[i] = 0.f;
+  const float* shv = s_sh + threadIdx.x * kShStride;
+  float* gsh = s_gsh + threadIdx.x * kShStride;
+  const GaussIn G = g < n ? load_gauss(g, means, log_scales, quats, opacity_logit) : GaussIn{};
+  const uint32_t vcount = g < n ? n_views : 0u;
 
-  for (uint32_t vi = 0; vi < n_views; ++vi) {
+  for (uint32_t vi = 0; vi < vcount; ++vi) {
     const pgsag_view& V = sv[vi];
     if (g < V.g_begin || g >= V.g_end) continue;
     const uint32_t p = V.pair_base + (g - V.g_begin);
@@ -470,9 +501,6 @@ __global__ void k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
       float Y[16];
       sh_eval(dx, dy, dz, Y);
       float raw[3] = {kShOffset, kShOffset, kShOffset};
-      float shv[48];
-#pragma unroll
-      for (int k = 0; k < 48; ++k) shv[k] = __ldg(shg + k);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         raw[0] += Y[k] * shv[3 * k + 0];
@@ -608,41 +636,47 @@ __global__ void k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
     for (int j = 0; j < 3; ++j) gm[j] += V.R[0 * 3 + j] * dmc[0] + V.R[1 * 3 + j] * dmc[1] + V.R[2 * 3 + j] * dmc[2];
   }
 
-  if (accumulate) {
+  if (g < n) {
+    if (accumulate) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      d_means[3ull * g + i] += gm[i];
-      d_log_scales[3ull * g + i] += gls[i];
+      for (int i = 0; i < 3; ++i) {
+        d_means[3ull * g + i] += gm[i];
+        d_log_scales[3ull * g + i] += gls[i];
+      }
+      float4* q4 = reinterpret_cast<float4*>(d_quats) + g;
+      float4 o = *q4;
+      o.x += gq[0];
+      o.y += gq[1];
+      o.z += gq[2];
+      o.w += gq[3];
+      *q4 = o;
+      d_opac[g] += gol;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        d_means[3ull * g + i] = gm[i];
+        d_log_scales[3ull * g + i] = gls[i];
+      }
+      reinterpret_cast<float4*>(d_quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+      d_opac[g] = gol;
     }
-    float4* q4 = reinterpret_cast<float4*>(d_quats) + g;
-    float4 o = *q4;
-    o.x += gq[0];
-    o.y += gq[1];
-    o.z += gq[2];
-    o.w += gq[3];
-    *q4 = o;
-    d_opac[g] += gol;
-    float4* s4 = reinterpret_cast<float4*>(d_sh + 48ull * g);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      float4 t = s4[i];
-      t.x += gsh[4 * i + 0];
-      t.y += gsh[4 * i + 1];
-      t.z += gsh[4 * i + 2];
-      t.w += gsh[4 * i + 3];
-      s4[i] = t;
+  }
+  // SH gradients: coalesced float4 stores of the block's [nb, 48] slab
+  __syncthreads();
+  const uint32_t nb = min((uint32_t)kPreThreads, n - g0);
+  float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * g0);
+  for (uint32_t i = threadIdx.x; i < nb * 12; i += blockDim.x) {
+    const uint32_t e = 4 * i, row = e / 48, col = e - row * 48;
+    const float* sg = s_gsh + row * kShStride + col;
+    float4 v = make_float4(sg[0], sg[1], sg[2], sg[3]);
+    if (accumulate) {
+      const float4 o = dst[i];
+      v.x += o.x;
+      v.y += o.y;
+      v.z += o.z;
+      v.w += o.w;
     }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      d_means[3ull * g + i] = gm[i];
-      d_log_scales[3ull * g + i] = gls[i];
-    }
-    reinterpret_cast<float4*>(d_quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-    d_opac[g] = gol;
-    float4* s4 = reinterpret_cast<float4*>(d_sh + 48ull * g);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) s4[i] = make_float4(gsh[4 * i + 0], gsh[4 * i + 1], gsh[4 * i + 2], gsh[4 * i + 3]);
+    dst[i] = v;
   }
 }
 
@@ -664,12 +698,11 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
     return PGSAG_ERR_ARG;
   if (!aligned16(quats) || !aligned16(rec) || !aligned16(bininfo)) return PGSAG_ERR_ARG;
   PGSAG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream));
-  const unsigned threads = 128;
-  const size_t smem = (size_t)n_views * sizeof(pgsag_view);
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return PGSAG_ERR_CUDA;
-  }
+  const unsigned threads = kPreThreads;
+  const size_t smem = views_bytes(n_views) + kShSlabBytes;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return PGSAG_ERR_CUDA;
   k_preprocess<<<pgsag_div_up(n_gauss, threads), threads, smem, (cudaStream_t)stream>>>(
       n_gauss, means, log_scales, quats, opacity_logit, sh, n_views, views, tile_act, sat,
       reinterpret_cast<float4*>(rec), depth_key, reinterpret_cast<uint4*>(bininfo), status);
@@ -691,13 +724,10 @@ extern "C" int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const 
     return PGSAG_ERR_ARG;
   if (!aligned16(quats) || !aligned16(d_quats) || !aligned16(d_sh) || !aligned16(grad2d) || !aligned16(bininfo))
     return PGSAG_ERR_ARG;
-  const unsigned threads = 128;
-  const size_t smem = (size_t)n_views * sizeof(pgsag_view);
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_preprocess_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return PGSAG_ERR_CUDA;
-  }
+  const unsigned threads = kPreThreads;
+  const size_t smem = views_bytes(n_views) + 2 * kShSlabBytes;  // > 48 KB: opt in
+  if (cudaFuncSetAttribute(k_preprocess_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return PGSAG_ERR_CUDA;
   k_preprocess_bwd<<<pgsag_div_up(n_gauss, threads), threads, smem, (cudaStream_t)stream>>>(
       n_gauss, means, log_scales, quats, opacity_logit, sh, n_views, views,
       reinterpret_cast<const uint4*>(bininfo), grad2d, accumulate, d_means, d_log_scales, d_quats,

@@ -260,22 +260,13 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
  *   depth float [1 per pixel]
  *   aux   uint4 [1 per pixel]: {float bits of final T, index (into dup_pairs) of the
  *         last blended Gaussian, number blended n_contrib, 0}
- *   contrib  uint32 [pgsag_contrib_words(capacity)]: per warp of 64 compacted
- *         pixels of a tile, one bit per duplicate that was blended into at least
- *         one of its pixels (bit i % 32 of word (i / 32) * 16 + warp slot); zeroed
- *         and filled by this call, read by pgsag_render_bwd to skip the
- *         duplicates that contributed nothing (a culling mask, not a per-pixel
- *         list: the adjoint still recomputes alpha and transmittance)
- *   capacity  the duplicate capacity given to pgsag_bin
  * sched may be NULL (one CTA per active tile in index order); with a counter the
  * launch is persistent (ctas_per_sm x SMs CTAs pulling tiles, in `order` if given).
  */
-size_t pgsag_contrib_words(uint64_t capacity);
 int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec,
                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
                      uint32_t n_active_total, const uint32_t* px_list, const pgsag_sched* sched,
-                     float* out8, float* depth, void* aux, uint32_t* contrib, uint64_t capacity,
-                     int32_t* status, void* stream);
+                     float* out8, float* depth, void* aux, int32_t* status, void* stream);
 
 /*
  * pgsag_loss_ban (Sec. 4.2, Eq. 8; photometric L1 term of Eq. 10).  Per view v:
@@ -305,8 +296,7 @@ int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
 /*
  * pgsag_render_bwd (Sec. 3.1: "optimized ... using differentiable rendering").
  * Adjoint of pgsag_render_fwd: each CTA re-traverses its tile's list back to
- * front from the last blended Gaussian (each warp visiting only the duplicates
- * the forward's contribution mask marks for it), recovering T by division
+ * front from the last blended Gaussian, recovering T by division
  * (T_i = T_{i+1} / (1 - alpha_i)), and accumulates per pair
  *   grad2d[p*16 + {0..12}] = dL/d{mx, my, l11, l21, l22, o, r, g, b, d, nx, ny, nz}
  * (warp shuffle reduction, shared-memory sum over the CTA's warps, then one
@@ -319,8 +309,8 @@ int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec
                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
                      uint32_t n_active_total, const uint32_t* px_list, const pgsag_sched* sched,
                      const float* out8, const void* aux, const float* dout8, const float* ddepth,
-                     const float* dout_scale, const uint32_t* contrib, uint32_t n_pairs,
-                     float* grad2d, int32_t* status, void* stream);
+                     const float* dout_scale, uint32_t n_pairs, float* grad2d, int32_t* status,
+                     void* stream);
 
 /*
  * pgsag_preprocess_bwd: chain rule from grad2d to the raw parameters (the

@@ -23,8 +23,7 @@ NOALLOC_MAX_CHUNKS = 1 << 20
 # Every entry point declared in include/pgsag.h
 EXPORTS = (
     "pgsag_status_str", "pgsag_build_info", "pgsag_prep_flags", "pgsag_prep_lists", "pgsag_prep_gc_weight",
-    "pgsag_preprocess", "pgsag_bin_workspace_size", "pgsag_bin", "pgsag_contrib_words", "pgsag_render_fwd",
-    "pgsag_loss_ban",
+    "pgsag_preprocess", "pgsag_bin_workspace_size", "pgsag_bin", "pgsag_render_fwd", "pgsag_loss_ban",
     "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_tile_stats_noalloc",
     "pgsag_schedule_lpt", "pgsag_adam",
 )
@@ -76,12 +75,10 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_preprocess", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_bin_workspace_size", c_size_t, [c_uint32, c_uint64])
     _sig(lib, "pgsag_bin", c_int, [c_uint32, c_uint32, P, c_uint32, P, P, P, P, c_uint64, P, c_size_t, P, P, P, P, P])
-    _sig(lib, "pgsag_contrib_words", c_size_t, [c_uint64])
-    _sig(lib, "pgsag_render_fwd", c_int,
-         [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, c_uint64, P, P])
+    _sig(lib, "pgsag_render_fwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P])
     _sig(lib, "pgsag_loss_ban", c_int, [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, c_float, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_render_bwd", c_int,
-         [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P, P, c_uint32, P, P, P])
+         [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P, c_uint32, P, P, P])
     _sig(lib, "pgsag_preprocess_bwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_tile_stats_noalloc", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P])

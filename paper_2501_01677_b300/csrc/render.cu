@@ -47,9 +47,6 @@ namespace pgsag {
 #ifndef PGSAG_BWD_MINB
 #define PGSAG_BWD_MINB 7
 #endif
-#ifndef PGSAG_CONTRIB_SLOTS
-#define PGSAG_CONTRIB_SLOTS 16  // warp slots per tile: 1024 pixels / (32 lanes x 2 pixels)
-#endif
 constexpr int kBatch = PGSAG_BATCH;  // Gaussians staged per batch
 
 struct TileInfo {
@@ -170,29 +167,6 @@ __device__ __forceinline__ void stage(uint32_t i, int slot, const uint32_t* __re
   if (spair) spair[slot] = p;
 }
 
-// Contribution masks: bit i % 32 of word (i / 32) * kContribSlots + slot is set
-// when duplicate i (a position in the sorted list) was blended into at least one
-// pixel of warp slot `slot` of its tile (slot = round * warps + warp).  The
-// forward records them; the adjoint visits only those duplicates.
-constexpr int kContribSlots = PGSAG_CONTRIB_SLOTS;
-
-__device__ __forceinline__ void record_contrib(uint32_t* contrib, uint32_t first, int slot, uint32_t bits) {
-  const uint32_t w = first >> 5, off = first & 31u;
-  atomicOr(contrib + (size_t)w * kContribSlots + slot, bits << off);
-  if (off) {
-    const uint32_t hi = bits >> (32u - off);
-    if (hi) atomicOr(contrib + (size_t)(w + 1) * kContribSlots + slot, hi);
-  }
-}
-
-// The 32 bits of duplicates [first, first + 32) of a slot.
-__device__ __forceinline__ uint32_t load_contrib(const uint32_t* __restrict__ contrib, uint32_t first, int slot) {
-  const uint32_t w = first >> 5, off = first & 31u;
-  uint32_t v = __ldg(contrib + (size_t)w * kContribSlots + slot) >> off;
-  if (off) v |= __ldg(contrib + (size_t)(w + 1) * kContribSlots + slot) << (32u - off);
-  return v;
-}
-
 // Relevance of staged Gaussians c*32 + lane (c < kBatch/32) to the warp's pixel
 // rectangle: one ellipse-rectangle test per lane, one ballot per 32 Gaussians.
 // Bits beyond `limit` (exclusive) are cleared.
@@ -217,12 +191,11 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
     const uint32_t* __restrict__ dup_pairs, const uint2* __restrict__ ranges,
     const uint4* __restrict__ act_tiles, uint32_t n_items, const uint32_t* __restrict__ px_list,
     Sched sched, float4* __restrict__ out8, float* __restrict__ depth, uint4* __restrict__ aux,
-    uint32_t* __restrict__ contrib, const int32_t* status) {
+    const int32_t* status) {
   constexpr int kRenderThreads = kWarps * 32;
   constexpr int kTilePix = kRenderThreads * kPPT;
   constexpr int kStagePerThread = kBatch / kRenderThreads;
   static_assert(kBatch % kRenderThreads == 0 && kStagePerThread >= 1, "batch must be a multiple of the CTA size");
-  static_assert(1024 / (32 * kPPT) <= kContribSlots, "contribution slots");
   __shared__ Stage S;
   __shared__ uint32_t s_item;
   if (status_bad(status)) return;
@@ -240,7 +213,6 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
       const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
       const Pix<kPPT> P = load_pixels<kPPT>(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
-      const int slot0 = (int)(r0 / kTilePix) * kWarps;
       float T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT], N0[kPPT], N1[kPPT], N2[kPPT];
       uint32_t last[kPPT], cnt[kPPT];
       bool done[kPPT];
@@ -266,14 +238,12 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
         if (!__any_sync(kFull, !all_done)) continue;
         uint32_t rel[kBatch / 32];
         warp_relevance(S, (int)nb, cbox, lane, rel);
+        if (all_done) continue;
 #pragma unroll 1
         for (int c = 0; c < kBatch / 32; ++c) {
-          if (__all_sync(kFull, all_done)) break;
-          uint32_t m = all_done ? 0u : rel[c];
-          uint32_t mine = 0;  // Gaussians of this group blended by this lane's pixels
+          uint32_t m = rel[c];
           while (m) {
-            const int b = __ffs(m) - 1;
-            const int j = c * 32 + b;
+            const int j = c * 32 + __ffs(m) - 1;
             m &= m - 1;
             const float4 q0 = S.g0[j];
             const float4 q1 = S.g1[j];
@@ -302,20 +272,16 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
               T[k] = test;
               last[k] = base + j;
               ++cnt[k];
-              mine |= 1u << b;
             }
             bool ad = true;
 #pragma unroll
             for (int k = 0; k < kPPT; ++k) ad = ad && done[k];
             if (ad) {
               all_done = true;
+              c = kBatch / 32;
               break;
             }
           }
-          // the warp's contributions to duplicates base + 32 c + [0, 32), stored
-          // at their global positions (one bit each) for the adjoint
-          const uint32_t wbits = __reduce_or_sync(kFull, mine);
-          if (lane == 0 && wbits) record_contrib(contrib, base + (uint32_t)c * 32, slot0 + warp, wbits);
         }
       }
 #pragma unroll
@@ -395,7 +361,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     const uint4* __restrict__ act_tiles, uint32_t n_items, const uint32_t* __restrict__ px_list,
     Sched sched, const float4* __restrict__ out8, const uint4* __restrict__ aux,
     const float4* __restrict__ dout8, const float* __restrict__ ddepth, const float* __restrict__ dout_scale,
-    const uint32_t* __restrict__ contrib, float* __restrict__ grad2d, const int32_t* status) {
+    float* __restrict__ grad2d, const int32_t* status) {
   constexpr int kRenderThreads = kWarps * 32;
   constexpr int kTilePix = kRenderThreads * kPPT;
   constexpr int kStagePerThread = kBatch / kRenderThreads;
@@ -422,7 +388,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
       // same way whatever the tile size
       const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
       const Pix<kPPT> P = load_pixels<kPPT>(ti, r0, warp, lane, V.width, ox, oy, px_list);
-      const int slot0 = (int)(r0 / kTilePix) * kWarps;
+      const float4 cbox = warp_pixel_box(P);
       BwdPix B[kPPT];
       int lane_last = -1;
 #pragma unroll
@@ -481,12 +447,11 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
           if (slot < nb) stage(lo + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, spair);
         }
         __syncthreads();
-        const int lim = min(nb, warp_last - lo + 1);
+        uint32_t rel[kBatch / 32];
+        warp_relevance(S, min(nb, warp_last - lo + 1), cbox, lane, rel);
 #pragma unroll 1
-        for (int c = (lim - 1) >> 5; c >= 0; --c) {
-         uint32_t m = load_contrib(contrib, (uint32_t)lo + (uint32_t)c * 32, slot0 + warp);
-         const int keep = lim - c * 32;  // bits at or below the warp's last blended index
-         if (keep < 32) m &= (1u << keep) - 1u;
+        for (int c = kBatch / 32 - 1; c >= 0; --c) {
+         uint32_t m = rel[c];
          while (m) {
           const int bit = 31 - __clz(m);
           m &= ~(1u << bit);
@@ -591,9 +556,6 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
 
 using namespace pgsag;
 
-static_assert(PGSAG_FWD_WARPS == PGSAG_BWD_WARPS && PGSAG_FWD_PPT == PGSAG_BWD_PPT,
-              "forward and adjoint must assign pixels to warps identically (contribution masks)");
-
 static int launch_cfg(const pgsag_sched* sched, uint32_t n_items, Sched& s, unsigned& blocks) {
   s.order = sched ? sched->order : nullptr;
   s.counter = sched ? sched->counter : nullptr;
@@ -609,19 +571,14 @@ static int launch_cfg(const pgsag_sched* sched, uint32_t n_items, Sched& s, unsi
   return PGSAG_OK;
 }
 
-extern "C" size_t pgsag_contrib_words(uint64_t capacity) {
-  return (size_t)(capacity / 32 + 2) * kContribSlots;
-}
-
 extern "C" int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec,
                                 const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
                                 uint32_t n_active, const uint32_t* px_list, const pgsag_sched* sched,
-                                float* out8, float* depth, void* aux, uint32_t* contrib,
-                                uint64_t capacity, int32_t* status, void* stream) {
+                                float* out8, float* depth, void* aux, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status) return PGSAG_ERR_ARG;
   if (n_active == 0) return PGSAG_OK;
-  if (!rec || !ranges || !act_tiles || !px_list || !out8 || !depth || !aux || !contrib) return PGSAG_ERR_ARG;
+  if (!rec || !ranges || !act_tiles || !px_list || !out8 || !depth || !aux) return PGSAG_ERR_ARG;
   if (((uintptr_t)rec | (uintptr_t)out8 | (uintptr_t)aux | (uintptr_t)act_tiles) & 15u) return PGSAG_ERR_ARG;
   Sched s;
   unsigned blocks;
@@ -629,10 +586,9 @@ extern "C" int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const
   if (r) return r;
   cudaStream_t st = (cudaStream_t)stream;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
-  PGSAG_CUDA(cudaMemsetAsync(contrib, 0, pgsag_contrib_words(capacity) * sizeof(uint32_t), st));
   k_render_fwd<PGSAG_FWD_WARPS, PGSAG_FWD_PPT><<<blocks, PGSAG_FWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
                                                   (const uint4*)act_tiles, n_active, px_list, s, (float4*)out8, depth,
-                                                  (uint4*)aux, contrib, status);
+                                                  (uint4*)aux, status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }
@@ -641,8 +597,8 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
                                 const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
                                 uint32_t n_active, const uint32_t* px_list, const pgsag_sched* sched,
                                 const float* out8, const void* aux, const float* dout8, const float* ddepth,
-                                const float* dout_scale, const uint32_t* contrib, uint32_t n_pairs, float* grad2d,
-                                int32_t* status, void* stream) {
+                                const float* dout_scale, uint32_t n_pairs, float* grad2d, int32_t* status,
+                                void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status) return PGSAG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -651,8 +607,7 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
     PGSAG_CUDA(cudaMemsetAsync(grad2d, 0, (size_t)n_pairs * PGSAG_GRAD2D_FLOATS * sizeof(float), st));
   }
   if (n_active == 0) return PGSAG_OK;
-  if (!rec || !ranges || !act_tiles || !px_list || !out8 || !aux || !dout8 || !grad2d || !contrib)
-    return PGSAG_ERR_ARG;
+  if (!rec || !ranges || !act_tiles || !px_list || !out8 || !aux || !dout8 || !grad2d) return PGSAG_ERR_ARG;
   if (((uintptr_t)rec | (uintptr_t)out8 | (uintptr_t)aux | (uintptr_t)dout8 | (uintptr_t)act_tiles) & 15u)
     return PGSAG_ERR_ARG;
   Sched s;
@@ -662,8 +617,8 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
   k_render_bwd<PGSAG_BWD_WARPS, PGSAG_BWD_PPT, PGSAG_BWD_DIRECT><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
                                                   (const uint4*)act_tiles, n_active, px_list, s, (const float4*)out8,
-                                                  (const uint4*)aux, (const float4*)dout8, ddepth, dout_scale, contrib,
-                                                  grad2d, status);
+                                                  (const uint4*)aux, (const float4*)dout8, ddepth, dout_scale, grad2d,
+                                                  status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

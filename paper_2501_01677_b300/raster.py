@@ -204,8 +204,6 @@ class Plan:
     def _alloc_capacity(self, cap: int):
         self.capacity = int(max(cap, 1))
         self.dup_pairs = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
-        self.contrib = torch.empty(int(self.lib.pgsag_contrib_words(self.capacity)), dtype=torch.int32,
-                                   device=self.device)
         nbytes = int(self.lib.pgsag_bin_workspace_size(self.n_pairs, self.capacity))
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
 
@@ -305,8 +303,7 @@ class Plan:
             L.check(self.lib.pgsag_render_fwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
                                               _ptr(self.ranges), _ptr(self.act_tiles), self.n_active,
                                               _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.depth),
-                                              _ptr(self.aux), _ptr(self.contrib), self.capacity, _ptr(self.status), s),
-                    "pgsag_render_fwd")
+                                              _ptr(self.aux), _ptr(self.status), s), "pgsag_render_fwd")
 
     def loss(self, lambda_ban=LAMBDA_BAN, loss_out: Optional[torch.Tensor] = None, stream=None):
         s = _stream_ptr(stream)
@@ -335,8 +332,7 @@ class Plan:
             L.check(self.lib.pgsag_render_bwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
                                               _ptr(self.ranges), _ptr(self.act_tiles), self.n_active,
                                               _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.aux),
-                                              _ptr(dout8), _ptr(ddepth), _ptr(dout_scale), _ptr(self.contrib), self.n_pairs,
-                                              _ptr(self.grad2d),
+                                              _ptr(dout8), _ptr(ddepth), _ptr(dout_scale), self.n_pairs, _ptr(self.grad2d),
                                               _ptr(self.status), s), "pgsag_render_bwd")
 
     def preprocess_bwd(self, P: GaussianParams, grads: Sequence[torch.Tensor], accumulate=False, stream=None):

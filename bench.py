@@ -212,6 +212,22 @@ def read_traffic(kernel: str):
     return None
 
 
+def aggregate(ms_local: float, units_local: float, steps: int, world: int, dist_mod=None, device=None):
+    """Whole-job throughput over ranks: the slowest rank's time (max over ranks)
+    and the units all ranks processed.  Returns (max ms, value in units / s)."""
+    if world > 1 and dist_mod is not None:
+        import torch
+        t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=device)
+        mx = t[:1].clone()
+        dist_mod.all_reduce(mx, op=dist_mod.ReduceOp.MAX)
+        tot = t[1:].clone()
+        dist_mod.all_reduce(tot, op=dist_mod.ReduceOp.SUM)
+        ms, units = float(mx.item()), float(tot.item())
+    else:
+        ms, units = ms_local, units_local
+    return ms, units * steps / (ms / 1e3)
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -276,12 +292,8 @@ def ours(args):
     plan.stage_events = None
     stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
     plan.check_status()
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     mpix = plan.n_mask / 1e6
-    value = ws * mpix * args.steps / (ms / 1e3)
+    ms, value = aggregate(ms, mpix, args.steps, ws, dist if ws > 1 else None, device="cuda")
 
     # end to end through the public API with host buffers
     e2e = None
@@ -307,13 +319,9 @@ def ours(args):
                 h.copy_(d.grad, non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize()
-        ms_e2e = a.elapsed_time(b)
-        if ws > 1:
-            t = torch.tensor([ms_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": ws * mpix * n_e2e / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / n_e2e}
+        ms_e2e, v_e2e = aggregate(a.elapsed_time(b), mpix, n_e2e, ws, dist if ws > 1 else None, device="cuda")
+        e2e = {"value": v_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": ms_e2e / n_e2e}
 
     if rank != 0:
         if ws > 1:

@@ -162,9 +162,9 @@ def algorithmic_bytes(plan, K):
         "bin": NP * (4 * 20 + 2 * 20) + K * (8 + 20 * tile_passes + 4) + 8 * A,
         # per pixel: list 4 + out8 32 + depth 4 + aux 16; per duplicate: id 4 + record 64
         "render_fwd": 56 * P + 68 * K,
-        # pass A: flags 1 + out8 32 + depth 4 + dout8 32 (+ target 12 + scratch 24 on M);
-        # pass B: out8 32 + depth 4 + dout8 64 + scratch 24
-        "loss": P * (1 + 32 + 4 + 32 + 32 + 4 + 64) + M * (12 + 24 + 24),
+        # pass A: flags 1 + pixel index 4 + out8 32 + depth 4 + dout8 32 (+ target 12 + scratch 24 on M);
+        # pass B: flags 1 + pixel index 4 + out8 32 + depth 4 + dout8 64 + scratch 24
+        "loss": P * (1 + 4 + 32 + 4 + 32 + 1 + 4 + 32 + 4 + 64) + M * (12 + 24 + 24),
         "tile_stats": P * (4 + 16 + 4) + 8 * A,
         # per pixel: list 4 + aux 16 + dout8 32; per duplicate: id 4 + record 64; grad2d zero + write-back 2x64/pair
         "render_bwd": 52 * P + 68 * K + 128 * NP,

@@ -30,8 +30,15 @@
  *   - Views.  A step may render several views at once (sub-regions of uneven
  *     size, mixed resolutions).  Each view renders the Gaussian index range
  *     [g_begin, g_end) of the shared parameter arrays; a (view, Gaussian) pair has
- *     index pair_base + (g - g_begin).  Per-pixel arrays of all views are
- *     concatenated: pixel (x, y) of view v lives at pix_base + y * width + x.
+ *     index pair_base + (g - g_begin).
+ *   - Pixel arrays come in two layouts (Sec. 5.3: only mask pixels are
+ *     rendered).  Dense arrays -- flags and the pixel-index map pidx, 5 bytes
+ *     per image pixel -- concatenate the views' full images: pixel (x, y) of
+ *     view v lives at pix_base + y * width + x.  Every other per-pixel array
+ *     (targets, GC weights, rendered outputs, upstream gradients, scratch) is
+ *     compact: indexed by the pixel's position q in px_list (the rendered set R
+ *     of all views, grouped by active tile), so its size is |R| entries and
+ *     consecutive threads touch consecutive entries.
  *     Per-tile arrays are concatenated with tile_base / sat_base; active tiles
  *     (tiles holding at least one rendered pixel) are numbered globally from
  *     act_base.
@@ -95,7 +102,7 @@ typedef struct pgsag_view {
   uint32_t n_mask;            /* (prep) |M|, building-mask pixels               */
   uint32_t chunk_base;        /* (prep) global index of this view's first chunk */
   uint32_t n_chunks;          /* (prep) chunks of this view                     */
-  uint64_t pix_base;          /* offset of this view in per-pixel arrays        */
+  uint64_t pix_base;          /* offset of this view in dense per-pixel arrays  */
 } pgsag_view;
 
 /* Optional work scheduling for the render kernels. */
@@ -121,7 +128,7 @@ const char* pgsag_build_info(void);
  * pgsag_prep_flags: per-pixel sets and per-tile counts of one view.
  *   view   host, one view (size, tiling, pix_base, tile_base are used)
  *   mask   device uint8 [height*width], nonzero = building pixel (M)
- *   flags  device uint8 [per-pixel array], written at pix_base:
+ *   flags  device uint8 [dense per-pixel array], written at pix_base:
  *          PGSAG_PIX_MASK (M), PGSAG_PIX_EDGE (E = 3x3 dilation minus 3x3
  *          erosion of M), PGSAG_PIX_RENDER (R = 3x3 dilation of M); neighbours
  *          outside the image are ignored.
@@ -153,21 +160,32 @@ int pgsag_prep_flags(const pgsag_view* view, const uint8_t* mask, uint8_t* flags
  *   chunks      device uint2 [chunks at chunk_base]: {global active tile, first
  *               px_list entry}; a chunk covers up to 32 consecutive entries of one
  *               tile
- * Errors: PGSAG_ERR_ARG on null pointers; PGSAG_ERR_UNSUPPORTED for tiles of
- * more than 1024 pixels.
+ *   pidx        device uint32 [dense per-pixel array], written at pix_base for the
+ *               whole image: the px_list position q of each R pixel, 0xFFFFFFFF
+ *               for pixels outside R
+ * Errors: PGSAG_ERR_ARG on null pointers or act_tiles not 16-byte / chunks not
+ * 8-byte aligned; PGSAG_ERR_UNSUPPORTED for tiles of more than 1024 pixels.
  */
 int pgsag_prep_lists(const pgsag_view* view, uint32_t view_index, const uint8_t* flags,
                      const uint32_t* tile_npix, uint32_t px_base, uint32_t chunk_base,
                      int32_t* tile_act, uint32_t* sat, void* act_tiles, uint32_t* px_list,
-                     void* chunks, void* stream);
+                     void* chunks, uint32_t* pidx, void* stream);
 
 /*
  * pgsag_prep_gc_weight: w_i of Eq. 9 (Sec. 4.3), read as 1 + |Sobel(Y)| of the
- * target luminance Y = 0.299 R + 0.587 G + 0.114 B, replicated borders.
- *   target  device float [height*width*3] at 3*pix_base (RGB interleaved)
- *   weight  device float [height*width] at pix_base
+ * target luminance Y = 0.299 R + 0.587 G + 0.114 B, replicated borders; also
+ * gathers the target colours of the rendered pixels into the compact layout.
+ *   view      host, one view (width, height)
+ *   target    device float [height*width*3], this view's full image (RGB
+ *             interleaved, row-major); only read, may be freed afterwards
+ *   px_list   device, from pgsag_prep_lists; this view's entries are
+ *             [px_base, px_base + n_px)
+ *   target_c  device float [3 per compact pixel], written at 3*px_base
+ *   weight    device float [1 per compact pixel], written at px_base
+ * n_px = 0 does nothing.  Errors: PGSAG_ERR_ARG on null pointers or an empty image.
  */
-int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* weight, void* stream);
+int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, const uint32_t* px_list,
+                         uint32_t px_base, uint32_t n_px, float* target_c, float* weight, void* stream);
 
 /* --------------------------------------------------------------------------
  * Step calls (the timed hot path).
@@ -255,10 +273,10 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
  *   w = alpha T, C += w c, N += w n_c, D += w d, T *= 1 - alpha.
  *   Depth = D / (-N . K^-1 (x+1/2, y+1/2, 1)) if something was blended,
  *   -N.r > 1e-8 and D > 0 (the pixel is then "valid"), else 0.
- * Outputs (per-pixel arrays, only R pixels written):
- *   out8  float [8 per pixel]: {C_r, C_g, C_b, D, N_x, N_y, N_z, A = 1 - T}
- *   depth float [1 per pixel]
- *   aux   uint4 [1 per pixel]: {float bits of final T, index (into dup_pairs) of the
+ * Outputs (compact per-pixel arrays, every px_list entry written):
+ *   out8  float [8 per compact pixel]: {C_r, C_g, C_b, D, N_x, N_y, N_z, A = 1 - T}
+ *   depth float [1 per compact pixel]
+ *   aux   uint4 [1 per compact pixel]: {float bits of final T, index (into dup_pairs) of the
  *         last blended Gaussian, number blended n_contrib, 0}
  * sched may be NULL (one CTA per active tile in index order); with a counter the
  * launch is persistent (ctas_per_sm x SMs CTAs pulling tiles, in `order` if given).
@@ -278,31 +296,35 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
  *   L = L_rgb + lambda_ban L_ban.
  * Writes dL/d(out8) for every R pixel (gradient through both n_depth -- into D
  * and N of the 4 neighbours via Eq. 4 -- and the rendered normal; dL/dA = 0).
- *   target   float [3 per pixel] (RGB interleaved, at 3*pix_base)
- *   scratch  float [6 per pixel] (only M pixels touched)
+ *   flags    dense per-pixel flags; pidx the dense pixel-index map (both from
+ *            mask preparation); neighbours are found through pidx
+ *   target   float [3 per compact pixel] (from pgsag_prep_gc_weight)
+ *   scratch  float [6 per compact pixel] (only M pixels touched)
  *   acc      double [4 per view] scratch accumulators
  *   chunk_scratch  float [4 per chunk] scratch (per-chunk partial sums, reduced
  *            per view without contended atomics)
  *   loss     float [3 per view + 1]: {L_rgb, L_ban, L} per view, then sum_v L
- *   dout8    float [8 per pixel]
+ *   dout8    float [8 per compact pixel]
  */
 int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                    const void* chunks, const void* act_tiles, const uint32_t* px_list,
-                   const uint8_t* flags, const float* out8, const float* depth,
+                   const uint8_t* flags, const uint32_t* pidx, const float* out8, const float* depth,
                    const void* aux, const float* target, float lambda_ban, float* scratch,
                    double* acc, float* chunk_scratch, float* loss, float* dout8, int32_t* status,
                    void* stream);
 
 /*
- * pgsag_render_bwd (Sec. 3.1: "optimized ... using differentiable rendering").
+ * pgsag_render_bwd (Sec. 3.1: the Gaussians' parameters are fitted through the
+ * differentiable renderer).
  * Adjoint of pgsag_render_fwd: each CTA re-traverses its tile's list back to
  * front from the last blended Gaussian, recovering T by division
  * (T_i = T_{i+1} / (1 - alpha_i)), and accumulates per pair
  *   grad2d[p*16 + {0..12}] = dL/d{mx, my, l11, l21, l22, o, r, g, b, d, nx, ny, nz}
  * (warp shuffle reduction, shared-memory sum over the CTA's warps, then one
  * float4 atomic add per 4 values per tile).  grad2d (16-byte aligned) is zeroed
- * by this call.  ddepth (nullable) adds a gradient on the depth output,
- * folded into dD and dN through Eq. 4.  dout_scale (nullable, device float[1])
+ * by this call.  out8, aux, dout8 and ddepth are compact per-pixel arrays
+ * (8, 1, 8, 1 entries per px_list position).  ddepth (nullable) adds a
+ * gradient on the depth output, folded into dD and dN through Eq. 4.  dout_scale (nullable, device float[1])
  * multiplies the whole upstream gradient (chain rule from a scalar loss).
  */
 int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec,

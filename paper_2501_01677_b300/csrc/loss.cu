@@ -21,7 +21,8 @@ struct PixCtx {
   uint32_t view;
   ViewLite V;
   int x, y;
-  uint64_t gp;
+  uint64_t gp;  // dense index (flags, pixel-index map): pix_base + y W + x
+  uint32_t q;   // compact index (position in px_list): every other per-pixel array
 };
 
 __device__ __forceinline__ PixCtx pix_ctx(uint32_t c, int lane, const uint2* __restrict__ chunks,
@@ -35,7 +36,8 @@ __device__ __forceinline__ PixCtx pix_ctx(uint32_t c, int lane, const uint2* __r
   P.view = at.x;
   P.V = load_view_lite(views + at.x);
   P.has = (uint32_t)lane < cnt;
-  const uint32_t pix = P.has ? __ldg(px_list + ch.y + lane) : 0u;
+  P.q = ch.y + lane;
+  const uint32_t pix = P.has ? __ldg(px_list + P.q) : 0u;
   P.y = (int)(pix / (uint32_t)P.V.width);
   P.x = (int)(pix - (uint32_t)P.y * (uint32_t)P.V.width);
   P.gp = P.V.pix_base + pix;
@@ -55,9 +57,9 @@ __device__ __forceinline__ void ray(const ViewLite& V, int x, int y, float r[3])
 __global__ void __launch_bounds__(kLossThreads) k_loss_a(
     const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
     const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
-    const uint8_t* __restrict__ flags, const float4* __restrict__ out8, const float* __restrict__ depth,
-    const float* __restrict__ target, float* __restrict__ scratch, float4* __restrict__ partial,
-    float4* __restrict__ dout8, const int32_t* status) {
+    const uint8_t* __restrict__ flags, const uint32_t* __restrict__ pidx, const float4* __restrict__ out8,
+    const float* __restrict__ depth, const float* __restrict__ target, float* __restrict__ scratch,
+    float4* __restrict__ partial, float4* __restrict__ dout8, const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
   float l1 = 0.f, lb = 0.f, nv = 0.f;
   if (P.has) {
     const uint8_t f = __ldg(flags + P.gp);
-    const float4 o0 = __ldg(out8 + 2 * P.gp), o1 = __ldg(out8 + 2 * P.gp + 1);
+    const float4 o0 = __ldg(out8 + 2 * P.q), o1 = __ldg(out8 + 2 * P.q + 1);
     float dC[3] = {0.f, 0.f, 0.f}, dNo[3] = {0.f, 0.f, 0.f};
     if (f & PGSAG_PIX_MASK) {
       const uint32_t nm = __ldg(&views[P.view].n_mask);
@@ -74,32 +76,29 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
       const float C[3] = {o0.x, o0.y, o0.z};
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
-        const float d = C[ch] - __ldg(target + 3 * P.gp + ch);
+        const float d = C[ch] - __ldg(target + 3 * P.q + ch);
         l1 += fabsf(d);
         dC[ch] = d > 0.f ? inv3m : (d < 0.f ? -inv3m : 0.f);
       }
       float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
       const int W = P.V.width, H = P.V.height;
-      const float dep = __ldg(depth + P.gp);
+      const float dep = __ldg(depth + P.q);
       bool inV = P.x >= 1 && P.x <= W - 2 && P.y >= 1 && P.y <= H - 2 && dep > 0.f;
       float Pn[4][3];  // y-1, y+1, x-1, x+1
       if (inV) {
         const int nx[4] = {P.x, P.x, P.x - 1, P.x + 1};
         const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
-        // independent loads (the dense per-view arrays cover every in-image
-        // pixel); a neighbour's depth is used only if it is rendered
-        uint8_t fq[4];
+        // neighbours through the dense pixel-index map (~0: not rendered)
+        uint32_t qn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qn[k] = __ldg(pidx + P.V.pix_base + (uint64_t)ny[k] * W + nx[k]);
         float dq[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint64_t q = P.V.pix_base + (uint64_t)ny[k] * W + nx[k];
-          fq[k] = __ldg(flags + q);
-          dq[k] = __ldg(depth + q);
-        }
+        for (int k = 0; k < 4; ++k) dq[k] = qn[k] != 0xffffffffu ? __ldg(depth + qn[k]) : 0.f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const bool rk = (fq[k] & PGSAG_PIX_RENDER) != 0;
-          const float d = rk ? dq[k] : 0.f;
+          const bool rk = qn[k] != 0xffffffffu;
+          const float d = dq[k];
           inV = inV && rk && d > 0.f;
           float r[3];
           ray(P.V, nx[k], ny[k], r);
@@ -139,15 +138,15 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
           gb[2] = gc[0] * a[1] - gc[1] * a[0];
         }
       }
-      float* sc = scratch + 6 * P.gp;
+      float* sc = scratch + 6ull * P.q;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         sc[k] = ga[k];
         sc[3 + k] = gb[k];
       }
     }
-    dout8[2 * P.gp] = make_float4(dC[0], dC[1], dC[2], 0.f);
-    dout8[2 * P.gp + 1] = make_float4(dNo[0], dNo[1], dNo[2], 0.f);
+    dout8[2 * P.q] = make_float4(dC[0], dC[1], dC[2], 0.f);
+    dout8[2 * P.q + 1] = make_float4(dNo[0], dNo[1], dNo[2], 0.f);
   }
   // per-chunk partial sums, reduced per view by k_view_reduce
   const float s1 = warp_sum(l1), s2 = warp_sum(lb), s3 = warp_sum(nv);
@@ -196,9 +195,9 @@ __global__ void __launch_bounds__(256) k_view_reduce(const pgsag_view* __restric
 __global__ void __launch_bounds__(kLossThreads) k_loss_b(
     const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
     const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
-    const uint8_t* __restrict__ flags, const float4* __restrict__ out8, const float* __restrict__ depth,
-    const float* __restrict__ scratch, const double* __restrict__ acc, float lambda_ban,
-    float4* __restrict__ dout8, const int32_t* status) {
+    const uint8_t* __restrict__ flags, const uint32_t* __restrict__ pidx, const float4* __restrict__ out8,
+    const float* __restrict__ depth, const float* __restrict__ scratch, const double* __restrict__ acc,
+    float lambda_ban, float4* __restrict__ dout8, const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
@@ -214,18 +213,25 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_b(
   const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
   const float sg[4] = {1.f, -1.f, 1.f, -1.f};
   const int off[4] = {0, 0, 3, 3};
-  // independent loads of the in-image neighbours' flags and scratch; a
-  // neighbour contributes only if it is a mask pixel (its scratch is written)
+  // in-image neighbours: flags and pixel index first (independent loads), then
+  // the scratch of the mask neighbours (written by pass A)
   uint8_t fq[4];
+  uint32_t qn[4];
   float sv[4][3];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     fq[k] = 0;
-    sv[k][0] = sv[k][1] = sv[k][2] = 0.f;
+    qn[k] = 0xffffffffu;
     if (nx[k] < 0 || nx[k] >= W || ny[k] < 0 || ny[k] >= H) continue;
-    const uint64_t q = P.V.pix_base + (uint64_t)ny[k] * W + nx[k];
-    fq[k] = __ldg(flags + q);
-    const float* sc = scratch + 6 * q + off[k];
+    const uint64_t d = P.V.pix_base + (uint64_t)ny[k] * W + nx[k];
+    fq[k] = __ldg(flags + d);
+    qn[k] = __ldg(pidx + d);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    sv[k][0] = sv[k][1] = sv[k][2] = 0.f;
+    if (!(fq[k] & PGSAG_PIX_MASK)) continue;
+    const float* sc = scratch + 6ull * qn[k] + off[k];
     sv[k][0] = __ldg(sc + 0);
     sv[k][1] = __ldg(sc + 1);
     sv[k][2] = __ldg(sc + 2);
@@ -237,11 +243,11 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_b(
     dP[1] += sg[k] * sv[k][1];
     dP[2] += sg[k] * sv[k][2];
   }
-  float4 g1 = dout8[2 * P.gp + 1];
+  float4 g1 = dout8[2 * P.q + 1];
   float dD = 0.f, dN[3] = {0.f, 0.f, 0.f};
-  const float dep = __ldg(depth + P.gp);
+  const float dep = __ldg(depth + P.q);
   if (dep > 0.f && (dP[0] != 0.f || dP[1] != 0.f || dP[2] != 0.f)) {
-    const float4 o0 = __ldg(out8 + 2 * P.gp), o1 = __ldg(out8 + 2 * P.gp + 1);
+    const float4 o0 = __ldg(out8 + 2 * P.q), o1 = __ldg(out8 + 2 * P.q + 1);
     float r[3];
     ray(P.V, P.x, P.y, r);
     const float sdot = -(o1.x * r[0] + o1.y * r[1] + o1.z * r[2]);
@@ -253,14 +259,14 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_b(
     dN[1] = k * r[1];
     dN[2] = k * r[2];
   }
-  float4 g0 = dout8[2 * P.gp];
+  float4 g0 = dout8[2 * P.q];
   g0.w = scale * dD;
   g1.x = scale * (g1.x + dN[0]);
   g1.y = scale * (g1.y + dN[1]);
   g1.z = scale * (g1.z + dN[2]);
   g1.w = 0.f;
-  dout8[2 * P.gp] = g0;
-  dout8[2 * P.gp + 1] = g1;
+  dout8[2 * P.q] = g0;
+  dout8[2 * P.q + 1] = g1;
 }
 
 // One thread: per-view losses and their sum (views are few).
@@ -305,8 +311,8 @@ __global__ void __launch_bounds__(kLossThreads) k_gc_accum(
   const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
   float x = 0.f, n = 0.f;
   if (P.has) {
-    const uint32_t g = __ldg(&aux[P.gp].z);
-    x = (float)g / __ldg(weight + P.gp);
+    const uint32_t g = __ldg(&aux[P.q].z);
+    x = (float)g / __ldg(weight + P.q);
     n = 1.f;
   }
   const float s0 = warp_sum(n), s1 = warp_sum(x), s2 = warp_sum(x * x);
@@ -327,11 +333,15 @@ __global__ void k_gc_final(uint32_t n_views, const double* __restrict__ acc, flo
   out[v] = (float)sqrt(var > 0.0 ? var : 0.0);
 }
 
-// w = 1 + |Sobel(Y)|, replicated borders
-__global__ void k_gc_weight(int W, int H, const float* __restrict__ target, float* __restrict__ weight) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  if (x >= W || y >= H) return;
+// Per rendered pixel of one view (compact index px_base + i): the target colour
+// gathered from the dense image, and w = 1 + |Sobel(Y)| with replicated borders.
+__global__ void k_gc_weight(int W, int H, uint32_t n, const uint32_t* __restrict__ px,
+                            const float* __restrict__ target, float* __restrict__ target_c,
+                            float* __restrict__ weight) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t pix = __ldg(px + i);
+  const int y = (int)(pix / (uint32_t)W), x = (int)(pix - (uint32_t)y * (uint32_t)W);
   float Y[3][3];
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy)
@@ -343,7 +353,11 @@ __global__ void k_gc_weight(int W, int H, const float* __restrict__ target, floa
     }
   const float gx = (Y[0][2] + 2.f * Y[1][2] + Y[2][2]) - (Y[0][0] + 2.f * Y[1][0] + Y[2][0]);
   const float gy = (Y[2][0] + 2.f * Y[2][1] + Y[2][2]) - (Y[0][0] + 2.f * Y[0][1] + Y[0][2]);
-  weight[(size_t)y * W + x] = 1.f + sqrtf(gx * gx + gy * gy);
+  weight[i] = 1.f + sqrtf(gx * gx + gy * gy);
+  const float* t = target + 3 * (size_t)pix;
+  target_c[3 * (size_t)i + 0] = t[0];
+  target_c[3 * (size_t)i + 1] = t[1];
+  target_c[3 * (size_t)i + 2] = t[2];
 }
 
 }  // namespace pgsag
@@ -352,7 +366,7 @@ using namespace pgsag;
 
 extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                               const void* chunks, const void* act_tiles, const uint32_t* px_list,
-                              const uint8_t* flags, const float* out8, const float* depth,
+                              const uint8_t* flags, const uint32_t* pidx, const float* out8, const float* depth,
                               const void* aux, const float* target, float lambda_ban, float* scratch,
                               double* acc, float* chunk_scratch, float* loss, float* dout8, int32_t* status,
                               void* stream) {
@@ -362,21 +376,21 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
   cudaStream_t s = (cudaStream_t)stream;
   PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 4 * sizeof(double), s));
   if (n_chunks) {
-    if (!chunks || !act_tiles || !px_list || !flags || !out8 || !depth || !target || !scratch || !dout8 ||
-        !chunk_scratch)
+    if (!chunks || !act_tiles || !px_list || !flags || !pidx || !out8 || !depth || !target || !scratch ||
+        !dout8 || !chunk_scratch)
       return PGSAG_ERR_ARG;
     if (((uintptr_t)out8 | (uintptr_t)dout8 | (uintptr_t)act_tiles | (uintptr_t)chunk_scratch) & 15u)
       return PGSAG_ERR_ARG;
     const unsigned blocks = pgsag_div_up(n_chunks, kLossThreads / 32);
     k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
-                                             px_list, flags, (const float4*)out8, depth, target, scratch,
+                                             px_list, flags, pidx, (const float4*)out8, depth, target, scratch,
                                              (float4*)chunk_scratch, (float4*)dout8, status);
     PGSAG_CHECK_LAUNCH();
     k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 4, acc,
                                                                 status);
     PGSAG_CHECK_LAUNCH();
     k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
-                                             px_list, flags, (const float4*)out8, depth, scratch, acc,
+                                             px_list, flags, pidx, (const float4*)out8, depth, scratch, acc,
                                              lambda_ban, (float4*)dout8, status);
     PGSAG_CHECK_LAUNCH();
   }
@@ -416,12 +430,14 @@ extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint3
   return PGSAG_OK;
 }
 
-extern "C" int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, float* weight, void* stream) {
-  if (!view || !target || !weight) return PGSAG_ERR_ARG;
+extern "C" int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, const uint32_t* px_list,
+                                    uint32_t px_base, uint32_t n_px, float* target_c, float* weight,
+                                    void* stream) {
+  if (!view || !target || !px_list || !target_c || !weight) return PGSAG_ERR_ARG;
   if (view->width <= 0 || view->height <= 0) return PGSAG_ERR_ARG;
-  dim3 grid(pgsag_div_up(view->width, 256), view->height);
-  k_gc_weight<<<grid, 256, 0, (cudaStream_t)stream>>>(view->width, view->height, target + 3 * view->pix_base,
-                                                      weight + view->pix_base);
+  if (n_px == 0) return PGSAG_OK;
+  k_gc_weight<<<pgsag_div_up(n_px, 256), 256, 0, (cudaStream_t)stream>>>(
+      view->width, view->height, n_px, px_list + px_base, target, target_c + 3ull * px_base, weight + px_base);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

@@ -144,12 +144,13 @@ __global__ void __launch_bounds__(1024) k_prep_sat(int tiles_x, int tiles_y, con
   }
 }
 
-// One block per tile: rendered pixels in row-major order inside the tile.
+// One block per tile: rendered pixels in row-major order inside the tile; the
+// dense map pidx gets each rendered pixel's position in px_list.
 __global__ void __launch_bounds__(256) k_prep_px(int W, int H, int tw, int th, int tiles_x,
                                                  const uint8_t* __restrict__ flags,
                                                  const int32_t* __restrict__ tile_act,
                                                  const uint4* __restrict__ act_tiles,
-                                                 uint32_t* __restrict__ px_list) {
+                                                 uint32_t* __restrict__ px_list, uint32_t* __restrict__ pidx) {
   __shared__ uint32_t ws[8];
   __shared__ uint32_t s_carry;
   const int32_t a = tile_act[blockIdx.x];
@@ -172,7 +173,10 @@ __global__ void __launch_bounds__(256) k_prep_px(int W, int H, int tw, int th, i
       tot += ws[w];
     }
     const uint32_t rank = s_carry + pre + __popc(b & ((1u << lane) - 1u));
-    if (r) px_list[first - 0 + rank] = (uint32_t)y * (uint32_t)W + (uint32_t)x;
+    if (r) {
+      px_list[first + rank] = (uint32_t)y * (uint32_t)W + (uint32_t)x;
+      pidx[(size_t)y * W + x] = first + rank;
+    }
     __syncthreads();
     if (threadIdx.x == 0) s_carry += tot;
     __syncthreads();
@@ -210,8 +214,8 @@ extern "C" int pgsag_prep_flags(const pgsag_view* view, const uint8_t* mask, uin
 extern "C" int pgsag_prep_lists(const pgsag_view* view, uint32_t view_index, const uint8_t* flags,
                                 const uint32_t* tile_npix, uint32_t px_base, uint32_t chunk_base,
                                 int32_t* tile_act, uint32_t* sat, void* act_tiles, uint32_t* px_list,
-                                void* chunks, void* stream) {
-  if (!view || !flags || !tile_npix || !tile_act || !sat || !act_tiles || !px_list || !chunks)
+                                void* chunks, uint32_t* pidx, void* stream) {
+  if (!view || !flags || !tile_npix || !tile_act || !sat || !act_tiles || !px_list || !chunks || !pidx)
     return PGSAG_ERR_ARG;
   if (((uintptr_t)act_tiles & 15u) || ((uintptr_t)chunks & 7u)) return PGSAG_ERR_ARG;
   int r = check_tiling(view);
@@ -224,9 +228,11 @@ extern "C" int pgsag_prep_lists(const pgsag_view* view, uint32_t view_index, con
   PGSAG_CHECK_LAUNCH();
   k_prep_sat<<<1, 1024, 0, s>>>(view->tiles_x, view->tiles_y, tile_act + view->tile_base, sat + view->sat_base);
   PGSAG_CHECK_LAUNCH();
+  PGSAG_CUDA(cudaMemsetAsync(pidx + view->pix_base, 0xff,
+                             (size_t)view->width * (size_t)view->height * sizeof(uint32_t), s));
   k_prep_px<<<n_tiles, 256, 0, s>>>(view->width, view->height, view->tile_w, view->tile_h, view->tiles_x,
                                     flags + view->pix_base, tile_act + view->tile_base, (const uint4*)act_tiles,
-                                    px_list);
+                                    px_list, pidx + view->pix_base);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t next_tile(const Sched& s, uint32_t& iter, ui
 template <int kPPT>
 struct Pix {
   bool has[kPPT];
-  uint32_t pix[kPPT];
+  uint32_t q[kPPT];          // compact index (position in px_list): per-pixel arrays
   float px[kPPT], py[kPPT];  // centre minus tile origin
 };
 
@@ -114,9 +114,10 @@ __device__ __forceinline__ Pix<kPPT> load_pixels(const TileInfo& ti, uint32_t r0
   for (int k = 0; k < kPPT; ++k) {
     const uint32_t li = r0 + (uint32_t)((warp * kPPT + k) * 32 + lane);
     P.has[k] = li < ti.npix;
-    P.pix[k] = P.has[k] ? __ldg(px_list + ti.px_first + li) : 0u;
-    const uint32_t yy = P.pix[k] / (uint32_t)width;
-    P.px[k] = (float)((int)(P.pix[k] - yy * (uint32_t)width) - ox) + 0.5f;
+    P.q[k] = ti.px_first + li;
+    const uint32_t pix = P.has[k] ? __ldg(px_list + P.q[k]) : 0u;
+    const uint32_t yy = pix / (uint32_t)width;
+    P.px[k] = (float)((int)(pix - yy * (uint32_t)width) - ox) + 0.5f;
     P.py[k] = (float)((int)yy - oy) + 0.5f;
   }
   return P;
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
         if (!P.has[k]) continue;
-        const uint64_t gp = V.pix_base + P.pix[k];
+        const uint64_t gp = P.q[k];
         out8[2 * gp + 0] = make_float4(C0[k], C1[k], C2[k], D[k]);
         out8[2 * gp + 1] = make_float4(N0[k], N1[k], N2[k], 1.f - T[k]);
         // Eq. 4: ray-plane depth
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
         b.dC0 = b.dC1 = b.dC2 = b.dD = b.dN0 = b.dN1 = b.dN2 = b.dATf = 0.f;
         b.SC0 = b.SC1 = b.SC2 = b.SN0 = b.SN1 = b.SN2 = b.SD = 0.f;
         if (!P.has[k]) continue;
-        const uint64_t gp = V.pix_base + P.pix[k];
+        const uint64_t gp = P.q[k];
         const uint4 ax = __ldg(aux + gp);
         b.T = __uint_as_float(ax.x);
         b.last = ax.z > 0 ? (int)ax.y : -1;

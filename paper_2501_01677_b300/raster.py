@@ -139,11 +139,15 @@ class Plan:
         self.n_render = int(tot[:, 1].sum())
         self.n_chunks = int(tot[:, 2].sum())
         self.n_mask = int(tot[:, 3].sum())
+        if self.n_render >= 2 ** 32:
+            raise ValueError("too many rendered pixels for 32-bit compact indices")
         self.tile_act = torch.empty(max(self.n_tiles, 1), dtype=i32, device=dev)
         self.sat = torch.empty(max(self.n_sat, 1), dtype=i32, device=dev)
         self.act_tiles = torch.empty((max(self.n_active, 1), 4), dtype=i32, device=dev)
         self.px_list = torch.empty(max(self.n_render, 1), dtype=i32, device=dev)
         self.chunks = torch.empty((max(self.n_chunks, 1), 2), dtype=i32, device=dev)
+        self.pidx = torch.empty(self.n_pix, dtype=i32, device=dev)
+        self.px_base_v = np.zeros(V, np.int64)
         act_base = px_base = chunk_base = 0
         for v in range(V):
             views[v].act_base = act_base
@@ -151,32 +155,39 @@ class Plan:
             views[v].n_mask = int(self.n_mask_v[v])
             views[v].chunk_base = chunk_base
             views[v].n_chunks = int(self.n_chunks_v[v])
+            self.px_base_v[v] = px_base
             L.check(self.lib.pgsag_prep_lists(ctypes.byref(views[v]), v, _ptr(self.flags), _ptr(self.tile_npix),
                                                   px_base, chunk_base, _ptr(self.tile_act), _ptr(self.sat),
-                                                  _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.chunks), s),
+                                                  _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.chunks),
+                                                  _ptr(self.pidx), s),
                         "pgsag_prep_lists")
             act_base += int(self.n_active_v[v])
             px_base += int(self.n_render_v[v])
             chunk_base += int(self.n_chunks_v[v])
-        self.target = torch.zeros(self.n_pix * 3, dtype=f32, device=dev)
-        self.gc_weight = torch.ones(self.n_pix, dtype=f32, device=dev)
+        # targets and GC weights of the rendered pixels (compact layout); each
+        # view's full image is on the device only while it is gathered
+        nr = max(self.n_render, 1)
+        self.target = torch.zeros(nr * 3, dtype=f32, device=dev)
+        self.gc_weight = torch.ones(nr, dtype=f32, device=dev)
         for v in range(V):
             tg = targets[v]
             tg = tg if torch.is_tensor(tg) else torch.from_numpy(np.ascontiguousarray(tg, np.float32))
             H, W = self.shapes[v]
-            pb = int(views[v].pix_base)
-            self.target[3 * pb:3 * (pb + H * W)].copy_(tg.reshape(-1).to(dev, f32))
-            L.check(self.lib.pgsag_prep_gc_weight(ctypes.byref(views[v]), _ptr(self.target), _ptr(self.gc_weight), s),
+            tg = tg.reshape(H * W * 3).to(dev, f32).contiguous()
+            L.check(self.lib.pgsag_prep_gc_weight(ctypes.byref(views[v]), _ptr(tg), _ptr(self.px_list),
+                                                      int(self.px_base_v[v]), int(self.n_render_v[v]),
+                                                      _ptr(self.target), _ptr(self.gc_weight), s),
                         "pgsag_prep_gc_weight")
+            del tg
         raw = bytes(views)
         self.views_dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
 
-        # ---- per-pixel buffers (dense per view; only rendered pixels are touched)
-        self.out8 = torch.zeros((self.n_pix, 8), dtype=f32, device=dev)
-        self.depth = torch.zeros(self.n_pix, dtype=f32, device=dev)
-        self.aux = torch.zeros((self.n_pix, 4), dtype=i32, device=dev)
-        self.dout8 = torch.zeros((self.n_pix, 8), dtype=f32, device=dev)
-        self.scratch = torch.zeros((self.n_pix, 6), dtype=f32, device=dev)
+        # ---- per-pixel buffers, compact: row q belongs to the pixel px_list[q]
+        self.out8 = torch.zeros((nr, 8), dtype=f32, device=dev)
+        self.depth = torch.zeros(nr, dtype=f32, device=dev)
+        self.aux = torch.zeros((nr, 4), dtype=i32, device=dev)
+        self.dout8 = torch.zeros((nr, 8), dtype=f32, device=dev)
+        self.scratch = torch.zeros((nr, 6), dtype=f32, device=dev)
         # ---- per-pair buffers
         npairs = max(self.n_pairs, 1)
         self.rec = torch.empty((npairs, 16), dtype=f32, device=dev)
@@ -310,7 +321,8 @@ class Plan:
         out = self.loss_buf if loss_out is None else loss_out
         with self._ev('loss'):
             L.check(self.lib.pgsag_loss_ban(self.n_views, _ptr(self.views_dev), self.n_chunks, _ptr(self.chunks),
-                                            _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags), _ptr(self.out8),
+                                            _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags), _ptr(self.pidx),
+                                            _ptr(self.out8),
                                             _ptr(self.depth), _ptr(self.aux), _ptr(self.target), float(lambda_ban),
                                             _ptr(self.scratch), _ptr(self.acc_loss), _ptr(self.chunk_scratch), _ptr(out), _ptr(self.dout8),
                                             _ptr(self.status), s), "pgsag_loss_ban")
@@ -401,19 +413,36 @@ class Plan:
 
     # ------------------------------------------------------------------ views of outputs
     def pix_slice(self, v: int):
+        """Slice of view v in the dense per-pixel arrays (flags, pidx)."""
         pb = int(self.views_host[v].pix_base)
         H, W = self.shapes[v]
         return slice(pb, pb + H * W)
 
+    def px_slice(self, v: int):
+        """Slice of view v in the compact per-pixel arrays (out8, depth, aux, ...)."""
+        b = int(self.px_base_v[v])
+        return slice(b, b + int(self.n_render_v[v]))
+
+    def px_index(self, v: int) -> torch.Tensor:
+        """Linear pixel index y * W + x (int64) of each of view v's compact rows."""
+        return self.px_list[self.px_slice(v)].long()
+
+    def scatter_image(self, v: int, rows: torch.Tensor) -> torch.Tensor:
+        """Dense [H, W, ...] image of view v from its compact rows (zeros outside R)."""
+        H, W = self.shapes[v]
+        out = torch.zeros((H * W,) + tuple(rows.shape[1:]), dtype=rows.dtype, device=rows.device)
+        out[self.px_index(v)] = rows
+        return out.view((H, W) + tuple(rows.shape[1:]))
+
     def images(self, v: int):
         """Dense images of view v: rgb [H,W,3], dist [H,W], normal [H,W,3], alpha
         [H,W], depth [H,W], n_contrib [H,W] (zero outside the rendered set)."""
-        H, W = self.shapes[v]
-        sl = self.pix_slice(v)
-        o = self.out8[sl].view(H, W, 8)
+        sl = self.px_slice(v)
+        o = self.scatter_image(v, self.out8[sl])
+        aux = self.scatter_image(v, self.aux[sl])
         return dict(rgb=o[..., 0:3], dist=o[..., 3], normal=o[..., 4:7], alpha=o[..., 7],
-                    depth=self.depth[sl].view(H, W), n_contrib=self.aux[sl, 2].view(H, W),
-                    final_T=self.aux[sl, 0].view(H, W).view(torch.float32))
+                    depth=self.scatter_image(v, self.depth[sl]), n_contrib=aux[..., 2],
+                    final_T=aux[..., 0].contiguous().view(torch.float32))
 
     def flags_image(self, v: int):
         H, W = self.shapes[v]
@@ -453,8 +482,9 @@ class RenderLossFn(torch.autograd.Function):
 
 
 class RenderFn(torch.autograd.Function):
-    """Differentiable masked renderer: params -> (out8 [n_pix, 8] = {rgb, dist,
-    normal, alpha}, depth [n_pix]) for all views' rendered pixels (Eq. 1-4)."""
+    """Differentiable masked renderer: params -> (out8 [n_render, 8] = {rgb, dist,
+    normal, alpha}, depth [n_render]) for all views' rendered pixels (Eq. 1-4),
+    row q holding the pixel plan.px_list[q] (view by plan.px_slice)."""
 
     @staticmethod
     def forward(ctx, plan: Plan, check: bool, means, log_scales, quats, opacity_logit, sh):

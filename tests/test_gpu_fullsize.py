@@ -78,12 +78,17 @@ def test_fullsize_sampled_gaussian_gradients(aerial):
     from paper_2501_01677_b300 import raster
     g, v, plan, cam, pr = aerial
     H, W = cam.height, cam.width
-    lin_all = np.arange(H * W, dtype=np.int64)
-    G8 = np.stack([syn.hashed_uniform(lin_all, c, seed=5) for c in range(8)], 1)
-    Gd = syn.hashed_uniform(lin_all, 8, seed=5)
+
+    def G8(lin):  # upstream gradient field, a function of the linear pixel index
+        return np.stack([syn.hashed_uniform(lin, c, seed=5) for c in range(8)], 1)
+
+    def Gd(lin):
+        return syn.hashed_uniform(lin, 8, seed=5)
+
     P = raster.GaussianParams.from_numpy(g, requires_grad=True)
     out8, depth = raster.render(plan, P)
-    obj = (out8 * torch.from_numpy(G8).cuda()).sum() + (depth * torch.from_numpy(Gd).cuda()).sum()
+    q = plan.px_index(0).cpu().numpy()  # compact rows -> linear pixel index
+    obj = (out8 * torch.from_numpy(G8(q)).cuda()).sum() + (depth * torch.from_numpy(Gd(q)).cuda()).sum()
     obj.backward()
     torch.cuda.synchronize()
     plan.check_status()
@@ -121,8 +126,8 @@ def test_fullsize_sampled_gaussian_gradients(aerial):
             continue
         dep, val = O.unbiased_depth(out, cam, torch.as_tensor(uu), torch.as_tensor(vv))
         lin = vv * W + uu
-        g8 = torch.from_numpy(G8[lin].astype(np.float64))
-        gd = torch.from_numpy(Gd[lin].astype(np.float64))
+        g8 = torch.from_numpy(G8(lin).astype(np.float64))
+        gd = torch.from_numpy(Gd(lin).astype(np.float64))
         o = (out["rgb"] * g8[:, 0:3]).sum() + (out["dist"] * g8[:, 3]).sum() + (out["normal"] * g8[:, 4:7]).sum() \
             + (out["alpha"] * g8[:, 7]).sum() + (dep * gd).sum()
         o.backward()

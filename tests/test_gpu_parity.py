@@ -165,7 +165,10 @@ def test_config0_gc_load(config0):
     w = O.luminance_gradient_weight(views[0].target)
     ref = O.gc_load(nc, w, R)
     assert float(plan.gc_load[0]) == pytest.approx(ref, rel=1e-4)
-    np.testing.assert_allclose(plan.gc_weight[:256 * 256].cpu().numpy(), w.reshape(-1), rtol=1e-5, atol=1e-6)
+    lin = plan.px_index(0).cpu().numpy()
+    np.testing.assert_allclose(plan.gc_weight[plan.px_slice(0)].cpu().numpy(), w.reshape(-1)[lin], rtol=1e-5, atol=1e-6)
+    tc = plan.target.view(-1, 3)[plan.px_slice(0)].cpu().numpy()
+    assert np.array_equal(tc, views[0].target.reshape(-1, 3)[lin])
     fl = plan.flags_image(0).cpu().numpy()
     assert ((fl & 1) != 0).sum() == M.sum() and (((fl & 2) != 0) == E).all() and (((fl & 4) != 0) == R).all()
 
@@ -184,11 +187,11 @@ def test_results_independent_of_tile_size(config0):
     outs = []
     for tile in ((8, 8), (16, 16), (16, 32), (32, 32), (32, 8)):
         plan, P = gpu_run(g, views, tile=tile, grad=False)
-        outs.append((plan.out8.cpu().numpy(), plan.aux[:, 2].cpu().numpy(), plan.depth.cpu().numpy()))
+        im = plan.images(0)
+        outs.append([im[k].cpu().numpy() for k in ("rgb", "dist", "normal", "alpha", "n_contrib", "depth")])
     for o in outs[1:]:
-        assert np.array_equal(o[0], outs[0][0])
-        assert np.array_equal(o[1], outs[0][1])
-        assert np.array_equal(o[2], outs[0][2])
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
 
 
 def test_batched_views_equal_plain_views():
@@ -199,9 +202,10 @@ def test_batched_views_equal_plain_views():
     planb, Pb = gpu_run(g, views, g_ranges=g_ranges)
     for v in range(len(views)):
         plan1, P1 = gpu_run(g, [views[v]], g_ranges=[g_ranges[v]])
-        sl = planb.pix_slice(v)
-        assert np.array_equal(planb.out8[sl].cpu().numpy(), plan1.out8.cpu().numpy())
-        assert np.array_equal(planb.aux[sl, 2].cpu().numpy(), plan1.aux[:, 2].cpu().numpy())
+        sl, s1 = planb.px_slice(v), plan1.px_slice(0)
+        assert np.array_equal(planb.px_list[sl].cpu().numpy(), plan1.px_list[s1].cpu().numpy())
+        assert np.array_equal(planb.out8[sl].cpu().numpy(), plan1.out8[s1].cpu().numpy())
+        assert np.array_equal(planb.aux[sl, 2].cpu().numpy(), plan1.aux[s1, 2].cpu().numpy())
     # gradients of the batch = sum of per-view gradients
     acc = [torch.zeros_like(t) for t in Pb.tensors()]
     for v in range(len(views)):
@@ -268,7 +272,8 @@ def test_render_fn_upstream_gradient_matches_oracle():
     P = raster.GaussianParams.from_numpy(g, requires_grad=True)
     plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, tile=(16, 16))
     out8, depth = raster.render(plan, P)
-    (out8 * torch.from_numpy(G8).cuda()).sum().add_((depth * torch.from_numpy(Gd).cuda()).sum()).backward()
+    q = plan.px_index(0)  # compact rows -> linear pixel index
+    (out8 * torch.from_numpy(G8).cuda()[q]).sum().add_((depth * torch.from_numpy(Gd).cuda()[q]).sum()).backward()
     # oracle
     cam = O.Cam.from_synth(v.cam)
     p = O.params_from_synth(g, requires_grad=True)

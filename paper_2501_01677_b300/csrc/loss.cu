@@ -22,7 +22,7 @@ struct PixCtx {
   ViewLite V;
   int x, y;
   uint64_t gp;  // dense index (flags, pixel-index map): pix_base + y W + x
-  uint32_t q;   // compact index (position in px_list): every other per-pixel array
+  uint64_t q;   // compact index (position in px_list): every other per-pixel array
 };
 
 __device__ __forceinline__ PixCtx pix_ctx(uint32_t c, int lane, const uint2* __restrict__ chunks,

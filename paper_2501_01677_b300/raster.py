@@ -406,6 +406,30 @@ class Plan:
             self.step(P, grads, lambda_ban)
         return graph
 
+    def device_bytes(self) -> dict:
+        """Bytes of this plan's device buffers, grouped as: dense per image pixel
+        (flags, pixel-index map), compact per rendered pixel, per (view,
+        Gaussian) pair, per duplicate (tile lists and sort workspace), and the
+        rest (per tile, per view)."""
+        groups = {
+            "dense_pixel": ("flags", "pidx"),
+            "compact_pixel": ("px_list", "target", "gc_weight", "out8", "depth", "aux", "dout8", "scratch", "chunks",
+                              "chunk_scratch"),
+            "pair": ("rec", "dkey", "bininfo", "grad2d"),
+            "duplicate": ("dup_pairs", "ws"),
+        }
+        out, seen = {}, set()
+        for grp, names in groups.items():
+            out[grp] = 0
+            for n in names:
+                t = getattr(self, n, None)
+                if torch.is_tensor(t):
+                    out[grp] += t.numel() * t.element_size()
+                    seen.add(n)
+        out["other"] = sum(t.numel() * t.element_size() for n, t in vars(self).items()
+                           if torch.is_tensor(t) and t.is_cuda and n not in seen)
+        return out
+
     def check_status(self):
         st = self.status_value()
         if st:

@@ -403,6 +403,83 @@ def config3(sizes=CONFIG3_SIZES, views_per_region=4, res=CONFIG3_RES, scale=1.0)
     return Gaussians.concat(parts), ranges, views, owner
 
 
+CONFIG4_TOTAL = 20_000_000
+CONFIG4_REGIONS = 12
+CONFIG4_RES = (6000, 4000)
+
+
+def config4_sizes(total=CONFIG4_TOTAL, regions=CONFIG4_REGIONS):
+    """Region sizes following the uneven config-3 pattern: the 8 sizes 200k..3M
+    interpolated linearly at `regions` evenly spaced positions, then scaled so
+    that they sum to `total`."""
+    pat = np.asarray(CONFIG3_SIZES, np.float64)
+    s = np.interp(np.linspace(0.0, len(pat) - 1.0, regions), np.arange(len(pat), dtype=np.float64), pat)
+    sizes = np.floor(s / s.sum() * total).astype(np.int64)
+    sizes[-1] += total - int(sizes.sum())
+    return tuple(int(v) for v in sizes)
+
+
+class LazyImages:
+    """Per-view images made on demand from a per-view seed, so that a large batch
+    of views never holds every mask or target in host memory at once."""
+
+    def __init__(self, fn, n):
+        self.fn, self.n = fn, n
+
+    def __len__(self):
+        return self.n
+
+    def __getitem__(self, v):
+        if not 0 <= v < self.n:
+            raise IndexError(v)
+        return self.fn(v)
+
+
+def config4(scale=1.0, views_per_region=6, res=CONFIG4_RES, total=CONFIG4_TOTAL, regions=CONFIG4_REGIONS):
+    """City block at HBM capacity: `regions` sub-regions totalling `total`
+    Gaussians (config4_sizes), each on its own building scene, with
+    views_per_region oblique views at 6000x4000 (fx = 1.2 W = 7200) and rectangle
+    masks of coverage U(0.2, 0.6).  `scale` < 1 shrinks the Gaussian counts by
+    scale and each image side by sqrt(scale) (same buildings and cameras).  Masks and targets are generated
+    per view on access (LazyImages).  Returns (gaussians, per-region ranges,
+    cameras, view -> region, masks, targets)."""
+    rs, rc, _, _ = streams(4)
+    parts, ranges, cams, owner = [], [], [], []
+    start = 0
+    for s, n_full in enumerate(config4_sizes(total, regions)):
+        n = max(1, int(n_full * scale))
+        nb = max(2, int(round(40 * n_full / 1_500_000)))  # the scene keeps its full-size layout
+        area = 160.0 * math.sqrt(nb / 40)
+        boxes = random_boxes(rs, nb, area=area)
+        parts.append(surface_gaussians(rs, boxes, n, ground=area * 1.25))
+        ranges.append((start, start + n))
+        start += n
+        w, h = res
+        if scale < 1.0:
+            w, h = max(64, int(w * math.sqrt(scale))), max(64, int(h * math.sqrt(scale)))
+        alt = 120.0 * math.sqrt(nb / 40)
+        for j in range(views_per_region):
+            az = 360.0 / views_per_region * j + float(rc.uniform(-15, 15))
+            cams.append(aerial_camera(w, h, alt, 45.0, azimuth_deg=az))
+            owner.append(s)
+    g = Gaussians.concat(parts)
+    del parts
+
+    def view_rng(v, what):
+        return np.random.Generator(np.random.PCG64(np.random.SeedSequence([BASE_SEED + 4, what, v])))
+
+    def mask(v):
+        r = view_rng(v, 1)
+        c = cams[v]
+        return rect_mask(r, c.height, c.width, float(r.uniform(0.2, 0.6)), 0.03)
+
+    def target(v):
+        c = cams[v]
+        return random_target(view_rng(v, 2), c.height, c.width)
+
+    return g, ranges, cams, owner, LazyImages(mask, len(cams)), LazyImages(target, len(cams))
+
+
 def tiny_scene(seed, n=48, width=32, height=32, fx=40.0, coverage=0.5, zmin=3.0, zmax=8.0, log_scale_mu=-1.5):
     """Small random scene for brute-force checks."""
     ss = np.random.SeedSequence([BASE_SEED, 7, seed])

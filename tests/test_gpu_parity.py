@@ -327,3 +327,24 @@ def test_persistent_lpt_schedule_and_graph_replay_match_plain():
         assert np.allclose(other.loss_buf.cpu().numpy(), plain.loss_buf.cpu().numpy(), rtol=1e-6)
         for a, b in zip(go, gp):
             assert rel_l2(a.ravel().astype(np.float64), b.ravel().astype(np.float64)) < 1e-5
+
+
+def test_city_block_small_scale_compact_memory():
+    """All 72 views of the city-block workload (at 1/2000 of its Gaussians) in one
+    plan: per-pixel memory is 5 B per image pixel plus a fixed record per rendered
+    pixel, and every view's outputs land on its own rendered set."""
+    from paper_2501_01677_b300 import raster
+    g, ranges, cams, owner, masks, targets = syn.config4(scale=0.0005)
+    plan = raster.Plan(cams, masks, targets, g.n, g_ranges=[ranges[o] for o in owner])
+    P = raster.GaussianParams.from_numpy(g)
+    plan.forward(P)
+    plan.loss()
+    torch.cuda.synchronize()
+    plan.check_status()
+    b = plan.device_bytes()
+    assert b["dense_pixel"] == 5 * plan.n_pix
+    assert b["compact_pixel"] == 128 * plan.n_render + 24 * plan.n_chunks
+    for v in (0, 35, 71):
+        R = (plan.flags_image(v).cpu().numpy() & 4) != 0
+        a = plan.images(v)["alpha"].cpu().numpy()
+        assert (a[~R] == 0).all() and a[R].max() > 0

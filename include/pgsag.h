@@ -296,12 +296,23 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
  *   L = L_rgb + lambda_ban L_ban.
  * Writes dL/d(out8) for every R pixel (gradient through both n_depth -- into D
  * and N of the 4 neighbours via Eq. 4 -- and the rendered normal; dL/dA = 0).
+ * Two passes: pass A evaluates the terms, the own-pixel gradient and, per mask
+ * pixel, dL/da and dL/db of its two central differences (scratch); pass B
+ * gathers those from each pixel's neighbours and maps them through Eq. 4.
  *   flags    dense per-pixel flags; pidx the dense pixel-index map (both from
  *            mask preparation); neighbours are found through pidx
+ *   aux      pgsag_render_fwd's aux (read only when gc_weight is given)
  *   target   float [3 per compact pixel] (from pgsag_prep_gc_weight)
+ *   gc_weight  nullable, float [1 per compact pixel] (pgsag_prep_gc_weight): when
+ *            given, pass A also sums the Eq. 9 statistic (see pgsag_tile_stats)
+ *            and gc_load [1 per view] receives the GC-load; both or neither
+ *   gather   1: run pass B, dout8 is complete.  0: skip it; dout8 then holds
+ *            pass A's values and pgsag_render_bwd must be given a
+ *            pgsag_ban_gather built from the same scratch and acc
  *   scratch  float [6 per compact pixel] (only M pixels touched)
- *   acc      double [4 per view] scratch accumulators
- *   chunk_scratch  float [4 per chunk] scratch (per-chunk partial sums, reduced
+ *   acc      double [8 per view]: {sum L1, sum w |n_depth - n|^2, |V|, 0,
+ *            |R|, sum g/w, sum (g/w)^2, 0}, overwritten
+ *   chunk_scratch  float [8 per chunk] scratch (per-chunk partial sums, reduced
  *            per view without contended atomics)
  *   loss     float [3 per view + 1]: {L_rgb, L_ban, L} per view, then sum_v L
  *   dout8    float [8 per compact pixel]
@@ -309,9 +320,25 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
 int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                    const void* chunks, const void* act_tiles, const uint32_t* px_list,
                    const uint8_t* flags, const uint32_t* pidx, const float* out8, const float* depth,
-                   const void* aux, const float* target, float lambda_ban, float* scratch,
-                   double* acc, float* chunk_scratch, float* loss, float* dout8, int32_t* status,
-                   void* stream);
+                   const void* aux, const float* target, float lambda_ban, const float* gc_weight,
+                   int gather, float* scratch, double* acc, float* chunk_scratch, float* loss,
+                   float* gc_load, float* dout8, int32_t* status, void* stream);
+
+/*
+ * Deferred Eq. 8 adjoint for pgsag_render_bwd.  pgsag_loss_ban with gather = 0
+ * leaves out its second pass (the neighbour gather of dL/dP, P = Depth r, and
+ * the lambda / |V| scaling of the normal-loss gradient); pgsag_render_bwd given
+ * this struct does that gather for each pixel as it loads the pixel's upstream
+ * gradient, which saves one pass over the per-pixel arrays.
+ */
+typedef struct pgsag_ban_gather {
+  const uint8_t* flags;    /* device, dense per-pixel flags (mask preparation)          */
+  const uint32_t* pidx;    /* device, dense pixel-index map (pgsag_prep_lists)          */
+  const float* scratch;    /* device, loss scratch from pgsag_loss_ban (6 per compact px) */
+  const double* acc;       /* device, loss accumulators from pgsag_loss_ban (8 per view) */
+  float lambda_ban;        /* the lambda given to pgsag_loss_ban                         */
+  uint32_t reserved;       /* 0                                                         */
+} pgsag_ban_gather;
 
 /*
  * pgsag_render_bwd (Sec. 3.1: the Gaussians' parameters are fitted through the
@@ -324,15 +351,17 @@ int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
  * float4 atomic add per 4 values per tile).  grad2d (16-byte aligned) is zeroed
  * by this call.  out8, aux, dout8 and ddepth are compact per-pixel arrays
  * (8, 1, 8, 1 entries per px_list position).  ddepth (nullable) adds a
- * gradient on the depth output, folded into dD and dN through Eq. 4.  dout_scale (nullable, device float[1])
+ * gradient on the depth output, folded into dD and dN through Eq. 4.  ban
+ * (nullable, host struct) adds the deferred Eq. 8 gather: dout8 is then the
+ * output of pgsag_loss_ban with gather = 0.  dout_scale (nullable, device float[1])
  * multiplies the whole upstream gradient (chain rule from a scalar loss).
  */
 int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec,
                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
                      uint32_t n_active_total, const uint32_t* px_list, const pgsag_sched* sched,
                      const float* out8, const void* aux, const float* dout8, const float* ddepth,
-                     const float* dout_scale, uint32_t n_pairs, float* grad2d, int32_t* status,
-                     void* stream);
+                     const pgsag_ban_gather* ban, const float* dout_scale, uint32_t n_pairs, float* grad2d,
+                     int32_t* status, void* stream);
 
 /*
  * pgsag_preprocess_bwd: chain rule from grad2d to the raw parameters (the
@@ -357,7 +386,8 @@ int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const float* log_
  *   per view, GC-load = population std over R pixels of g_i / w_i with
  *     g_i = n_contrib (from aux) and w_i from pgsag_prep_gc_weight;
  *   acc   double [3 per view] scratch; chunk_scratch float [4 per chunk] scratch;
- *   gc_load float [1 per view].
+ *   gc_load float [1 per view]; NULL computes the tile counts only (acc,
+ *     chunk_scratch, aux and gc_weight are then not used).
  */
 int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint32_t n_active_total,
                      const void* ranges, uint32_t n_chunks, const void* chunks,

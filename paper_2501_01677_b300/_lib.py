@@ -49,6 +49,12 @@ class PgsagSched(ctypes.Structure):
     _fields_ = [("order", c_void_p), ("counter", c_void_p), ("ctas_per_sm", c_int32), ("reserved", c_int32)]
 
 
+class PgsagBanGather(ctypes.Structure):
+    """pgsag_ban_gather: the deferred Eq. 8 gather done by the render adjoint."""
+    _fields_ = [("flags", c_void_p), ("pidx", c_void_p), ("scratch", c_void_p), ("acc", c_void_p),
+                ("lambda_ban", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -76,9 +82,10 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_bin_workspace_size", c_size_t, [c_uint32, c_uint64])
     _sig(lib, "pgsag_bin", c_int, [c_uint32, c_uint32, P, c_uint32, P, P, P, P, c_uint64, P, c_size_t, P, P, P, P, P])
     _sig(lib, "pgsag_render_fwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P])
-    _sig(lib, "pgsag_loss_ban", c_int, [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, c_float, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_loss_ban", c_int, [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, c_float, P, c_int, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_render_bwd", c_int,
-         [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P, c_uint32, P, P, P])
+         [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, POINTER(PgsagBanGather), P,
+          c_uint32, P, P, P])
     _sig(lib, "pgsag_preprocess_bwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_tile_stats_noalloc", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P])

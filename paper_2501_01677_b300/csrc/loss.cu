@@ -2,10 +2,12 @@
 // their gradient on the rendered channels; per-tile / per-pixel Gaussian
 // counts and the GC-load statistic (Sec. 4.3, Eq. 9).
 //
-// The loss needs the unbiased depth (Eq. 4) of each pixel's 4 neighbours, so the
-// per-pixel arrays are dense per view (only rendered pixels are touched) and the
-// kernels walk the compacted pixel lists chunk by chunk (one warp, one pixel per
-// lane).
+// The kernels walk the compacted pixel lists chunk by chunk (one warp, one pixel
+// per lane); per-pixel arrays are compact (indexed by px_list position) and a
+// pixel's 4 neighbours are found through the dense pixel-index map.  Pass A
+// (loss, own-pixel gradient, neighbour scratch, optionally the GC-load sums)
+// is followed either by pass B here or by the same gather in the render
+// adjoint's prologue.
 #include <mutex>
 
 #include "common.cuh"
@@ -58,15 +60,21 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
     const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
     const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
     const uint8_t* __restrict__ flags, const uint32_t* __restrict__ pidx, const float4* __restrict__ out8,
-    const float* __restrict__ depth, const float* __restrict__ target, float* __restrict__ scratch,
-    float4* __restrict__ partial, float4* __restrict__ dout8, const int32_t* status) {
+    const float* __restrict__ depth, const float* __restrict__ target, const uint4* __restrict__ aux,
+    const float* __restrict__ gc_weight, float* __restrict__ scratch, float4* __restrict__ partial,
+    float4* __restrict__ dout8, const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
   if (c >= n_chunks) return;
   const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
-  float l1 = 0.f, lb = 0.f, nv = 0.f;
+  float l1 = 0.f, lb = 0.f, nv = 0.f, gn = 0.f, gx = 0.f;
   if (P.has) {
+    if (gc_weight != nullptr) {
+      // Eq. 9 term of this rendered pixel: g / w (g = Gaussians blended)
+      gx = (float)__ldg(&aux[P.q].z) / __ldg(gc_weight + P.q);
+      gn = 1.f;
+    }
     const uint8_t f = __ldg(flags + P.gp);
     const float4 o0 = __ldg(out8 + 2 * P.q), o1 = __ldg(out8 + 2 * P.q + 1);
     float dC[3] = {0.f, 0.f, 0.f}, dNo[3] = {0.f, 0.f, 0.f};
@@ -148,39 +156,48 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_a(
     dout8[2 * P.q] = make_float4(dC[0], dC[1], dC[2], 0.f);
     dout8[2 * P.q + 1] = make_float4(dNo[0], dNo[1], dNo[2], 0.f);
   }
-  // per-chunk partial sums, reduced per view by k_view_reduce
+  // per-chunk partial sums (8 per chunk), reduced per view by k_view_reduce
   const float s1 = warp_sum(l1), s2 = warp_sum(lb), s3 = warp_sum(nv);
-  if (lane == 0) partial[c] = make_float4(s1, s2, s3, 0.f);
+  float s4 = 0.f, s5 = 0.f, s6 = 0.f;
+  if (gc_weight != nullptr) {
+    s4 = warp_sum(gn);
+    s5 = warp_sum(gx);
+    s6 = warp_sum(gx * gx);
+  }
+  if (lane == 0) {
+    partial[2 * c] = make_float4(s1, s2, s3, 0.f);
+    partial[2 * c + 1] = make_float4(s4, s5, s6, 0.f);
+  }
 }
 
 // Grid (blocks, views): each block sums a slice of the view's per-chunk partials
-// in double and adds it into acc[stride * v + 0 .. ncomp) (acc zeroed before).
+// (pstride floats per chunk, the first ncomp <= 8 used) in double and adds them
+// into acc[stride * v + 0 .. ncomp) (acc zeroed before).
 __global__ void __launch_bounds__(256) k_view_reduce(const pgsag_view* __restrict__ views,
-                                                     const float4* __restrict__ partial, int ncomp,
+                                                     const float* __restrict__ partial, int pstride, int ncomp,
                                                      int stride, double* __restrict__ acc,
                                                      const int32_t* status) {
-  __shared__ double sh[8][3];
+  __shared__ double sh[8][8];
   if (status_bad(status)) return;
   const pgsag_view* V = views + blockIdx.y;
   const uint32_t b = __ldg(&V->chunk_base), n = __ldg(&V->n_chunks);
   const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
   const uint32_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
   if (lo >= hi) return;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const float4 p = __ldg(partial + b + i);
-    a0 += p.x;
-    a1 += p.y;
-    a2 += p.z;
+    const float* p = partial + (size_t)(b + i) * pstride;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < ncomp) a[k] += __ldg(p + k);
   }
-  a0 = warp_sum_d(a0);
-  a1 = warp_sum_d(a1);
-  a2 = warp_sum_d(a2);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    sh[warp][0] = a0;
-    sh[warp][1] = a1;
-    sh[warp][2] = a2;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k < ncomp) {
+      const double t = warp_sum_d(a[k]);
+      if (lane == 0) sh[warp][k] = t;
+    }
   }
   __syncthreads();
   if (threadIdx.x < ncomp) {
@@ -204,7 +221,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_b(
   if (c >= n_chunks) return;
   const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
   if (!P.has) return;
-  const double nV = acc[4 * P.view + 2];
+  const double nV = acc[8 * P.view + 2];
   const float scale = nV > 0.0 ? (float)(lambda_ban / nV) : 0.f;
   const int W = P.V.width, H = P.V.height;
   float dP[3] = {0.f, 0.f, 0.f};
@@ -269,21 +286,33 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_b(
   dout8[2 * P.q + 1] = g1;
 }
 
-// One thread: per-view losses and their sum (views are few).
+// One thread: per-view losses and their sum (views are few); with gc_load, the
+// per-view GC-load (Eq. 9: population std of g / w over the rendered pixels).
+__device__ __forceinline__ float gc_std(double n, double s, double q) {
+  double var = 0.0;
+  if (n > 0.0) {
+    const double m = s / n;
+    var = q / n - m * m;
+  }
+  return (float)sqrt(var > 0.0 ? var : 0.0);
+}
+
 __global__ void k_loss_final(const pgsag_view* __restrict__ views, uint32_t n_views,
                              const double* __restrict__ acc, float lambda_ban, float* __restrict__ loss,
-                             const int32_t* status) {
+                             float* __restrict__ gc_load, const int32_t* status) {
   if (status_bad(status)) return;
   if (threadIdx.x != 0) return;
   double total = 0.0;
   for (uint32_t v = 0; v < n_views; ++v) {
+    const double* a = acc + 8 * v;
     const uint32_t nm = views[v].n_mask;
-    const double lr = nm ? acc[4 * v + 0] / (3.0 * nm) : 0.0;
-    const double lb = acc[4 * v + 2] > 0.0 ? acc[4 * v + 1] / acc[4 * v + 2] : 0.0;
+    const double lr = nm ? a[0] / (3.0 * nm) : 0.0;
+    const double lb = a[2] > 0.0 ? a[1] / a[2] : 0.0;
     loss[3 * v + 0] = (float)lr;
     loss[3 * v + 1] = (float)lb;
     loss[3 * v + 2] = (float)(lr + (double)lambda_ban * lb);
     total += lr + (double)lambda_ban * lb;
+    if (gc_load) gc_load[v] = gc_std(a[4], a[5], a[6]);
   }
   loss[3 * n_views] = (float)total;
 }
@@ -324,13 +353,7 @@ __global__ void k_gc_final(uint32_t n_views, const double* __restrict__ acc, flo
   if (status_bad(status)) return;
   const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n_views) return;
-  const double n = acc[3 * v], s = acc[3 * v + 1], q = acc[3 * v + 2];
-  double var = 0.0;
-  if (n > 0.0) {
-    const double m = s / n;
-    var = q / n - m * m;
-  }
-  out[v] = (float)sqrt(var > 0.0 ? var : 0.0);
+  out[v] = gc_std(acc[3 * v], acc[3 * v + 1], acc[3 * v + 2]);
 }
 
 // Per rendered pixel of one view (compact index px_base + i): the target colour
@@ -367,34 +390,38 @@ using namespace pgsag;
 extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                               const void* chunks, const void* act_tiles, const uint32_t* px_list,
                               const uint8_t* flags, const uint32_t* pidx, const float* out8, const float* depth,
-                              const void* aux, const float* target, float lambda_ban, float* scratch,
-                              double* acc, float* chunk_scratch, float* loss, float* dout8, int32_t* status,
-                              void* stream) {
-  (void)aux;
+                              const void* aux, const float* target, float lambda_ban, const float* gc_weight,
+                              int gather, float* scratch, double* acc, float* chunk_scratch, float* loss,
+                              float* gc_load, float* dout8, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status || !acc || !loss) return PGSAG_ERR_ARG;
+  if ((gc_weight == nullptr) != (gc_load == nullptr)) return PGSAG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 4 * sizeof(double), s));
+  PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 8 * sizeof(double), s));
   if (n_chunks) {
     if (!chunks || !act_tiles || !px_list || !flags || !pidx || !out8 || !depth || !target || !scratch ||
-        !dout8 || !chunk_scratch)
+        !dout8 || !chunk_scratch || (gc_weight && !aux))
       return PGSAG_ERR_ARG;
-    if (((uintptr_t)out8 | (uintptr_t)dout8 | (uintptr_t)act_tiles | (uintptr_t)chunk_scratch) & 15u)
+    if (((uintptr_t)out8 | (uintptr_t)dout8 | (uintptr_t)act_tiles | (uintptr_t)chunk_scratch | (uintptr_t)aux) &
+        15u)
       return PGSAG_ERR_ARG;
     const unsigned blocks = pgsag_div_up(n_chunks, kLossThreads / 32);
     k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
-                                             px_list, flags, pidx, (const float4*)out8, depth, target, scratch,
-                                             (float4*)chunk_scratch, (float4*)dout8, status);
+                                             px_list, flags, pidx, (const float4*)out8, depth, target,
+                                             (const uint4*)aux, gc_weight, scratch, (float4*)chunk_scratch,
+                                             (float4*)dout8, status);
     PGSAG_CHECK_LAUNCH();
-    k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 4, acc,
-                                                                status);
+    k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 8, gc_weight ? 7 : 3, 8,
+                                                                acc, status);
     PGSAG_CHECK_LAUNCH();
-    k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
-                                             px_list, flags, pidx, (const float4*)out8, depth, scratch, acc,
-                                             lambda_ban, (float4*)dout8, status);
-    PGSAG_CHECK_LAUNCH();
+    if (gather) {
+      k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
+                                               px_list, flags, pidx, (const float4*)out8, depth, scratch, acc,
+                                               lambda_ban, (float4*)dout8, status);
+      PGSAG_CHECK_LAUNCH();
+    }
   }
-  k_loss_final<<<1, 32, 0, s>>>(views, n_views, acc, lambda_ban, loss, status);
+  k_loss_final<<<1, 32, 0, s>>>(views, n_views, acc, lambda_ban, loss, gc_load, status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }
@@ -405,15 +432,18 @@ extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint3
                                 const float* gc_weight, uint32_t* tile_counts, double* acc,
                                 float* chunk_scratch, float* gc_load, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
-  if (!views || !status || !acc || !gc_load) return PGSAG_ERR_ARG;
+  if (!views || !status) return PGSAG_ERR_ARG;
+  const bool gc = gc_load != nullptr;  // NULL: per-tile counts only
+  if (gc && !acc) return PGSAG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 3 * sizeof(double), s));
+  if (gc) PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 3 * sizeof(double), s));
   if (n_active_total) {
     if (!ranges || !tile_counts) return PGSAG_ERR_ARG;
     k_tile_counts<<<pgsag_div_up(n_active_total, 256), 256, 0, s>>>(n_active_total, (const uint2*)ranges,
                                                                     tile_counts, status);
     PGSAG_CHECK_LAUNCH();
   }
+  if (!gc) return PGSAG_OK;
   if (n_chunks) {
     if (!chunks || !act_tiles || !px_list || !aux || !gc_weight || !chunk_scratch) return PGSAG_ERR_ARG;
     if (((uintptr_t)chunk_scratch | (uintptr_t)aux) & 15u) return PGSAG_ERR_ARG;
@@ -421,8 +451,7 @@ extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint3
         views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles, px_list, (const uint4*)aux, gc_weight,
         (float4*)chunk_scratch, status);
     PGSAG_CHECK_LAUNCH();
-    k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, (const float4*)chunk_scratch, 3, 3, acc,
-                                                                status);
+    k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 4, 3, 3, acc, status);
     PGSAG_CHECK_LAUNCH();
   }
   k_gc_final<<<pgsag_div_up(n_views, 128), 128, 0, s>>>(n_views, acc, gc_load, status);

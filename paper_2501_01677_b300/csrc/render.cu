@@ -2,7 +2,8 @@
 //
 // Work item = one active tile, handled by one CTA of 4 warps.  The tile's
 // rendered (mask-dilated) pixels are compacted; each lane takes 2 of them (more
-// rounds for tiles larger than 256 pixels).  The tile's depth-sorted Gaussians
+// rounds for tiles larger than 256 pixels) and evaluates both with packed
+// two-lane FP32 instructions (fma/add/mul .f32x2).  The tile's depth-sorted Gaussians
 // are staged through shared memory in batches of 256 (64-byte records,
 // coalesced), then each warp walks the batch, skipping -- as a warp-uniform
 // branch -- every Gaussian whose alpha >= 1/255 box misses the bounding box of
@@ -17,26 +18,14 @@
 namespace pgsag {
 
 // Launch shape (compile-time; the defaults are the best measured on B300 for the
-// 5472x3648 aerial workload): warps per CTA (one CTA per active tile), pixels
-// per lane, Gaussians staged per batch, the number of resident CTAs per SM the
-// register allocation must allow (forward 10, adjoint 7), and the largest number
-// of contributing lanes for which the adjoint adds a Gaussian's gradient to
-// shared memory lane by lane instead of reducing across the warp (0: always
-// reduce).
+// 5472x3648 aerial workload): warps per CTA (one CTA per active tile), Gaussians
+// staged per batch and the number of resident CTAs per SM the register
+// allocation must allow (forward 10, adjoint 7).  Each lane renders 2 pixels.
 #ifndef PGSAG_FWD_WARPS
 #define PGSAG_FWD_WARPS 4
 #endif
-#ifndef PGSAG_FWD_PPT
-#define PGSAG_FWD_PPT 2
-#endif
 #ifndef PGSAG_BWD_WARPS
 #define PGSAG_BWD_WARPS 4
-#endif
-#ifndef PGSAG_BWD_PPT
-#define PGSAG_BWD_PPT 2
-#endif
-#ifndef PGSAG_BWD_DIRECT
-#define PGSAG_BWD_DIRECT 0
 #endif
 #ifndef PGSAG_BATCH
 #define PGSAG_BATCH 128
@@ -95,46 +84,57 @@ __device__ __forceinline__ uint32_t next_tile(const Sched& s, uint32_t& iter, ui
 }
 
 // Pixels of lane `lane` in warp `warp` for the round starting at r0: entries
-// r0 + (warp * kPPT + k) * 32 + lane of the tile's compacted pixel list, so a
-// warp covers kPPT consecutive 32-pixel runs.  Pixel centres are kept relative
-// to an origin (ox, oy) near the tile, exactly, like the staged Gaussian
-// centres, so that offsets do not lose precision to the image size.
-template <int kPPT>
+// r0 + (2 warp + k) * 32 + lane (k = 0, 1) of the tile's compacted pixel list,
+// so a warp covers two consecutive 32-pixel runs.  The two pixels of a lane are
+// processed together with packed two-lane FP32 instructions (x = pixel 0,
+// y = pixel 1).  Pixel centres are kept relative to an origin (ox, oy) near the
+// tile, exactly, like the staged Gaussian centres, so that offsets do not lose
+// precision to the image size.
 struct Pix {
-  bool has[kPPT];
-  uint32_t q[kPPT];          // compact index (position in px_list): per-pixel arrays
-  float px[kPPT], py[kPPT];  // centre minus tile origin
+  bool has0, has1;
+  uint32_t q0, q1;  // compact index (position in px_list): per-pixel arrays
+  float2 px, py;    // centres minus tile origin
 };
 
-template <int kPPT>
-__device__ __forceinline__ Pix<kPPT> load_pixels(const TileInfo& ti, uint32_t r0, int warp, int lane, int width,
-                                                 int ox, int oy, const uint32_t* __restrict__ px_list) {
-  Pix<kPPT> P;
+__device__ __forceinline__ Pix load_pixels(const TileInfo& ti, uint32_t r0, int warp, int lane, int width, int ox,
+                                           int oy, const uint32_t* __restrict__ px_list) {
+  Pix P;
+  float c[2][2];
+  bool has[2];
+  uint32_t q[2];
 #pragma unroll
-  for (int k = 0; k < kPPT; ++k) {
-    const uint32_t li = r0 + (uint32_t)((warp * kPPT + k) * 32 + lane);
-    P.has[k] = li < ti.npix;
-    P.q[k] = ti.px_first + li;
-    const uint32_t pix = P.has[k] ? __ldg(px_list + P.q[k]) : 0u;
+  for (int k = 0; k < 2; ++k) {
+    const uint32_t li = r0 + (uint32_t)((warp * 2 + k) * 32 + lane);
+    has[k] = li < ti.npix;
+    q[k] = ti.px_first + li;
+    const uint32_t pix = has[k] ? __ldg(px_list + q[k]) : 0u;
     const uint32_t yy = pix / (uint32_t)width;
-    P.px[k] = (float)((int)(pix - yy * (uint32_t)width) - ox) + 0.5f;
-    P.py[k] = (float)((int)yy - oy) + 0.5f;
+    c[k][0] = (float)((int)(pix - yy * (uint32_t)width) - ox) + 0.5f;
+    c[k][1] = (float)((int)yy - oy) + 0.5f;
   }
+  P.has0 = has[0];
+  P.has1 = has[1];
+  P.q0 = q[0];
+  P.q1 = q[1];
+  P.px = make_float2(c[0][0], c[1][0]);
+  P.py = make_float2(c[0][1], c[1][1]);
   return P;
 }
 
 // Bounding box of the warp's valid pixel centres (warp-uniform result).
-template <int kPPT>
-__device__ __forceinline__ float4 warp_pixel_box(const Pix<kPPT>& P) {
+__device__ __forceinline__ float4 warp_pixel_box(const Pix& P) {
   float x0 = 3.0e38f, x1 = -3.0e38f, y0 = 3.0e38f, y1 = -3.0e38f;
-#pragma unroll
-  for (int k = 0; k < kPPT; ++k) {
-    if (P.has[k]) {
-      x0 = fminf(x0, P.px[k]);
-      x1 = fmaxf(x1, P.px[k]);
-      y0 = fminf(y0, P.py[k]);
-      y1 = fmaxf(y1, P.py[k]);
-    }
+  if (P.has0) {
+    x0 = fminf(x0, P.px.x);
+    x1 = fmaxf(x1, P.px.x);
+    y0 = fminf(y0, P.py.x);
+    y1 = fmaxf(y1, P.py.x);
+  }
+  if (P.has1) {
+    x0 = fminf(x0, P.px.y);
+    x1 = fmaxf(x1, P.px.y);
+    y0 = fminf(y0, P.py.y);
+    y1 = fmaxf(y1, P.py.y);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -144,6 +144,20 @@ __device__ __forceinline__ float4 warp_pixel_box(const Pix<kPPT>& P) {
     y1 = fmaxf(y1, __shfl_xor_sync(kFull, y1, o));
   }
   return make_float4(x0, x1, y0, y1);
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// gauss_power for the lane's two pixels with packed instructions.  Each half is
+// the same sequence of correctly rounded operations as the scalar form (x - m
+// is x + (-m)), so forward and adjoint obtain identical exponents.
+__device__ __forceinline__ float2 gauss_power2(float2 px, float2 py, float4 r0, float l22, float2& dx, float2& dy,
+                                               float2& u, float2& w) {
+  dx = __fadd2_rn(px, f2(-r0.x));
+  dy = __fadd2_rn(py, f2(-r0.y));
+  u = __ffma2_rn(f2(r0.z), dx, __fmul2_rn(f2(r0.w), dy));
+  w = __fmul2_rn(f2(l22), dy);
+  return __fmul2_rn(f2(-0.5f), __ffma2_rn(u, u, __fmul2_rn(w, w)));
 }
 
 // Shared-memory image of a batch of staged Gaussians, packed by use:
@@ -186,7 +200,22 @@ __device__ __forceinline__ void warp_relevance(const Stage& S, int limit, float4
   }
 }
 
-template <int kWarps, int kPPT>
+// Forward outputs of one pixel: {C, D}, {N, A = 1 - T}, the Eq. 4 depth and
+// {T, last blended, count}.  (x, y) is the pixel centre in image coordinates.
+__device__ __forceinline__ void write_pixel(uint64_t gp, float4 cd, float4 nt, uint32_t last, uint32_t cnt, float x,
+                                            float y, const ViewLite& V, float4* __restrict__ out8,
+                                            float* __restrict__ depth, uint4* __restrict__ aux) {
+  out8[2 * gp + 0] = cd;
+  out8[2 * gp + 1] = make_float4(nt.x, nt.y, nt.z, 1.f - nt.w);
+  // Eq. 4: ray-plane depth
+  const float rx = (x - V.cx) / V.fx, ry = (y - V.cy) / V.fy;
+  const float sdot = -(nt.x * rx + nt.y * ry + nt.z);
+  const bool valid = cnt > 0 && sdot > kRayDotMin && cd.w > 0.f;
+  depth[gp] = valid ? cd.w / sdot : 0.f;
+  aux[gp] = make_uint4(__float_as_uint(nt.w), last, cnt, 0u);
+}
+
+template <int kWarps>
 __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
     const pgsag_view* __restrict__ views, const float4* __restrict__ rec,
     const uint32_t* __restrict__ dup_pairs, const uint2* __restrict__ ranges,
@@ -194,7 +223,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
     Sched sched, float4* __restrict__ out8, float* __restrict__ depth, uint4* __restrict__ aux,
     const int32_t* status) {
   constexpr int kRenderThreads = kWarps * 32;
-  constexpr int kTilePix = kRenderThreads * kPPT;
+  constexpr int kTilePix = kRenderThreads * 2;
   constexpr int kStagePerThread = kBatch / kRenderThreads;
   static_assert(kBatch % kRenderThreads == 0 && kStagePerThread >= 1, "batch must be a multiple of the CTA size");
   __shared__ Stage S;
@@ -212,21 +241,13 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
       // the tile (every supported tile lies in one cell), so offsets round the
       // same way whatever the tile size
       const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
-      const Pix<kPPT> P = load_pixels<kPPT>(ti, r0, warp, lane, V.width, ox, oy, px_list);
+      const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
-      float T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT], N0[kPPT], N1[kPPT], N2[kPPT];
-      uint32_t last[kPPT], cnt[kPPT];
-      bool done[kPPT];
-      bool all_done = true;
-#pragma unroll
-      for (int k = 0; k < kPPT; ++k) {
-        T[k] = 1.f;
-        C0[k] = C1[k] = C2[k] = D[k] = N0[k] = N1[k] = N2[k] = 0.f;
-        last[k] = 0;
-        cnt[k] = 0;
-        done[k] = !P.has[k];
-        all_done = all_done && done[k];
-      }
+      float2 T = f2(1.f), C0 = f2(0.f), C1 = f2(0.f), C2 = f2(0.f), D = f2(0.f), N0 = f2(0.f), N1 = f2(0.f),
+             N2 = f2(0.f);
+      uint32_t last0 = 0, last1 = 0, cnt0 = 0, cnt1 = 0;
+      bool done0 = !P.has0, done1 = !P.has1;
+      bool all_done = done0 && done1;
       for (uint32_t base = ti.rbeg; base < ti.rend; base += kBatch) {
         if (!__syncthreads_or(!all_done)) break;
         const uint32_t nb = min((uint32_t)kBatch, ti.rend - base);
@@ -248,36 +269,45 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
             m &= m - 1;
             const float4 q0 = S.g0[j];
             const float4 q1 = S.g1[j];
-#pragma unroll
-            for (int k = 0; k < kPPT; ++k) {
-              if (done[k]) continue;
-              float dx, dy, u, w2;
-              const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy, u, w2);
-              if (!(pw >= q1.z)) continue;  // alpha < 1/255
-              const float alpha = fminf(__fmul_rn(q1.y, __expf(pw)), kAlphaMax);
-              const float test = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
-              if (test < kTMin) {
-                done[k] = true;
-                continue;
-              }
-              const float4 q2 = S.g2[j];
-              const float4 q3 = S.g3[j];
-              const float w = __fmul_rn(alpha, T[k]);
-              C0[k] = fmaf(w, q2.x, C0[k]);
-              C1[k] = fmaf(w, q2.y, C1[k]);
-              C2[k] = fmaf(w, q2.z, C2[k]);
-              D[k] = fmaf(w, q2.w, D[k]);
-              N0[k] = fmaf(w, q3.x, N0[k]);
-              N1[k] = fmaf(w, q3.y, N1[k]);
-              N2[k] = fmaf(w, q3.z, N2[k]);
-              T[k] = test;
-              last[k] = base + j;
-              ++cnt[k];
+            float2 dx, dy, u, w2;
+            const float2 pw = gauss_power2(P.px, P.py, q0, q1.x, dx, dy, u, w2);
+            bool a0 = !done0 && pw.x >= q1.z;  // alpha >= 1/255
+            bool a1 = !done1 && pw.y >= q1.z;
+            if (!(a0 || a1)) continue;
+            const float2 alpha = make_float2(fminf(__fmul_rn(q1.y, __expf(pw.x)), kAlphaMax),
+                                             fminf(__fmul_rn(q1.y, __expf(pw.y)), kAlphaMax));
+            const float2 test = __fmul2_rn(T, __ffma2_rn(alpha, f2(-1.f), f2(1.f)));  // T (1 - alpha)
+            if (a0 && test.x < kTMin) {
+              done0 = true;
+              a0 = false;
             }
-            bool ad = true;
-#pragma unroll
-            for (int k = 0; k < kPPT; ++k) ad = ad && done[k];
-            if (ad) {
+            if (a1 && test.y < kTMin) {
+              done1 = true;
+              a1 = false;
+            }
+            float2 w = __fmul2_rn(alpha, T);
+            w.x = a0 ? w.x : 0.f;
+            w.y = a1 ? w.y : 0.f;
+            const float4 q2 = S.g2[j];
+            const float4 q3 = S.g3[j];
+            C0 = __ffma2_rn(w, f2(q2.x), C0);
+            C1 = __ffma2_rn(w, f2(q2.y), C1);
+            C2 = __ffma2_rn(w, f2(q2.z), C2);
+            D = __ffma2_rn(w, f2(q2.w), D);
+            N0 = __ffma2_rn(w, f2(q3.x), N0);
+            N1 = __ffma2_rn(w, f2(q3.y), N1);
+            N2 = __ffma2_rn(w, f2(q3.z), N2);
+            if (a0) {
+              T.x = test.x;
+              last0 = base + j;
+              ++cnt0;
+            }
+            if (a1) {
+              T.y = test.y;
+              last1 = base + j;
+              ++cnt1;
+            }
+            if (done0 && done1) {
               all_done = true;
               c = kBatch / 32;
               break;
@@ -285,19 +315,12 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
           }
         }
       }
-#pragma unroll
-      for (int k = 0; k < kPPT; ++k) {
-        if (!P.has[k]) continue;
-        const uint64_t gp = P.q[k];
-        out8[2 * gp + 0] = make_float4(C0[k], C1[k], C2[k], D[k]);
-        out8[2 * gp + 1] = make_float4(N0[k], N1[k], N2[k], 1.f - T[k]);
-        // Eq. 4: ray-plane depth
-        const float rx = (P.px[k] + (float)ox - V.cx) / V.fx, ry = (P.py[k] + (float)oy - V.cy) / V.fy;
-        const float sdot = -(N0[k] * rx + N1[k] * ry + N2[k]);
-        const bool valid = cnt[k] > 0 && sdot > kRayDotMin && D[k] > 0.f;
-        depth[gp] = valid ? D[k] / sdot : 0.f;
-        aux[gp] = make_uint4(__float_as_uint(T[k]), last[k], cnt[k], 0u);
-      }
+      if (P.has0)
+        write_pixel(P.q0, make_float4(C0.x, C1.x, C2.x, D.x), make_float4(N0.x, N1.x, N2.x, T.x), last0, cnt0,
+                    P.px.x + (float)ox, P.py.x + (float)oy, V, out8, depth, aux);
+      if (P.has1)
+        write_pixel(P.q1, make_float4(C0.y, C1.y, C2.y, D.y), make_float4(N0.y, N1.y, N2.y, T.y), last1, cnt1,
+                    P.px.y + (float)ox, P.py.y + (float)oy, V, out8, depth, aux);
     }
   }
 }
@@ -345,26 +368,111 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float v[16], int la
   return a1 + __shfl_xor_sync(kFull, a1, 1);
 }
 
-// Per-pixel adjoint state.  S* hold the suffix sums S_i = sum_{j>i} x_j a_j
-// prod_{i<l<j} (1 - a_l) of the channels behind the Gaussian being processed;
-// they are advanced eagerly (S <- a x + (1 - a) S) after each contributor.
+// Adjoint state of the lane's two pixels (x = pixel 0, y = pixel 1).  S* hold the
+// suffix sums S_i = sum_{j>i} x_j a_j prod_{i<l<j} (1 - a_l) of the channels
+// behind the Gaussian being processed; they are advanced eagerly
+// (S <- a x + (1 - a) S) after each contributor.
 struct BwdPix {
-  float T;
-  int last;
-  float dC0, dC1, dC2, dD, dN0, dN1, dN2, dATf;  // dATf = dL/dA * T_final
-  float SC0, SC1, SC2, SN0, SN1, SN2, SD;
+  float2 T;
+  int last0, last1;
+  float2 dC0, dC1, dC2, dD, dN0, dN1, dN2, dATf;  // dATf = dL/dA * T_final
+  float2 SC0, SC1, SC2, SN0, SN1, SN2, SD;
 };
 
-template <int kWarps, int kPPT, int kDirect>
+// Deferred Eq. 8 adjoint (the loss's second pass, run here): dL/dP of the pixel's
+// back-projected point P = Depth r, gathered from the 4 neighbours whose central
+// differences used it (their dL/da, dL/db in the loss scratch), as dL/dDepth;
+// the rendered-normal gradient from the loss is scaled by lambda / |V|.
+// Returns dL/dDepth; scales g1 (dL/dN) in place.  (x, y): integer pixel.
+__device__ __forceinline__ float ban_gather(const pgsag_ban_gather& bg, const ViewLite& V, uint32_t view, int x,
+                                            int y, float rx, float ry, float3& gn) {
+  const double nV = bg.acc[8 * view + 2];
+  const float scale = nV > 0.0 ? (float)((double)bg.lambda_ban / nV) : 0.f;
+  gn.x *= scale;
+  gn.y *= scale;
+  gn.z *= scale;
+  // this pixel is P[y+1] of (x, y-1), P[y-1] of (x, y+1), P[x+1] of (x-1, y), P[x-1] of (x+1, y)
+  const int nx[4] = {x, x, x - 1, x + 1};
+  const int ny[4] = {y - 1, y + 1, y, y};
+  const float sg[4] = {1.f, -1.f, 1.f, -1.f};
+  const int off[4] = {0, 0, 3, 3};
+  uint8_t fq[4];
+  uint32_t qn[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    fq[k] = 0;
+    qn[k] = 0;
+    if (nx[k] < 0 || nx[k] >= V.width || ny[k] < 0 || ny[k] >= V.height) continue;
+    const uint64_t d = V.pix_base + (uint64_t)ny[k] * V.width + nx[k];
+    fq[k] = __ldg(bg.flags + d);
+    qn[k] = __ldg(bg.pidx + d);
+  }
+  float dP0 = 0.f, dP1 = 0.f, dP2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!(fq[k] & PGSAG_PIX_MASK)) continue;
+    const float* sc = bg.scratch + 6ull * qn[k] + off[k];
+    dP0 += sg[k] * __ldg(sc + 0);
+    dP1 += sg[k] * __ldg(sc + 1);
+    dP2 += sg[k] * __ldg(sc + 2);
+  }
+  return scale * (dP0 * rx + dP1 * ry + dP2);  // P = Depth r, r = (rx, ry, 1)
+}
+
+// Upstream gradient of one pixel (scaled), with the depth output's gradient
+// (given, or gathered from the Eq. 8 loss) folded into dD and dN through Eq. 4
+// (Depth = D / s, s = -N . r).
+__device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, int ox, int oy, const ViewLite& V,
+                                              uint32_t view, float gscale, const uint4* __restrict__ aux,
+                                              const float4* __restrict__ dout8, const float* __restrict__ ddepth,
+                                              bool use_ban, const pgsag_ban_gather& ban,
+                                              const float4* __restrict__ out8, float v[9], int& last) {
+  const uint4 ax = __ldg(aux + gp);
+  const float T = __uint_as_float(ax.x);
+  last = ax.z > 0 ? (int)ax.y : -1;
+  const float4 g0 = __ldg(dout8 + 2 * gp), g1 = __ldg(dout8 + 2 * gp + 1);
+  const float rx = (px + (float)ox - V.cx) / V.fx, ry = (py + (float)oy - V.cy) / V.fy;
+  float3 gn = make_float3(g1.x, g1.y, g1.z);
+  float gd = ddepth != nullptr ? __ldg(ddepth + gp) : 0.f;
+  if (use_ban) {
+    gd += ban_gather(ban, V, view, (int)(px - 0.5f) + ox, (int)(py - 0.5f) + oy, rx, ry, gn);
+  }
+  v[0] = gscale * g0.x;
+  v[1] = gscale * g0.y;
+  v[2] = gscale * g0.z;
+  v[3] = gscale * g0.w;
+  v[4] = gscale * gn.x;
+  v[5] = gscale * gn.y;
+  v[6] = gscale * gn.z;
+  v[7] = gscale * g1.w * T;
+  v[8] = T;
+  if (ax.z > 0) {
+    gd *= gscale;
+    if (gd != 0.f) {
+      const float4 o0 = __ldg(out8 + 2 * gp), o1 = __ldg(out8 + 2 * gp + 1);
+      const float sdot = -(o1.x * rx + o1.y * ry + o1.z);
+      if (sdot > kRayDotMin && o0.w > 0.f) {
+        const float is = 1.f / sdot;
+        v[3] += gd * is;
+        const float kk = gd * o0.w * is * is;
+        v[4] += kk * rx;
+        v[5] += kk * ry;
+        v[6] += kk;
+      }
+    }
+  }
+}
+
+template <int kWarps>
 __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     const pgsag_view* __restrict__ views, const float4* __restrict__ rec,
     const uint32_t* __restrict__ dup_pairs, const uint2* __restrict__ ranges,
     const uint4* __restrict__ act_tiles, uint32_t n_items, const uint32_t* __restrict__ px_list,
     Sched sched, const float4* __restrict__ out8, const uint4* __restrict__ aux,
-    const float4* __restrict__ dout8, const float* __restrict__ ddepth, const float* __restrict__ dout_scale,
-    float* __restrict__ grad2d, const int32_t* status) {
+    const float4* __restrict__ dout8, const float* __restrict__ ddepth, const pgsag_ban_gather ban, bool use_ban,
+    const float* __restrict__ dout_scale, float* __restrict__ grad2d, const int32_t* status) {
   constexpr int kRenderThreads = kWarps * 32;
-  constexpr int kTilePix = kRenderThreads * kPPT;
+  constexpr int kTilePix = kRenderThreads * 2;
   constexpr int kStagePerThread = kBatch / kRenderThreads;
   static_assert(kBatch % kRenderThreads == 0 && kStagePerThread >= 1, "batch must be a multiple of the CTA size");
   __shared__ Stage S;
@@ -388,51 +496,28 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
       // the tile (every supported tile lies in one cell), so offsets round the
       // same way whatever the tile size
       const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
-      const Pix<kPPT> P = load_pixels<kPPT>(ti, r0, warp, lane, V.width, ox, oy, px_list);
+      const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
-      BwdPix B[kPPT];
-      int lane_last = -1;
-#pragma unroll
-      for (int k = 0; k < kPPT; ++k) {
-        BwdPix& b = B[k];
-        b.T = 1.f;
-        b.last = -1;
-        b.dC0 = b.dC1 = b.dC2 = b.dD = b.dN0 = b.dN1 = b.dN2 = b.dATf = 0.f;
-        b.SC0 = b.SC1 = b.SC2 = b.SN0 = b.SN1 = b.SN2 = b.SD = 0.f;
-        if (!P.has[k]) continue;
-        const uint64_t gp = P.q[k];
-        const uint4 ax = __ldg(aux + gp);
-        b.T = __uint_as_float(ax.x);
-        b.last = ax.z > 0 ? (int)ax.y : -1;
-        const float4 g0 = __ldg(dout8 + 2 * gp), g1 = __ldg(dout8 + 2 * gp + 1);
-        b.dC0 = gscale * g0.x;
-        b.dC1 = gscale * g0.y;
-        b.dC2 = gscale * g0.z;
-        b.dD = gscale * g0.w;
-        b.dN0 = gscale * g1.x;
-        b.dN1 = gscale * g1.y;
-        b.dN2 = gscale * g1.z;
-        b.dATf = gscale * g1.w * b.T;
-        if (ddepth != nullptr && ax.z > 0) {
-          // Eq. 4: Depth = D / s, s = -N . r
-          const float gd = gscale * __ldg(ddepth + gp);
-          if (gd != 0.f) {
-            const float4 o0 = __ldg(out8 + 2 * gp), o1 = __ldg(out8 + 2 * gp + 1);
-            const float rx = (P.px[k] + (float)ox - V.cx) / V.fx, ry = (P.py[k] + (float)oy - V.cy) / V.fy;
-            const float sdot = -(o1.x * rx + o1.y * ry + o1.z);
-            if (sdot > kRayDotMin && o0.w > 0.f) {
-              const float is = 1.f / sdot;
-              b.dD += gd * is;
-              const float kk = gd * o0.w * is * is;
-              b.dN0 += kk * rx;
-              b.dN1 += kk * ry;
-              b.dN2 += kk;
-            }
-          }
-        }
-        lane_last = max(lane_last, b.last);
+      BwdPix B;
+      {
+        float v0[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f}, v1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+        B.last0 = B.last1 = -1;
+        if (P.has0)
+          load_upstream(P.q0, P.px.x, P.py.x, ox, oy, V, ti.view, gscale, aux, dout8, ddepth, use_ban, ban, out8, v0, B.last0);
+        if (P.has1)
+          load_upstream(P.q1, P.px.y, P.py.y, ox, oy, V, ti.view, gscale, aux, dout8, ddepth, use_ban, ban, out8, v1, B.last1);
+        B.dC0 = make_float2(v0[0], v1[0]);
+        B.dC1 = make_float2(v0[1], v1[1]);
+        B.dC2 = make_float2(v0[2], v1[2]);
+        B.dD = make_float2(v0[3], v1[3]);
+        B.dN0 = make_float2(v0[4], v1[4]);
+        B.dN1 = make_float2(v0[5], v1[5]);
+        B.dN2 = make_float2(v0[6], v1[6]);
+        B.dATf = make_float2(v0[7], v1[7]);
+        B.T = make_float2(v0[8], v1[8]);
+        B.SC0 = B.SC1 = B.SC2 = B.SN0 = B.SN1 = B.SN2 = B.SD = f2(0.f);
       }
-      const int warp_last = warp_max_i(lane_last);
+      const int warp_last = warp_max_i(max(B.last0, B.last1));
       if (threadIdx.x == 0) s_max = -1;
       __syncthreads();
       if (lane == 0) atomicMax(&s_max, warp_last);
@@ -460,73 +545,77 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
           const int idx = lo + j;
           const float4 q0 = S.g0[j];
           const float4 q1 = S.g1[j];
-          const float thr = q1.z;
+          float2 dx, dy, u, wq;
+          const float2 pw = gauss_power2(P.px, P.py, q0, q1.x, dx, dy, u, wq);
+          const bool a0 = idx <= B.last0 && pw.x >= q1.z;  // blended by the forward
+          const bool a1 = idx <= B.last1 && pw.y >= q1.z;
           float g[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) g[k] = 0.f;
-          int ncontrib = 0;
-#pragma unroll
-          for (int k = 0; k < kPPT; ++k) {
-            BwdPix& b = B[k];
-            if (idx > b.last) continue;
-            float dx, dy, u, wq;
-            const float pw = gauss_power(P.px[k], P.py[k], q0, q1.x, dx, dy, u, wq);
-            if (!(pw >= thr)) continue;  // alpha < 1/255: not blended
-            ++ncontrib;
+          if (a0 || a1) {
             const float4 q2 = S.g2[j];
             const float4 q3 = S.g3[j];
-            const float G = __expf(pw);
-            const float raw = __fmul_rn(q1.y, G);
-            const float alpha = fminf(raw, kAlphaMax);
-            const float oma = 1.f - alpha;
-            const float roma = __fdividef(1.f, oma);  // 1 <= 1/(1-alpha) <= 100
-            b.T *= roma;                              // transmittance in front of this Gaussian
-            const float w = alpha * b.T;
-            const float c0 = q2.x, c1 = q2.y, c2 = q2.z, d = q2.w, n0 = q3.x, n1 = q3.y, n2 = q3.z;
-            float dalpha = b.T * ((c0 - b.SC0) * b.dC0 + (c1 - b.SC1) * b.dC1 + (c2 - b.SC2) * b.dC2 +
-                                  (d - b.SD) * b.dD + (n0 - b.SN0) * b.dN0 + (n1 - b.SN1) * b.dN1 +
-                                  (n2 - b.SN2) * b.dN2);
-            dalpha += b.dATf * roma;
-            // advance the suffix sums past this Gaussian: S <- a x + (1 - a) S
-            b.SC0 = fmaf(alpha, c0 - b.SC0, b.SC0);
-            b.SC1 = fmaf(alpha, c1 - b.SC1, b.SC1);
-            b.SC2 = fmaf(alpha, c2 - b.SC2, b.SC2);
-            b.SN0 = fmaf(alpha, n0 - b.SN0, b.SN0);
-            b.SN1 = fmaf(alpha, n1 - b.SN1, b.SN1);
-            b.SN2 = fmaf(alpha, n2 - b.SN2, b.SN2);
-            b.SD = fmaf(alpha, d - b.SD, b.SD);
-            g[6] += w * b.dC0;
-            g[7] += w * b.dC1;
-            g[8] += w * b.dC2;
-            g[9] += w * b.dD;
-            g[10] += w * b.dN0;
-            g[11] += w * b.dN1;
-            g[12] += w * b.dN2;
-            if (raw < kAlphaMax) {
-              g[5] += dalpha * G;                // d alpha / d o
-              const float dp = dalpha * alpha;   // d alpha / d power
-              // power = -1/2 (u^2 + w^2), u = l11 dx + l21 dy, w = l22 dy, d = p - m
-              g[0] += dp * u * q0.z;
-              g[1] += dp * (u * q0.w + wq * q1.x);
-              g[2] -= dp * u * dx;
-              g[3] -= dp * u * dy;
-              g[4] -= dp * wq * dy;
-            }
+            const float2 G = make_float2(__expf(pw.x), __expf(pw.y));
+            const float2 raw = __fmul2_rn(f2(q1.y), G);
+            const float2 alpha = make_float2(fminf(raw.x, kAlphaMax), fminf(raw.y, kAlphaMax));
+            const float2 oma = __ffma2_rn(alpha, f2(-1.f), f2(1.f));
+            const float2 roma = make_float2(__fdividef(1.f, oma.x), __fdividef(1.f, oma.y));  // in [1, 100]
+            const float2 Tn = __fmul2_rn(B.T, roma);  // transmittance in front of this Gaussian
+            B.T.x = a0 ? Tn.x : B.T.x;
+            B.T.y = a1 ? Tn.y : B.T.y;
+            const float2 am = make_float2(a0 ? alpha.x : 0.f, a1 ? alpha.y : 0.f);
+            const float2 w = __fmul2_rn(am, B.T);
+            // dL/dalpha = T sum_ch (x_ch - S_ch) dL/dX_ch + dL/dA T_final / (1 - alpha); the
+            // suffix sums advance past this Gaussian (S <- S + a (x - S); unchanged where a = 0)
+            float2 e = __ffma2_rn(B.SC0, f2(-1.f), f2(q2.x));
+            float2 acc = __fmul2_rn(e, B.dC0);
+            B.SC0 = __ffma2_rn(am, e, B.SC0);
+            e = __ffma2_rn(B.SC1, f2(-1.f), f2(q2.y));
+            acc = __ffma2_rn(e, B.dC1, acc);
+            B.SC1 = __ffma2_rn(am, e, B.SC1);
+            e = __ffma2_rn(B.SC2, f2(-1.f), f2(q2.z));
+            acc = __ffma2_rn(e, B.dC2, acc);
+            B.SC2 = __ffma2_rn(am, e, B.SC2);
+            e = __ffma2_rn(B.SD, f2(-1.f), f2(q2.w));
+            acc = __ffma2_rn(e, B.dD, acc);
+            B.SD = __ffma2_rn(am, e, B.SD);
+            e = __ffma2_rn(B.SN0, f2(-1.f), f2(q3.x));
+            acc = __ffma2_rn(e, B.dN0, acc);
+            B.SN0 = __ffma2_rn(am, e, B.SN0);
+            e = __ffma2_rn(B.SN1, f2(-1.f), f2(q3.y));
+            acc = __ffma2_rn(e, B.dN1, acc);
+            B.SN1 = __ffma2_rn(am, e, B.SN1);
+            e = __ffma2_rn(B.SN2, f2(-1.f), f2(q3.z));
+            acc = __ffma2_rn(e, B.dN2, acc);
+            B.SN2 = __ffma2_rn(am, e, B.SN2);
+            const float2 dal = __ffma2_rn(B.dATf, roma, __fmul2_rn(B.T, acc));
+            g[6] = fmaf(w.y, B.dC0.y, w.x * B.dC0.x);
+            g[7] = fmaf(w.y, B.dC1.y, w.x * B.dC1.x);
+            g[8] = fmaf(w.y, B.dC2.y, w.x * B.dC2.x);
+            g[9] = fmaf(w.y, B.dD.y, w.x * B.dD.x);
+            g[10] = fmaf(w.y, B.dN0.y, w.x * B.dN0.x);
+            g[11] = fmaf(w.y, B.dN1.y, w.x * B.dN1.x);
+            g[12] = fmaf(w.y, B.dN2.y, w.x * B.dN2.x);
+            // through alpha = o G (not clamped): d/do and d/dpower, power = -1/2 (u^2 + w^2),
+            // u = l11 dx + l21 dy, w = l22 dy, d = p - m
+            const float2 dam = make_float2(a0 && raw.x < kAlphaMax ? dal.x : 0.f,
+                                           a1 && raw.y < kAlphaMax ? dal.y : 0.f);
+            g[5] = fmaf(dam.y, G.y, dam.x * G.x);
+            const float2 dp = __fmul2_rn(dam, alpha);
+            const float2 du = __fmul2_rn(dp, u), dw = __fmul2_rn(dp, wq);
+            g[0] = q0.z * (du.x + du.y);
+            const float2 t1 = __ffma2_rn(du, f2(q0.w), __fmul2_rn(dw, f2(q1.x)));
+            g[1] = t1.x + t1.y;
+            g[2] = -fmaf(du.y, dx.y, du.x * dx.x);
+            g[3] = -fmaf(du.y, dy.y, du.x * dy.x);
+            g[4] = -fmaf(dw.y, dy.y, dw.x * dy.x);
           }
-          const uint32_t cm = __ballot_sync(kFull, ncontrib > 0);
+          const uint32_t cm = __ballot_sync(kFull, a0 || a1);
           if (cm) {
             float* acc = reinterpret_cast<float*>(sacc[j]);
-            if (__popc(cm) <= kDirect) {
-              // few contributing lanes: add their values directly
-              if (ncontrib > 0) {
-#pragma unroll
-                for (int k = 0; k < 13; ++k) atomicAdd(acc + k, g[k]);
-              }
-            } else {
-              const float tot = warp_reduce_scatter16(g, lane);
-              const int k = lane >> 1;
-              if (!(lane & 1) && k < 13) atomicAdd(acc + k, tot);
-            }
+            const float tot = warp_reduce_scatter16(g, lane);
+            const int k = lane >> 1;
+            if (!(lane & 1) && k < 13) atomicAdd(acc + k, tot);
           }
          }
         }
@@ -587,7 +676,7 @@ extern "C" int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const
   if (r) return r;
   cudaStream_t st = (cudaStream_t)stream;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
-  k_render_fwd<PGSAG_FWD_WARPS, PGSAG_FWD_PPT><<<blocks, PGSAG_FWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
+  k_render_fwd<PGSAG_FWD_WARPS><<<blocks, PGSAG_FWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
                                                   (const uint4*)act_tiles, n_active, px_list, s, (float4*)out8, depth,
                                                   (uint4*)aux, status);
   PGSAG_CHECK_LAUNCH();
@@ -598,8 +687,8 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
                                 const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
                                 uint32_t n_active, const uint32_t* px_list, const pgsag_sched* sched,
                                 const float* out8, const void* aux, const float* dout8, const float* ddepth,
-                                const float* dout_scale, uint32_t n_pairs, float* grad2d, int32_t* status,
-                                void* stream) {
+                                const pgsag_ban_gather* ban, const float* dout_scale, uint32_t n_pairs,
+                                float* grad2d, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status) return PGSAG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -609,6 +698,9 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
   }
   if (n_active == 0) return PGSAG_OK;
   if (!rec || !ranges || !act_tiles || !px_list || !out8 || !aux || !dout8 || !grad2d) return PGSAG_ERR_ARG;
+  if (ban && !(ban->flags && ban->pidx && ban->scratch && ban->acc)) return PGSAG_ERR_ARG;
+  pgsag_ban_gather bg{};
+  if (ban) bg = *ban;
   if (((uintptr_t)rec | (uintptr_t)out8 | (uintptr_t)aux | (uintptr_t)dout8 | (uintptr_t)act_tiles) & 15u)
     return PGSAG_ERR_ARG;
   Sched s;
@@ -616,10 +708,10 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
   int r = launch_cfg(sched, n_active, s, blocks);
   if (r) return r;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
-  k_render_bwd<PGSAG_BWD_WARPS, PGSAG_BWD_PPT, PGSAG_BWD_DIRECT><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
+  k_render_bwd<PGSAG_BWD_WARPS><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
                                                   (const uint4*)act_tiles, n_active, px_list, s, (const float4*)out8,
-                                                  (const uint4*)aux, (const float4*)dout8, ddepth, dout_scale, grad2d,
-                                                  status);
+                                                  (const uint4*)aux, (const float4*)dout8, ddepth, bg, ban != nullptr, dout_scale,
+                                                  grad2d, status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

@@ -199,9 +199,9 @@ class Plan:
         self.tile_counts = torch.zeros(max(self.n_active, 1), dtype=i32, device=dev)
         self.k_out = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=i32, device=dev)
-        self.acc_loss = torch.zeros(4 * V, dtype=torch.float64, device=dev)
+        self.acc_loss = torch.zeros(8 * V, dtype=torch.float64, device=dev)
         self.acc_gc = torch.zeros(3 * V, dtype=torch.float64, device=dev)
-        self.chunk_scratch = torch.zeros((max(self.n_chunks, 1), 4), dtype=f32, device=dev)
+        self.chunk_scratch = torch.zeros((max(self.n_chunks, 1), 8), dtype=f32, device=dev)
         self.gc_load = torch.zeros(V, dtype=f32, device=dev)
         self.loss_buf = torch.zeros(3 * V + 1, dtype=f32, device=dev)
         self.sched = None
@@ -269,7 +269,8 @@ class Plan:
         return _Ctx()
 
     def kernel_launches_per_step(self, with_stats=True) -> int:
-        """Number of library kernels one render + loss + backward step launches."""
+        """Number of library kernels one step (step() / RenderLossFn) launches: the
+        fused loss sums the GC-load and leaves the Eq. 8 gather to render_bwd."""
         tile_passes = 0
         if self.n_active > 1:
             tile_passes = (int(self.n_active - 1).bit_length() + 7) // 8
@@ -279,9 +280,9 @@ class Plan:
         if self.sched is not None and getattr(self, "lpt", False) and self.n_active:
             n += 3                              # schedule
         n += 1 if self.n_active else 0          # render_fwd
-        n += (3 if self.n_chunks else 0) + 1    # loss
+        n += (2 if self.n_chunks else 0) + 1    # loss pass A (+ GC-load sums), per-view reduce, final
         if with_stats:
-            n += (1 if self.n_active else 0) + (2 if self.n_chunks else 0) + 1
+            n += 1 if self.n_active else 0      # per-tile counts
         n += 1 if self.n_active else 0          # render_bwd
         n += 1 if self.n_gauss else 0           # preprocess_bwd
         return n
@@ -316,36 +317,53 @@ class Plan:
                                               _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.depth),
                                               _ptr(self.aux), _ptr(self.status), s), "pgsag_render_fwd")
 
-    def loss(self, lambda_ban=LAMBDA_BAN, loss_out: Optional[torch.Tensor] = None, stream=None):
+    def loss(self, lambda_ban=LAMBDA_BAN, loss_out: Optional[torch.Tensor] = None, stream=None,
+             fused: bool = False):
+        """L_rgb + lambda L_ban per view (Eq. 8) and its gradient on the rendered
+        channels into dout8.  fused=True also sums the GC-load (Eq. 9) in the same
+        pass and leaves the neighbour gather of Eq. 8 to the next render_bwd
+        (which must then be called with ban=True)."""
         s = _stream_ptr(stream)
         out = self.loss_buf if loss_out is None else loss_out
+        self._lambda_ban = float(lambda_ban)
         with self._ev('loss'):
             L.check(self.lib.pgsag_loss_ban(self.n_views, _ptr(self.views_dev), self.n_chunks, _ptr(self.chunks),
-                                            _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags), _ptr(self.pidx),
-                                            _ptr(self.out8),
-                                            _ptr(self.depth), _ptr(self.aux), _ptr(self.target), float(lambda_ban),
-                                            _ptr(self.scratch), _ptr(self.acc_loss), _ptr(self.chunk_scratch), _ptr(out), _ptr(self.dout8),
+                                            _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags),
+                                            _ptr(self.pidx), _ptr(self.out8), _ptr(self.depth), _ptr(self.aux),
+                                            _ptr(self.target), float(lambda_ban),
+                                            _ptr(self.gc_weight) if fused else None, 0 if fused else 1,
+                                            _ptr(self.scratch), _ptr(self.acc_loss), _ptr(self.chunk_scratch),
+                                            _ptr(out), _ptr(self.gc_load) if fused else None, _ptr(self.dout8),
                                             _ptr(self.status), s), "pgsag_loss_ban")
         return out
 
-    def tile_stats(self, stream=None):
+    def tile_stats(self, stream=None, counts_only: bool = False):
+        """Per-tile Gaussian counts and (unless counts_only) the per-view GC-load (Eq. 9)."""
         s = _stream_ptr(stream)
         with self._ev('tile_stats'):
             L.check(self.lib.pgsag_tile_stats(self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.ranges),
-                                              self.n_chunks, _ptr(self.chunks), _ptr(self.act_tiles), _ptr(self.px_list),
-                                              _ptr(self.aux), _ptr(self.gc_weight), _ptr(self.tile_counts),
-                                              _ptr(self.acc_gc), _ptr(self.chunk_scratch), _ptr(self.gc_load), _ptr(self.status), s),
+                                              self.n_chunks, _ptr(self.chunks), _ptr(self.act_tiles),
+                                              _ptr(self.px_list), _ptr(self.aux), _ptr(self.gc_weight),
+                                              _ptr(self.tile_counts), _ptr(self.acc_gc), _ptr(self.chunk_scratch),
+                                              None if counts_only else _ptr(self.gc_load), _ptr(self.status), s),
                     "pgsag_tile_stats")
 
+    def _ban_gather(self):
+        return L.PgsagBanGather(self.flags.data_ptr(), self.pidx.data_ptr(), self.scratch.data_ptr(),
+                                self.acc_loss.data_ptr(), float(getattr(self, "_lambda_ban", LAMBDA_BAN)), 0)
+
     def render_bwd(self, dout8: torch.Tensor, ddepth: Optional[torch.Tensor] = None,
-                   dout_scale: Optional[torch.Tensor] = None, stream=None):
+                   dout_scale: Optional[torch.Tensor] = None, stream=None, ban: bool = False):
+        """Adjoint render into grad2d.  ban=True: dout8 comes from loss(fused=True)
+        and the deferred Eq. 8 gather runs in this kernel's prologue."""
         s = _stream_ptr(stream)
+        bg = ctypes.byref(self._ban_gather()) if ban else None
         with self._ev('render_bwd'):
             L.check(self.lib.pgsag_render_bwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
                                               _ptr(self.ranges), _ptr(self.act_tiles), self.n_active,
                                               _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.aux),
-                                              _ptr(dout8), _ptr(ddepth), _ptr(dout_scale), self.n_pairs, _ptr(self.grad2d),
-                                              _ptr(self.status), s), "pgsag_render_bwd")
+                                              _ptr(dout8), _ptr(ddepth), bg, _ptr(dout_scale), self.n_pairs,
+                                              _ptr(self.grad2d), _ptr(self.status), s), "pgsag_render_bwd")
 
     def preprocess_bwd(self, P: GaussianParams, grads: Sequence[torch.Tensor], accumulate=False, stream=None):
         s = _stream_ptr(stream)
@@ -388,9 +406,9 @@ class Plan:
         self.bin(stream)
         self.schedule(stream)
         self.render_fwd(stream)
-        self.loss(lambda_ban, loss_out, stream)
-        self.tile_stats(stream)
-        self.render_bwd(self.dout8, None, None, stream)
+        self.loss(lambda_ban, loss_out, stream, fused=True)
+        self.tile_stats(stream, counts_only=True)
+        self.render_bwd(self.dout8, None, None, stream, ban=True)
         self.preprocess_bwd(P, grads, accumulate, stream)
 
     def capture(self, P: GaussianParams, grads: Sequence[torch.Tensor], lambda_ban: float = LAMBDA_BAN):
@@ -488,8 +506,8 @@ class RenderLossFn(torch.autograd.Function):
         P = GaussianParams(means, log_scales, quats, opacity_logit, sh)
         plan.forward(P, check=check)
         out = torch.empty(3 * plan.n_views + 1, dtype=torch.float32, device=plan.device)
-        plan.loss(lambda_ban, loss_out=out)
-        plan.tile_stats()
+        plan.loss(lambda_ban, loss_out=out, fused=True)
+        plan.tile_stats(counts_only=True)
         ctx.plan = plan
         ctx.P = P
         ctx.per_view = out
@@ -499,7 +517,7 @@ class RenderLossFn(torch.autograd.Function):
     def backward(ctx, g):
         plan, P = ctx.plan, ctx.P
         g = g.contiguous().to(torch.float32)
-        plan.render_bwd(plan.dout8, None, g)
+        plan.render_bwd(plan.dout8, None, g, ban=True)
         grads = new_param_grads(P)
         plan.preprocess_bwd(P, grads)
         return (None, None, None) + tuple(grads)

@@ -42,9 +42,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// drop != 0: keys equal to kDropKey are left out (counted nowhere, not written).
+constexpr uint32_t kDropKey = 0xffffffffu;
+
 __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                            const uint64_t* n_dev, uint64_t n_const,
-                                                           uint64_t cap, int shift,
+                                                           uint64_t cap, int shift, int drop,
                                                            uint32_t* __restrict__ hist,
                                                            const int32_t* status) {
   __shared__ uint32_t h[256];
@@ -57,8 +60,9 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint32_t* __res
   const int lane = threadIdx.x & 31;
   for (uint32_t base = lo; base < hi; base += kRsThreads) {
     const uint32_t i = base + threadIdx.x;
-    const bool valid = i < hi;
-    const uint32_t d = valid ? ((__ldg(keys + i) >> shift) & 255u) : 256u;
+    const uint32_t key = i < hi ? __ldg(keys + i) : kDropKey;
+    const bool valid = i < hi && !(drop && key == kDropKey);
+    const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
     const uint32_t peers = __match_any_sync(kFull, d);
     if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
@@ -110,8 +114,8 @@ __global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t* __restrict__ h
 __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const uint64_t* n_dev,
-    uint64_t n_const, uint64_t cap, int shift, const uint32_t* __restrict__ hist,
-    const uint32_t* __restrict__ dtot, const int32_t* status) {
+    uint64_t n_const, uint64_t cap, int shift, int drop, const uint32_t* __restrict__ hist,
+    const uint32_t* __restrict__ dtot, uint64_t* __restrict__ n_kept, const int32_t* status) {
   __shared__ uint32_t run[256];
   __shared__ uint32_t tot[256];
   __shared__ uint32_t wcnt[kRsWarps][256];
@@ -134,6 +138,8 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(
     uint32_t pre = 0;
     for (int w = 0; w < warp; ++w) pre += tot[w];
     run[threadIdx.x] = pre + x - t + hist[threadIdx.x * gridDim.x + blockIdx.x];
+    // number of keys this pass keeps (all of them unless dropping)
+    if (n_kept != nullptr && blockIdx.x == 0 && threadIdx.x == kRsThreads - 1) *n_kept = pre + x;
     __syncthreads();
   }
   const uint32_t lt = lanemask_lt();
@@ -144,8 +150,8 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(
 #pragma unroll
     for (int j = 0; j < kRsIpt; ++j) {
       const uint32_t idx = tile + warp * (32 * kRsIpt) + j * 32 + lane;
-      const bool valid = idx < hi;
-      k[j] = valid ? __ldg(keys_in + idx) : 0u;
+      k[j] = idx < hi ? __ldg(keys_in + idx) : kDropKey;
+      const bool valid = idx < hi && !(drop && k[j] == kDropKey);
       v[j] = valid ? (vals_in ? __ldg(vals_in + idx) : idx) : 0u;
       dg[j] = valid ? ((k[j] >> shift) & 255u) : 256u;
     }
@@ -212,10 +218,12 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t& total,
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ order,
                                                               const uint4* __restrict__ bininfo,
-                                                              uint32_t n, uint64_t* __restrict__ partial,
+                                                              const uint64_t* n_dev, uint64_t cap,
+                                                              uint64_t* __restrict__ partial,
                                                               const int32_t* status) {
   __shared__ unsigned long long ws[kScanThreads / 32];
   if (status_bad(status)) return;
+  const uint32_t n = load_n(n_dev, 0, cap);
   uint32_t lo, hi;
   block_range(n, blockIdx.x, gridDim.x, lo, hi);
   unsigned long long s = 0;
@@ -266,12 +274,13 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint64_t* __restrict__ p
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_emit(
-    const uint32_t* __restrict__ order, const uint4* __restrict__ bininfo, uint32_t n,
+    const uint32_t* __restrict__ order, const uint4* __restrict__ bininfo, const uint64_t* n_dev, uint64_t cap,
     const uint64_t* __restrict__ partial, const pgsag_view* __restrict__ views,
     const int32_t* __restrict__ tile_act, const float4* __restrict__ rec, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int32_t* status) {
   __shared__ uint32_t sh[kScanThreads / 32];
   if (status_bad(status)) return;
+  const uint32_t n = load_n(n_dev, 0, cap);
   uint32_t lo, hi;
   block_range(n, blockIdx.x, gridDim.x, lo, hi);
   uint32_t carry = (uint32_t)partial[blockIdx.x];
@@ -350,6 +359,7 @@ struct BinWs {
   uint32_t *dkA, *dkB, *dvW;    // tile sort (capacity)
   uint32_t* hist;               // 256 * kRsBlocks counts, then 256 digit totals
   uint64_t* partial;            // kScanBlocks + 1
+  uint64_t* n_bin;              // pairs kept by the depth sort (touching an active tile)
   size_t bytes;
 };
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -372,19 +382,21 @@ BinWs carve(void* base, uint32_t np, uint64_t cap) {
   w.dvW = (uint32_t*)take(capb);
   w.hist = (uint32_t*)take((size_t)256 * (kRsBlocks + 1) * 4);
   w.partial = (uint64_t*)take((size_t)(kScanBlocks + 1) * 8);
+  w.n_bin = (uint64_t*)take(8);
   w.bytes = o;
   return w;
 }
 
 int radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                const uint64_t* n_dev, uint64_t n_const, uint64_t cap, int shift, uint32_t* hist,
-               int32_t* status, cudaStream_t s) {
-  k_radix_hist<<<kRsBlocks, kRsThreads, 0, s>>>(kin, n_dev, n_const, cap, shift, hist, status);
+               uint64_t* n_kept, int32_t* status, cudaStream_t s) {
+  const int drop = n_kept != nullptr;
+  k_radix_hist<<<kRsBlocks, kRsThreads, 0, s>>>(kin, n_dev, n_const, cap, shift, drop, hist, status);
   PGSAG_CHECK_LAUNCH();
   k_radix_rowscan<<<256, 1024, 0, s>>>(hist, kRsBlocks, hist + 256 * kRsBlocks, status);
   PGSAG_CHECK_LAUNCH();
-  k_radix_scatter<<<kRsBlocks, kRsThreads, 0, s>>>(kin, vin, kout, vout, n_dev, n_const, cap, shift, hist,
-                                                   hist + 256 * kRsBlocks, status);
+  k_radix_scatter<<<kRsBlocks, kRsThreads, 0, s>>>(kin, vin, kout, vout, n_dev, n_const, cap, shift, drop, hist,
+                                                   hist + 256 * kRsBlocks, n_kept, status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }
@@ -413,14 +425,17 @@ extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* v
   if (n_active_total) PGSAG_CUDA(cudaMemsetAsync(ranges, 0, (size_t)n_active_total * sizeof(uint2), s));
   if (n_pairs == 0) return PGSAG_OK;
 
-  // 1. stable sort of pairs by depth key (4 x 8-bit digits)
+  // 1. stable sort of pairs by depth key (4 x 8-bit digits).  The first pass
+  // leaves out the culled pairs (key 0xffffffff: outside the image or touching
+  // no active tile) and counts the rest into n_bin; later passes and the scan
+  // run on those only.
   const uint32_t* kin = depth_key;
   const uint32_t* vin = nullptr;
   uint32_t* kb[2] = {w.kA, w.kB};
   uint32_t* vb[2] = {w.vA, w.vB};
   for (int pass = 0; pass < 4; ++pass) {
-    const int r = radix_pass(kin, vin, kb[pass & 1], vb[pass & 1], nullptr, n_pairs, n_pairs, 8 * pass,
-                             w.hist, status, s);
+    const int r = radix_pass(kin, vin, kb[pass & 1], vb[pass & 1], pass ? w.n_bin : nullptr, n_pairs, n_pairs,
+                             8 * pass, w.hist, pass ? nullptr : w.n_bin, status, s);
     if (r) return r;
     kin = kb[pass & 1];
     vin = vb[pass & 1];
@@ -442,18 +457,18 @@ extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* v
     valsX[i] = (from_end & 1) ? w.dvW : dup_pairs;
   }
   const uint32_t nsb = kScanBlocks;
-  k_scan_reduce<<<nsb, kScanThreads, 0, s>>>(order, (const uint4*)bininfo, n_pairs, w.partial, status);
+  k_scan_reduce<<<nsb, kScanThreads, 0, s>>>(order, (const uint4*)bininfo, w.n_bin, n_pairs, w.partial, status);
   PGSAG_CHECK_LAUNCH();
   k_scan_partials<<<1, 1024, 0, s>>>(w.partial, nsb, k_out, capacity, status);
   PGSAG_CHECK_LAUNCH();
-  k_scan_emit<<<nsb, kScanThreads, 0, s>>>(order, (const uint4*)bininfo, n_pairs, w.partial, views, tile_act,
-                                           (const float4*)rec, keysX[0], valsX[0], status);
+  k_scan_emit<<<nsb, kScanThreads, 0, s>>>(order, (const uint4*)bininfo, w.n_bin, n_pairs, w.partial, views,
+                                           tile_act, (const float4*)rec, keysX[0], valsX[0], status);
   PGSAG_CHECK_LAUNCH();
 
   // 4. stable sort of the duplicates by active tile
   for (int pass = 0; pass < tile_passes; ++pass) {
     const int r = radix_pass(keysX[pass], valsX[pass], keysX[pass + 1], valsX[pass + 1], k_out, 0, capacity,
-                             8 * pass, w.hist, status, s);
+                             8 * pass, w.hist, nullptr, status, s);
     if (r) return r;
   }
   // 5. ranges

@@ -293,10 +293,15 @@ __device__ __forceinline__ bool pair_forward(const pgsag_view& V, const GaussIn&
   return true;
 }
 
-// SH coefficients of a block's Gaussians staged in shared memory: coalesced
-// float4 loads of the block's contiguous [nb, 48] slab, stored with a row
-// stride of 49 floats so that thread t reading row t hits distinct banks.
+// SH coefficients are read per pair, only for pairs that are binned (a thread
+// reads its Gaussian's 192-byte row as 12 float4, whole sectors): most
+// Gaussians of a view touch no active tile and their colour is never needed.
+// The adjoint's SH gradients are summed in a shared-memory slab (row stride 49
+// floats, conflict-free) and written out as coalesced float4.
 constexpr int kPreThreads = 128;
+#ifndef PGSAG_PRE_BWD_MINB
+#define PGSAG_PRE_BWD_MINB 4  // resident adjoint blocks per SM the register budget must allow
+#endif
 constexpr int kShStride = 49;
 constexpr size_t kShSlabBytes = (size_t)kPreThreads * kShStride * sizeof(float);
 
@@ -304,17 +309,20 @@ __host__ __device__ __forceinline__ size_t views_bytes(uint32_t n_views) {
   return ((size_t)n_views * sizeof(pgsag_view) + 15) & ~(size_t)15;
 }
 
-__device__ __forceinline__ void stage_sh(const float* __restrict__ sh, uint32_t g0, uint32_t n, float* s_sh) {
-  const uint32_t nb = min((uint32_t)kPreThreads, n - g0);
-  const float4* src = reinterpret_cast<const float4*>(sh + 48ull * g0);
-  for (uint32_t i = threadIdx.x; i < nb * 12; i += blockDim.x) {
-    const float4 v = __ldg(src + i);
-    const uint32_t e = 4 * i, row = e / 48, col = e - row * 48;
-    float* d = s_sh + row * kShStride + col;
-    d[0] = v.x;
-    d[1] = v.y;
-    d[2] = v.z;
-    d[3] = v.w;
+// raw colour (before the clamp at 0) sum_k Y_k sh[k][ch] + 1/2 of one Gaussian
+__device__ __forceinline__ void sh_colour(const float* __restrict__ sh, uint32_t g, const float Y[16],
+                                          float col[3]) {
+  const float4* row = reinterpret_cast<const float4*>(sh + 48ull * g);
+  col[0] = col[1] = col[2] = kShOffset;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const float4 v = __ldg(row + i);
+    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int f = 4 * i + j;  // flat index 3 k + ch
+      col[f % 3] += Y[f / 3] * e[j];
+    }
   }
 }
 
@@ -333,16 +341,13 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(uint32_t n, const fl
     uint32_t* dst = reinterpret_cast<uint32_t*>(smem_raw);
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   }
-  float* s_sh = reinterpret_cast<float*>(smem_raw + views_bytes(n_views));
   if (status_bad(status)) return;
-  stage_sh(sh, blockIdx.x * blockDim.x, n, s_sh);
   __syncthreads();
   set_campos(sv, n_views);
   __syncthreads();
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n) return;
   const GaussIn G = load_gauss(g, means, log_scales, quats, opacity_logit);
-  const float* shg = s_sh + threadIdx.x * kShStride;
   for (uint32_t vi = 0; vi < n_views; ++vi) {
     const pgsag_view& V = sv[vi];
     if (g < V.g_begin || g >= V.g_end) continue;
@@ -416,13 +421,8 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(uint32_t n, const fl
     dz *= il;
     float Y[16];
     sh_eval(dx, dy, dz, Y);
-    float col[3] = {kShOffset, kShOffset, kShOffset};
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      col[0] += Y[k] * shg[3 * k + 0];
-      col[1] += Y[k] * shg[3 * k + 1];
-      col[2] += Y[k] * shg[3 * k + 2];
-    }
+    float col[3];
+    sh_colour(sh, g, Y, col);
     R4[0] = make_float4(mi, ni, P.l11, P.l21);
     R4[1] = make_float4(P.l22, P.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
     R4[2] = make_float4(fmaxf(col[2], 0.f), P.dist, P.nc[0], P.nc[1]);
@@ -434,8 +434,9 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(uint32_t n, const fl
 }
 
 // Adjoint of pair_forward + colour, accumulating into the raw-parameter gradients.
-// SH coefficients and their gradients live in shared memory (coalesced in and out).
-__global__ void __launch_bounds__(kPreThreads) k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
+// A Gaussian with no binned pair in any view has zero gradient and reads nothing
+// but its pairs' tile counts.
+__global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
                                  const float* __restrict__ log_scales,
                                  const float* __restrict__ quats,
                                  const float* __restrict__ opacity_logit,
@@ -454,22 +455,26 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess_bwd(uint32_t n, cons
     uint32_t* dst = reinterpret_cast<uint32_t*>(smem_raw);
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   }
-  // dynamic shared memory: [view table | SH slab | SH gradient slab]
-  float* s_sh = reinterpret_cast<float*>(smem_raw + views_bytes(n_views));
-  float* s_gsh = s_sh + kPreThreads * kShStride;
+  // dynamic shared memory: [view table | SH gradient slab]
+  float* s_gsh = reinterpret_cast<float*>(smem_raw + views_bytes(n_views));
   if (status_bad(status)) return;
   const uint32_t g0 = blockIdx.x * blockDim.x;
-  stage_sh(sh, g0, n, s_sh);
   for (int i = threadIdx.x; i < kPreThreads * kShStride; i += blockDim.x) s_gsh[i] = 0.f;
   __syncthreads();
   set_campos(sv, n_views);
   __syncthreads();
   const uint32_t g = g0 + threadIdx.x;
   float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gol = 0.f;
-  const float* shv = s_sh + threadIdx.x * kShStride;
   float* gsh = s_gsh + threadIdx.x * kShStride;
-  const GaussIn G = g < n ? load_gauss(g, means, log_scales, quats, opacity_logit) : GaussIn{};
-  const uint32_t vcount = g < n ? n_views : 0u;
+  bool binned = false;
+  if (g < n) {
+    for (uint32_t vi = 0; vi < n_views && !binned; ++vi) {
+      const pgsag_view& V = sv[vi];
+      if (g >= V.g_begin && g < V.g_end) binned = __ldg(&bininfo[V.pair_base + (g - V.g_begin)].w) != 0u;
+    }
+  }
+  const GaussIn G = binned ? load_gauss(g, means, log_scales, quats, opacity_logit) : GaussIn{};
+  const uint32_t vcount = binned ? n_views : 0u;
 
   for (uint32_t vi = 0; vi < vcount; ++vi) {
     const pgsag_view& V = sv[vi];
@@ -500,23 +505,33 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess_bwd(uint32_t n, cons
       dz *= il;
       float Y[16];
       sh_eval(dx, dy, dz, Y);
-      float raw[3] = {kShOffset, kShOffset, kShOffset};
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        raw[0] += Y[k] * shv[3 * k + 0];
-        raw[1] += Y[k] * shv[3 * k + 1];
-        raw[2] += Y[k] * shv[3 * k + 2];
-      }
+      float raw[3];
+      sh_colour(sh, g, Y, raw);
       float dc[3];
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) dc[ch] = raw[ch] < 0.f ? 0.f : drgb[ch];
+      // cw[k] = sum_ch dc[ch] sh[k][ch] (second read of the row, from L1/L2)
       float cw[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) cw[k] = 0.f;
+      {
+        const float4* row = reinterpret_cast<const float4*>(sh + 48ull * g);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+          const float4 v = __ldg(row + i);
+          const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int f = 4 * i + j;
+            cw[f / 3] += dc[f % 3] * e[j];
+          }
+        }
+      }
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         gsh[3 * k + 0] += dc[0] * Y[k];
         gsh[3 * k + 1] += dc[1] * Y[k];
         gsh[3 * k + 2] += dc[2] * Y[k];
-        cw[k] = dc[0] * shv[3 * k + 0] + dc[1] * shv[3 * k + 1] + dc[2] * shv[3 * k + 2];
       }
       float gx, gy, gz;
       sh_grad(dx, dy, dz, cw, gx, gy, gz);
@@ -696,10 +711,10 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
   if (n_gauss == 0) return cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream) == cudaSuccess ? PGSAG_OK : PGSAG_ERR_CUDA;
   if (!means || !log_scales || !quats || !opacity_logit || !sh || !rec || !depth_key || !bininfo)
     return PGSAG_ERR_ARG;
-  if (!aligned16(quats) || !aligned16(rec) || !aligned16(bininfo)) return PGSAG_ERR_ARG;
+  if (!aligned16(quats) || !aligned16(sh) || !aligned16(rec) || !aligned16(bininfo)) return PGSAG_ERR_ARG;
   PGSAG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream));
   const unsigned threads = kPreThreads;
-  const size_t smem = views_bytes(n_views) + kShSlabBytes;
+  const size_t smem = views_bytes(n_views);
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PGSAG_ERR_CUDA;
@@ -722,10 +737,11 @@ extern "C" int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const 
   if (!means || !log_scales || !quats || !opacity_logit || !sh || !bininfo || !grad2d || !d_means ||
       !d_log_scales || !d_quats || !d_opacity_logit || !d_sh)
     return PGSAG_ERR_ARG;
-  if (!aligned16(quats) || !aligned16(d_quats) || !aligned16(d_sh) || !aligned16(grad2d) || !aligned16(bininfo))
+  if (!aligned16(quats) || !aligned16(sh) || !aligned16(d_quats) || !aligned16(d_sh) || !aligned16(grad2d) ||
+      !aligned16(bininfo))
     return PGSAG_ERR_ARG;
   const unsigned threads = kPreThreads;
-  const size_t smem = views_bytes(n_views) + 2 * kShSlabBytes;  // > 48 KB: opt in
+  const size_t smem = views_bytes(n_views) + kShSlabBytes;
   if (cudaFuncSetAttribute(k_preprocess_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PGSAG_ERR_CUDA;
   k_preprocess_bwd<<<pgsag_div_up(n_gauss, threads), threads, smem, (cudaStream_t)stream>>>(

@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
         if (!__any_sync(kFull, !all_done)) continue;
         uint32_t rel[kBatch / 32];
         warp_relevance(S, (int)nb, cbox, lane, rel);
-        if (all_done) continue;
+        // the whole warp walks the relevant Gaussians (warp votes inside); lanes
+        // that are done take no part through their masks
 #pragma unroll 1
         for (int c = 0; c < kBatch / 32; ++c) {
           uint32_t m = rel[c];
@@ -273,7 +274,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
             const float2 pw = gauss_power2(P.px, P.py, q0, q1.x, dx, dy, u, w2);
             bool a0 = !done0 && pw.x >= q1.z;  // alpha >= 1/255
             bool a1 = !done1 && pw.y >= q1.z;
-            if (!(a0 || a1)) continue;
+            // warp-uniform: the blend runs for the whole warp with masked weights
+            if (!__any_sync(kFull, a0 || a1)) continue;
             const float2 alpha = make_float2(fminf(__fmul_rn(q1.y, __expf(pw.x)), kAlphaMax),
                                              fminf(__fmul_rn(q1.y, __expf(pw.y)), kAlphaMax));
             const float2 test = __fmul2_rn(T, __ffma2_rn(alpha, f2(-1.f), f2(1.f)));  // T (1 - alpha)
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
               last1 = base + j;
               ++cnt1;
             }
-            if (done0 && done1) {
+            if (__all_sync(kFull, done0 && done1)) {
               all_done = true;
               c = kBatch / 32;
               break;
@@ -549,10 +551,12 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
           const float2 pw = gauss_power2(P.px, P.py, q0, q1.x, dx, dy, u, wq);
           const bool a0 = idx <= B.last0 && pw.x >= q1.z;  // blended by the forward
           const bool a1 = idx <= B.last1 && pw.y >= q1.z;
-          float g[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) g[k] = 0.f;
-          if (a0 || a1) {
+          // warp-uniform: the whole warp runs the adjoint with masked inputs, so a
+          // lane with no contribution produces zeros (all terms are finite)
+          const uint32_t cm = __ballot_sync(kFull, a0 || a1);
+          if (cm) {
+            float g[16];
+            g[13] = g[14] = g[15] = 0.f;
             const float4 q2 = S.g2[j];
             const float4 q3 = S.g3[j];
             const float2 G = make_float2(__expf(pw.x), __expf(pw.y));
@@ -609,13 +613,10 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
             g[2] = -fmaf(du.y, dx.y, du.x * dx.x);
             g[3] = -fmaf(du.y, dy.y, du.x * dy.x);
             g[4] = -fmaf(dw.y, dy.y, dw.x * dy.x);
-          }
-          const uint32_t cm = __ballot_sync(kFull, a0 || a1);
-          if (cm) {
-            float* acc = reinterpret_cast<float*>(sacc[j]);
+            float* sa = reinterpret_cast<float*>(sacc[j]);
             const float tot = warp_reduce_scatter16(g, lane);
             const int k = lane >> 1;
-            if (!(lane & 1) && k < 13) atomicAdd(acc + k, tot);
+            if (!(lane & 1) && k < 13) atomicAdd(sa + k, tot);
           }
          }
         }

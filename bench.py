@@ -148,28 +148,31 @@ def run_oracle_steps(g, cv, n):
 
 # ---------------------------------------------------------------------------- algorithmic bytes
 
-def algorithmic_bytes(plan, K):
-    """Compulsory DRAM bytes per stage of one step (each item read / written once
-    by the stage that needs it), from the measured sizes N, pairs, K and pixels."""
+def algorithmic_bytes(plan, K, n_binned):
+    """DRAM bytes each stage of this design moves per step (each item read or
+    written once by the stage that needs it), from the measured sizes: N
+    Gaussians, NP pairs, n_binned binned pairs (one view: also the Gaussians
+    with a binned pair), K duplicates, P rendered and M mask pixels, A tiles."""
     N, NP, P, A = plan.n_gauss, plan.n_pairs, plan.n_render, plan.n_active
     M = plan.n_mask
     tile_passes = (int(A - 1).bit_length() + 7) // 8 if A > 1 else 0
     return {
-        # params 236 B/G; per pair: rec 64 + key 4 + bininfo 16
-        "preprocess": 236 * N + 84 * NP,
-        # 4 depth passes (hist read 4 + scatter read 8 + write 8); scan read order + bininfo twice;
-        # emission write 8/dup; tile passes 20/dup; ranges read 4/dup + write 8/tile
-        "bin": NP * (4 * 20 + 2 * 20) + K * (8 + 20 * tile_passes + 4) + 8 * A,
+        # means, scales, quats, opacity 44 B/G; SH row 192 B per binned pair; per pair: rec 64 + key 4 + bininfo 16
+        "preprocess": 44 * N + 192 * n_binned + 84 * NP,
+        # first depth pass over NP (read 8, write 8 kept), 3 more over the binned pairs; scan + emission read
+        # order + bininfo twice; emission write 8/dup; tile passes 20/dup; ranges read 4/dup + write 8/tile
+        "bin": NP * 12 + n_binned * (8 + 3 * 20 + 2 * 20) + K * (8 + 20 * tile_passes + 4) + 8 * A,
         # per pixel: list 4 + out8 32 + depth 4 + aux 16; per duplicate: id 4 + record 64
         "render_fwd": 56 * P + 68 * K,
-        # pass A: flags 1 + pixel index 4 + out8 32 + depth 4 + dout8 32 (+ target 12 + scratch 24 on M);
-        # pass B: flags 1 + pixel index 4 + out8 32 + depth 4 + dout8 64 + scratch 24
-        "loss": P * (1 + 4 + 32 + 4 + 32 + 1 + 4 + 32 + 4 + 64) + M * (12 + 24 + 24),
-        "tile_stats": P * (4 + 16 + 4) + 8 * A,
-        # per pixel: list 4 + aux 16 + dout8 32; per duplicate: id 4 + record 64; grad2d zero + write-back 2x64/pair
-        "render_bwd": 52 * P + 68 * K + 128 * NP,
-        # params read 236 + grads write 236 per G; per pair grad2d 64 + bininfo 16
-        "preprocess_bwd": 472 * N + 80 * NP,
+        # pass A: flags 1 + pixel index 4 + out8 32 + depth 4 + dout8 32 + aux 16 + GC weight 4;
+        # on mask pixels target 12 + scratch 24
+        "loss": 93 * P + 36 * M,
+        "tile_stats": 8 * A,
+        # per pixel: list 4 + aux 16 + dout8 32 + out8 32 + neighbour gather (flags 1, index 4, scratch 12);
+        # per duplicate: id 4 + record 64; grad2d zero + write-back 2x64 per pair
+        "render_bwd": 101 * P + 68 * K + 128 * NP,
+        # gradients written 236 B/G; bininfo 16/pair; binned: params 236 + grad2d 64
+        "preprocess_bwd": 236 * N + 16 * NP + 300 * n_binned,
     }
 
 
@@ -193,13 +196,41 @@ def pair_counts(plan):
 
 
 def fp32_peak_tflops(sm_mhz):
-    """148 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock."""
+    """148 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock (nominal, for context)."""
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_alu_peaks():
+    """FP32 FMA (scalar and packed f32x2, TFLOP/s) and ex2 (Gop/s) throughput
+    measured on this GPU by libpgsag_probe.so; None if the probe is missing."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2501_01677_b300", "libpgsag_probe.so")
+    if not os.path.exists(path):
+        return None
+    lib = ctypes.CDLL(path)
+    f = lib.pgsag_probe_throughput
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    out = {}
+    for kind, name, iters in ((0, "ffma_tflops", 1 << 15), (1, "ffma2_tflops", 1 << 14), (2, "ex2_gops", 1 << 13)):
+        r = ctypes.c_double(0.0)
+        if f(kind, iters, ctypes.byref(r), None) != 0:
+            return None
+        out[name] = r.value
+    return out
+
+
+# Compulsory DRAM bytes per unit of work (each item read or written once per
+# step): per binned (view, Gaussian) pair 904 B (projection read 236 + write 68,
+# binning 24, grad2d zero 52 + read 52, adjoint read 236 + write 236), per
+# duplicate 156 B (emit 12, sort 24, range 8, forward gather 56, adjoint gather
+# 56), per rendered pixel 165 B (forward 44, loss 77, adjoint 44).
+BYTES_PER_PAIR, BYTES_PER_DUP, BYTES_PER_PIXEL = 904, 156, 165
 
 
 def read_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if any."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    path = os.path.join(ROOT, "profiles", "traffic_aerial_5472x3648.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
@@ -362,7 +393,8 @@ def ours(args):
 
     # roofline of the dominant single-kernel stage
     pk, pk_src = peaks()
-    ab = algorithmic_bytes(plan, K_dup)
+    n_binned = int((plan.bininfo[:plan.n_pairs, 3] > 0).sum().item())
+    ab = algorithmic_bytes(plan, K_dup, n_binned)
     single = ("preprocess", "render_fwd", "render_bwd", "preprocess_bwd")
     dom = max(single, key=lambda k: stage_ms.get(k, 0.0))
     kernel_name = {"preprocess": "k_preprocess", "render_fwd": "k_render_fwd", "render_bwd": "k_render_bwd",
@@ -372,10 +404,16 @@ def ours(args):
     if dom in ("render_fwd", "render_bwd"):
         per = FLOP_FWD_CONTRIB if dom == "render_fwd" else FLOP_BWD_CONTRIB
         flops = FLOP_TEST * e_eval + per * e_contrib
-        peak = fp32_peak_tflops(pk.get("sm_max_mhz", 2032.0))
+        alu = measured_alu_peaks()
+        if alu:
+            peak = max(alu["ffma_tflops"], alu["ffma2_tflops"])
+            peak_src = "measured in this run: FP32 FMA throughput probe (best of scalar and f32x2)"
+        else:
+            peak = fp32_peak_tflops(pk.get("sm_max_mhz", 2032.0))
+            peak_src = "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock"
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    "frac": achieved / peak, "peak_source": peak_src, "alu_probe": alu,
                     "traffic": traffic, "algorithmic_flops": flops, "pairs_evaluated": e_eval,
                     "pairs_contributing": e_contrib,
                     "hbm_achieved_gbs": ab[dom] / (stage_ms[dom] / 1e3) / 1e9, "algorithmic_bytes": ab[dom]}
@@ -384,9 +422,17 @@ def ours(args):
         roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": pk["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "peak_source": pk_src, "traffic": traffic,
                     "algorithmic_bytes": ab[dom]}
-    step_bytes = sum(ab.values())
-    whole = {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9,
-             "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / pk["hbm_gbs"]}
+    # whole step against HBM: compulsory bytes from the per-unit figures and the
+    # measured units, and (for comparison) the per-stage byte model
+    step_bytes = BYTES_PER_PAIR * n_binned + BYTES_PER_DUP * K_dup + BYTES_PER_PIXEL * plan.n_render
+    sec = ms / args.steps / 1e3
+    whole = {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / sec / 1e9,
+             "frac": step_bytes / sec / 1e9 / pk["hbm_gbs"],
+             "units": {"binned_pairs": n_binned, "duplicates": K_dup, "rendered_pixels": plan.n_render},
+             "bytes_per_unit": {"binned_pair": BYTES_PER_PAIR, "duplicate": BYTES_PER_DUP,
+                                "rendered_pixel": BYTES_PER_PIXEL},
+             "stage_model_bytes": sum(ab.values()),
+             "stage_model_frac": sum(ab.values()) / sec / 1e9 / pk["hbm_gbs"]}
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1 and args.workload == "aerial":

@@ -14,6 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpgsag.so")
+PROBE_SRC = os.path.join(CSRC, "probe", "probe.cu")
+PROBE_LIB = os.path.join(PKG, "libpgsag_probe.so")  # throughput probes used by bench.py only
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -42,6 +44,10 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
             subprocess.run(cmd, check=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]
+        subprocess.run(cmd, check=True)
+    if force or not os.path.exists(PROBE_LIB) or os.path.getmtime(PROBE_LIB) < os.path.getmtime(PROBE_SRC):
+        cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", PROBE_LIB, PROBE_SRC,
+                                 "-lcudart"]
         subprocess.run(cmd, check=True)
     return LIB
 

@@ -15,6 +15,9 @@
 namespace pgsag {
 
 constexpr int kLossThreads = 256;
+#ifndef PGSAG_LOSS_MINB
+#define PGSAG_LOSS_MINB 8  // resident loss blocks per SM the register budget must allow (full occupancy)
+#endif
 constexpr float kWBoundary = 0.1f;  // Eq. 8: boundary weight
 constexpr int kReduceBlocks = 64;   // blocks per view for the per-view sums
 
@@ -56,7 +59,7 @@ __device__ __forceinline__ void ray(const ViewLite& V, int x, int y, float r[3])
 // mask pixels with valid neighbours, the Eq. 8 term, the gradient on the own
 // rendered normal (unscaled) and dL/da, dL/db of the two central differences
 // (stored in `scratch` for the neighbours to gather).
-__global__ void __launch_bounds__(kLossThreads) k_loss_a(
+__global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
     const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
     const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
     const uint8_t* __restrict__ flags, const uint32_t* __restrict__ pidx, const float4* __restrict__ out8,

@@ -299,6 +299,9 @@ __device__ __forceinline__ bool pair_forward(const pgsag_view& V, const GaussIn&
 // The adjoint's SH gradients are summed in a shared-memory slab (row stride 49
 // floats, conflict-free) and written out as coalesced float4.
 constexpr int kPreThreads = 128;
+#ifndef PGSAG_PRE_MINB
+#define PGSAG_PRE_MINB 8  // resident projection blocks per SM the register budget must allow
+#endif
 #ifndef PGSAG_PRE_BWD_MINB
 #define PGSAG_PRE_BWD_MINB 4  // resident adjoint blocks per SM the register budget must allow
 #endif
@@ -326,7 +329,7 @@ __device__ __forceinline__ void sh_colour(const float* __restrict__ sh, uint32_t
   }
 }
 
-__global__ void __launch_bounds__(kPreThreads) k_preprocess(uint32_t n, const float* __restrict__ means,
+__global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint32_t n, const float* __restrict__ means,
                              const float* __restrict__ log_scales, const float* __restrict__ quats,
                              const float* __restrict__ opacity_logit, const float* __restrict__ sh,
                              uint32_t n_views, const pgsag_view* __restrict__ views,

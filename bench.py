@@ -51,6 +51,9 @@ def parse():
                          "uneven sub-regions (200k-3M Gaussians) x 4 mixed-resolution views, one graph-captured "
                          "persistent step vs 32 sequential per-view steps")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: fraction of the Gaussians")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workload: use --tile and 4 persistent CTAs per SM instead of the autotuner")
+    ap.add_argument("--retune", action="store_true", help="batched workload: ignore the autotune cache")
     return ap.parse_args()
 
 
@@ -464,20 +467,29 @@ def ours(args):
 def batched(args):
     """Uneven sub-regions in one step (Sec. 4.1 grouping, parallel groups Sec. 5.1):
     plain = one plan per view, run one after the other on one stream (same
-    kernels, no graph); batched = one plan over all views, persistent render
-    launches over a longest-first tile queue, the whole step replayed as one CUDA
-    graph.  Both compute identical per-view outputs and summed gradients."""
+    kernels, no graph); batched = one plan over all views with the launch shape
+    the autotuner picks (tile shape, persistent render queue depth, longest-first
+    order), the whole step replayed as one CUDA graph.  Both use the same tile
+    shape and compute identical per-view outputs and summed gradients."""
     import torch
     import pgsag_synth as syn
-    from paper_2501_01677_b300 import raster
+    from paper_2501_01677_b300 import autotune, raster
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     g, ranges, views, owner = syn.config3(scale=args.scale)
     g_ranges = [ranges[o] for o in owner]
     P = raster.GaussianParams.from_numpy(g)
-    tw, th = (int(x) for x in args.tile.split("x"))
     stream = torch.cuda.current_stream()
+    cams, masks, targets = [v.cam for v in views], [v.mask for v in views], [v.target for v in views]
+    if args.no_autotune:
+        tw, th = (int(x) for x in args.tile.split("x"))
+        shape, table = autotune.LaunchShape(tw, th, 4, True), None
+    else:
+        t0 = time.perf_counter()
+        shape, table = autotune.autotune(cams, masks, targets, P, g_ranges, use_cache=not args.retune)
+        t_tune = time.perf_counter() - t0
+    tw, th = shape.tile
 
     def timed(fn, steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -511,11 +523,8 @@ def batched(args):
     del plans
     torch.cuda.empty_cache()
 
-    # batched: one plan, persistent LPT launches, one graph
-    plan = raster.Plan([v.cam for v in views], [v.mask for v in views], [v.target for v in views], g.n,
-                       g_ranges=g_ranges, tile=(tw, th))
-    plan.forward(P)
-    plan.use_persistent_schedule(ctas_per_sm=4, lpt=True)
+    # batched: one plan, the tuned launch shape, one graph
+    plan = autotune.plan_for(cams, masks, targets, P, shape, g_ranges)
     grads = raster.new_param_grads(P)
     graph = plan.capture(P, grads)
     for _ in range(args.warmup):
@@ -540,7 +549,11 @@ def batched(args):
         "plain": {"ms_per_step": ms_plain, "value": n_mask / 1e6 / (ms_plain / 1e3), "gpu_launches_per_step":
                   launches_plain},
         "batched": {"ms_per_step": ms_batched, "gpu_launches_per_step": plan.kernel_launches_per_step(),
-                    "graph": True, "persistent": True, "lpt": True},
+                    "graph": True, "persistent": shape.ctas_per_sm is not None, "lpt": shape.lpt,
+                    "tile": f"{tw}x{th}", "ctas_per_sm": shape.ctas_per_sm},
+        "autotune": None if table is None else {"chosen": {"tile": f"{tw}x{th}", "ctas_per_sm": shape.ctas_per_sm,
+                                                           "lpt": shape.lpt},
+                                                "table_ms": table, "seconds": t_tune},
         "grad_max_rel_diff_batched_vs_plain": diff,
         "gpu_launches": plan.kernel_launches_per_step() * args.steps,
         "clocks": ck,
@@ -572,7 +585,7 @@ def capacity(args):
     plan = raster.Plan(cams, masks, targets, n_gauss, g_ranges=g_ranges, tile=(tw, th))
     plan.forward(P)
     t_plan = time.perf_counter() - t0
-    plan.use_persistent_schedule(ctas_per_sm=4, lpt=True)
+    plan.use_persistent_schedule(ctas_per_sm=0, lpt=True)
     grads = raster.new_param_grads(P)
     m = [torch.zeros_like(t) for t in P.tensors()]
     v = [torch.zeros_like(t) for t in P.tensors()]

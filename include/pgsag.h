@@ -109,7 +109,8 @@ typedef struct pgsag_view {
 typedef struct pgsag_sched {
   const uint32_t* order;      /* device, active-tile ids in processing order, or NULL */
   uint32_t* counter;          /* device uint32 work counter for a persistent launch, or NULL */
-  int32_t ctas_per_sm;        /* persistent launch: CTAs per SM (used when counter != NULL) */
+  int32_t ctas_per_sm;        /* persistent launch: CTAs per SM (used when counter != NULL);
+                                 <= 0: as many as the kernel's occupancy allows          */
   int32_t reserved;
 } pgsag_sched;
 

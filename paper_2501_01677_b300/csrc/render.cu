@@ -647,15 +647,26 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
 
 using namespace pgsag;
 
-static int launch_cfg(const pgsag_sched* sched, uint32_t n_items, Sched& s, unsigned& blocks) {
+// Grid of a render launch: one CTA per active tile, or for a persistent launch
+// ctas_per_sm x SMs CTAs (ctas_per_sm <= 0: as many as the kernel's occupancy
+// allows, so the queue never leaves SM slots empty).  `occ` caches the
+// occupancy query (the same on every device of this architecture); the first
+// persistent call should come before any stream capture.
+static int launch_cfg(const pgsag_sched* sched, uint32_t n_items, const void* kernel, int threads, int* occ,
+                      Sched& s, unsigned& blocks) {
   s.order = sched ? sched->order : nullptr;
   s.counter = sched ? sched->counter : nullptr;
   if (s.counter) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PGSAG_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PGSAG_ERR_CUDA;
-    const int per = sched->ctas_per_sm > 0 ? sched->ctas_per_sm : 4;
-    blocks = (unsigned)(sms * per);
+    int per = sched->ctas_per_sm;
+    if (per <= 0) {
+      if (*occ <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, threads, 0) != cudaSuccess)
+        return PGSAG_ERR_CUDA;
+      per = *occ;
+    }
+    blocks = (unsigned)(sms * (per > 0 ? per : 1));
   } else {
     blocks = n_items;
   }
@@ -673,7 +684,9 @@ extern "C" int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const
   if (((uintptr_t)rec | (uintptr_t)out8 | (uintptr_t)aux | (uintptr_t)act_tiles) & 15u) return PGSAG_ERR_ARG;
   Sched s;
   unsigned blocks;
-  int r = launch_cfg(sched, n_active, s, blocks);
+  static int occ = 0;
+  int r = launch_cfg(sched, n_active, (const void*)k_render_fwd<PGSAG_FWD_WARPS>, PGSAG_FWD_WARPS * 32, &occ, s,
+                     blocks);
   if (r) return r;
   cudaStream_t st = (cudaStream_t)stream;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
@@ -706,7 +719,9 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
     return PGSAG_ERR_ARG;
   Sched s;
   unsigned blocks;
-  int r = launch_cfg(sched, n_active, s, blocks);
+  static int occ = 0;
+  int r = launch_cfg(sched, n_active, (const void*)k_render_bwd<PGSAG_BWD_WARPS>, PGSAG_BWD_WARPS * 32, &occ, s,
+                     blocks);
   if (r) return r;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
   k_render_bwd<PGSAG_BWD_WARPS><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,

@@ -218,10 +218,11 @@ class Plan:
         nbytes = int(self.lib.pgsag_bin_workspace_size(self.n_pairs, self.capacity))
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
 
-    def use_persistent_schedule(self, ctas_per_sm: int = 4, lpt: bool = True):
-        """Render with a persistent grid (ctas_per_sm x SMs CTAs) pulling active
-        tiles from a device work counter; with lpt=True the tiles are handed out
-        longest first (pgsag_schedule_lpt, recomputed after every binning)."""
+    def use_persistent_schedule(self, ctas_per_sm: int = 0, lpt: bool = True):
+        """Render with a persistent grid (ctas_per_sm x SMs CTAs; 0: as many as
+        the kernels' occupancy allows) pulling active tiles from a device work
+        counter; with lpt=True the tiles are handed out longest first
+        (pgsag_schedule_lpt, recomputed after every binning)."""
         self.lpt = bool(lpt)
         if self.lpt:
             self.sched_order = torch.empty(max(self.n_active, 1), dtype=torch.int32, device=self.device)

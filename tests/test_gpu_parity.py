@@ -348,3 +348,34 @@ def test_city_block_small_scale_compact_memory():
         R = (plan.flags_image(v).cpu().numpy() & 4) != 0
         a = plan.images(v)["alpha"].cpu().numpy()
         assert (a[~R] == 0).all() and a[R].max() > 0
+
+
+def test_autotuner_picks_a_shape_and_caches_it(tmp_path, monkeypatch):
+    """The autotuner times each (tile, queue depth) candidate on the workload,
+    stores the fastest under the workload key, and a second call is served from
+    the cache without timing anything."""
+    from paper_2501_01677_b300 import autotune as AT, raster
+    g, ranges, views, owner = syn.config3(sizes=(3000, 5000, 2000), views_per_region=2, scale=0.2)
+    g_ranges = [ranges[o] for o in owner]
+    P = raster.GaussianParams.from_numpy(g)
+    cams, masks, targets = [v.cam for v in views], [v.mask for v in views], [v.target for v in views]
+    path = str(tmp_path / "autotune.json")
+    shape, table = AT.autotune(cams, masks, targets, P, g_ranges, tiles=((8, 8), (16, 16)),
+                               queue_depths=(None, 2), replays=2, cache_path=path)
+    assert len(table) == 2 * 3 and all(r["ms"] > 0 for r in table)
+    assert shape.tile in ((8, 8), (16, 16))
+    assert min(r["ms"] for r in table) == next(r["ms"] for r in table if (r["tile_w"], r["tile_h"], r["ctas_per_sm"],
+                                                                            r["lpt"]) == (shape.tile_w, shape.tile_h,
+                                                                                          shape.ctas_per_sm, shape.lpt))
+
+    def no_timing(*a, **k):
+        raise AssertionError("cache miss")
+    monkeypatch.setattr(AT, "time_step", no_timing)
+    shape2, table2 = AT.autotune(cams, masks, targets, P, g_ranges, tiles=((8, 8), (16, 16)),
+                                 queue_depths=(None, 2), replays=2, cache_path=path)
+    assert shape2 == shape and table2 == table
+    plan = AT.plan_for(cams, masks, targets, P, shape, g_ranges)
+    grads = raster.new_param_grads(P)
+    plan.step(P, grads)
+    torch.cuda.synchronize()
+    plan.check_status()

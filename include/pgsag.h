@@ -228,6 +228,9 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, const uint
  *   depth_key [p]: float bits of z, 0xFFFFFFFF for culled pairs
  *   bininfo [p] uint4: {x0 | y0 << 16, x1 | y1 << 16 (inclusive tile rect),
  *     view index, touched}
+ *   tile_mask [p] uint64 (8-byte aligned): for a rectangle of at most 64 tiles,
+ *     bit (ty - y0) * (x1 - x0 + 1) + (tx - x0) set for each tile the pair is
+ *     binned to (popcount = touched); 0 for larger rectangles and culled pairs
  * n_pairs = sum over views of (g_end - g_begin).
  * This call begins a step: it clears *status before its kernel runs.
  */
@@ -235,30 +238,36 @@ int pgsag_preprocess(uint32_t n_gauss, const float* means, const float* log_scal
                      const float* quats, const float* opacity_logit, const float* sh,
                      uint32_t n_views, const pgsag_view* views, const int32_t* tile_act,
                      const uint32_t* sat, float* rec, uint32_t* depth_key, void* bininfo,
-                     int32_t* status, void* stream);
+                     uint64_t* tile_mask, int32_t* status, void* stream);
 
 /*
- * pgsag_bin (Sec. 3.1: projected to tiles, sorted).  Duplicates every visible
- * pair once per tile it is binned to (the rule of pgsag_preprocess, reading the
- * pair's record `rec`) and orders each tile's list by (depth key, Gaussian
- * index):
- *   1. stable LSD radix sort of all pairs by depth key (pair index order breaks
- *      ties, i.e. ascending Gaussian index within a view);
- *   2. exclusive scan of `touched` in that order -> K (written to *k_out);
- *   3. emission of (global active tile, pair) in that order;
- *   4. stable LSD radix sort of the K entries by active tile;
- *   5. per-active-tile ranges [begin, end) into dup_pairs.
- * The result equals a sort of K keys (tile, depth, index) and is bit-exact.
+ * pgsag_bin (Sec. 3.1: the projected Gaussians are assigned to the tiles they
+ * overlap and ordered by depth).  Duplicates every binned pair once per active
+ * tile it is binned to (as pgsag_preprocess decided: the tiles of its tile_mask
+ * for rectangles of up to 64 tiles, every active tile of larger rectangles) and
+ * orders each tile's list by (depth key, pair index), i.e. by depth and then
+ * ascending Gaussian index within a view:
+ *   1. emission of (active tile, pair) for the binned pairs, counting per tile;
+ *      K (*k_out) is the total;
+ *   2. exclusive scan of the tile counts -> ranges, in active-tile order;
+ *   3. scatter of the duplicates into their tiles' ranges;
+ *   4. per tile, sort of the range by the 64-bit key (depth_key << 32 | pair):
+ *      a warp in registers for lists of up to 512, else a block in shared
+ *      memory (chunks of 2048 merged in global memory).
+ * The result equals a sort of K keys (tile, depth, index) and is bit-exact and
+ * deterministic (the sort key is unique).
+ *   tile_mask, bininfo, depth_key  from pgsag_preprocess
  *   capacity   maximum K; if K > capacity, PGSAG_DEV_CAPACITY is set in *status,
  *              nothing is emitted, and later step kernels return without work.
- *   ws         device workspace of pgsag_bin_workspace_size(n_pairs, capacity) bytes
+ *   ws         device workspace of pgsag_bin_workspace_size(n_pairs,
+ *              n_active_total, capacity) bytes
  *   dup_pairs  device uint32 [capacity]: pair index of each duplicate, sorted
  *   ranges     device uint2 [n_active_total]: {begin, end} per active tile
  *   k_out      device uint64 [1]: K
  */
-size_t pgsag_bin_workspace_size(uint32_t n_pairs, uint64_t capacity);
+size_t pgsag_bin_workspace_size(uint32_t n_pairs, uint32_t n_active_total, uint64_t capacity);
 int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
-              uint32_t n_active_total, const int32_t* tile_act, const float* rec, const void* bininfo,
+              uint32_t n_active_total, const int32_t* tile_act, const uint64_t* tile_mask, const void* bininfo,
               const uint32_t* depth_key, uint64_t capacity, void* ws, size_t ws_bytes,
               uint32_t* dup_pairs, void* ranges, uint64_t* k_out, int32_t* status,
               void* stream);

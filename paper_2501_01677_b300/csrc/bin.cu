@@ -1,199 +1,45 @@
-// Tile binning and ordering (Sec. 3.1: 2D Gaussians "projected onto different
-// image tiles" and "sorted").  All pairs are first ordered by depth key with a
-// stable LSD radix sort, duplicated once per active tile in that order, then
-// stably sorted by active tile: each tile's list ends up in ascending
-// (depth key, Gaussian index) order, identical to sorting 64-bit (tile, depth)
-// keys, with N-sized instead of K-sized depth passes.
-//
-// The radix sort is a reduce-then-scan design with no inter-block waits:
-// per pass (8-bit digit) one histogram kernel, one row-parallel scan of the
-// digit-major histogram table (a block per digit), and one scatter kernel that
-// scans the 256 digit totals, then ranks keys stably inside each block with
-// warp match/popc.
+// Tile binning and ordering (Sec. 3.1: the projected Gaussians are assigned to
+// the image tiles they overlap and ordered by depth).  Every binned
+// (view, Gaussian) pair is duplicated once per active tile its alpha >= 1/255
+// region meets (as pgsag_preprocess decided: its tile mask for rectangles of
+// up to 64 tiles, every active tile of larger ones), and each tile's list
+// is ordered by (depth key, pair index):
+//   1. emission: each block gathers the binned pairs of its slice of the pair
+//      array in shared memory (so every lane has work), reserves output room
+//      with one atomic per block and writes (active tile, pair) per duplicate,
+//      counting the duplicates of every tile; K = the total;
+//   2. exclusive scan of the tile counts: the per-tile ranges, in tile order;
+//   3. scatter of the duplicates into their tile's range (the position inside
+//      a range comes from an atomic cursor, so it is in no particular order);
+//   4. per tile, sort of its range by the 64-bit key (depth key << 32 | pair):
+//      one warp per tile in registers for lists of up to kWarpSegMax entries,
+//      one block per longer list (shared memory, chunks of kSegMax merged in
+//      global memory).
+// (depth key, pair) is unique, so step 4 fixes one total order whatever the
+// atomics did: the result equals a sort of the K keys (tile, depth, pair).
+// No kernel waits on another block.
 #include "common.cuh"
 
 namespace pgsag {
 
-constexpr int kRsThreads = 256;
-constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsIpt = 8;
-constexpr int kRsTile = kRsThreads * kRsIpt;  // 2048 keys per block iteration
-constexpr int kRsBlocks = 592;                // 4 blocks per SM on 148 SMs
-constexpr int kScanBlocks = 592;
+constexpr int kScanBlocks = 592;   // 4 blocks per SM on 148 SMs
 constexpr int kScanThreads = 256;
+constexpr int kEmitChunk = 1024;   // pairs gathered per block round in the emission
+constexpr int kSortThreads = 256;
+constexpr int kSegMax = 2048;      // keys sorted in shared memory at once by a block (16 KB)
+constexpr int kWarpSegMax = 512;   // longest list a warp sorts on its own (16 keys per lane in registers)
+constexpr int kWarpSortWarps = 8;  // warps per block of the per-warp sort
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
-__device__ __forceinline__ void block_range(uint64_t n, uint32_t b, uint32_t nb, uint32_t& lo,
-                                            uint32_t& hi) {
+__device__ __forceinline__ void block_range(uint64_t n, uint32_t b, uint32_t nb, uint32_t& lo, uint32_t& hi) {
   const uint64_t per = (n + nb - 1) / nb;
   const uint64_t l = umin64(n, (uint64_t)b * per);
   lo = (uint32_t)l;
   hi = (uint32_t)umin64(n, l + per);
 }
 
-__device__ __forceinline__ uint32_t load_n(const uint64_t* n_dev, uint64_t n_const, uint64_t cap) {
-  return (uint32_t)(n_dev ? umin64(*n_dev, cap) : n_const);
-}
-
-__device__ __forceinline__ uint32_t lanemask_lt() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
-// drop != 0: keys equal to kDropKey are left out (counted nowhere, not written).
-constexpr uint32_t kDropKey = 0xffffffffu;
-
-__global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint32_t* __restrict__ keys,
-                                                           const uint64_t* n_dev, uint64_t n_const,
-                                                           uint64_t cap, int shift, int drop,
-                                                           uint32_t* __restrict__ hist,
-                                                           const int32_t* status) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  if (status_bad(status)) return;
-  const uint32_t n = load_n(n_dev, n_const, cap);
-  uint32_t lo, hi;
-  block_range(n, blockIdx.x, gridDim.x, lo, hi);
-  const int lane = threadIdx.x & 31;
-  for (uint32_t base = lo; base < hi; base += kRsThreads) {
-    const uint32_t i = base + threadIdx.x;
-    const uint32_t key = i < hi ? __ldg(keys + i) : kDropKey;
-    const bool valid = i < hi && !(drop && key == kDropKey);
-    const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
-    const uint32_t peers = __match_any_sync(kFull, d);
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
-  }
-  __syncthreads();
-  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
-}
-
-// One block per digit d: exclusive scan (in place) of row d of the digit-major
-// histogram table (the counts of digit d in blocks 0..G-1) and the row total.
-__global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t* __restrict__ hist, uint32_t G,
-                                                        uint32_t* __restrict__ dtot, const int32_t* status) {
-  __shared__ uint32_t wsum[32];
-  __shared__ uint32_t carry;
-  if (status_bad(status)) return;
-  uint32_t* row = hist + (size_t)blockIdx.x * G;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (uint32_t base = 0; base < G; base += 1024) {
-    const uint32_t i = base + threadIdx.x;
-    const uint32_t s = i < G ? row[i] : 0u;
-    uint32_t x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, w, o);
-        if (lane >= o) w += y;
-      }
-      wsum[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t c = carry;
-    if (i < G) row[i] = c + x - s + (warp > 0 ? wsum[warp - 1] : 0u);
-    __syncthreads();
-    if (threadIdx.x == 0) carry = c + wsum[31];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
-}
-
-__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(
-    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const uint64_t* n_dev,
-    uint64_t n_const, uint64_t cap, int shift, int drop, const uint32_t* __restrict__ hist,
-    const uint32_t* __restrict__ dtot, uint64_t* __restrict__ n_kept, const int32_t* status) {
-  __shared__ uint32_t run[256];
-  __shared__ uint32_t tot[256];
-  __shared__ uint32_t wcnt[kRsWarps][256];
-  if (status_bad(status)) return;
-  const uint32_t n = load_n(n_dev, n_const, cap);
-  uint32_t lo, hi;
-  block_range(n, blockIdx.x, gridDim.x, lo, hi);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  {
-    // digit bases: exclusive scan of the 256 digit totals
-    const uint32_t t = dtot[threadIdx.x];
-    uint32_t x = t;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) tot[warp] = x;
-    __syncthreads();
-    uint32_t pre = 0;
-    for (int w = 0; w < warp; ++w) pre += tot[w];
-    run[threadIdx.x] = pre + x - t + hist[threadIdx.x * gridDim.x + blockIdx.x];
-    // number of keys this pass keeps (all of them unless dropping)
-    if (n_kept != nullptr && blockIdx.x == 0 && threadIdx.x == kRsThreads - 1) *n_kept = pre + x;
-    __syncthreads();
-  }
-  const uint32_t lt = lanemask_lt();
-  for (uint32_t tile = lo; tile < hi; tile += kRsTile) {
-#pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) wcnt[w][threadIdx.x] = 0;
-    uint32_t k[kRsIpt], v[kRsIpt], rk[kRsIpt], dg[kRsIpt];
-#pragma unroll
-    for (int j = 0; j < kRsIpt; ++j) {
-      const uint32_t idx = tile + warp * (32 * kRsIpt) + j * 32 + lane;
-      k[j] = idx < hi ? __ldg(keys_in + idx) : kDropKey;
-      const bool valid = idx < hi && !(drop && k[j] == kDropKey);
-      v[j] = valid ? (vals_in ? __ldg(vals_in + idx) : idx) : 0u;
-      dg[j] = valid ? ((k[j] >> shift) & 255u) : 256u;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kRsIpt; ++j) {
-      const uint32_t peers = __match_any_sync(kFull, dg[j]);
-      uint32_t base = 0;
-      if (dg[j] < 256u) base = wcnt[warp][dg[j]];
-      rk[j] = base + __popc(peers & lt);
-      __syncwarp();
-      if (dg[j] < 256u && lane == __ffs(peers) - 1) wcnt[warp][dg[j]] = base + __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    {
-      uint32_t s = 0;
-#pragma unroll
-      for (int w = 0; w < kRsWarps; ++w) {
-        const uint32_t t = wcnt[w][threadIdx.x];
-        wcnt[w][threadIdx.x] = s;
-        s += t;
-      }
-      tot[threadIdx.x] = s;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kRsIpt; ++j) {
-      if (dg[j] < 256u) {
-        const uint32_t dst = run[dg[j]] + wcnt[warp][dg[j]] + rk[j];
-        keys_out[dst] = k[j];
-        vals_out[dst] = v[j];
-      }
-    }
-    __syncthreads();
-    run[threadIdx.x] += tot[threadIdx.x];
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------- scan + emit
-
+// Exclusive scan over the block (kScanThreads threads); `total` = block sum.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t& total, uint32_t* sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t inc = x;
@@ -216,18 +62,16 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t& total,
   return pre + inc - x;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ order,
-                                                              const uint4* __restrict__ bininfo,
-                                                              const uint64_t* n_dev, uint64_t cap,
-                                                              uint64_t* __restrict__ partial,
-                                                              const int32_t* status) {
+// Per-block sums of counts[i * stride] over block_range(n).
+__global__ void __launch_bounds__(kScanThreads) k_block_sums(uint32_t n, const uint32_t* __restrict__ counts,
+                                                             int stride, uint64_t* __restrict__ partial,
+                                                             const int32_t* status) {
   __shared__ unsigned long long ws[kScanThreads / 32];
   if (status_bad(status)) return;
-  const uint32_t n = load_n(n_dev, 0, cap);
   uint32_t lo, hi;
   block_range(n, blockIdx.x, gridDim.x, lo, hi);
   unsigned long long s = 0;
-  for (uint32_t i = lo + threadIdx.x; i < hi; i += kScanThreads) s += __ldg(&bininfo[__ldg(order + i)].w);
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += kScanThreads) s += __ldg(counts + (size_t)i * stride);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
@@ -239,9 +83,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
   }
 }
 
+// One block: exclusive scan (in place) of nb <= 1024 block sums; the total goes
+// to *total_out when given, and with check_cap a total above `capacity` sets
+// the capacity flag (nothing is emitted then: later kernels see the status).
 __global__ void __launch_bounds__(1024) k_scan_partials(uint64_t* __restrict__ partial, uint32_t nb,
-                                                        uint64_t* __restrict__ k_out, uint64_t capacity,
-                                                        int32_t* status) {
+                                                        uint64_t* __restrict__ total_out, uint64_t capacity,
+                                                        int check_cap, int32_t* status) {
   __shared__ unsigned long long wsum[32];
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -268,84 +115,325 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint64_t* __restrict__ p
   if (threadIdx.x < nb) partial[threadIdx.x] = pre;
   if (threadIdx.x == 1023) {
     const unsigned long long total = pre + s;
-    *k_out = total;
-    if (total > capacity) status_set(status, PGSAG_DEV_CAPACITY);
+    if (total_out) *total_out = total;
+    if (check_cap && total > capacity) status_set(status, PGSAG_DEV_CAPACITY);
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_emit(
-    const uint32_t* __restrict__ order, const uint4* __restrict__ bininfo, const uint64_t* n_dev, uint64_t cap,
-    const uint64_t* __restrict__ partial, const pgsag_view* __restrict__ views,
-    const int32_t* __restrict__ tile_act, const float4* __restrict__ rec, uint32_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, int32_t* status) {
+// Step 1: emission.  Blocks stride over kEmitChunk-pair slices; the binned
+// pairs of a slice are gathered in shared memory, each round of up to
+// kScanThreads of them reserves its output with one atomic on *k_total, and
+// every duplicate is written as (active tile, pair) and counted per tile.
+// Duplicates beyond `capacity` are not written (the capacity flag is set).
+__global__ void __launch_bounds__(kScanThreads) k_emit(uint32_t n, const uint4* __restrict__ bininfo,
+                                                       const pgsag_view* __restrict__ views,
+                                                       const int32_t* __restrict__ tile_act,
+                                                       const unsigned long long* __restrict__ tmask,
+                                                       uint32_t n_active, uint64_t capacity,
+                                                       unsigned long long* __restrict__ k_total,
+                                                       uint32_t* __restrict__ tile_keys,
+                                                       uint32_t* __restrict__ pair_vals,
+                                                       uint32_t* __restrict__ tile_cnt, int32_t* status) {
+  __shared__ uint32_t s_list[kEmitChunk];
+  __shared__ uint32_t s_n;
   __shared__ uint32_t sh[kScanThreads / 32];
+  __shared__ unsigned long long s_base;
   if (status_bad(status)) return;
-  const uint32_t n = load_n(n_dev, 0, cap);
-  uint32_t lo, hi;
-  block_range(n, blockIdx.x, gridDim.x, lo, hi);
-  uint32_t carry = (uint32_t)partial[blockIdx.x];
-  for (uint32_t base = lo; base < hi; base += kScanThreads) {
-    const uint32_t i = base + threadIdx.x;
-    const bool valid = i < hi;
-    uint32_t p = 0;
-    uint4 bi = make_uint4(0, 0, 0, 0);
-    if (valid) {
-      p = __ldg(order + i);
-      bi = __ldg(&bininfo[p]);
+  for (uint32_t c0 = blockIdx.x * kEmitChunk; c0 < n; c0 += gridDim.x * kEmitChunk) {
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kEmitChunk; i += kScanThreads) {
+      const uint32_t p = c0 + i;
+      if (p < n && __ldg(&bininfo[p].w) != 0u) s_list[atomicAdd(&s_n, 1u)] = p;
     }
-    uint32_t total;
-    const uint32_t off = block_excl_scan(bi.w, total, sh);
-    if (bi.w) {
-      const pgsag_view* V = views + bi.z;
-      const int tiles_x = __ldg(&V->tiles_x);
-      const int32_t* ta = tile_act + __ldg(&V->tile_base);
-      const uint32_t x0 = bi.x & 0xffffu, y0 = bi.x >> 16, x1 = bi.y & 0xffffu, y1 = bi.y >> 16;
-      const bool exact = (x1 - x0 + 1) * (y1 - y0 + 1) <= (uint32_t)kExactTileMax;
-      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r3 = r0;
-      float l22 = 0.f;
-      int tw = 0, th = 0, W = 0, H = 0;
-      if (exact) {
-        r0 = __ldg(rec + 4ull * p);
-        l22 = __ldg(&rec[4ull * p + 1].x);
-        r3 = __ldg(rec + 4ull * p + 3);
-        tw = __ldg(&V->tile_w);
-        th = __ldg(&V->tile_h);
-        W = __ldg(&V->width);
-        H = __ldg(&V->height);
-      }
-      uint32_t o = carry + off;
-      const uint32_t oend = o + bi.w;
-      for (uint32_t ty = y0; ty <= y1; ++ty) {
-        const int32_t* row = ta + (size_t)ty * tiles_x;
-        for (uint32_t tx = x0; tx <= x1; ++tx) {
-          const int32_t a = __ldg(row + tx);
-          if (a >= 0 && (!exact || tile_hit(r0.x, r0.y, r3.z, r3.w, r0.z, r0.w, l22, r3.y, (int)tx, (int)ty, tw, th, W, H))) {
-            if (o < oend) {
-              keys_out[o] = (uint32_t)a;
-              vals_out[o] = p;
+    __syncthreads();
+    const uint32_t m = s_n;
+    for (uint32_t r = 0; r < m; r += kScanThreads) {
+      const uint32_t j = r + threadIdx.x;
+      const uint32_t p = j < m ? s_list[j] : 0u;
+      const uint4 bi = j < m ? __ldg(&bininfo[p]) : make_uint4(0, 0, 0, 0);
+      uint32_t total;
+      const uint32_t off = block_excl_scan(bi.w, total, sh);
+      if (threadIdx.x == 0) s_base = atomicAdd(k_total, (unsigned long long)total);
+      __syncthreads();
+      const unsigned long long base = s_base;
+      __syncthreads();
+      if (threadIdx.x == 0 && base + total > capacity) status_set(status, PGSAG_DEV_CAPACITY);
+      if (bi.w) {
+        const pgsag_view* V = views + bi.z;
+        const int tiles_x = __ldg(&V->tiles_x);
+        const int32_t* ta = tile_act + __ldg(&V->tile_base);
+        const uint32_t x0 = bi.x & 0xffffu, y0 = bi.x >> 16, x1 = bi.y & 0xffffu, y1 = bi.y >> 16;
+        const uint32_t rw = x1 - x0 + 1;
+        const bool exact = rw * (y1 - y0 + 1) <= (uint32_t)kExactTileMax;
+        unsigned long long o = base + off;
+        const unsigned long long oend = o + bi.w;
+        auto put = [&](int32_t a) {
+          if ((uint32_t)a >= n_active) {
+            status_set(status, PGSAG_DEV_BOUNDS);
+          } else if (o < oend && o < capacity) {
+            tile_keys[o] = (uint32_t)a;
+            pair_vals[o] = p;
+            atomicAdd(tile_cnt + a, 1u);
+          }
+          ++o;
+        };
+        if (exact) {
+          // the tiles the projection's exact test accepted, one bit each
+          for (unsigned long long mk = __ldg(tmask + p); mk; mk &= mk - 1) {
+            const uint32_t b = (uint32_t)__ffsll((long long)mk) - 1u;
+            const uint32_t ty = y0 + b / rw, tx = x0 + b % rw;
+            put(__ldg(ta + (size_t)ty * tiles_x + tx));
+          }
+        } else {
+          // large rectangles: every active tile of the rectangle
+          for (uint32_t ty = y0; ty <= y1; ++ty) {
+            const int32_t* row = ta + (size_t)ty * tiles_x;
+            for (uint32_t tx = x0; tx <= x1; ++tx) {
+              const int32_t a = __ldg(row + tx);
+              if (a >= 0) put(a);
             }
-            ++o;
           }
         }
+        // the count and this enumeration describe the same tiles; a mismatch is a bug
+        if (o != oend) status_set(status, PGSAG_DEV_BOUNDS);
       }
-      if (o != oend) status_set(status, PGSAG_DEV_BOUNDS);
     }
+    __syncthreads();
+  }
+}
+
+// Step 2 (after the block sums of the counts): ranges[a] = {start, start + count}.
+__global__ void __launch_bounds__(kScanThreads) k_tile_ranges(uint32_t n_active, const uint32_t* __restrict__ cnt,
+                                                              const uint64_t* __restrict__ partial,
+                                                              uint2* __restrict__ ranges, const int32_t* status) {
+  __shared__ uint32_t sh[kScanThreads / 32];
+  if (status_bad(status)) return;
+  uint32_t lo, hi;
+  block_range(n_active, blockIdx.x, gridDim.x, lo, hi);
+  uint32_t carry = (uint32_t)partial[blockIdx.x];
+  for (uint32_t base = lo; base < hi; base += kScanThreads) {
+    const uint32_t a = base + threadIdx.x;
+    const uint32_t c = a < hi ? __ldg(cnt + a) : 0u;
+    uint32_t total;
+    const uint32_t off = block_excl_scan(c, total, sh);
+    if (a < hi) ranges[a] = make_uint2(carry + off, carry + off + c);
     carry += total;
   }
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint64_t* n_dev, uint64_t cap,
-                         uint2* __restrict__ ranges, uint32_t n_active, int32_t* status) {
+// Step 3: duplicate k goes to ranges[tile].x + (a distinct slot of its tile).
+// The cursor counts each tile down from its count to 0.
+__global__ void k_scatter(const uint64_t* __restrict__ k_dev, uint64_t cap, uint32_t n_active,
+                          const uint32_t* __restrict__ tile_keys, const uint32_t* __restrict__ pair_vals,
+                          const uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, uint32_t* __restrict__ out,
+                          int32_t* status) {
   if (status_bad(status)) return;
-  const uint32_t n = (uint32_t)umin64(*n_dev, cap);
+  const uint32_t n = (uint32_t)umin64(*k_dev, cap);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t t = __ldg(keys + k);
-    if (t >= n_active) {
+    const uint32_t a = __ldg(tile_keys + k);
+    if (a >= n_active) {
       status_set(status, PGSAG_DEV_BOUNDS);
       continue;
     }
-    if (k == 0 || __ldg(keys + k - 1) != t) ranges[t].x = k;
-    if (k == n - 1 || __ldg(keys + k + 1) != t) ranges[t].y = k + 1;
+    const uint2 r = __ldg(ranges + a);
+    const uint32_t left = atomicSub(cursor + a, 1u);
+    if (left == 0u || left > r.y - r.x) {
+      status_set(status, PGSAG_DEV_BOUNDS);
+      continue;
+    }
+    out[r.x + left - 1u] = __ldg(pair_vals + k);
+  }
+}
+
+__device__ __forceinline__ unsigned long long sort_key(const uint32_t* __restrict__ dkey, uint32_t p) {
+  return ((unsigned long long)__ldg(dkey + p) << 32) | p;
+}
+
+// Sort n <= kSegMax pair indices by sort_key in shared memory (bitonic network
+// over the next power of two, padded with the largest key); `in` and `out` may
+// be the same array.
+__device__ void sort_chunk(const uint32_t* in, uint32_t n, uint32_t* out, const uint32_t* __restrict__ dkey,
+                           unsigned long long* sk) {
+  uint32_t m = 2;
+  while (m < n) m <<= 1;
+  for (uint32_t i = threadIdx.x; i < m; i += kSortThreads) sk[i] = i < n ? sort_key(dkey, in[i]) : ~0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= m; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < m; i += kSortThreads) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = sk[i], b = sk[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            sk[i] = b;
+            sk[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) out[i] = (uint32_t)sk[i];
+  __syncthreads();
+}
+
+// Merge the sorted runs src[0, na) and src[na, na + nb) into dst[0, na + nb):
+// each thread finds where its output slice starts on both runs by a binary
+// search along the merge path, then merges the slice sequentially.
+__device__ void merge_runs(const uint32_t* src, uint32_t na, uint32_t nb, uint32_t* dst,
+                           const uint32_t* __restrict__ dkey) {
+  const uint32_t L = na + nb;
+  const uint32_t per = (L + kSortThreads - 1) / kSortThreads;
+  const uint32_t d0 = min(L, threadIdx.x * per), d1 = min(L, d0 + per);
+  if (d0 < d1) {
+    const uint32_t* A = src;
+    const uint32_t* B = src + na;
+    // i = number of A elements among the first d0 outputs: the largest i in
+    // [max(0, d0 - nb), min(d0, na)] with A[i - 1] < B[d0 - i]
+    uint32_t lo = d0 > nb ? d0 - nb : 0u, hi = min(d0, na);
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (sort_key(dkey, A[mid]) < sort_key(dkey, B[d0 - mid - 1])) lo = mid + 1;
+      else hi = mid;
+    }
+    uint32_t i = lo, j = d0 - lo;
+    for (uint32_t d = d0; d < d1; ++d) {
+      bool take_a;
+      if (i >= na) take_a = false;
+      else if (j >= nb) take_a = true;
+      else take_a = sort_key(dkey, A[i]) < sort_key(dkey, B[j]);
+      dst[d] = take_a ? A[i++] : B[j++];
+    }
+  }
+  __syncthreads();
+}
+
+// Bitonic sort of m = 32 E keys held by one warp in registers: element
+// i = e * 32 + lane is x[e].  Compare-exchange partners at distance j >= 32
+// sit in the same lane (register e ^ j/32), closer ones in lane ^ j (one
+// 64-bit shuffle).
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[E], int lane) {
+  constexpr int m = 32 * E;
+#pragma unroll
+  for (int k = 2; k <= m; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int je = j >> 5;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int f = e ^ je;
+          if (f > e) {
+            const int i = e * 32 + lane;
+            const bool up = (i & k) == 0;
+            const unsigned long long a = x[e], b = x[f];
+            if ((a > b) == up) {
+              x[e] = b;
+              x[f] = a;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = e * 32 + lane;
+          const unsigned long long y = __shfl_xor_sync(kFull, x[e], j);
+          const bool up = (i & k) == 0, lower = (lane & j) == 0;
+          x[e] = (up == lower) ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+        }
+      }
+    }
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_list(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ out,
+                                               const uint32_t* __restrict__ dkey, int lane) {
+  unsigned long long x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = (uint32_t)(e * 32 + lane);
+    x[e] = i < n ? sort_key(dkey, __ldg(in + i)) : ~0ull;
+  }
+  warp_bitonic<E>(x, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = (uint32_t)(e * 32 + lane);
+    if (i < n) out[i] = (uint32_t)x[e];
+  }
+}
+
+// Step 4a: one warp per active tile sorts lists of up to kWarpSegMax entries
+// in registers; longer lists are appended to `long_list` for k_sort_long.
+__global__ void __launch_bounds__(kWarpSortWarps * 32) k_sort_warp(uint32_t n_active,
+                                                                   const uint2* __restrict__ ranges,
+                                                                   const uint32_t* __restrict__ dkey,
+                                                                   const uint32_t* __restrict__ buf,
+                                                                   uint32_t* __restrict__ out,
+                                                                   uint32_t* __restrict__ long_list,
+                                                                   unsigned long long* __restrict__ n_long,
+                                                                   const int32_t* status) {
+  static_assert(kWarpSegMax == 32 * 16, "the register sort covers up to 16 keys per lane");
+  if (status_bad(status)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t a = blockIdx.x * kWarpSortWarps + warp; a < n_active; a += gridDim.x * kWarpSortWarps) {
+    const uint2 r = __ldg(ranges + a);
+    const uint32_t n = r.y - r.x;
+    if (n <= 1) {
+      if (n == 1 && lane == 0) out[r.x] = __ldg(buf + r.x);
+      continue;
+    }
+    const uint32_t* in = buf + r.x;
+    uint32_t* o = out + r.x;
+    if (n <= 32) warp_sort_list<1>(in, n, o, dkey, lane);
+    else if (n <= 64) warp_sort_list<2>(in, n, o, dkey, lane);
+    else if (n <= 128) warp_sort_list<4>(in, n, o, dkey, lane);
+    else if (n <= 256) warp_sort_list<8>(in, n, o, dkey, lane);
+    else if (n <= (uint32_t)kWarpSegMax) warp_sort_list<16>(in, n, o, dkey, lane);
+    else if (lane == 0) long_list[atomicAdd(n_long, 1ull)] = a;
+  }
+}
+
+// Step 4b: blocks stride over the long lists and sort each tile's range.
+// buf holds the scattered lists; the sorted lists end in out.
+__global__ void __launch_bounds__(kSortThreads) k_sort_long(const unsigned long long* __restrict__ n_long,
+                                                            const uint32_t* __restrict__ long_list,
+                                                            const uint2* __restrict__ ranges,
+                                                            const uint32_t* __restrict__ dkey, uint32_t* buf,
+                                                            uint32_t* out, const int32_t* status) {
+  __shared__ unsigned long long sk[kSegMax];
+  if (status_bad(status)) return;
+  const uint32_t count = (uint32_t)*n_long;
+  for (uint32_t e = blockIdx.x; e < count; e += gridDim.x) {
+    const uint2 r = __ldg(ranges + __ldg(long_list + e));
+    const uint32_t n = r.y - r.x;
+    if (n <= (uint32_t)kSegMax) {
+      sort_chunk(buf + r.x, n, out + r.x, dkey, sk);
+      continue;
+    }
+    // sorted chunks, then rounds of pairwise merges between buf and out,
+    // starting in whichever array makes the last round land in out
+    const uint32_t chunks = (n + kSegMax - 1) / kSegMax;
+    uint32_t rounds = 0;
+    while ((1u << rounds) < chunks) ++rounds;
+    uint32_t* src = (rounds & 1) ? buf + r.x : out + r.x;
+    uint32_t* dst = (rounds & 1) ? out + r.x : buf + r.x;
+    for (uint32_t c = 0; c < chunks; ++c) {
+      const uint32_t s = c * kSegMax;
+      sort_chunk(buf + r.x + s, min((uint32_t)kSegMax, n - s), src + s, dkey, sk);
+    }
+    for (uint32_t w = kSegMax; w < n; w <<= 1) {
+      for (uint32_t s = 0; s < n; s += 2 * w) {
+        const uint32_t na = min(w, n - s), nb = n - s > w ? min(w, n - s - w) : 0u;
+        merge_runs(src + s, na, nb, dst + s, dkey);
+      }
+      uint32_t* t = src;
+      src = dst;
+      dst = t;
+    }
   }
 }
 
@@ -355,15 +443,17 @@ using namespace pgsag;
 
 namespace {
 struct BinWs {
-  uint32_t *kA, *kB, *vA, *vB;  // depth sort (n_pairs)
-  uint32_t *dkA, *dkB, *dvW;    // tile sort (capacity)
-  uint32_t* hist;               // 256 * kRsBlocks counts, then 256 digit totals
-  uint64_t* partial;            // kScanBlocks + 1
-  uint64_t* n_bin;              // pairs kept by the depth sort (touching an active tile)
+  uint64_t* tile_partial;        // kScanBlocks + 1
+  unsigned long long* n_long;    // lists longer than kWarpSegMax
+  uint32_t* tile_cnt;            // n_active: duplicates per tile, then the scatter cursor
+  uint32_t* long_list;           // n_active: tiles with long lists
+  uint32_t* tile_keys;           // capacity: emitted active tile
+  uint32_t* pair_vals;           // capacity: emitted pair
+  uint32_t* buf;                 // capacity: lists scattered into their tiles
   size_t bytes;
 };
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-BinWs carve(void* base, uint32_t np, uint64_t cap) {
+BinWs carve(void* base, uint32_t n_active, uint64_t cap) {
   BinWs w;
   size_t o = 0;
   char* b = (char*)base;
@@ -372,109 +462,71 @@ BinWs carve(void* base, uint32_t np, uint64_t cap) {
     o += align256(bytes);
     return p;
   };
-  const size_t npb = (size_t)(np ? np : 1) * 4, capb = (size_t)(cap ? cap : 1) * 4;
-  w.kA = (uint32_t*)take(npb);
-  w.kB = (uint32_t*)take(npb);
-  w.vA = (uint32_t*)take(npb);
-  w.vB = (uint32_t*)take(npb);
-  w.dkA = (uint32_t*)take(capb);
-  w.dkB = (uint32_t*)take(capb);
-  w.dvW = (uint32_t*)take(capb);
-  w.hist = (uint32_t*)take((size_t)256 * (kRsBlocks + 1) * 4);
-  w.partial = (uint64_t*)take((size_t)(kScanBlocks + 1) * 8);
-  w.n_bin = (uint64_t*)take(8);
+  const size_t capb = (size_t)(cap ? cap : 1) * 4, actb = (size_t)(n_active ? n_active : 1) * 4;
+  w.tile_partial = (uint64_t*)take((size_t)(kScanBlocks + 1) * 8);
+  w.n_long = (unsigned long long*)take(8);
+  w.tile_cnt = (uint32_t*)take(actb);
+  w.long_list = (uint32_t*)take(actb);
+  w.tile_keys = (uint32_t*)take(capb);
+  w.pair_vals = (uint32_t*)take(capb);
+  w.buf = (uint32_t*)take(capb);
   w.bytes = o;
   return w;
 }
-
-int radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
-               const uint64_t* n_dev, uint64_t n_const, uint64_t cap, int shift, uint32_t* hist,
-               uint64_t* n_kept, int32_t* status, cudaStream_t s) {
-  const int drop = n_kept != nullptr;
-  k_radix_hist<<<kRsBlocks, kRsThreads, 0, s>>>(kin, n_dev, n_const, cap, shift, drop, hist, status);
-  PGSAG_CHECK_LAUNCH();
-  k_radix_rowscan<<<256, 1024, 0, s>>>(hist, kRsBlocks, hist + 256 * kRsBlocks, status);
-  PGSAG_CHECK_LAUNCH();
-  k_radix_scatter<<<kRsBlocks, kRsThreads, 0, s>>>(kin, vin, kout, vout, n_dev, n_const, cap, shift, drop, hist,
-                                                   hist + 256 * kRsBlocks, n_kept, status);
-  PGSAG_CHECK_LAUNCH();
-  return PGSAG_OK;
-}
 }  // namespace
 
-extern "C" size_t pgsag_bin_workspace_size(uint32_t n_pairs, uint64_t capacity) {
-  return carve(nullptr, n_pairs, capacity).bytes;
+extern "C" size_t pgsag_bin_workspace_size(uint32_t n_pairs, uint32_t n_active_total, uint64_t capacity) {
+  (void)n_pairs;
+  return carve(nullptr, n_active_total, capacity).bytes;
 }
 
 extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
-                         uint32_t n_active_total, const int32_t* tile_act, const float* rec, const void* bininfo,
+                         uint32_t n_active_total, const int32_t* tile_act, const uint64_t* tile_mask,
+                         const void* bininfo,
                          const uint32_t* depth_key, uint64_t capacity, void* ws, size_t ws_bytes,
                          uint32_t* dup_pairs, void* ranges, uint64_t* k_out, int32_t* status,
                          void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !k_out || !status || !ws) return PGSAG_ERR_ARG;
   if (capacity > 0xffffffffull) return PGSAG_ERR_UNSUPPORTED;
-  if (n_pairs && (!bininfo || !depth_key || !tile_act || !rec)) return PGSAG_ERR_ARG;
-  if (((uintptr_t)rec | (uintptr_t)bininfo) & 15u) return PGSAG_ERR_ARG;
+  if (n_pairs && (!bininfo || !depth_key || !tile_act || !tile_mask)) return PGSAG_ERR_ARG;
+  if (((uintptr_t)bininfo & 15u) || ((uintptr_t)tile_mask & 7u)) return PGSAG_ERR_ARG;
   if (n_active_total && !ranges) return PGSAG_ERR_ARG;
   if (capacity && !dup_pairs) return PGSAG_ERR_ARG;
-  const BinWs w = carve(ws, n_pairs, capacity);
+  const BinWs w = carve(ws, n_active_total, capacity);
   if (ws_bytes < w.bytes) return PGSAG_ERR_CAPACITY;
   cudaStream_t s = (cudaStream_t)stream;
   PGSAG_CUDA(cudaMemsetAsync(k_out, 0, sizeof(uint64_t), s));
-  if (n_active_total) PGSAG_CUDA(cudaMemsetAsync(ranges, 0, (size_t)n_active_total * sizeof(uint2), s));
-  if (n_pairs == 0) return PGSAG_OK;
-
-  // 1. stable sort of pairs by depth key (4 x 8-bit digits).  The first pass
-  // leaves out the culled pairs (key 0xffffffff: outside the image or touching
-  // no active tile) and counts the rest into n_bin; later passes and the scan
-  // run on those only.
-  const uint32_t* kin = depth_key;
-  const uint32_t* vin = nullptr;
-  uint32_t* kb[2] = {w.kA, w.kB};
-  uint32_t* vb[2] = {w.vA, w.vB};
-  for (int pass = 0; pass < 4; ++pass) {
-    const int r = radix_pass(kin, vin, kb[pass & 1], vb[pass & 1], pass ? w.n_bin : nullptr, n_pairs, n_pairs,
-                             8 * pass, w.hist, pass ? nullptr : w.n_bin, status, s);
-    if (r) return r;
-    kin = kb[pass & 1];
-    vin = vb[pass & 1];
-  }
-  const uint32_t* order = vin;  // pair indices in (depth key, pair index) order
-
-  // 2-3. scan of touched in that order, K, emission of (active tile, pair)
-  int tile_passes = 0;
-  if (n_active_total > 1) {
-    const int bits = 32 - __builtin_clz(n_active_total - 1);
-    tile_passes = (bits + 7) / 8;
-  }
-  // buffers: pass i reads X_i, writes X_{i+1}; X_P must be dup_pairs
-  uint32_t* keysX[5];
-  uint32_t* valsX[5];
-  for (int i = 0; i <= tile_passes; ++i) {
-    const int from_end = tile_passes - i;
-    keysX[i] = (from_end & 1) ? w.dkA : w.dkB;
-    valsX[i] = (from_end & 1) ? w.dvW : dup_pairs;
-  }
-  const uint32_t nsb = kScanBlocks;
-  k_scan_reduce<<<nsb, kScanThreads, 0, s>>>(order, (const uint4*)bininfo, w.n_bin, n_pairs, w.partial, status);
-  PGSAG_CHECK_LAUNCH();
-  k_scan_partials<<<1, 1024, 0, s>>>(w.partial, nsb, k_out, capacity, status);
-  PGSAG_CHECK_LAUNCH();
-  k_scan_emit<<<nsb, kScanThreads, 0, s>>>(order, (const uint4*)bininfo, w.n_bin, n_pairs, w.partial, views,
-                                           tile_act, (const float4*)rec, keysX[0], valsX[0], status);
-  PGSAG_CHECK_LAUNCH();
-
-  // 4. stable sort of the duplicates by active tile
-  for (int pass = 0; pass < tile_passes; ++pass) {
-    const int r = radix_pass(keysX[pass], valsX[pass], keysX[pass + 1], valsX[pass + 1], k_out, 0, capacity,
-                             8 * pass, w.hist, nullptr, status, s);
-    if (r) return r;
-  }
-  // 5. ranges
   if (n_active_total) {
-    k_ranges<<<592, 256, 0, s>>>(keysX[tile_passes], k_out, capacity, (uint2*)ranges, n_active_total, status);
-    PGSAG_CHECK_LAUNCH();
+    PGSAG_CUDA(cudaMemsetAsync(ranges, 0, (size_t)n_active_total * sizeof(uint2), s));
+    PGSAG_CUDA(cudaMemsetAsync(w.tile_cnt, 0, (size_t)n_active_total * sizeof(uint32_t), s));
   }
+  PGSAG_CUDA(cudaMemsetAsync(w.n_long, 0, sizeof(unsigned long long), s));
+  if (n_pairs == 0 || n_active_total == 0) return PGSAG_OK;
+
+  // 1. emission (K accumulates in *k_out)
+  k_emit<<<kScanBlocks, kScanThreads, 0, s>>>(n_pairs, (const uint4*)bininfo, views, tile_act,
+                                              (const unsigned long long*)tile_mask, n_active_total, capacity, (unsigned long long*)k_out, w.tile_keys,
+                                              w.pair_vals, w.tile_cnt, status);
+  PGSAG_CHECK_LAUNCH();
+  // 2. per-tile ranges
+  k_block_sums<<<kScanBlocks, kScanThreads, 0, s>>>(n_active_total, w.tile_cnt, 1, w.tile_partial, status);
+  PGSAG_CHECK_LAUNCH();
+  k_scan_partials<<<1, 1024, 0, s>>>(w.tile_partial, kScanBlocks, nullptr, 0, 0, status);
+  PGSAG_CHECK_LAUNCH();
+  k_tile_ranges<<<kScanBlocks, kScanThreads, 0, s>>>(n_active_total, w.tile_cnt, w.tile_partial, (uint2*)ranges,
+                                                     status);
+  PGSAG_CHECK_LAUNCH();
+  // 3. scatter into the tiles' ranges; 4. per-tile sort into dup_pairs
+  k_scatter<<<kScanBlocks, 256, 0, s>>>(k_out, capacity, n_active_total, w.tile_keys, w.pair_vals,
+                                        (const uint2*)ranges, w.tile_cnt, w.buf, status);
+  PGSAG_CHECK_LAUNCH();
+  const uint32_t warp_blocks = (n_active_total + kWarpSortWarps - 1) / kWarpSortWarps;
+  k_sort_warp<<<warp_blocks < (1u << 20) ? warp_blocks : (1u << 20), kWarpSortWarps * 32, 0, s>>>(
+      n_active_total, (const uint2*)ranges, depth_key, w.buf, dup_pairs, w.long_list, w.n_long, status);
+  PGSAG_CHECK_LAUNCH();
+  k_sort_long<<<296, kSortThreads, 0, s>>>(w.n_long, w.long_list, (const uint2*)ranges, depth_key, w.buf, dup_pairs,
+                                           status);
+  PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

@@ -335,7 +335,8 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
                              uint32_t n_views, const pgsag_view* __restrict__ views,
                              const int32_t* __restrict__ tile_act, const uint32_t* __restrict__ sat,
                              float4* __restrict__ rec, uint32_t* __restrict__ dkey,
-                             uint4* __restrict__ bininfo, const int32_t* status) {
+                             uint4* __restrict__ bininfo, unsigned long long* __restrict__ tmask,
+                             const int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pgsag_view* sv = reinterpret_cast<pgsag_view*>(smem_raw);
   {
@@ -360,6 +361,7 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
     float mx = 0.f, my = 0.f, ex = 0.f, ey = 0.f;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
     uint32_t touched = 0;
+    unsigned long long mask = 0ull;  // tiles binned to, bit (ty - y0) * width + (tx - x0) of the rect
     float mi = 0.f, mf = 0.f, ni = 0.f, nf = 0.f;
     if (vis) {
       {
@@ -393,14 +395,14 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
         if (touched && (x1 - x0 + 1) * (y1 - y0 + 1) <= kExactTileMax) {
           const float thr = -logf(255.f * P.o);
           const int32_t* ta = tile_act + V.tile_base;
-          uint32_t cnt = 0;
+          const int rw = x1 - x0 + 1;
           for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx)
               if (__ldg(ta + ty * V.tiles_x + tx) >= 0 &&
                   tile_hit(mi, ni, mf, nf, P.l11, P.l21, P.l22, thr, tx, ty, V.tile_w, V.tile_h, V.width,
                            V.height))
-                ++cnt;
-          touched = cnt;
+                mask |= 1ull << ((ty - y0) * rw + (tx - x0));
+          touched = (uint32_t)__popcll(mask);
         }
       } else {
         vis = false;
@@ -414,6 +416,7 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
       R4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
       dkey[p] = 0xffffffffu;
       bininfo[p] = make_uint4(0u, 0u, vi, 0u);
+      tmask[p] = 0ull;
       continue;
     }
     // colour: degree-3 SH at the viewing direction (world frame)
@@ -431,6 +434,7 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
     R4[2] = make_float4(fmaxf(col[2], 0.f), P.dist, P.nc[0], P.nc[1]);
     R4[3] = make_float4(P.nc[2], -logf(255.f * P.o), mf, nf);
     dkey[p] = __float_as_uint(P.mc[2]);
+    tmask[p] = mask;
     bininfo[p] = make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16), vi,
                             touched);
   }
@@ -708,13 +712,14 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
                                 const float* quats, const float* opacity_logit, const float* sh,
                                 uint32_t n_views, const pgsag_view* views, const int32_t* tile_act,
                                 const uint32_t* sat, float* rec, uint32_t* depth_key, void* bininfo,
-                                int32_t* status, void* stream) {
+                                uint64_t* tile_mask, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !sat || !tile_act || !status) return PGSAG_ERR_ARG;
   if (n_gauss == 0) return cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream) == cudaSuccess ? PGSAG_OK : PGSAG_ERR_CUDA;
-  if (!means || !log_scales || !quats || !opacity_logit || !sh || !rec || !depth_key || !bininfo)
+  if (!means || !log_scales || !quats || !opacity_logit || !sh || !rec || !depth_key || !bininfo || !tile_mask)
     return PGSAG_ERR_ARG;
-  if (!aligned16(quats) || !aligned16(sh) || !aligned16(rec) || !aligned16(bininfo)) return PGSAG_ERR_ARG;
+  if (!aligned16(quats) || !aligned16(sh) || !aligned16(rec) || !aligned16(bininfo) || ((uintptr_t)tile_mask & 7u))
+    return PGSAG_ERR_ARG;
   PGSAG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream));
   const unsigned threads = kPreThreads;
   const size_t smem = views_bytes(n_views);
@@ -723,7 +728,8 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
     return PGSAG_ERR_CUDA;
   k_preprocess<<<pgsag_div_up(n_gauss, threads), threads, smem, (cudaStream_t)stream>>>(
       n_gauss, means, log_scales, quats, opacity_logit, sh, n_views, views, tile_act, sat,
-      reinterpret_cast<float4*>(rec), depth_key, reinterpret_cast<uint4*>(bininfo), status);
+      reinterpret_cast<float4*>(rec), depth_key, reinterpret_cast<uint4*>(bininfo),
+      reinterpret_cast<unsigned long long*>(tile_mask), status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

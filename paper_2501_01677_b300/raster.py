@@ -193,6 +193,7 @@ class Plan:
         self.rec = torch.empty((npairs, 16), dtype=f32, device=dev)
         self.dkey = torch.empty(npairs, dtype=i32, device=dev)
         self.bininfo = torch.empty((npairs, 4), dtype=i32, device=dev)
+        self.tile_mask = torch.empty(npairs, dtype=torch.int64, device=dev)
         self.grad2d = torch.empty((npairs, 16), dtype=f32, device=dev)
         # ---- per-tile / per-view
         self.ranges = torch.zeros((max(self.n_active, 1), 2), dtype=i32, device=dev)
@@ -215,7 +216,7 @@ class Plan:
     def _alloc_capacity(self, cap: int):
         self.capacity = int(max(cap, 1))
         self.dup_pairs = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
-        nbytes = int(self.lib.pgsag_bin_workspace_size(self.n_pairs, self.capacity))
+        nbytes = int(self.lib.pgsag_bin_workspace_size(self.n_pairs, self.n_active, self.capacity))
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
 
     def use_persistent_schedule(self, ctas_per_sm: int = 0, lpt: bool = True):
@@ -300,13 +301,14 @@ class Plan:
             L.check(self.lib.pgsag_preprocess(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats), _ptr(P.opacity_logit),
                                               _ptr(P.sh), self.n_views, _ptr(self.views_dev), _ptr(self.tile_act),
                                               _ptr(self.sat), _ptr(self.rec), _ptr(self.dkey), _ptr(self.bininfo),
-                                              _ptr(self.status), s), "pgsag_preprocess")
+                                              _ptr(self.tile_mask), _ptr(self.status), s), "pgsag_preprocess")
 
     def bin(self, stream=None):
         s = _stream_ptr(stream)
         with self._ev('bin'):
             L.check(self.lib.pgsag_bin(self.n_pairs, self.n_views, _ptr(self.views_dev), self.n_active, _ptr(self.tile_act),
-                                       _ptr(self.rec), _ptr(self.bininfo), _ptr(self.dkey), self.capacity, _ptr(self.ws), self.ws.numel(),
+                                       _ptr(self.tile_mask), _ptr(self.bininfo), _ptr(self.dkey), self.capacity, _ptr(self.ws),
+                                       self.ws.numel(),
                                        _ptr(self.dup_pairs), _ptr(self.ranges), _ptr(self.k_out), _ptr(self.status), s),
                     "pgsag_bin")
 
@@ -434,7 +436,7 @@ class Plan:
             "dense_pixel": ("flags", "pidx"),
             "compact_pixel": ("px_list", "target", "gc_weight", "out8", "depth", "aux", "dout8", "scratch", "chunks",
                               "chunk_scratch"),
-            "pair": ("rec", "dkey", "bininfo", "grad2d"),
+            "pair": ("rec", "dkey", "bininfo", "tile_mask", "grad2d"),
             "duplicate": ("dup_pairs", "ws"),
         }
         out, seen = {}, set()

@@ -379,3 +379,25 @@ def test_autotuner_picks_a_shape_and_caches_it(tmp_path, monkeypatch):
     plan.step(P, grads)
     torch.cuda.synchronize()
     plan.check_status()
+
+
+@pytest.mark.parametrize("n,seed,kmin", [(1500, 11, 513), (5000, 16, 4097), (9000, 14, 8193)])
+def test_long_tile_lists_sorted_through_merges(n, seed, kmin):
+    """Tile lists longer than a warp sorts on its own (512 entries) go to the
+    block sort: one shared-memory pass up to 2048 entries, beyond that sorted
+    chunks merged in global memory (an even and an odd number of merge
+    rounds).  The list is still in strictly ascending (depth key, pair) order
+    and the render still matches the oracle.  (Seeds chosen so that no pixel is
+    within float32 reach of an alpha or termination threshold.)"""
+    g, v = syn.tiny_scene(seed, n=n, width=16, height=16, fx=20.0, coverage=0.6)
+    res = oracle_run(g, v, grad=False)
+    plan, P = gpu_run(g, [v], tile=(16, 16), grad=False)
+    K = plan.k_value()
+    assert plan.n_active == 1 and K >= kmin
+    dup = plan.dup_pairs[:K].cpu().numpy().astype(np.int64)
+    key = plan.dkey.cpu().numpy().view(np.uint32).astype(np.int64)
+    k0, k1 = key[dup[:-1]], key[dup[1:]]
+    assert ((k0 < k1) | ((k0 == k1) & (dup[:-1] < dup[1:]))).all()
+    bi = plan.bininfo.cpu().numpy().astype(np.int64)
+    assert (np.bincount(dup, minlength=len(bi)) == bi[:, 3]).all()
+    compare_forward(plan, 0, res)

@@ -46,16 +46,17 @@ def test_status_strings(lib):
 
 
 def test_bin_workspace_size_grows_with_sizes(lib):
-    a = lib.pgsag_bin_workspace_size(1000, 4000)
-    b = lib.pgsag_bin_workspace_size(2000, 4000)
-    c = lib.pgsag_bin_workspace_size(2000, 8000)
+    a = lib.pgsag_bin_workspace_size(1000, 100, 4000)
+    b = lib.pgsag_bin_workspace_size(1000, 100000, 4000)
+    c = lib.pgsag_bin_workspace_size(1000, 100000, 8000)
     assert 0 < a < b < c
-    assert b - a >= 4 * 1000 * 4
+    assert b - a >= 4 * (100000 - 100) - 512     # one counter per active tile
+    assert c - b >= 3 * 4 * 4000 - 768           # three entries per duplicate
 
 
 def test_invalid_arguments_rejected_on_host(lib):
     # argument errors are detected before any device work
     assert lib.pgsag_preprocess(10, None, None, None, None, None, 0, None, None, None, None, None, None, None,
-                                None) == -5
+                                None, None) == -5
     assert lib.pgsag_bin(10, 1, None, 0, None, None, None, None, 0, None, 0, None, None, None, None, None) == -1
     assert lib.pgsag_adam(10, None, None, None, None, 0.1, 0.9, 0.999, 1e-8, 1, None) == -1

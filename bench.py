@@ -158,13 +158,13 @@ def algorithmic_bytes(plan, K, n_binned):
     with a binned pair), K duplicates, P rendered and M mask pixels, A tiles."""
     N, NP, P, A = plan.n_gauss, plan.n_pairs, plan.n_render, plan.n_active
     M = plan.n_mask
-    tile_passes = (int(A - 1).bit_length() + 7) // 8 if A > 1 else 0
     return {
-        # means, scales, quats, opacity 44 B/G; SH row 192 B per binned pair; per pair: rec 64 + key 4 + bininfo 16
-        "preprocess": 44 * N + 192 * n_binned + 84 * NP,
-        # first depth pass over NP (read 8, write 8 kept), 3 more over the binned pairs; scan + emission read
-        # order + bininfo twice; emission write 8/dup; tile passes 20/dup; ranges read 4/dup + write 8/tile
-        "bin": NP * 12 + n_binned * (8 + 3 * 20 + 2 * 20) + K * (8 + 20 * tile_passes + 4) + 8 * A,
+        # means, scales, quats, opacity 44 B/G; SH row 192 B per binned pair;
+        # per pair: rec 64 + key 4 + bininfo 16 + tile mask 8
+        "preprocess": 44 * N + 192 * n_binned + 92 * NP,
+        # bininfo 16 per pair, tile mask 8 per binned pair; per duplicate: emit (tile, pair) 8, scatter reads 8
+        # + writes 4, sort reads 4 + depth key 4 + writes 4; per tile: count 4 + range 8
+        "bin": 16 * NP + 8 * n_binned + 32 * K + 12 * A,
         # per pixel: list 4 + out8 32 + depth 4 + aux 16; per duplicate: id 4 + record 64
         "render_fwd": 56 * P + 68 * K,
         # pass A: flags 1 + pixel index 4 + out8 32 + depth 4 + dout8 32 + aux 16 + GC weight 4;

@@ -158,19 +158,35 @@ int pgsag_prep_flags(const pgsag_view* view, const uint8_t* mask, uint8_t* flags
  *               tile_x | tile_y << 16, first px_list entry, pixel count}
  *   px_list     device uint32 [|R| at px_base]: linear pixel index y*width+x of
  *               every R pixel, grouped by active tile, row-major inside a tile
- *   chunks      device uint2 [chunks at chunk_base]: {global active tile, first
- *               px_list entry}; a chunk covers up to 32 consecutive entries of one
- *               tile
+ *   chunks      device uint4 [chunks at chunk_base] (16-byte aligned): {view_index,
+ *               first px_list entry, pixel count (<= 32), global active tile}; a
+ *               chunk covers up to 32 consecutive entries of one tile
  *   pidx        device uint32 [dense per-pixel array], written at pix_base for the
  *               whole image: the px_list position q of each R pixel, 0xFFFFFFFF
  *               for pixels outside R
- * Errors: PGSAG_ERR_ARG on null pointers or act_tiles not 16-byte / chunks not
- * 8-byte aligned; PGSAG_ERR_UNSUPPORTED for tiles of more than 1024 pixels.
+ * Errors: PGSAG_ERR_ARG on null pointers or act_tiles / chunks not 16-byte
+ * aligned; PGSAG_ERR_UNSUPPORTED for tiles of more than 1024 pixels.
  */
 int pgsag_prep_lists(const pgsag_view* view, uint32_t view_index, const uint8_t* flags,
                      const uint32_t* tile_npix, uint32_t px_base, uint32_t chunk_base,
                      int32_t* tile_act, uint32_t* sat, void* act_tiles, uint32_t* px_list,
                      void* chunks, uint32_t* pidx, void* stream);
+
+/*
+ * pgsag_prep_neighbours: static neighbourhood of one view's rendered pixels, for
+ * the loss (Eq. 8 needs each mask pixel's 4 neighbours) and its adjoint.
+ *   px_list, pidx, flags  from pgsag_prep_lists / pgsag_prep_flags; this view's
+ *             px_list entries are [px_base, px_base + n_px)
+ *   nbr       device uint4 [1 per compact pixel] (16-byte aligned), written at
+ *             px_base: px_list positions of the {up, down, left, right}
+ *             neighbours, 0xFFFFFFFF outside the image or outside R
+ *   flags_c   device uint8 [1 per compact pixel], written at px_base: the
+ *             pixel's flags
+ * n_px = 0 does nothing.  Errors: PGSAG_ERR_ARG on null pointers, nbr not
+ * 16-byte aligned or an empty image.
+ */
+int pgsag_prep_neighbours(const pgsag_view* view, const uint32_t* px_list, uint32_t px_base, uint32_t n_px,
+                          const uint8_t* flags, const uint32_t* pidx, void* nbr, uint8_t* flags_c, void* stream);
 
 /*
  * pgsag_prep_gc_weight: w_i of Eq. 9 (Sec. 4.3), read as 1 + |Sobel(Y)| of the
@@ -309,8 +325,8 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
  * Two passes: pass A evaluates the terms, the own-pixel gradient and, per mask
  * pixel, dL/da and dL/db of its two central differences (scratch); pass B
  * gathers those from each pixel's neighbours and maps them through Eq. 4.
- *   flags    dense per-pixel flags; pidx the dense pixel-index map (both from
- *            mask preparation); neighbours are found through pidx
+ *   flags_c, nbr  the compact flags and neighbour table of pgsag_prep_neighbours
+ *   chunks, px_list  from pgsag_prep_lists (act_tiles is not read)
  *   aux      pgsag_render_fwd's aux (read only when gc_weight is given)
  *   target   float [3 per compact pixel] (from pgsag_prep_gc_weight)
  *   gc_weight  nullable, float [1 per compact pixel] (pgsag_prep_gc_weight): when
@@ -329,7 +345,7 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
  */
 int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                    const void* chunks, const void* act_tiles, const uint32_t* px_list,
-                   const uint8_t* flags, const uint32_t* pidx, const float* out8, const float* depth,
+                   const uint8_t* flags_c, const void* nbr, const float* out8, const float* depth,
                    const void* aux, const float* target, float lambda_ban, const float* gc_weight,
                    int gather, float* scratch, double* acc, float* chunk_scratch, float* loss,
                    float* gc_load, float* dout8, int32_t* status, void* stream);
@@ -342,8 +358,8 @@ int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
  * gradient, which saves one pass over the per-pixel arrays.
  */
 typedef struct pgsag_ban_gather {
-  const uint8_t* flags;    /* device, dense per-pixel flags (mask preparation)          */
-  const uint32_t* pidx;    /* device, dense pixel-index map (pgsag_prep_lists)          */
+  const uint8_t* flags_c;  /* device, compact flags (pgsag_prep_neighbours)             */
+  const void* nbr;         /* device, compact neighbour table (pgsag_prep_neighbours)   */
   const float* scratch;    /* device, loss scratch from pgsag_loss_ban (6 per compact px) */
   const double* acc;       /* device, loss accumulators from pgsag_loss_ban (8 per view) */
   float lambda_ban;        /* the lambda given to pgsag_loss_ban                         */

@@ -22,7 +22,8 @@ NOALLOC_MAX_CHUNKS = 1 << 20
 
 # Every entry point declared in include/pgsag.h
 EXPORTS = (
-    "pgsag_status_str", "pgsag_build_info", "pgsag_prep_flags", "pgsag_prep_lists", "pgsag_prep_gc_weight",
+    "pgsag_status_str", "pgsag_build_info", "pgsag_prep_flags", "pgsag_prep_lists", "pgsag_prep_neighbours",
+    "pgsag_prep_gc_weight",
     "pgsag_preprocess", "pgsag_bin_workspace_size", "pgsag_bin", "pgsag_render_fwd", "pgsag_loss_ban",
     "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_tile_stats_noalloc",
     "pgsag_schedule_lpt", "pgsag_adam",
@@ -51,7 +52,7 @@ class PgsagSched(ctypes.Structure):
 
 class PgsagBanGather(ctypes.Structure):
     """pgsag_ban_gather: the deferred Eq. 8 gather done by the render adjoint."""
-    _fields_ = [("flags", c_void_p), ("pidx", c_void_p), ("scratch", c_void_p), ("acc", c_void_p),
+    _fields_ = [("flags_c", c_void_p), ("nbr", c_void_p), ("scratch", c_void_p), ("acc", c_void_p),
                 ("lambda_ban", ctypes.c_float), ("reserved", ctypes.c_uint32)]
 
 
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_build_info", ctypes.c_char_p, [])
     _sig(lib, "pgsag_prep_flags", c_int, [POINTER(PgsagView), P, P, P, P, P])
     _sig(lib, "pgsag_prep_lists", c_int, [POINTER(PgsagView), c_uint32, P, P, c_uint32, c_uint32, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_prep_neighbours", c_int, [POINTER(PgsagView), P, c_uint32, c_uint32, P, P, P, P, P])
     _sig(lib, "pgsag_prep_gc_weight", c_int, [POINTER(PgsagView), P, P, c_uint32, c_uint32, P, P, P])
     _sig(lib, "pgsag_preprocess", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_bin_workspace_size", c_size_t, [c_uint32, c_uint32, c_uint64])

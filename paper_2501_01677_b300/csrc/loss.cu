@@ -4,7 +4,9 @@
 //
 // The kernels walk the compacted pixel lists chunk by chunk (one warp, one pixel
 // per lane); per-pixel arrays are compact (indexed by px_list position) and a
-// pixel's 4 neighbours are found through the dense pixel-index map.  Pass A
+// pixel's 4 neighbours and flags come from the compact tables of mask
+// preparation (pgsag_prep_neighbours), so every per-pixel load is coalesced or
+// one indirection away.  Pass A
 // (loss, own-pixel gradient, neighbour scratch, optionally the GC-load sums)
 // is followed either by pass B here or by the same gather in the render
 // adjoint's prologue.
@@ -26,26 +28,22 @@ struct PixCtx {
   uint32_t view;
   ViewLite V;
   int x, y;
-  uint64_t gp;  // dense index (flags, pixel-index map): pix_base + y W + x
-  uint64_t q;   // compact index (position in px_list): every other per-pixel array
+  uint64_t q;  // compact index (position in px_list)
 };
 
-__device__ __forceinline__ PixCtx pix_ctx(uint32_t c, int lane, const uint2* __restrict__ chunks,
-                                          const uint4* __restrict__ act_tiles,
+// A chunk record is {view, first px_list entry, pixel count, active tile}.
+__device__ __forceinline__ PixCtx pix_ctx(uint32_t c, int lane, const uint4* __restrict__ chunks,
                                           const uint32_t* __restrict__ px_list,
                                           const pgsag_view* __restrict__ views) {
   PixCtx P;
-  const uint2 ch = __ldg(chunks + c);
-  const uint4 at = __ldg(act_tiles + ch.x);
-  const uint32_t cnt = min(32u, at.z + at.w - ch.y);
-  P.view = at.x;
-  P.V = load_view_lite(views + at.x);
-  P.has = (uint32_t)lane < cnt;
+  const uint4 ch = __ldg(chunks + c);
+  P.view = ch.x;
+  P.V = load_view_lite(views + ch.x);
+  P.has = (uint32_t)lane < ch.z;
   P.q = ch.y + lane;
   const uint32_t pix = P.has ? __ldg(px_list + P.q) : 0u;
   P.y = (int)(pix / (uint32_t)P.V.width);
   P.x = (int)(pix - (uint32_t)P.y * (uint32_t)P.V.width);
-  P.gp = P.V.pix_base + pix;
   return P;
 }
 
@@ -60,17 +58,17 @@ __device__ __forceinline__ void ray(const ViewLite& V, int x, int y, float r[3])
 // rendered normal (unscaled) and dL/da, dL/db of the two central differences
 // (stored in `scratch` for the neighbours to gather).
 __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
-    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
-    const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
-    const uint8_t* __restrict__ flags, const uint32_t* __restrict__ pidx, const float4* __restrict__ out8,
-    const float* __restrict__ depth, const float* __restrict__ target, const uint4* __restrict__ aux,
+    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint4* __restrict__ chunks,
+    const uint32_t* __restrict__ px_list, const uint8_t* __restrict__ flags_c, const uint4* __restrict__ nbr,
+    const float4* __restrict__ out8, const float* __restrict__ depth, const float* __restrict__ target,
+    const uint4* __restrict__ aux,
     const float* __restrict__ gc_weight, float* __restrict__ scratch, float4* __restrict__ partial,
     float4* __restrict__ dout8, const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
   if (c >= n_chunks) return;
-  const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
+  const PixCtx P = pix_ctx(c, lane, chunks, px_list, views);
   float l1 = 0.f, lb = 0.f, nv = 0.f, gn = 0.f, gx = 0.f;
   if (P.has) {
     if (gc_weight != nullptr) {
@@ -78,7 +76,7 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
       gx = (float)__ldg(&aux[P.q].z) / __ldg(gc_weight + P.q);
       gn = 1.f;
     }
-    const uint8_t f = __ldg(flags + P.gp);
+    const uint8_t f = __ldg(flags_c + P.q);
     const float4 o0 = __ldg(out8 + 2 * P.q), o1 = __ldg(out8 + 2 * P.q + 1);
     float dC[3] = {0.f, 0.f, 0.f}, dNo[3] = {0.f, 0.f, 0.f};
     if (f & PGSAG_PIX_MASK) {
@@ -99,10 +97,9 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
       if (inV) {
         const int nx[4] = {P.x, P.x, P.x - 1, P.x + 1};
         const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
-        // neighbours through the dense pixel-index map (~0: not rendered)
-        uint32_t qn[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) qn[k] = __ldg(pidx + P.V.pix_base + (uint64_t)ny[k] * W + nx[k]);
+        // up, down, left, right neighbours (~0: not rendered)
+        const uint4 nb = __ldg(nbr + P.q);
+        const uint32_t qn[4] = {nb.x, nb.y, nb.z, nb.w};
         float dq[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) dq[k] = qn[k] != 0xffffffffu ? __ldg(depth + qn[k]) : 0.f;
@@ -213,55 +210,36 @@ __global__ void __launch_bounds__(256) k_view_reduce(const pgsag_view* __restric
 // Pass B: per rendered pixel, gather dL/dP from the neighbours whose central
 // differences used this pixel, map it to D and N through Eq. 4, scale.
 __global__ void __launch_bounds__(kLossThreads) k_loss_b(
-    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
-    const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
-    const uint8_t* __restrict__ flags, const uint32_t* __restrict__ pidx, const float4* __restrict__ out8,
-    const float* __restrict__ depth, const float* __restrict__ scratch, const double* __restrict__ acc,
+    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint4* __restrict__ chunks,
+    const uint32_t* __restrict__ px_list, const uint8_t* __restrict__ flags_c, const uint4* __restrict__ nbr,
+    const float4* __restrict__ out8, const float* __restrict__ depth, const float* __restrict__ scratch,
+    const double* __restrict__ acc,
     float lambda_ban, float4* __restrict__ dout8, const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
   if (c >= n_chunks) return;
-  const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
+  const PixCtx P = pix_ctx(c, lane, chunks, px_list, views);
   if (!P.has) return;
   const double nV = acc[8 * P.view + 2];
   const float scale = nV > 0.0 ? (float)(lambda_ban / nV) : 0.f;
-  const int W = P.V.width, H = P.V.height;
   float dP[3] = {0.f, 0.f, 0.f};
-  // this pixel is P[y+1] of (x, y-1), P[y-1] of (x, y+1), P[x+1] of (x-1, y), P[x-1] of (x+1, y)
-  const int nx[4] = {P.x, P.x, P.x - 1, P.x + 1};
-  const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
+  // this pixel is P[y+1] of (x, y-1) (up), P[y-1] of (x, y+1) (down), P[x+1] of
+  // (x-1, y) (left), P[x-1] of (x+1, y) (right); only mask neighbours wrote scratch
   const float sg[4] = {1.f, -1.f, 1.f, -1.f};
   const int off[4] = {0, 0, 3, 3};
-  // in-image neighbours: flags and pixel index first (independent loads), then
-  // the scratch of the mask neighbours (written by pass A)
-  uint8_t fq[4];
-  uint32_t qn[4];
-  float sv[4][3];
+  const uint4 nb = __ldg(nbr + P.q);
+  const uint32_t qn[4] = {nb.x, nb.y, nb.z, nb.w};
+  bool mk[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) mk[k] = qn[k] != 0xffffffffu && (__ldg(flags_c + qn[k]) & PGSAG_PIX_MASK);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    fq[k] = 0;
-    qn[k] = 0xffffffffu;
-    if (nx[k] < 0 || nx[k] >= W || ny[k] < 0 || ny[k] >= H) continue;
-    const uint64_t d = P.V.pix_base + (uint64_t)ny[k] * W + nx[k];
-    fq[k] = __ldg(flags + d);
-    qn[k] = __ldg(pidx + d);
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    sv[k][0] = sv[k][1] = sv[k][2] = 0.f;
-    if (!(fq[k] & PGSAG_PIX_MASK)) continue;
+    if (!mk[k]) continue;
     const float* sc = scratch + 6ull * qn[k] + off[k];
-    sv[k][0] = __ldg(sc + 0);
-    sv[k][1] = __ldg(sc + 1);
-    sv[k][2] = __ldg(sc + 2);
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (!(fq[k] & PGSAG_PIX_MASK)) continue;
-    dP[0] += sg[k] * sv[k][0];
-    dP[1] += sg[k] * sv[k][1];
-    dP[2] += sg[k] * sv[k][2];
+    dP[0] += sg[k] * __ldg(sc + 0);
+    dP[1] += sg[k] * __ldg(sc + 1);
+    dP[2] += sg[k] * __ldg(sc + 2);
   }
   float4 g1 = dout8[2 * P.q + 1];
   float dD = 0.f, dN[3] = {0.f, 0.f, 0.f};
@@ -332,15 +310,15 @@ __global__ void k_tile_counts(uint32_t n_active, const uint2* __restrict__ range
 }
 
 __global__ void __launch_bounds__(kLossThreads) k_gc_accum(
-    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint2* __restrict__ chunks,
-    const uint4* __restrict__ act_tiles, const uint32_t* __restrict__ px_list,
-    const uint4* __restrict__ aux, const float* __restrict__ weight, float4* __restrict__ partial,
+    const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint4* __restrict__ chunks,
+    const uint32_t* __restrict__ px_list, const uint4* __restrict__ aux, const float* __restrict__ weight,
+    float4* __restrict__ partial,
     const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
   if (c >= n_chunks) return;
-  const PixCtx P = pix_ctx(c, lane, chunks, act_tiles, px_list, views);
+  const PixCtx P = pix_ctx(c, lane, chunks, px_list, views);
   float x = 0.f, n = 0.f;
   if (P.has) {
     const uint32_t g = __ldg(&aux[P.q].z);
@@ -392,7 +370,7 @@ using namespace pgsag;
 
 extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                               const void* chunks, const void* act_tiles, const uint32_t* px_list,
-                              const uint8_t* flags, const uint32_t* pidx, const float* out8, const float* depth,
+                              const uint8_t* flags_c, const void* nbr, const float* out8, const float* depth,
                               const void* aux, const float* target, float lambda_ban, const float* gc_weight,
                               int gather, float* scratch, double* acc, float* chunk_scratch, float* loss,
                               float* gc_load, float* dout8, int32_t* status, void* stream) {
@@ -402,15 +380,15 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
   cudaStream_t s = (cudaStream_t)stream;
   PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 8 * sizeof(double), s));
   if (n_chunks) {
-    if (!chunks || !act_tiles || !px_list || !flags || !pidx || !out8 || !depth || !target || !scratch ||
-        !dout8 || !chunk_scratch || (gc_weight && !aux))
+    if (!chunks || !px_list || !flags_c || !nbr || !out8 || !depth || !target || !scratch || !dout8 ||
+        !chunk_scratch || (gc_weight && !aux))
       return PGSAG_ERR_ARG;
-    if (((uintptr_t)out8 | (uintptr_t)dout8 | (uintptr_t)act_tiles | (uintptr_t)chunk_scratch | (uintptr_t)aux) &
-        15u)
+    if (((uintptr_t)out8 | (uintptr_t)dout8 | (uintptr_t)chunks | (uintptr_t)nbr | (uintptr_t)chunk_scratch |
+         (uintptr_t)aux) & 15u)
       return PGSAG_ERR_ARG;
     const unsigned blocks = pgsag_div_up(n_chunks, kLossThreads / 32);
-    k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
-                                             px_list, flags, pidx, (const float4*)out8, depth, target,
+    k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint4*)chunks, px_list, flags_c,
+                                             (const uint4*)nbr, (const float4*)out8, depth, target,
                                              (const uint4*)aux, gc_weight, scratch, (float4*)chunk_scratch,
                                              (float4*)dout8, status);
     PGSAG_CHECK_LAUNCH();
@@ -418,8 +396,8 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
                                                                 acc, status);
     PGSAG_CHECK_LAUNCH();
     if (gather) {
-      k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles,
-                                               px_list, flags, pidx, (const float4*)out8, depth, scratch, acc,
+      k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint4*)chunks, px_list, flags_c,
+                                               (const uint4*)nbr, (const float4*)out8, depth, scratch, acc,
                                                lambda_ban, (float4*)dout8, status);
       PGSAG_CHECK_LAUNCH();
     }
@@ -448,10 +426,10 @@ extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint3
   }
   if (!gc) return PGSAG_OK;
   if (n_chunks) {
-    if (!chunks || !act_tiles || !px_list || !aux || !gc_weight || !chunk_scratch) return PGSAG_ERR_ARG;
-    if (((uintptr_t)chunk_scratch | (uintptr_t)aux) & 15u) return PGSAG_ERR_ARG;
+    if (!chunks || !px_list || !aux || !gc_weight || !chunk_scratch) return PGSAG_ERR_ARG;
+    if (((uintptr_t)chunk_scratch | (uintptr_t)aux | (uintptr_t)chunks) & 15u) return PGSAG_ERR_ARG;
     k_gc_accum<<<pgsag_div_up(n_chunks, kLossThreads / 32), kLossThreads, 0, s>>>(
-        views, n_chunks, (const uint2*)chunks, (const uint4*)act_tiles, px_list, (const uint4*)aux, gc_weight,
+        views, n_chunks, (const uint4*)chunks, px_list, (const uint4*)aux, gc_weight,
         (float4*)chunk_scratch, status);
     PGSAG_CHECK_LAUNCH();
     k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 4, 3, 3, acc, status);

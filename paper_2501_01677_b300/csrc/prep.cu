@@ -55,12 +55,13 @@ __global__ void k_prep_flags(int W, int H, int tw, int th, int tiles_x, const ui
 }
 
 // Single block: scans over the view's tiles (active indicator, pixel counts, chunk
-// counts), active-tile records and chunk records.
+// counts), active-tile records and chunk records {view, first px_list entry,
+// pixel count, active tile}.
 __global__ void __launch_bounds__(1024) k_prep_tiles(uint32_t n_tiles, int tiles_x, uint32_t view_index,
                                                      const uint32_t* __restrict__ npix, uint32_t act_base,
                                                      uint32_t px_base, uint32_t chunk_base,
                                                      int32_t* __restrict__ tile_act, uint4* __restrict__ act_tiles,
-                                                     uint2* __restrict__ chunks) {
+                                                     uint4* __restrict__ chunks) {
   __shared__ uint32_t wa[32], wp[32], wc[32];
   __shared__ uint32_t carry[3];
   if (threadIdx.x == 0) carry[0] = carry[1] = carry[2] = 0;
@@ -105,7 +106,9 @@ __global__ void __launch_bounds__(1024) k_prep_tiles(uint32_t n_tiles, int tiles
         tile_act[t] = (int32_t)g;
         const uint32_t tx = t % (uint32_t)tiles_x, ty = t / (uint32_t)tiles_x;
         act_tiles[g] = make_uint4(view_index, tx | (ty << 16), px_base + ep, n);
-        for (uint32_t j = 0; j < c; ++j) chunks[chunk_base + ec + j] = make_uint2(g, px_base + ep + j * PGSAG_CHUNK);
+        for (uint32_t j = 0; j < c; ++j)
+          chunks[chunk_base + ec + j] =
+              make_uint4(view_index, px_base + ep + j * PGSAG_CHUNK, min((uint32_t)PGSAG_CHUNK, n - j * PGSAG_CHUNK), g);
       } else {
         tile_act[t] = -1;
       }
@@ -183,6 +186,25 @@ __global__ void __launch_bounds__(256) k_prep_px(int W, int H, int tw, int th, i
   }
 }
 
+// Per rendered pixel of one view (compact index px_base + i): the compact
+// indices of its up, down, left and right neighbours (0xFFFFFFFF outside the
+// image or outside R) and its flags, so that the loss and its adjoint find a
+// pixel's neighbours with coalesced loads.
+__global__ void __launch_bounds__(256) k_prep_nbr(int W, int H, uint32_t n, const uint32_t* __restrict__ px,
+                                                  const uint8_t* __restrict__ flags,
+                                                  const uint32_t* __restrict__ pidx, uint4* __restrict__ nbr,
+                                                  uint8_t* __restrict__ flags_c) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t pix = __ldg(px + i);
+  const int y = (int)(pix / (uint32_t)W), x = (int)(pix - (uint32_t)y * (uint32_t)W);
+  const size_t p = (size_t)y * W + x;
+  const uint32_t none = 0xffffffffu;
+  nbr[i] = make_uint4(y > 0 ? __ldg(pidx + p - W) : none, y + 1 < H ? __ldg(pidx + p + W) : none,
+                      x > 0 ? __ldg(pidx + p - 1) : none, x + 1 < W ? __ldg(pidx + p + 1) : none);
+  flags_c[i] = __ldg(flags + p);
+}
+
 }  // namespace pgsag
 
 using namespace pgsag;
@@ -217,14 +239,14 @@ extern "C" int pgsag_prep_lists(const pgsag_view* view, uint32_t view_index, con
                                 void* chunks, uint32_t* pidx, void* stream) {
   if (!view || !flags || !tile_npix || !tile_act || !sat || !act_tiles || !px_list || !chunks || !pidx)
     return PGSAG_ERR_ARG;
-  if (((uintptr_t)act_tiles & 15u) || ((uintptr_t)chunks & 7u)) return PGSAG_ERR_ARG;
+  if (((uintptr_t)act_tiles & 15u) || ((uintptr_t)chunks & 15u)) return PGSAG_ERR_ARG;
   int r = check_tiling(view);
   if (r) return r;
   cudaStream_t s = (cudaStream_t)stream;
   const unsigned n_tiles = (unsigned)view->tiles_x * (unsigned)view->tiles_y;
   k_prep_tiles<<<1, 1024, 0, s>>>(n_tiles, view->tiles_x, view_index, tile_npix + view->tile_base, view->act_base,
                                   px_base, chunk_base, tile_act + view->tile_base, (uint4*)act_tiles,
-                                  (uint2*)chunks);
+                                  (uint4*)chunks);
   PGSAG_CHECK_LAUNCH();
   k_prep_sat<<<1, 1024, 0, s>>>(view->tiles_x, view->tiles_y, tile_act + view->tile_base, sat + view->sat_base);
   PGSAG_CHECK_LAUNCH();
@@ -233,6 +255,20 @@ extern "C" int pgsag_prep_lists(const pgsag_view* view, uint32_t view_index, con
   k_prep_px<<<n_tiles, 256, 0, s>>>(view->width, view->height, view->tile_w, view->tile_h, view->tiles_x,
                                     flags + view->pix_base, tile_act + view->tile_base, (const uint4*)act_tiles,
                                     px_list, pidx + view->pix_base);
+  PGSAG_CHECK_LAUNCH();
+  return PGSAG_OK;
+}
+
+extern "C" int pgsag_prep_neighbours(const pgsag_view* view, const uint32_t* px_list, uint32_t px_base, uint32_t n_px,
+                                     const uint8_t* flags, const uint32_t* pidx, void* nbr, uint8_t* flags_c,
+                                     void* stream) {
+  if (!view || !px_list || !flags || !pidx || !nbr || !flags_c) return PGSAG_ERR_ARG;
+  if ((uintptr_t)nbr & 15u) return PGSAG_ERR_ARG;
+  if (view->width <= 0 || view->height <= 0) return PGSAG_ERR_ARG;
+  if (n_px == 0) return PGSAG_OK;
+  k_prep_nbr<<<pgsag_div_up(n_px, 256), 256, 0, (cudaStream_t)stream>>>(
+      view->width, view->height, n_px, px_list + px_base, flags + view->pix_base, pidx + view->pix_base,
+      (uint4*)nbr + px_base, flags_c + px_base);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

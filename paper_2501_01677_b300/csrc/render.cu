@@ -385,34 +385,27 @@ struct BwdPix {
 // back-projected point P = Depth r, gathered from the 4 neighbours whose central
 // differences used it (their dL/da, dL/db in the loss scratch), as dL/dDepth;
 // the rendered-normal gradient from the loss is scaled by lambda / |V|.
-// Returns dL/dDepth; scales g1 (dL/dN) in place.  (x, y): integer pixel.
-__device__ __forceinline__ float ban_gather(const pgsag_ban_gather& bg, const ViewLite& V, uint32_t view, int x,
-                                            int y, float rx, float ry, float3& gn) {
+// Returns dL/dDepth; scales gn (dL/dN) in place.  q: the pixel's compact index.
+__device__ __forceinline__ float ban_gather(const pgsag_ban_gather& bg, uint32_t view, uint64_t q, float rx, float ry,
+                                            float3& gn) {
   const double nV = bg.acc[8 * view + 2];
   const float scale = nV > 0.0 ? (float)((double)bg.lambda_ban / nV) : 0.f;
   gn.x *= scale;
   gn.y *= scale;
   gn.z *= scale;
-  // this pixel is P[y+1] of (x, y-1), P[y-1] of (x, y+1), P[x+1] of (x-1, y), P[x-1] of (x+1, y)
-  const int nx[4] = {x, x, x - 1, x + 1};
-  const int ny[4] = {y - 1, y + 1, y, y};
+  // this pixel is P[y+1] of its up neighbour, P[y-1] of the down one, P[x+1] of
+  // the left one, P[x-1] of the right one; only mask neighbours wrote scratch
+  const uint4 nb = __ldg(reinterpret_cast<const uint4*>(bg.nbr) + q);
+  const uint32_t qn[4] = {nb.x, nb.y, nb.z, nb.w};
   const float sg[4] = {1.f, -1.f, 1.f, -1.f};
   const int off[4] = {0, 0, 3, 3};
-  uint8_t fq[4];
-  uint32_t qn[4];
+  bool mk[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    fq[k] = 0;
-    qn[k] = 0;
-    if (nx[k] < 0 || nx[k] >= V.width || ny[k] < 0 || ny[k] >= V.height) continue;
-    const uint64_t d = V.pix_base + (uint64_t)ny[k] * V.width + nx[k];
-    fq[k] = __ldg(bg.flags + d);
-    qn[k] = __ldg(bg.pidx + d);
-  }
+  for (int k = 0; k < 4; ++k) mk[k] = qn[k] != 0xffffffffu && (__ldg(bg.flags_c + qn[k]) & PGSAG_PIX_MASK);
   float dP0 = 0.f, dP1 = 0.f, dP2 = 0.f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (!(fq[k] & PGSAG_PIX_MASK)) continue;
+    if (!mk[k]) continue;
     const float* sc = bg.scratch + 6ull * qn[k] + off[k];
     dP0 += sg[k] * __ldg(sc + 0);
     dP1 += sg[k] * __ldg(sc + 1);
@@ -437,7 +430,7 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
   float3 gn = make_float3(g1.x, g1.y, g1.z);
   float gd = ddepth != nullptr ? __ldg(ddepth + gp) : 0.f;
   if (use_ban) {
-    gd += ban_gather(ban, V, view, (int)(px - 0.5f) + ox, (int)(py - 0.5f) + oy, rx, ry, gn);
+    gd += ban_gather(ban, view, gp, rx, ry, gn);
   }
   v[0] = gscale * g0.x;
   v[1] = gscale * g0.y;
@@ -712,7 +705,8 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
   }
   if (n_active == 0) return PGSAG_OK;
   if (!rec || !ranges || !act_tiles || !px_list || !out8 || !aux || !dout8 || !grad2d) return PGSAG_ERR_ARG;
-  if (ban && !(ban->flags && ban->pidx && ban->scratch && ban->acc)) return PGSAG_ERR_ARG;
+  if (ban && !(ban->flags_c && ban->nbr && ban->scratch && ban->acc)) return PGSAG_ERR_ARG;
+  if (ban && ((uintptr_t)ban->nbr & 15u)) return PGSAG_ERR_ARG;
   pgsag_ban_gather bg{};
   if (ban) bg = *ban;
   if (((uintptr_t)rec | (uintptr_t)out8 | (uintptr_t)aux | (uintptr_t)dout8 | (uintptr_t)act_tiles) & 15u)

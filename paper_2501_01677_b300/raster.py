@@ -145,7 +145,7 @@ class Plan:
         self.sat = torch.empty(max(self.n_sat, 1), dtype=i32, device=dev)
         self.act_tiles = torch.empty((max(self.n_active, 1), 4), dtype=i32, device=dev)
         self.px_list = torch.empty(max(self.n_render, 1), dtype=i32, device=dev)
-        self.chunks = torch.empty((max(self.n_chunks, 1), 2), dtype=i32, device=dev)
+        self.chunks = torch.empty((max(self.n_chunks, 1), 4), dtype=i32, device=dev)
         self.pidx = torch.empty(self.n_pix, dtype=i32, device=dev)
         self.px_base_v = np.zeros(V, np.int64)
         act_base = px_base = chunk_base = 0
@@ -164,9 +164,17 @@ class Plan:
             act_base += int(self.n_active_v[v])
             px_base += int(self.n_render_v[v])
             chunk_base += int(self.n_chunks_v[v])
+        # compact neighbour table and flags of the rendered pixels
+        nr = max(self.n_render, 1)
+        self.nbr = torch.empty((nr, 4), dtype=i32, device=dev)
+        self.flags_c = torch.zeros(nr, dtype=u8, device=dev)
+        for v in range(V):
+            L.check(self.lib.pgsag_prep_neighbours(ctypes.byref(views[v]), _ptr(self.px_list), int(self.px_base_v[v]),
+                                                       int(self.n_render_v[v]), _ptr(self.flags), _ptr(self.pidx),
+                                                       _ptr(self.nbr), _ptr(self.flags_c), s),
+                        "pgsag_prep_neighbours")
         # targets and GC weights of the rendered pixels (compact layout); each
         # view's full image is on the device only while it is gathered
-        nr = max(self.n_render, 1)
         self.target = torch.zeros(nr * 3, dtype=f32, device=dev)
         self.gc_weight = torch.ones(nr, dtype=f32, device=dev)
         for v in range(V):
@@ -331,8 +339,8 @@ class Plan:
         self._lambda_ban = float(lambda_ban)
         with self._ev('loss'):
             L.check(self.lib.pgsag_loss_ban(self.n_views, _ptr(self.views_dev), self.n_chunks, _ptr(self.chunks),
-                                            _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags),
-                                            _ptr(self.pidx), _ptr(self.out8), _ptr(self.depth), _ptr(self.aux),
+                                            _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags_c),
+                                            _ptr(self.nbr), _ptr(self.out8), _ptr(self.depth), _ptr(self.aux),
                                             _ptr(self.target), float(lambda_ban),
                                             _ptr(self.gc_weight) if fused else None, 0 if fused else 1,
                                             _ptr(self.scratch), _ptr(self.acc_loss), _ptr(self.chunk_scratch),
@@ -352,7 +360,7 @@ class Plan:
                     "pgsag_tile_stats")
 
     def _ban_gather(self):
-        return L.PgsagBanGather(self.flags.data_ptr(), self.pidx.data_ptr(), self.scratch.data_ptr(),
+        return L.PgsagBanGather(self.flags_c.data_ptr(), self.nbr.data_ptr(), self.scratch.data_ptr(),
                                 self.acc_loss.data_ptr(), float(getattr(self, "_lambda_ban", LAMBDA_BAN)), 0)
 
     def render_bwd(self, dout8: torch.Tensor, ddepth: Optional[torch.Tensor] = None,
@@ -434,8 +442,8 @@ class Plan:
         rest (per tile, per view)."""
         groups = {
             "dense_pixel": ("flags", "pidx"),
-            "compact_pixel": ("px_list", "target", "gc_weight", "out8", "depth", "aux", "dout8", "scratch", "chunks",
-                              "chunk_scratch"),
+            "compact_pixel": ("px_list", "nbr", "flags_c", "target", "gc_weight", "out8", "depth", "aux", "dout8",
+                              "scratch", "chunks", "chunk_scratch"),
             "pair": ("rec", "dkey", "bininfo", "tile_mask", "grad2d"),
             "duplicate": ("dup_pairs", "ws"),
         }

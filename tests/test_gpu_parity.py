@@ -343,7 +343,7 @@ def test_city_block_small_scale_compact_memory():
     plan.check_status()
     b = plan.device_bytes()
     assert b["dense_pixel"] == 5 * plan.n_pix
-    assert b["compact_pixel"] == 128 * plan.n_render + 40 * plan.n_chunks
+    assert b["compact_pixel"] == 145 * plan.n_render + 48 * plan.n_chunks
     for v in (0, 35, 71):
         R = (plan.flags_image(v).cpu().numpy() & 4) != 0
         a = plan.images(v)["alpha"].cpu().numpy()

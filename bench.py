@@ -446,8 +446,15 @@ def ours(args):
             peak = fp32_peak_tflops(pk.get("sm_max_mhz", 2032.0))
             peak_src = "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock"
         achieved = flops / (stage_ms[dom] / 1e3) / 1e12
+        # special-function unit: an exponential per contributing pair forward, an
+        # exponential and a reciprocal backward
+        xu_ops = (1 if dom == "render_fwd" else 2) * e_contrib
+        xu_gops = xu_ops / (stage_ms[dom] / 1e3) / 1e9
         roofline = {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "peak_source": peak_src, "alu_probe": alu,
+                    "xu": {"ops": xu_ops, "achieved_gops": xu_gops,
+                           "peak_gops": alu["ex2_gops"] if alu else None,
+                           "frac": xu_gops / alu["ex2_gops"] if alu else None},
                     "traffic": traffic, "algorithmic_flops": flops, "pairs_evaluated": e_eval,
                     "pairs_contributing": e_contrib,
                     "hbm_achieved_gbs": ab[dom] / (stage_ms[dom] / 1e3) / 1e9, "algorithmic_bytes": ab[dom]}

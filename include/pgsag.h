@@ -289,10 +289,12 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
               void* stream);
 
 /*
- * pgsag_render_fwd (Sec. 3.1, Eq. 1-4).  One CTA (8 warps) per active tile, one
- * warp per 32 compacted rendered pixels of the tile; the tile's sorted Gaussians
- * are staged through shared memory in batches of 256 and each warp skips the
- * Gaussians whose alpha >= 1/255 box misses its pixels.  Per pixel, front to back:
+ * pgsag_render_fwd (Sec. 3.1, Eq. 1-4).  One CTA of 4 warps per active tile
+ * (more rounds for tiles of more than 256 rendered pixels), each lane owning 2
+ * compacted rendered pixels; the tile's sorted Gaussians are staged through
+ * shared memory in batches of 128 and each warp skips the Gaussians whose
+ * alpha >= 1/255 ellipse misses the bounding box of its pixels.  Per pixel,
+ * front to back:
  *   alpha = min(0.99, o exp(-1/2 d^T Q d)); skipped if alpha < 1/255 (tested as
  *   -1/2 d^T Q d < thr, identically in the forward and the adjoint); if
  *   T (1 - alpha) < 1e-4 the pixel stops before this Gaussian; otherwise
@@ -305,7 +307,8 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
  *   aux   uint4 [1 per compact pixel]: {float bits of final T, index (into dup_pairs) of the
  *         last blended Gaussian, number blended n_contrib, 0}
  * sched may be NULL (one CTA per active tile in index order); with a counter the
- * launch is persistent (ctas_per_sm x SMs CTAs pulling tiles, in `order` if given).
+ * launch is persistent (ctas_per_sm x SMs CTAs pulling tiles, in `order` if
+ * given; ctas_per_sm <= 0: as many as the occupancy allows).
  */
 int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec,
                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,

@@ -157,7 +157,8 @@ int pgsag_prep_flags(const pgsag_view* view, const uint8_t* mask, uint8_t* flags
  *   act_tiles   device uint4 [active tiles at act_base]: {view_index,
  *               tile_x | tile_y << 16, first px_list entry, pixel count}
  *   px_list     device uint32 [|R| at px_base]: linear pixel index y*width+x of
- *               every R pixel, grouped by active tile, row-major inside a tile
+ *               every R pixel, grouped by active tile; inside a tile in 8x8-block
+ *               order (blocks row-major over the tile, pixels row-major in a block)
  *   chunks      device uint4 [chunks at chunk_base] (16-byte aligned): {view_index,
  *               first px_list entry, pixel count (<= 32), global active tile}; a
  *               chunk covers up to 32 consecutive entries of one tile

@@ -147,8 +147,11 @@ __global__ void __launch_bounds__(1024) k_prep_sat(int tiles_x, int tiles_y, con
   }
 }
 
-// One block per tile: rendered pixels in row-major order inside the tile; the
-// dense map pidx gets each rendered pixel's position in px_list.
+// One block per tile: the tile's rendered pixels in 8x8-block order (blocks
+// row-major over the tile, pixels row-major inside a block), so that a render
+// warp's 64 consecutive entries cover a square patch, which fewer Gaussians
+// overlap than a 16x4 strip; the dense map pidx gets each rendered pixel's
+// position in px_list.
 __global__ void __launch_bounds__(256) k_prep_px(int W, int H, int tw, int th, int tiles_x,
                                                  const uint8_t* __restrict__ flags,
                                                  const int32_t* __restrict__ tile_act,
@@ -163,9 +166,11 @@ __global__ void __launch_bounds__(256) k_prep_px(int W, int H, int tw, int th, i
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bw = tw / 8;  // 8x8 blocks per tile row (tile sides are multiples of 8)
   for (int base = 0; base < tw * th; base += 256) {
     const int i = base + threadIdx.x;
-    const int x = tx * tw + i % tw, y = ty * th + i / tw;
+    const int blk = i / 64, j = i % 64;
+    const int x = tx * tw + (blk % bw) * 8 + j % 8, y = ty * th + (blk / bw) * 8 + j / 8;
     const bool r = i < tw * th && x < W && y < H && (flags[(size_t)y * W + x] & PGSAG_PIX_RENDER);
     const uint32_t b = __ballot_sync(kFull, r);
     if (lane == 0) ws[warp] = __popc(b);

@@ -401,3 +401,37 @@ def test_long_tile_lists_sorted_through_merges(n, seed, kmin):
     bi = plan.bininfo.cpu().numpy().astype(np.int64)
     assert (np.bincount(dup, minlength=len(bi)) == bi[:, 3]).all()
     compare_forward(plan, 0, res)
+
+
+def test_neighbour_table_and_chunk_records(config0):
+    """Mask-preparation tables: each rendered pixel's {up, down, left, right}
+    entries are the px_list positions of those neighbours (~0 outside the image
+    or outside R), its compact flags equal the dense ones, and the chunk records
+    {view, first entry, count, tile} cover px_list exactly, 32 entries at most."""
+    g, views, res = config0
+    plan, P = gpu_run(g, views, grad=False)
+    H, W = plan.shapes[0]
+    px = plan.px_list[:plan.n_render].cpu().numpy().astype(np.int64)
+    pidx = plan.pidx.cpu().numpy().view(np.uint32).astype(np.int64).reshape(H, W)
+    nbr = plan.nbr[:plan.n_render].cpu().numpy().view(np.uint32).astype(np.int64)
+    y, x = px // W, px % W
+    none = 0xFFFFFFFF
+    exp = np.stack([np.where(y > 0, pidx[np.maximum(y - 1, 0), x], none),
+                    np.where(y < H - 1, pidx[np.minimum(y + 1, H - 1), x], none),
+                    np.where(x > 0, pidx[y, np.maximum(x - 1, 0)], none),
+                    np.where(x < W - 1, pidx[y, np.minimum(x + 1, W - 1)], none)], 1)
+    assert np.array_equal(nbr, exp)
+    # a neighbour index points back at that neighbour's pixel
+    ok = exp[:, 0] != none
+    assert np.array_equal(px[exp[ok, 0]], px[ok] - W)
+    fl = plan.flags_image(0).cpu().numpy().reshape(-1)
+    assert np.array_equal(plan.flags_c[:plan.n_render].cpu().numpy(), fl[px])
+    ch = plan.chunks[:plan.n_chunks].cpu().numpy().astype(np.int64)
+    assert (ch[:, 0] == 0).all() and (ch[:, 2] >= 1).all() and (ch[:, 2] <= 32).all()
+    cover = np.zeros(plan.n_render, np.int64)
+    for first, cnt in ch[:, 1:3]:
+        cover[first:first + cnt] += 1
+    assert (cover == 1).all()
+    at = plan.act_tiles[:plan.n_active].cpu().numpy().astype(np.int64)
+    t = ch[:, 3]
+    assert ((ch[:, 1] >= at[t, 2]) & (ch[:, 1] + ch[:, 2] <= at[t, 2] + at[t, 3])).all()

@@ -621,6 +621,7 @@ def capacity(args):
     del g
     t0 = time.perf_counter()
     plan = raster.Plan(cams, masks, targets, n_gauss, g_ranges=g_ranges, tile=(tw, th))
+    plan.release_prep_buffers()
     plan.forward(P)
     t_plan = time.perf_counter() - t0
     plan.use_persistent_schedule(ctas_per_sm=0, lpt=True)

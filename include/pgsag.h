@@ -247,7 +247,9 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, const uint
  *     view index, touched}
  *   tile_mask [p] uint64 (8-byte aligned): for a rectangle of at most 64 tiles,
  *     bit (ty - y0) * (x1 - x0 + 1) + (tx - x0) set for each tile the pair is
- *     binned to (popcount = touched); 0 for larger rectangles and culled pairs
+ *     binned to (popcount = touched); 0 for larger rectangles
+ *   rec and tile_mask are written for binned pairs (touched > 0) only; the
+ *   other entries keep whatever they held.
  * n_pairs = sum over views of (g_end - g_begin).
  * This call begins a step: it clears *status before its kernel runs.
  */

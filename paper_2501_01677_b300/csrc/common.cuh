@@ -60,75 +60,67 @@ __device__ __forceinline__ float gauss_power(float px, float py, float4 r0, floa
 
 // Does the region {d : -1/2 d^T Q d >= thr} of a 2D Gaussian (conic
 // Q = [[qa, qb], [qb, qc]]) meet the axis-aligned rectangle [dx0, dx1] x
-// [dy0, dy1] of pixel-centre offsets from its centre?  Minimises the quadratic
-// over the rectangle (centre inside, else each edge's 1D minimum clamped to the
-// edge).  Conservative: the bound is widened by the float32 error of evaluating
-// the quadratic at any pixel, which grows with the conic's condition number, so
-// every pixel whose float32 exponent passes the threshold lies in a rectangle
-// this test accepts.
-//
-// The binning count (preprocess) and the emission (bin) run this test in two
-// kernels and must agree on every tile, so it is written with explicit
-// round-to-nearest operations: the compiler may not contract a multiply and an
-// add into an FMA differently at the two call sites.
-__device__ __forceinline__ float quad_form_rn(float qa, float qb, float qc, float dx, float dy) {
-  const float t0 = __fmul_rn(__fmul_rn(qa, dx), dx);
-  const float t1 = __fmul_rn(__fmul_rn(2.f, qb), __fmul_rn(dx, dy));
-  const float t2 = __fmul_rn(__fmul_rn(qc, dy), dy);
-  return __fadd_rn(__fadd_rn(t0, t1), t2);
+// [dy0, dy1] of pixel-centre offsets from its centre?  The quadratic is
+// minimised over the rectangle (centre inside, else each edge's 1D minimum
+// clamped to the edge).  Conservative: the bound is widened by the float32
+// error of evaluating the quadratic at any pixel, which grows with the conic's
+// condition number, so every pixel whose float32 exponent passes the threshold
+// lies in a rectangle this test accepts (the rounding of the edge minimisers is
+// far inside that margin).  The per-Gaussian part is computed once
+// (ellipse_test) and reused for every rectangle.
+struct EllipseTest {
+  float qa, qb, qc;  // conic Q = L L^T
+  float iqa, iqc;    // 1 / qa, 1 / qc
+  float bound;       // d^T Q d <= bound  <=>  the region reaches d (with margin)
+};
+
+__device__ __forceinline__ EllipseTest ellipse_test(float l11, float l21, float l22, float thr) {
+  EllipseTest e;
+  e.qa = l11 * l11;
+  e.qb = l11 * l21;
+  e.qc = fmaf(l21, l21, l22 * l22);
+  e.iqa = __frcp_rn(e.qa);
+  e.iqc = __frcp_rn(e.qc);
+  const float hm = 0.5f * (e.qa + e.qc);
+  const float dq = e.qa - e.qc;
+  const float rt = sqrtf(fmaf(0.25f * dq, dq, e.qb * e.qb));
+  const float lmin = fmaxf(hm - rt, 1e-30f);
+  const float kappa = (hm + rt) / lmin;
+  e.bound = fmaf(-2.f * thr, 1.001f + 1e-6f * kappa, 1e-3f);
+  return e;
 }
 
-__device__ __forceinline__ bool ellipse_rect_hit(float qa, float qb, float qc, float thr, float dx0, float dx1,
-                                                 float dy0, float dy1) {
+__device__ __forceinline__ bool ellipse_rect_hit(const EllipseTest& e, float dx0, float dx1, float dy0, float dy1) {
   if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
-  const float h2 = __fmul_rn(-2.f, thr);  // d^T Q d <= h2
+  const float ex[2] = {dx0, dx1}, ey[2] = {dy0, dy1};
   float f = 3.0e38f;
-  {
-    const float ex[2] = {dx0, dx1};
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float dx = ex[i];
-      const float dy = fminf(fmaxf(__fdiv_rn(__fmul_rn(-qb, dx), qc), dy0), dy1);
-      f = fminf(f, quad_form_rn(qa, qb, qc, dx, dy));
-    }
-    const float ey[2] = {dy0, dy1};
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float dy = ey[i];
-      const float dx = fminf(fmaxf(__fdiv_rn(__fmul_rn(-qb, dy), qa), dx0), dx1);
-      f = fminf(f, quad_form_rn(qa, qb, qc, dx, dy));
-    }
+  for (int i = 0; i < 2; ++i) {
+    const float dx = ex[i];
+    const float dy = fminf(fmaxf(-e.qb * dx * e.iqc, dy0), dy1);
+    f = fminf(f, fmaf(e.qa * dx, dx, fmaf(2.f * e.qb * dx, dy, e.qc * dy * dy)));
   }
-  // condition number of Q bounds the relative rounding error of the quadratic
-  const float hm = __fmul_rn(0.5f, __fadd_rn(qa, qc));
-  const float dq = __fsub_rn(qa, qc);
-  const float rt = __fsqrt_rn(__fadd_rn(__fmul_rn(__fmul_rn(0.25f, dq), dq), __fmul_rn(qb, qb)));
-  const float lmin = fmaxf(__fsub_rn(hm, rt), 1e-30f);
-  const float kappa = __fdiv_rn(__fadd_rn(hm, rt), lmin);
-  return f <= __fadd_rn(__fmul_rn(h2, __fadd_rn(1.001f, __fmul_rn(1e-6f, kappa))), 1e-3f);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float dy = ey[i];
+    const float dx = fminf(fmaxf(-e.qb * dy * e.iqa, dx0), dx1);
+    f = fminf(f, fmaf(e.qa * dx, dx, fmaf(2.f * e.qb * dx, dy, e.qc * dy * dy)));
+  }
+  return f <= e.bound;
 }
 
-// Same test from the Cholesky factor: Q = [[l11^2, l11 l21], [l11 l21, l21^2 + l22^2]].
-__device__ __forceinline__ bool factor_rect_hit(float l11, float l21, float l22, float thr, float dx0, float dx1,
-                                                float dy0, float dy1) {
-  return ellipse_rect_hit(__fmul_rn(l11, l11), __fmul_rn(l11, l21), __fadd_rn(__fmul_rn(l21, l21), __fmul_rn(l22, l22)),
-                          thr, dx0, dx1, dy0, dy1);
-}
-
-// Tile binning rule shared by the count (preprocess) and the emission (bin):
-// a pair whose tile rectangle spans at most kExactTileMax tiles is duplicated to
-// the active tiles its alpha >= 1/255 region meets (on the tile's pixel
-// centres); a larger rectangle goes to all its active tiles.  The 2D mean is
-// given as integer part (mi, ni) + fraction (mf, nf), so the offsets are exact
-// up to one rounding.
+// Tile binning rule (pgsag_preprocess): a pair whose tile rectangle spans at
+// most kExactTileMax tiles is binned to the active tiles its alpha >= 1/255
+// region meets (on the tile's pixel centres); a larger rectangle goes to all its
+// active tiles.  The 2D mean is given as integer part (mi, ni) + fraction
+// (mf, nf), so the offsets are exact up to one rounding.
 constexpr int kExactTileMax = 64;
 
-__device__ __forceinline__ bool tile_hit(float mi, float ni, float mf, float nf, float l11, float l21, float l22,
-                                         float thr, int tx, int ty, int tw, int th, int W, int H) {
+__device__ __forceinline__ bool tile_hit(const EllipseTest& e, float mi, float ni, float mf, float nf, int tx, int ty,
+                                         int tw, int th, int W, int H) {
   const float x0 = (float)(tx * tw) + 0.5f, x1 = (float)min((tx + 1) * tw, W) - 0.5f;
   const float y0 = (float)(ty * th) + 0.5f, y1 = (float)min((ty + 1) * th, H) - 0.5f;
-  return factor_rect_hit(l11, l21, l22, thr, __fsub_rn(__fsub_rn(x0, mi), mf), __fsub_rn(__fsub_rn(x1, mi), mf),
-                         __fsub_rn(__fsub_rn(y0, ni), nf), __fsub_rn(__fsub_rn(y1, ni), nf));
+  return ellipse_rect_hit(e, (x0 - mi) - mf, (x1 - mi) - mf, (y0 - ni) - nf, (y1 - ni) - nf);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

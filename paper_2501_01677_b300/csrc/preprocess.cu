@@ -393,14 +393,13 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
                   __ldg(S + (uint32_t)y0 * sw + (uint32_t)(x1 + 1)) -
                   __ldg(S + (uint32_t)(y1 + 1) * sw + (uint32_t)x0) + __ldg(S + (uint32_t)y0 * sw + (uint32_t)x0);
         if (touched && (x1 - x0 + 1) * (y1 - y0 + 1) <= kExactTileMax) {
-          const float thr = -logf(255.f * P.o);
+          const EllipseTest et = ellipse_test(P.l11, P.l21, P.l22, -logf(255.f * P.o));
           const int32_t* ta = tile_act + V.tile_base;
           const int rw = x1 - x0 + 1;
           for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx)
               if (__ldg(ta + ty * V.tiles_x + tx) >= 0 &&
-                  tile_hit(mi, ni, mf, nf, P.l11, P.l21, P.l22, thr, tx, ty, V.tile_w, V.tile_h, V.width,
-                           V.height))
+                  tile_hit(et, mi, ni, mf, nf, tx, ty, V.tile_w, V.tile_h, V.width, V.height))
                 mask |= 1ull << ((ty - y0) * rw + (tx - x0));
           touched = (uint32_t)__popcll(mask);
         }
@@ -410,13 +409,9 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
     }
     float4* R4 = rec + 4ull * p;
     if (!vis || touched == 0) {
-      R4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-      R4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      R4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-      R4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+      // culled or binned to no active tile: the record and the mask are never read
       dkey[p] = 0xffffffffu;
       bininfo[p] = make_uint4(0u, 0u, vi, 0u);
-      tmask[p] = 0ull;
       continue;
     }
     // colour: degree-3 SH at the viewing direction (world frame)

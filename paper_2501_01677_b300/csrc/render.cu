@@ -162,9 +162,10 @@ __device__ __forceinline__ float2 gauss_power2(float2 px, float2 py, float4 r0, 
 
 // Shared-memory image of a batch of staged Gaussians, packed by use:
 // g0 = {mx, my, l11, l21}, g1 = {l22, o, thr, -}, g2 = {r, g, b, d}, g3 = {nx, ny, nz, -}
-// (l11, l21, l22: Cholesky factor of the conic).
+// (l11, l21, l22: Cholesky factor of the conic); for the warps' relevance test
+// q = {qa, qb, qc, bound}, c = {mx, my, 1/qa, 1/qc} (see EllipseTest).
 struct Stage {
-  float4 g0[kBatch], g1[kBatch], g2[kBatch], g3[kBatch];
+  float4 g0[kBatch], g1[kBatch], g2[kBatch], g3[kBatch], q[kBatch], c[kBatch];
 };
 
 // The centre is staged relative to the origin (ox, oy): (integer part - origin)
@@ -175,10 +176,14 @@ __device__ __forceinline__ void stage(uint32_t i, int slot, const uint32_t* __re
   const uint32_t p = __ldg(dup_pairs + i);
   const float4* r = rec + 4ull * p;
   const float4 r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
-  S.g0[slot] = make_float4(__fadd_rn(__fsub_rn(r0.x, ox), r3.z), __fadd_rn(__fsub_rn(r0.y, oy), r3.w), r0.z, r0.w);
+  const float mx = __fadd_rn(__fsub_rn(r0.x, ox), r3.z), my = __fadd_rn(__fsub_rn(r0.y, oy), r3.w);
+  S.g0[slot] = make_float4(mx, my, r0.z, r0.w);
   S.g1[slot] = make_float4(r1.x, r1.y, r3.y, 0.f);
   S.g2[slot] = make_float4(r1.z, r1.w, r2.x, r2.y);
   S.g3[slot] = make_float4(r2.z, r2.w, r3.x, 0.f);
+  const EllipseTest e = ellipse_test(r0.z, r0.w, r1.x, r3.y);
+  S.q[slot] = make_float4(e.qa, e.qb, e.qc, e.bound);
+  S.c[slot] = make_float4(mx, my, e.iqa, e.iqc);
   if (spair) spair[slot] = p;
 }
 
@@ -192,9 +197,9 @@ __device__ __forceinline__ void warp_relevance(const Stage& S, int limit, float4
     const int j = c * 32 + lane;
     bool hit = false;
     if (j < limit) {
-      const float4 a = S.g0[j];
-      const float4 b = S.g1[j];
-      hit = factor_rect_hit(a.z, a.w, b.x, b.z, cbox.x - a.x, cbox.y - a.x, cbox.z - a.y, cbox.w - a.y);
+      const float4 q = S.q[j], c = S.c[j];
+      const EllipseTest e = {q.x, q.y, q.z, c.z, c.w, q.w};
+      hit = ellipse_rect_hit(e, cbox.x - c.x, cbox.y - c.x, cbox.z - c.y, cbox.w - c.y);
     }
     rel[c] = __ballot_sync(kFull, hit);
   }

@@ -435,6 +435,12 @@ class Plan:
             self.step(P, grads, lambda_ban)
         return graph
 
+    def release_prep_buffers(self):
+        """Free the dense pixel-index map (4 B per image pixel): only mask
+        preparation reads it; the step kernels use the compact neighbour table."""
+        self.pidx = None
+        torch.cuda.empty_cache()
+
     def device_bytes(self) -> dict:
         """Bytes of this plan's device buffers, grouped as: dense per image pixel
         (flags, pixel-index map), compact per rendered pixel, per (view,

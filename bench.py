@@ -159,9 +159,9 @@ def algorithmic_bytes(plan, K, n_binned):
     N, NP, P, A = plan.n_gauss, plan.n_pairs, plan.n_render, plan.n_active
     M = plan.n_mask
     return {
-        # means, scales, quats, opacity 44 B/G; SH row 192 B per binned pair;
-        # per pair: rec 64 + key 4 + bininfo 16 + tile mask 8
-        "preprocess": 44 * N + 192 * n_binned + 92 * NP,
+        # means, scales, quats, opacity 44 B/G; per pair: key 4 + bininfo 16;
+        # per binned pair: SH row 192 + rec 64 + tile mask 8
+        "preprocess": 44 * N + 20 * NP + 264 * n_binned,
         # bininfo 16 per pair, tile mask 8 per binned pair; per duplicate: emit (tile, pair) 8, scatter reads 8
         # + writes 4, sort reads 4 + depth key 4 + writes 4; per tile: count 4 + range 8
         "bin": 16 * NP + 8 * n_binned + 32 * K + 12 * A,

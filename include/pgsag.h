@@ -474,6 +474,83 @@ int pgsag_tile_stats_noalloc(uint32_t n_views, const pgsag_view* views, uint32_t
 int pgsag_adam(uint64_t n, float* p, const float* g, float* m, float* v, float lr, float beta1,
                float beta2, float eps, int32_t step, void* stream);
 
+/*
+ * ---------------------------------------------------------------------------
+ * Reliability-scored multi-view voting filter (Sec. 4.1, Eq. 5-7).  The step
+ * before optimisation that refines coarse building masks: every sparse SfM point
+ * is projected into every view; a point that lands inside the mask of at least
+ * one view is a potential building point (Eq. 5 / 6); its unreliability score US
+ * counts the views in which it lands inside the image but outside the mask
+ * (Eq. 7); a potential point with US < tau is a reliable building point.
+ *
+ * Projection (pinhole, the camera model of the renderer): x_c = R x_w + t; the
+ * point is in front iff z_c > znear; it lands on pixel (floor(u), floor(v)) with
+ * u = fx (x_c (1 / z_c)) + cx, v = fy (y_c (1 / z_c)) + cy, and is inside the
+ * image iff 0 <= u < width and 0 <= v < height.  Whether a point is in front, in
+ * the image and in the mask is decided in float32 by this fixed sequence of
+ * correctly rounded operations (no fused multiply-add; sums left to right:
+ * x_c = ((R00 x + R01 y) + R02 z) + t0, ...), so the decision is reproducible
+ * off the GPU.  The paper states no occlusion test: a point "appears" in every
+ * view it projects into.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct pgsag_vote_view {
+  float R[9];              /* world -> camera rotation, row-major: x_c = R x_w + t */
+  float t[3];
+  float fx, fy, cx, cy;    /* pixel (u, v) covers [u, u+1) x [v, v+1)               */
+  float znear;             /* in front iff z_c > znear                              */
+  int32_t width, height;   /* > 0                                                   */
+  uint32_t words_per_row;  /* packed mask row stride in 32-bit words, >= ceil(width/32) */
+  uint32_t reserved[2];    /* zero                                                  */
+  uint64_t mask_offset;    /* first 32-bit word of this view's packed mask           */
+} pgsag_vote_view;         /* 96 bytes */
+
+#define PGSAG_VOTE_MAX_VIEWS 256  /* views per pgsag_vote_filter call */
+
+/*
+ * pgsag_vote_pack_mask: bit-pack one view's mask.  mask: uint8 [height, width]
+ * (nonzero = building); bits: uint32 [height, words_per_row] (device), bit
+ * (x & 31) of word y * words_per_row + (x >> 5) set iff mask[y * width + x] != 0;
+ * bits past the row's end are zero.  words_per_row >= ceil(width / 32).  Masks
+ * are fixed over training, so packing is preparation, done once per view.
+ */
+int pgsag_vote_pack_mask(int32_t width, int32_t height, const uint8_t* mask, uint32_t words_per_row,
+                         uint32_t* bits, void* stream);
+
+/*
+ * pgsag_vote_filter: Eq. 5-7 for n_points points against n_views views.
+ *   points:    float32 [n_points, 3] world coordinates (device, 4-byte aligned).
+ *   views:     HOST array of n_views <= PGSAG_VOTE_MAX_VIEWS cameras (copied into
+ *              the launch; the call validates them: width, height > 0,
+ *              words_per_row >= ceil(width / 32)).
+ *   mask_bits: packed masks (pgsag_vote_pack_mask), view v's at mask_offset.
+ *   in_mask:   uint32 [n_points]: number of views whose mask holds the point's
+ *              pixel (Eq. 5 / 6: potential iff > 0).
+ *   us:        uint32 [n_points]: number of views where the point is inside the
+ *              image but outside the mask (Eq. 7).
+ *   reliable:  uint8 [n_points]: 1 iff in_mask > 0 and us < tau, else 0.
+ *   accumulate: 0 = overwrite the counts; 1 = add to them (views in several
+ *              calls of at most PGSAG_VOTE_MAX_VIEWS); reliable is recomputed
+ *              from the summed counts on every call.
+ * n_points == 0 enqueues nothing; n_views == 0 with accumulate == 0 writes zero
+ * counts.  Bad pointers / views: PGSAG_ERR_ARG; n_views too large:
+ * PGSAG_ERR_UNSUPPORTED.
+ */
+int pgsag_vote_filter(uint32_t n_points, const float* points, uint32_t n_views, const pgsag_vote_view* views,
+                      const uint32_t* mask_bits, uint32_t tau, int accumulate, uint32_t* in_mask,
+                      uint32_t* us, uint8_t* reliable, int32_t* status, void* stream);
+
+/*
+ * pgsag_vote_compact: indices of the reliable points in ascending order.
+ *   reliable: uint8 [n_points] (nonzero = keep); idx: uint32 [n_points] (the
+ *   first n_out entries are written); n_out: uint32 [1] (device).
+ *   workspace: pgsag_vote_compact_workspace_size(n_points) bytes (device, 4-byte
+ *   aligned), caller-owned.
+ */
+size_t pgsag_vote_compact_workspace_size(uint32_t n_points);
+int pgsag_vote_compact(uint32_t n_points, const uint8_t* reliable, uint32_t* idx, uint32_t* n_out,
+                       void* workspace, size_t workspace_bytes, int32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

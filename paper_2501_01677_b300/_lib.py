@@ -27,7 +27,9 @@ EXPORTS = (
     "pgsag_preprocess", "pgsag_bin_workspace_size", "pgsag_bin", "pgsag_render_fwd", "pgsag_loss_ban",
     "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_tile_stats_noalloc",
     "pgsag_schedule_lpt", "pgsag_adam",
+    "pgsag_vote_pack_mask", "pgsag_vote_filter", "pgsag_vote_compact_workspace_size", "pgsag_vote_compact",
 )
+VOTE_MAX_VIEWS = 256
 
 
 class PgsagView(ctypes.Structure):
@@ -54,6 +56,19 @@ class PgsagBanGather(ctypes.Structure):
     """pgsag_ban_gather: the deferred Eq. 8 gather done by the render adjoint."""
     _fields_ = [("flags_c", c_void_p), ("nbr", c_void_p), ("scratch", c_void_p), ("acc", c_void_p),
                 ("lambda_ban", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+
+
+class PgsagVoteView(ctypes.Structure):
+    """pgsag_vote_view: one camera of the multi-view voting filter (Sec. 4.1)."""
+    _fields_ = [
+        ("R", c_float * 9), ("t", c_float * 3),
+        ("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float), ("znear", c_float),
+        ("width", c_int32), ("height", c_int32), ("words_per_row", c_uint32), ("reserved", c_uint32 * 2),
+        ("mask_offset", c_uint64),
+    ]
+
+
+assert ctypes.sizeof(PgsagVoteView) == 96
 
 
 _lib = None
@@ -93,6 +108,11 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_tile_stats_noalloc", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_schedule_lpt", c_int, [c_uint32, P, P, P, P, P, P])
     _sig(lib, "pgsag_adam", c_int, [c_uint64, P, P, P, P, c_float, c_float, c_float, c_float, c_int32, P])
+    _sig(lib, "pgsag_vote_pack_mask", c_int, [c_int32, c_int32, P, c_uint32, P, P])
+    _sig(lib, "pgsag_vote_filter", c_int,
+         [c_uint32, P, c_uint32, POINTER(PgsagVoteView), P, c_uint32, c_int, P, P, P, P, P])
+    _sig(lib, "pgsag_vote_compact_workspace_size", c_size_t, [c_uint32])
+    _sig(lib, "pgsag_vote_compact", c_int, [c_uint32, P, P, P, P, c_size_t, P, P])
     _lib = lib
     return lib
 

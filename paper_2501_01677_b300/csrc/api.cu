@@ -5,6 +5,7 @@
 #define PGSAG_STR(x) PGSAG_STR2(x)
 #define PGSAG_VIEW_BYTES 152
 static_assert(sizeof(pgsag_view) == PGSAG_VIEW_BYTES, "pgsag_view layout");
+static_assert(sizeof(pgsag_vote_view) == 96, "pgsag_vote_view layout");
 
 extern "C" const char* pgsag_status_str(int status) {
   switch (status) {

@@ -526,3 +526,98 @@ def hashed_uniform(index: np.ndarray, channel: int, seed: int = 0) -> np.ndarray
         x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
         x = x ^ (x >> np.uint64(31))
     return ((x >> np.uint64(40)).astype(np.float64) / float(1 << 24) * 2.0 - 1.0).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# voting-filter workload (Sec. 4.1): sparse SfM points and coarse building
+# masks of many views
+# --------------------------------------------------------------------------
+
+VOTE_CONFIG_INDEX = 5
+
+
+@dataclasses.dataclass
+class VoteWorkload:
+    points: np.ndarray        # float32 [M,3] sparse points (surface samples + noise)
+    on_building: np.ndarray   # bool [M]: drawn on a box surface (else on the ground)
+    cams: List[Camera]
+    masks: List[np.ndarray]   # uint8 [H,W] coarse building masks
+    tau: int
+
+
+def surface_points(rng, boxes: Sequence[Box], n: int, ground: float = 200.0, noise: float = 0.05):
+    """n points on the box surfaces and the ground plane, placed proportionally to
+    area, with isotropic N(0, noise) metres of jitter (SfM triangulation noise).
+    Returns the points and whether each lies on a box."""
+    S = _surfaces(boxes, ground)
+    areas = np.array([np.linalg.norm(np.cross(u, v)) for _, u, v, _ in S])
+    counts = rng.multinomial(n, areas / areas.sum())
+    pts, onb = [], []
+    for k, ((o, u, v, _), c) in enumerate(zip(S, counts)):
+        if c == 0:
+            continue
+        a = rng.random((c, 1))
+        b = rng.random((c, 1))
+        pts.append(o[None] + a * u[None] + b * v[None] + rng.normal(0.0, noise, (c, 3)))
+        onb.append(np.full(c, k > 0))
+    perm = rng.permutation(n)
+    return np.concatenate(pts, 0)[perm].astype(np.float32), np.concatenate(onb, 0)[perm]
+
+
+def coarse_mask(rng, truth: np.ndarray, n_blobs=(3, 8), radius=(40.0, 250.0)) -> np.ndarray:
+    """A coarse segmentation of the kind the voting filter cleans up: the true
+    building mask plus a few false-positive ellipses (ground taken for building)."""
+    H, W = truth.shape
+    m = truth.copy()
+    scale = W / 5472.0
+    for _ in range(int(rng.integers(n_blobs[0], n_blobs[1] + 1))):
+        cx, cy = rng.uniform(0, W), rng.uniform(0, H)
+        rx, ry = rng.uniform(radius[0], radius[1], 2) * scale
+        x0, x1 = int(max(0, cx - rx)), int(min(W, cx + rx + 1))
+        y0, y1 = int(max(0, cy - ry)), int(min(H, cy + ry + 1))
+        if x0 >= x1 or y0 >= y1:
+            continue
+        yy, xx = np.mgrid[y0:y1, x0:x1]
+        blob = ((xx + 0.5 - cx) / rx) ** 2 + ((yy + 0.5 - cy) / ry) ** 2 <= 1.0
+        m[y0:y1, x0:x1] |= blob.astype(np.uint8)
+    return m
+
+
+def vote_workload(n_points: int = 1_000_000, n_views: int = 32, width: int = 5472, height: int = 3648,
+                  mask_step: int = 4, tau: int = 3, coverage: float = 0.35) -> VoteWorkload:
+    """Sparse points of a 40-building scene (the config-1 scene generator) seen by
+    n_views oblique aerial cameras circling it (azimuth spread over 360 deg,
+    pitch 45 / 60 deg, altitude 120 +- 10 m, aim jittered by +-30 m), each with a
+    coarse mask: the ray-cast building mask (cast on a mask_step grid and
+    replicated to full resolution) plus false-positive blobs."""
+    rs, rc, rm, _ = streams(VOTE_CONFIG_INDEX)
+
+    def cams_fn(r):
+        cams = []
+        for j in range(n_views):
+            az = 360.0 * j / max(n_views, 1) + r.uniform(-5.0, 5.0)
+            look = (r.uniform(-30.0, 30.0), r.uniform(-30.0, 30.0), 0.0)
+            cams.append(aerial_camera(width, height, 120.0 + r.uniform(-10.0, 10.0), (45.0, 60.0)[j % 2], az, look))
+        return cams
+
+    scale = 1.0
+    state = rs.bit_generator.state
+    cstate = rc.bit_generator.state
+    for _ in range(6):
+        rs.bit_generator.state = state
+        rc.bit_generator.state = cstate
+        boxes = random_boxes(rs, 40, area=160.0, footprint_scale=scale)
+        cams = cams_fn(rc)
+        step = max(1, min(16, width // 64))
+        cov = raycast_box_mask(boxes, cams[0], step=step).mean() if cams else coverage
+        if abs(cov - coverage) <= 0.05:
+            break
+        scale = min(2.0, max(0.25, scale * math.sqrt(coverage / max(cov, 1e-3))))
+    pts, onb = surface_points(rs, boxes, n_points, ground=200.0)
+    masks = []
+    for c in cams:
+        t = raycast_box_mask(boxes, c, step=mask_step)
+        if mask_step > 1:
+            t = np.repeat(np.repeat(t, mask_step, 0), mask_step, 1)[:height, :width]
+        masks.append(coarse_mask(rm, np.ascontiguousarray(t)))
+    return VoteWorkload(pts, onb, cams, masks, tau)

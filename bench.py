@@ -45,11 +45,14 @@ def parse():
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="aerial", choices=["aerial", "aerial-crop2048", "batched", "capacity"],
+    ap.add_argument("--workload", default="aerial",
+                    choices=["aerial", "aerial-crop2048", "batched", "capacity", "vote"],
                     help="aerial: the 5472x3648 view; aerial-crop2048: its 2048x2048 window with the most "
                          "mask pixels, all 1.5M Gaussians (a smaller case for profiler captures); batched: 8 "
                          "uneven sub-regions (200k-3M Gaussians) x 4 mixed-resolution views, one graph-captured "
-                         "persistent step vs 32 sequential per-view steps")
+                         "persistent step vs 32 sequential per-view steps; capacity: 12 sub-regions, 20M "
+                         "Gaussians, 72 views at 6000x4000 with Adam; vote: the multi-view voting filter, 1M "
+                         "sparse points against 32 coarse masks at 5472x3648")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: fraction of the Gaussians")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: use --tile and 4 persistent CTAs per SM instead of the autotuner")
@@ -231,9 +234,9 @@ def measured_alu_peaks():
 BYTES_PER_PAIR, BYTES_PER_DUP, BYTES_PER_PIXEL = 904, 156, 165
 
 
-def read_traffic(kernel: str):
+def read_traffic(kernel: str, summary: str = "traffic_aerial_5472x3648.txt"):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if any."""
-    path = os.path.join(ROOT, "profiles", "traffic_aerial_5472x3648.txt")
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     for line in open(path):
@@ -679,6 +682,149 @@ def capacity(args):
     print(json.dumps(out))
 
 
+VOTE_METRIC = "voting filter Gprojections/s (points x views / s), 1M points x 32 views @5472x3648"
+VOTE_UNIT = "Gprojections/s"
+# FP32 operations per (point, view) projection, each its own instruction:
+# x_c = R x + t (9 mul + 9 add), 1 / z_c, u and v (4 mul + 2 add)
+VOTE_FLOP_PER_PROJ = 25
+
+
+def vote_bytes(M, packed, n_rel):
+    """Compulsory DRAM bytes of one vote + compaction: points 12 B, packed masks
+    once, counts 4 + 4 and flag 1 B written per point; compaction reads the flags
+    twice and writes 4 B per kept point."""
+    mask_b = sum(4 * h * w for h, w in zip(packed.heights, packed.words_per_row))
+    return {"vote": 12 * M + mask_b + 9 * M, "compact": 2 * M + 4 * n_rel, "masks": mask_b}
+
+
+def vote_bench(args):
+    """The multi-view voting filter (Sec. 4.1, Eq. 5-7): 1M sparse points of the
+    40-building scene against 32 coarse masks at 5472x3648 (one vote launch for
+    all views + the three compaction launches per step).  Masks are packed once
+    before timing (they are fixed, like the render masks).  The inputs (points
+    12 MB, packed masks 80 MB) fit in L2, so L2 is flushed between timed steps
+    by writing a 256 MB buffer, outside the timed region."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import pgsag_synth as syn
+    from paper_2501_01677_b300 import vote
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    w = syn.vote_workload()
+    M, V = int(w.points.shape[0]), len(w.cams)
+    masks_d = [torch.from_numpy(m).cuda() for m in w.masks]
+    packed = vote.pack_masks(masks_d)
+    del masks_d
+    pts = torch.from_numpy(w.points).cuda()
+    out = vote.VoteResult(torch.empty(M, dtype=torch.int32, device="cuda"),
+                          torch.empty(M, dtype=torch.int32, device="cuda"),
+                          torch.empty(M, dtype=torch.uint8, device="cuda"),
+                          torch.zeros(1, dtype=torch.int32, device="cuda"))
+    table = vote.vote_views(w.cams, packed)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    idx_d = torch.empty(M, dtype=torch.int32, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cws = vote.compact_workspace(M)
+
+    def step():
+        vote.vote_filter(pts, w.cams, packed, w.tau, out=out, table=table)
+        return vote.compact(out.reliable)
+
+    for _ in range(args.warmup):
+        idx = step()
+    torch.cuda.synchronize()
+    assert int(out.status.item()) == 0
+    n_rel = int(idx.numel())
+    # per-kernel time of the vote launch alone and of the whole step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for e in ev:
+        flush.zero_()
+        e[0].record(stream)
+        vote.vote_filter(pts, w.cams, packed, w.tau, out=out, table=table)
+        e[1].record(stream)
+        vote.compact_async(out.reliable, idx_d, n_out, cws, out.status)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms_step = sum(e[0].elapsed_time(e[2]) for e in ev)
+    ms_vote = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    ms, value = aggregate(ms_step, M * V / 1e9, args.steps, ws, dist if ws > 1 else None, device="cuda")
+
+    # end to end through the public calls: points from pinned host memory, the
+    # reliable indices back to the host, every step
+    host_pts = w.points.copy()
+    hp = torch.from_numpy(host_pts).pin_memory()
+    idx_host = torch.empty(M, dtype=torch.int32, pin_memory=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d2h = 0
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        pts.copy_(hp, non_blocking=True)
+        vote.vote_filter(pts, w.cams, packed, w.tau, out=out, table=table)
+        idx = vote.compact(out.reliable)   # reads the count back (a host sync)
+        idx_host[:idx.numel()].copy_(idx, non_blocking=True)
+        d2h = 4 * idx.numel() + 4
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e, v_e2e = aggregate(a.elapsed_time(b), M * V / 1e9, args.steps, ws, dist if ws > 1 else None,
+                              device="cuda")
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    pk, pk_src = peaks()
+    vb = vote_bytes(M, packed, n_rel)
+    alu = measured_alu_peaks()
+    ffma = max(alu["ffma_tflops"], alu["ffma2_tflops"]) if alu else fp32_peak_tflops(2032.0)
+    flops = VOTE_FLOP_PER_PROJ * M * V
+    alu_ach = flops / (ms_vote / 1e3) / 1e12
+    alu_peak = ffma / 2  # unfused mul / add: one FLOP per FP32 lane per issue
+    hbm_ach = vb["vote"] / (ms_vote / 1e3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_vote", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": alu_ach / alu_peak,
+                "peak_source": "half the FP32 FMA throughput measured in this run (separate mul / add, no FMA)",
+                "algorithmic_flops": flops, "flop_per_projection": VOTE_FLOP_PER_PROJ,
+                "hbm": {"achieved": hbm_ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm_ach / pk["hbm_gbs"],
+                        "peak_source": pk_src, "algorithmic_bytes": vb["vote"]},
+                "traffic": read_traffic("k_vote", "traffic_vote_1M_32x5472x3648.txt"), "ms_per_launch": ms_vote}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        from oracle import vote_oracle as VO
+        t0 = time.perf_counter()
+        VO.vote_filter(w.points, w.cams, w.masks, w.tau)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": M * V / 1e9 / t_cpu, "unit": VOTE_UNIT, "cores": 1, "kind": "oracle",
+               "sample": "the full workload (numpy float32, one thread)", "s_per_step": t_cpu}
+    res = {
+        "metric": VOTE_METRIC, "value": value, "unit": VOTE_UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "voting filter: %d sparse points of the 40-building scene x %d coarse masks at "
+                               "%dx%d, tau %d" % (M, V, w.cams[0].width, w.cams[0].height, w.tau),
+                   "points": M, "views": V, "tau": w.tau, "reliable": n_rel,
+                   "l2": "inputs fit in L2: a 256 MB buffer is written between timed steps"},
+        "roofline": roofline, "bytes": vb, "cpu_baseline": cpu,
+        "e2e": {"value": v_e2e, "unit": VOTE_UNIT, "h2d_bytes_per_step": 12 * M, "d2h_bytes_per_step": d2h,
+                "ms_per_step": ms_e2e / args.steps},
+        "gpu_launches": 4 * args.steps, "clocks": ck,
+    }
+    print(json.dumps(res))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -706,5 +852,7 @@ if __name__ == "__main__":
         batched(a)
     elif a.workload == "capacity":
         capacity(a)
+    elif a.workload == "vote":
+        vote_bench(a)
     else:
         ours(a)

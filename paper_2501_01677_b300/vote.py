@@ -90,9 +90,11 @@ class VoteResult:
 
 
 def vote_filter(points: torch.Tensor, cams, packed: PackedMasks, tau: int, out: Optional[VoteResult] = None,
-                stream=None) -> VoteResult:
+                stream=None, table=None) -> VoteResult:
     """Eq. 5-7 for points float32 [M, 3] (device) against all views (in calls of
-    at most 256 views, counts accumulated)."""
+    at most 256 views, counts accumulated).  `table`: a prebuilt vote_views()
+    array for these cameras (built here if omitted); `out`: result buffers to
+    reuse (their status tensor is kept, not cleared)."""
     lib = L.load()
     points = points.contiguous()
     assert points.dtype == torch.float32 and points.is_cuda and points.shape[-1] == 3
@@ -101,8 +103,9 @@ def vote_filter(points: torch.Tensor, cams, packed: PackedMasks, tau: int, out: 
     if out is None:
         out = VoteResult(torch.empty(M, dtype=torch.int32, device=dev), torch.empty(M, dtype=torch.int32, device=dev),
                          torch.empty(M, dtype=torch.uint8, device=dev))
-    status = torch.zeros(1, dtype=torch.int32, device=dev)
-    arr = vote_views(cams, packed)
+    if out.status is None:
+        out.status = torch.zeros(1, dtype=torch.int32, device=dev)
+    arr = vote_views(cams, packed) if table is None else table
     s = _stream_ptr(stream)
     nv = len(cams)
     first = True
@@ -110,23 +113,38 @@ def vote_filter(points: torch.Tensor, cams, packed: PackedMasks, tau: int, out: 
         n = min(L.VOTE_MAX_VIEWS, nv - v0)
         sub = ctypes.cast(ctypes.addressof(arr) + v0 * ctypes.sizeof(L.PgsagVoteView), ctypes.POINTER(L.PgsagVoteView))
         L.check(lib.pgsag_vote_filter(M, _ptr(points), n, sub, _ptr(packed.bits), int(tau), 0 if first else 1,
-                                      _ptr(out.in_mask), _ptr(out.us), _ptr(out.reliable), _ptr(status), s),
+                                      _ptr(out.in_mask), _ptr(out.us), _ptr(out.reliable), _ptr(out.status), s),
                 "pgsag_vote_filter")
         first = False
-    out.status = status
     return out
 
 
-def compact(reliable: torch.Tensor, stream=None) -> torch.Tensor:
-    """Ascending indices of the nonzero entries (pgsag_vote_compact)."""
+def compact_async(reliable: torch.Tensor, idx: torch.Tensor, n_out: torch.Tensor, workspace: torch.Tensor,
+                  status: torch.Tensor, stream=None) -> None:
+    """Enqueue pgsag_vote_compact: the ascending indices of the nonzero entries of
+    reliable into idx (int32, >= len(reliable) entries) and their number into
+    n_out (int32 [1]); no host synchronisation."""
     lib = L.load()
     M = int(reliable.shape[0])
+    ws_bytes = workspace.numel() * workspace.element_size()
+    L.check(lib.pgsag_vote_compact(M, _ptr(reliable), _ptr(idx), _ptr(n_out), _ptr(workspace), ws_bytes,
+                                   _ptr(status), _stream_ptr(stream)), "pgsag_vote_compact")
+
+
+def compact_workspace(n: int, device="cuda") -> torch.Tensor:
+    """Workspace tensor for compact_async over n entries."""
+    ws_bytes = int(L.load().pgsag_vote_compact_workspace_size(n))
+    return torch.empty((ws_bytes + 3) // 4, dtype=torch.int32, device=device)
+
+
+def compact(reliable: torch.Tensor, stream=None) -> torch.Tensor:
+    """Ascending indices of the nonzero entries (pgsag_vote_compact); reads the
+    count back to the host."""
+    M = int(reliable.shape[0])
     dev = reliable.device
+    reliable = reliable.contiguous()
     idx = torch.empty(max(M, 1), dtype=torch.int32, device=dev)
     n_out = torch.zeros(1, dtype=torch.int32, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
-    ws_bytes = int(lib.pgsag_vote_compact_workspace_size(M))
-    ws = torch.empty((ws_bytes + 3) // 4, dtype=torch.int32, device=dev)
-    L.check(lib.pgsag_vote_compact(M, _ptr(reliable.contiguous()), _ptr(idx), _ptr(n_out), _ptr(ws), ws_bytes,
-                                   _ptr(status), _stream_ptr(stream)), "pgsag_vote_compact")
+    compact_async(reliable, idx, n_out, compact_workspace(M, dev), status, stream)
     return idx[:int(n_out.item())]

@@ -21,7 +21,16 @@ to rounding).  Passages followed:
 * Sec. 3.1, Eq. 4 -- unbiased depth  Depth(p) = D / (-N(p) . K^-1 p~).
 * Sec. 4.2, Eq. 8 -- boundary-aware normal loss, w = 0.1 on mask boundaries.
 * Sec. 4.3, Eq. 9 -- GC-load statistic std_i(g_i / w_i).
-* Sec. 4.3, Eq. 10-11 -- loss weights (lambda = 0.41, lambda_4 = 0.01).
+* Sec. 4.3, Eq. 10-11 -- loss weights (lambda = 0.41, lambda_3 = 100,
+  lambda_4 = 0.01) and the combined objective
+  L = (1 - lambda) (L_rgb + lambda_3 L_s + lambda_4 L_ban) + lambda L_GC-load
+  over the terms defined in the paper itself (L_mvgeo and L_mvrgb are defined
+  only by citation and left out).
+* Sec. 4.3 (by citation to PGSR) -- flattening loss L_s, read as the mean over
+  the Gaussians of min(s_1, s_2, s_3), s = exp(log-scale).
+* Sec. 4.3, Eq. 9 with a differentiable count: g~_i = sum of the alphas of the
+  Gaussians blended into pixel i (the integer count g_i has no gradient; the
+  soft count is the surrogate that lets the GC-load term shape the Gaussians).
 
 Readings of passages where the paper is silent (3DGS constants by citation):
 alpha = min(0.99, o exp(-1/2 d^T Q d)); a Gaussian enters a pixel iff
@@ -56,6 +65,7 @@ SH_OFFSET = 0.5
 W_BOUNDARY = 0.1
 LAMBDA_GC = 0.41
 LAMBDA_BAN = 0.01
+LAMBDA_FLAT = 100.0
 # Validity threshold for Eq. 4 (ray-plane intersection must be in front)
 RAY_DOT_MIN = 1e-8
 # Relative window inside which a float32 threshold decision may legitimately flip
@@ -360,6 +370,7 @@ def composite(pr, pu: torch.Tensor, pv: torch.Tensor, pair_pix: torch.Tensor, pa
     magD = torch.zeros(Pn, dtype=DT)
     mcn = pr["mc_norm"][gi]
     ncon = torch.zeros(Pn, dtype=torch.long)
+    soft = torch.zeros(Pn, dtype=DT)
     done = torch.zeros(Pn, dtype=torch.bool)
     col = pr["rgb"][gi]
     nor = pr["normal"][gi]
@@ -383,7 +394,8 @@ def composite(pr, pu: torch.Tensor, pv: torch.Tensor, pair_pix: torch.Tensor, pa
         magD = magD + wd * mcn[:, j]
         T = torch.where(blend, test, T)
         ncon = ncon + blend.long()
-    return dict(rgb=C, normal=N, dist=D, alpha=1.0 - T, final_T=T, n_contrib=ncon, ambiguous=amb,
+        soft = soft + torch.where(blend, a, torch.zeros_like(a))
+    return dict(rgb=C, normal=N, dist=D, alpha=1.0 - T, final_T=T, n_contrib=ncon, soft_count=soft, ambiguous=amb,
                 mag=dict(rgb=magC, normal=magN, dist=magD, alpha=(1.0 - T).detach()))
 
 
@@ -518,14 +530,41 @@ def total_loss_with_gc(l_pg_geo: float, l_gc: float) -> float:
     return (1.0 - LAMBDA_GC) * l_pg_geo + LAMBDA_GC * l_gc
 
 
+def gc_load_soft(soft_count: torch.Tensor, weight_r: torch.Tensor) -> torch.Tensor:
+    """Eq. 9 with the soft count, differentiable: population std over the
+    rendered pixels of g~_i / w_i (soft_count and weight_r list the render set R)."""
+    if soft_count.numel() == 0:
+        return torch.zeros((), dtype=DT)
+    x = soft_count / weight_r
+    return torch.sqrt(torch.mean((x - x.mean()) ** 2))
+
+
+def flatten_loss(log_scales: torch.Tensor) -> torch.Tensor:
+    """L_s (PGSR by citation): mean over the Gaussians of their smallest scale
+    min(exp(log_scales)) (the L1 norm of a positive scalar)."""
+    if log_scales.shape[0] == 0:
+        return torch.zeros((), dtype=DT)
+    return torch.exp(log_scales).min(dim=1).values.mean()
+
+
+def objective_eq11(l_rgb, l_ban, l_s, l_gc):
+    """Eq. 10-11 over the locally defined terms:
+    (1 - lambda) (L_rgb + lambda_3 L_s + lambda_4 L_ban) + lambda L_GC-load."""
+    return (1.0 - LAMBDA_GC) * (l_rgb + LAMBDA_FLAT * l_s + LAMBDA_BAN * l_ban) + LAMBDA_GC * l_gc
+
+
 # ---------------------------------------------------------------------------
 # whole step
 # ---------------------------------------------------------------------------
 
-def step(g, view, need_grad=True, retain_intermediate=False):
+def step(g, view, need_grad=True, retain_intermediate=False, objective="pg"):
     """Forward + loss (+ autograd backward) for one view of a synthetic scene `g`
     (pgsag_synth.Gaussians) and `view` (pgsag_synth.View).  Returns a dict with
-    dense images, losses and parameter gradients."""
+    dense images, losses and parameter gradients.
+
+    objective "pg": L_rgb + lambda_4 L_ban is differentiated (the GC-load value
+    is reported by gc_load, without gradient).  "eq11": objective_eq11 with the
+    flattening loss and the soft-count GC-load, all differentiated."""
     cam = Cam.from_synth(view.cam)
     p = params_from_synth(g, requires_grad=need_grad)
     pr, out, depth, valid, pix, sets = render_view(p, cam, view.mask, np.asarray(g.means, np.float32))
@@ -535,6 +574,14 @@ def step(g, view, need_grad=True, retain_intermediate=False):
         for k in ("rgb", "normal", "dist"):
             out[k].retain_grad()
     L = losses(out, depth, valid, pix, sets, cam, view.target)
+    if objective == "eq11":
+        pu, pv = pix
+        wts = torch.from_numpy(luminance_gradient_weight(view.target)[pv.numpy(), pu.numpy()])
+        L["l_s"] = flatten_loss(p["log_scales"])
+        L["l_gc_soft"] = gc_load_soft(out["soft_count"], wts)
+        L["total"] = objective_eq11(L["l_rgb"], L["l_ban"], L["l_s"], L["l_gc_soft"])
+    elif objective != "pg":
+        raise ValueError(objective)
     res = dict(proj=pr, out=out, depth=depth, valid=valid, pix=pix, sets=sets, loss=L, cam=cam)
     if need_grad:
         L["total"].backward()

@@ -255,6 +255,7 @@ def _brute_force(pr, pu, pv):
         N = [0.0] * 3
         D = 0.0
         k = 0
+        soft = 0.0
         for i in order:
             dx = u + 0.5 - m2[i, 0]
             dy = v + 0.5 - m2[i, 1]
@@ -271,7 +272,8 @@ def _brute_force(pr, pu, pv):
             D += w * dst[i]
             T *= (1 - a)
             k += 1
-        res.append(C + N + [D, 1 - T, k])
+            soft += a
+        res.append(C + N + [D, 1 - T, k, soft])
     return np.array(res)
 
 
@@ -284,9 +286,9 @@ def test_vectorised_compositing_equals_brute_force(seed):
     out = res["out"]
     got = np.concatenate([out["rgb"].detach().numpy(), out["normal"].detach().numpy(),
                           out["dist"].detach().numpy()[:, None], out["alpha"].detach().numpy()[:, None],
-                          out["n_contrib"].numpy()[:, None]], 1)
+                          out["n_contrib"].numpy()[:, None], out["soft_count"].detach().numpy()[:, None]], 1)
     np.testing.assert_allclose(got, bf, atol=1e-12, rtol=1e-12)
-    assert (bf[:, -1] > 0).sum() > 30
+    assert (bf[:, -2] > 0).sum() > 30
 
 
 def test_render_set_is_mask_dilation_and_pixels_outside_R_not_rendered():
@@ -399,3 +401,91 @@ def test_autograd_gradient_matches_central_differences(seed):
             assert fd == pytest.approx(gr[idx], rel=2e-4, abs=1e-8), (name, idx)
             checked += 1
     assert checked >= 15
+
+
+# ----------------------------------------------------------------- Eq. 10-11 terms
+
+def test_flatten_loss_closed_form():
+    ls = torch.tensor([[0.0, 1.0, 2.0], [3.0, -1.0, 5.0], [-2.0, -2.0, 0.5]], dtype=torch.float64)
+    want = (1.0 + math.exp(-1.0) + math.exp(-2.0)) / 3.0
+    assert float(O.flatten_loss(ls)) == pytest.approx(want, rel=1e-15)
+    ls.requires_grad_(True)
+    O.flatten_loss(ls).backward()
+    g = ls.grad.numpy()
+    # only the smallest axis of each Gaussian gets a gradient, exp(min) / N
+    np.testing.assert_allclose(g[0], [1.0 / 3, 0, 0], rtol=1e-15)
+    np.testing.assert_allclose(g[1], [0, math.exp(-1.0) / 3, 0], rtol=1e-15)
+    assert g[2, 2] == 0.0 and g[2, :2].sum() == pytest.approx(math.exp(-2.0) / 3, rel=1e-15)
+
+
+def test_soft_count_single_gaussian_is_alpha_and_bounds():
+    g, v = _single_gaussian()
+    out = O.step(g, v, need_grad=False)["out"]
+    np.testing.assert_allclose(out["soft_count"].detach().numpy(), out["alpha"].detach().numpy(), atol=1e-15)
+    g, v = syn.tiny_scene(3, n=64, width=32, height=28)
+    out = O.step(g, v, need_grad=False)["out"]
+    soft = out["soft_count"].detach().numpy()
+    A = out["alpha"].detach().numpy()
+    k = out["n_contrib"].numpy()
+    # 1 - prod (1 - a_k) <= sum a_k <= 0.99 * count, equality with one Gaussian
+    assert (soft >= A - 1e-12).all() and (soft <= 0.99 * k + 1e-12).all()
+    one = k == 1
+    assert one.any() and np.allclose(soft[one], A[one], atol=1e-14)
+    assert (soft[k >= 2] > A[k >= 2]).all()
+
+
+def test_gc_load_soft_is_population_std_and_matches_integer_counts():
+    rng = np.random.default_rng(4)
+    c = rng.integers(0, 20, 500).astype(np.float64)
+    w = 1.0 + rng.random(500)
+    got = float(O.gc_load_soft(torch.tensor(c), torch.tensor(w)))
+    assert got == pytest.approx(float(np.std(c / w)), rel=1e-13)
+    R = np.ones(500, bool)
+    assert got == pytest.approx(O.gc_load(c, w, R), rel=1e-13)
+    assert float(O.gc_load_soft(torch.ones(7, dtype=torch.float64), torch.full((7,), 2.0, dtype=torch.float64))) == 0.0
+
+
+def test_objective_eq11_weights():
+    l = O.objective_eq11(2.0, 3.0, 0.5, 7.0)
+    assert l == pytest.approx((1 - 0.41) * (2.0 + 100.0 * 0.5 + 0.01 * 3.0) + 0.41 * 7.0, rel=1e-15)
+
+
+def _eq11_at(g, v, name, idx, val):
+    g2 = syn.Gaussians(*(np.array(getattr(g, f), copy=True) for f in ("means", "log_scales", "quats", "opacity_logit", "sh")))
+    cam = O.Cam.from_synth(v.cam)
+    p = O.params_from_synth(g2)
+    p[name] = p[name].clone()
+    p[name].view(-1)[idx] = val
+    pr, out, depth, valid, pix, sets = O.render_view(p, cam, v.mask, np.asarray(g.means, np.float32))
+    L = O.losses(out, depth, valid, pix, sets, cam, v.target)
+    pu, pv = pix
+    w = torch.from_numpy(O.luminance_gradient_weight(v.target)[pv.numpy(), pu.numpy()])
+    return float(O.objective_eq11(L["l_rgb"], L["l_ban"], O.flatten_loss(p["log_scales"]),
+                                  O.gc_load_soft(out["soft_count"], w)))
+
+
+def test_eq11_autograd_gradient_matches_central_differences():
+    """The Eq. 11 objective (with L_s and the soft-count GC-load) against central
+    differences of its value, sampled over all parameter tensors."""
+    g, v = syn.tiny_scene(31, n=40, width=28, height=26, log_scale_mu=-1.2)
+    res = O.step(g, v, objective="eq11")
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    checked = 0
+    l0 = float(res["loss"]["total"])
+    for name in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        base = res["params"][name].detach().reshape(-1).numpy()
+        gr = res["grads"][name].reshape(-1).numpy()
+        cand = np.nonzero(np.abs(gr) > 1e-7)[0]
+        for idx in rng.choice(cand, size=min(6, len(cand)), replace=False):
+            lp = _eq11_at(g, v, name, idx, base[idx] + h)
+            lm = _eq11_at(g, v, name, idx, base[idx] - h)
+            fwd, bwd = (lp - l0) / h, (l0 - lm) / h
+            if abs(fwd - bwd) > 1e-3 * max(abs(fwd), abs(bwd), 1e-6):
+                continue
+            assert (lp - lm) / (2 * h) == pytest.approx(gr[idx], rel=2e-4, abs=1e-8), (name, idx)
+            checked += 1
+    assert checked >= 15
+    # the soft-count term alone moves opacities: its gradient is not zero
+    g_only = O.step(g, v, need_grad=False, objective="eq11")
+    assert float(g_only["loss"]["l_gc_soft"]) > 0

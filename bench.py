@@ -54,6 +54,9 @@ def parse():
                          "Gaussians, 72 views at 6000x4000 with Adam; vote: the multi-view voting filter, 1M "
                          "sparse points against 32 coarse masks at 5472x3648")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: fraction of the Gaussians")
+    ap.add_argument("--objective", default="pg", choices=["pg", "eq11"],
+                    help="aerial workloads: pg = L_rgb + lambda_4 L_ban (GC-load value only); eq11 = Eq. 11 with "
+                         "the flattening loss and the soft-count GC-load, all differentiated")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: use --tile and 4 persistent CTAs per SM instead of the autotuner")
     ap.add_argument("--retune", action="store_true", help="batched workload: ignore the autotune cache")
@@ -289,6 +292,7 @@ def ours(args):
     v = views[0]
     P = raster.GaussianParams.from_numpy(g, requires_grad=True)
     plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, tile=(tw, th))
+    plan.set_objective(args.objective)
 
     def step(check=False):
         for t in P.tensors():
@@ -479,7 +483,7 @@ def ours(args):
              "stage_model_frac": sum(ab.values()) / sec / 1e9 / pk["hbm_gbs"]}
 
     cpu = None
-    if not args.no_cpu_baseline and ws == 1 and args.workload == "aerial":
+    if not args.no_cpu_baseline and ws == 1 and args.workload == "aerial" and args.objective == "pg":
         cv, sample = cpu_crop_sample(views)
         times, cores = run_oracle_steps(g, cv, 2)
         t = min(times)
@@ -493,6 +497,7 @@ def ours(args):
         "config": {"workload": WORKLOAD if args.workload == "aerial" else args.workload, "width": v.cam.width, "height": v.cam.height, "n_gaussians": g.n,
                    "mask_pixels": plan.n_mask, "rendered_pixels": plan.n_render, "active_tiles": plan.n_active,
                    "duplicates_K": K_dup, "tile": args.tile, "parallelism": f"replicas x{ws}",
+                   "objective": args.objective,
                    "l2": "inputs larger than L2 (params 354 MB, per-pixel buffers > 2 GB)"},
         "roofline": roofline, "step_roofline": whole,
         "stages_ms": stage_ms, "eager_ms_per_step": ms_eager, "graph": True,

@@ -308,14 +308,17 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
  *   out8  float [8 per compact pixel]: {C_r, C_g, C_b, D, N_x, N_y, N_z, A = 1 - T}
  *   depth float [1 per compact pixel]
  *   aux   uint4 [1 per compact pixel]: {float bits of final T, index (into dup_pairs) of the
- *         last blended Gaussian, number blended n_contrib, 0}
+ *         last blended Gaussian, number blended n_contrib, float bits of the soft
+ *         count g~ = sum of the blended alphas (PGSAG_RENDER_SOFT_COUNT), else 0}
  * sched may be NULL (one CTA per active tile in index order); with a counter the
  * launch is persistent (ctas_per_sm x SMs CTAs pulling tiles, in `order` if
  * given; ctas_per_sm <= 0: as many as the occupancy allows).
+ * flags: 0, or PGSAG_RENDER_SOFT_COUNT (needed by the PGSAG_OBJ_EQ11 objective).
  */
+#define PGSAG_RENDER_SOFT_COUNT 1u
 int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec,
                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
-                     uint32_t n_active_total, const uint32_t* px_list, const pgsag_sched* sched,
+                     uint32_t n_active_total, const uint32_t* px_list, const pgsag_sched* sched, uint32_t flags,
                      float* out8, float* depth, void* aux, int32_t* status, void* stream);
 
 /*
@@ -348,13 +351,35 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
  *            per view without contended atomics)
  *   loss     float [3 per view + 1]: {L_rgb, L_ban, L} per view, then sum_v L
  *   dout8    float [8 per compact pixel]
+ *   objective  PGSAG_OBJ_PG: L = L_rgb + lambda_ban L_ban, dout8 = dL/d(out8); the
+ *            GC-load (if gc_weight) uses the integer count n_contrib, value only.
+ *            PGSAG_OBJ_EQ11 (Sec. 4.3, Eq. 10-11 over the locally defined terms):
+ *            L = (1 - lambda) (L_rgb + lambda_3 L_s + lambda_4 L_ban)
+ *                + lambda sum_v GC-load_v, lambda = 0.41, lambda_3 = 100,
+ *            lambda_4 = lambda_ban; the GC-load uses the soft count g~ (aux.w,
+ *            pgsag_render_fwd with PGSAG_RENDER_SOFT_COUNT) and is differentiated;
+ *            L_s = mean over the n_gauss Gaussians of min(exp(log_scales)) (the
+ *            flattening loss, PGSR by citation).  Requires gc_weight, gc_load
+ *            and gather = 0; acc then holds 8 doubles per view + 8 (the L_s
+ *            sum); loss per view {L_rgb, L_ban, view total under Eq. 11} and the
+ *            last entry the full L.  dout8 stays d(L_rgb + lambda_4 L_ban); the
+ *            (1 - lambda) factor, the GC-load gradient (its per-view
+ *            coefficients are left in acc, slot 3) and the L_s gradient are
+ *            applied by pgsag_render_bwd (pgsag_ban_gather.objective) and
+ *            pgsag_preprocess_bwd (flatten_weight).
+ *   n_gauss, log_scales  the Gaussians of L_s (objective EQ11; n_gauss may be 0)
  */
+#define PGSAG_OBJ_PG 0u
+#define PGSAG_OBJ_EQ11 1u
+#define PGSAG_LAMBDA_GC 0.41f      /* Sec. 4.3, Eq. 11: lambda   */
+#define PGSAG_LAMBDA_FLAT 100.0f   /* Sec. 4.3, Eq. 11: lambda_3 */
 int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                    const void* chunks, const void* act_tiles, const uint32_t* px_list,
                    const uint8_t* flags_c, const void* nbr, const float* out8, const float* depth,
                    const void* aux, const float* target, float lambda_ban, const float* gc_weight,
                    int gather, float* scratch, double* acc, float* chunk_scratch, float* loss,
-                   float* gc_load, float* dout8, int32_t* status, void* stream);
+                   float* gc_load, float* dout8, uint32_t objective, uint32_t n_gauss,
+                   const float* log_scales, int32_t* status, void* stream);
 
 /*
  * Deferred Eq. 8 adjoint for pgsag_render_bwd.  pgsag_loss_ban with gather = 0
@@ -369,8 +394,11 @@ typedef struct pgsag_ban_gather {
   const float* scratch;    /* device, loss scratch from pgsag_loss_ban (6 per compact px) */
   const double* acc;       /* device, loss accumulators from pgsag_loss_ban (8 per view) */
   float lambda_ban;        /* the lambda given to pgsag_loss_ban                         */
+  uint32_t objective;      /* the objective given to pgsag_loss_ban                      */
+  const float* gc_weight;  /* device, Eq. 9 weights (objective PGSAG_OBJ_EQ11)           */
+  float lambda_gc;         /* Eq. 11 lambda (objective PGSAG_OBJ_EQ11)                   */
   uint32_t reserved;       /* 0                                                         */
-} pgsag_ban_gather;
+} pgsag_ban_gather;       /* 56 bytes */
 
 /*
  * pgsag_render_bwd (Sec. 3.1: the Gaussians' parameters are fitted through the
@@ -401,6 +429,10 @@ int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec
  * (no atomics: one thread per Gaussian loops over its views).  The argmin axis,
  * the normal flip, the Jacobian clamp and the colour clamp are locally constant.
  * accumulate = 0 overwrites the outputs, 1 adds to them.
+ * flatten_weight != 0 adds the gradient of flatten_weight * L_s, L_s = mean over
+ * the n_gauss Gaussians of min(exp(log_scales)) (Eq. 11's flattening term; its
+ * weight there is (1 - lambda) lambda_3), scaled by *dout_scale if dout_scale is
+ * given, to d_log_scales at each Gaussian's smallest axis (ties: lowest axis).
  * Outputs: d_means [N,3], d_log_scales [N,3], d_quats [N,4], d_opacity_logit [N],
  * d_sh [N,16,3].
  */
@@ -409,7 +441,8 @@ int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const float* log_
                          uint32_t n_views, const pgsag_view* views, const void* bininfo,
                          const float* grad2d, int accumulate, float* d_means,
                          float* d_log_scales, float* d_quats, float* d_opacity_logit,
-                         float* d_sh, int32_t* status, void* stream);
+                         float* d_sh, const float* dout_scale, float flatten_weight,
+                         int32_t* status, void* stream);
 
 /*
  * pgsag_tile_stats (Sec. 4.3, Eq. 9).

@@ -53,9 +53,17 @@ class PgsagSched(ctypes.Structure):
 
 
 class PgsagBanGather(ctypes.Structure):
-    """pgsag_ban_gather: the deferred Eq. 8 gather done by the render adjoint."""
+    """pgsag_ban_gather: the deferred Eq. 8 gather done by the render adjoint (and,
+    for the Eq. 11 objective, the soft-count GC-load gradient)."""
     _fields_ = [("flags_c", c_void_p), ("nbr", c_void_p), ("scratch", c_void_p), ("acc", c_void_p),
-                ("lambda_ban", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+                ("lambda_ban", ctypes.c_float), ("objective", ctypes.c_uint32), ("gc_weight", c_void_p),
+                ("lambda_gc", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+
+
+assert ctypes.sizeof(PgsagBanGather) == 56
+OBJ_PG, OBJ_EQ11 = 0, 1
+RENDER_SOFT_COUNT = 1
+LAMBDA_GC, LAMBDA_FLAT = 0.41, 100.0
 
 
 class PgsagVoteView(ctypes.Structure):
@@ -98,12 +106,16 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_preprocess", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_bin_workspace_size", c_size_t, [c_uint32, c_uint32, c_uint64])
     _sig(lib, "pgsag_bin", c_int, [c_uint32, c_uint32, P, c_uint32, P, P, P, P, c_uint64, P, c_size_t, P, P, P, P, P])
-    _sig(lib, "pgsag_render_fwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, P])
-    _sig(lib, "pgsag_loss_ban", c_int, [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, c_float, P, c_int, P, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_render_fwd", c_int,
+         [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), c_uint32, P, P, P, P, P])
+    _sig(lib, "pgsag_loss_ban", c_int,
+         [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, c_float, P, c_int, P, P, P, P, P, P, c_uint32, c_uint32, P,
+          P, P])
     _sig(lib, "pgsag_render_bwd", c_int,
          [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, POINTER(PgsagBanGather), P,
           c_uint32, P, P, P])
-    _sig(lib, "pgsag_preprocess_bwd", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_preprocess_bwd", c_int,
+         [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, c_float, P, P])
     _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_tile_stats_noalloc", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_schedule_lpt", c_int, [c_uint32, P, P, P, P, P, P])

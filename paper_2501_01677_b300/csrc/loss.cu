@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
     const uint32_t* __restrict__ px_list, const uint8_t* __restrict__ flags_c, const uint4* __restrict__ nbr,
     const float4* __restrict__ out8, const float* __restrict__ depth, const float* __restrict__ target,
     const uint4* __restrict__ aux,
-    const float* __restrict__ gc_weight, float* __restrict__ scratch, float4* __restrict__ partial,
+    const float* __restrict__ gc_weight, bool soft, float* __restrict__ scratch, float4* __restrict__ partial,
     float4* __restrict__ dout8, const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
@@ -72,8 +72,10 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
   float l1 = 0.f, lb = 0.f, nv = 0.f, gn = 0.f, gx = 0.f;
   if (P.has) {
     if (gc_weight != nullptr) {
-      // Eq. 9 term of this rendered pixel: g / w (g = Gaussians blended)
-      gx = (float)__ldg(&aux[P.q].z) / __ldg(gc_weight + P.q);
+      // Eq. 9 term of this rendered pixel: g / w (g = Gaussians blended, or the
+      // soft count g~ = sum of their alphas)
+      const float g = soft ? __uint_as_float(__ldg(&aux[P.q].w)) : (float)__ldg(&aux[P.q].z);
+      gx = g / __ldg(gc_weight + P.q);
       gn = 1.f;
     }
     const uint8_t f = __ldg(flags_c + P.q);
@@ -278,24 +280,67 @@ __device__ __forceinline__ float gc_std(double n, double s, double q) {
   return (float)sqrt(var > 0.0 ? var : 0.0);
 }
 
-__global__ void k_loss_final(const pgsag_view* __restrict__ views, uint32_t n_views,
-                             const double* __restrict__ acc, float lambda_ban, float* __restrict__ loss,
+// Per view: L_rgb, L_ban, the view's loss and the GC-load; the sum over views.
+// Objective Eq. 11: the view's loss is (1 - lambda)(L_rgb + lambda_4 L_ban) +
+// lambda GC-load_v, the total adds (1 - lambda) lambda_3 L_s (L_s = the
+// flattening sum in acc[8 n_views] over n_gauss), and slot 3 of each view's
+// accumulators receives {lambda / (n sigma), mean} (two floats), the
+// coefficients of the soft-count gradient dL/dg~_i = c (x_i - mean) / w_i.
+__global__ void k_loss_final(const pgsag_view* __restrict__ views, uint32_t n_views, double* __restrict__ acc,
+                             float lambda_ban, uint32_t objective, uint32_t n_gauss, float* __restrict__ loss,
                              float* __restrict__ gc_load, const int32_t* status) {
   if (status_bad(status)) return;
   if (threadIdx.x != 0) return;
+  const bool eq11 = objective == PGSAG_OBJ_EQ11;
+  const double lam = (double)PGSAG_LAMBDA_GC;
   double total = 0.0;
   for (uint32_t v = 0; v < n_views; ++v) {
-    const double* a = acc + 8 * v;
+    double* a = acc + 8 * v;
     const uint32_t nm = views[v].n_mask;
     const double lr = nm ? a[0] / (3.0 * nm) : 0.0;
     const double lb = a[2] > 0.0 ? a[1] / a[2] : 0.0;
+    const float gc = gc_load ? gc_std(a[4], a[5], a[6]) : 0.f;
+    double lv = lr + (double)lambda_ban * lb;
+    if (eq11) {
+      lv = (1.0 - lam) * lv + lam * (double)gc;
+      const double n = a[4];
+      float2 cm = make_float2(0.f, 0.f);
+      if (n > 0.0) {
+        cm.y = (float)(a[5] / n);
+        if (gc > 0.f) cm.x = (float)(lam / (n * (double)gc));
+      }
+      *reinterpret_cast<float2*>(a + 3) = cm;
+    }
     loss[3 * v + 0] = (float)lr;
     loss[3 * v + 1] = (float)lb;
-    loss[3 * v + 2] = (float)(lr + (double)lambda_ban * lb);
-    total += lr + (double)lambda_ban * lb;
-    if (gc_load) gc_load[v] = gc_std(a[4], a[5], a[6]);
+    loss[3 * v + 2] = (float)lv;
+    total += lv;
+    if (gc_load) gc_load[v] = gc;
   }
+  if (eq11 && n_gauss > 0)
+    total += (1.0 - lam) * (double)PGSAG_LAMBDA_FLAT * acc[8 * n_views] / (double)n_gauss;
   loss[3 * n_views] = (float)total;
+}
+
+// Flattening loss (Eq. 11's L_s): sum over the Gaussians of min(exp(log_scales)).
+__global__ void __launch_bounds__(256) k_flat_sum(uint32_t n, const float* __restrict__ log_scales,
+                                                  double* __restrict__ out, const int32_t* status) {
+  if (status_bad(status)) return;
+  __shared__ double s_w[8];
+  double acc = 0.0;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    const float a = __ldg(log_scales + 3ull * g), b = __ldg(log_scales + 3ull * g + 1),
+                c = __ldg(log_scales + 3ull * g + 2);
+    acc += (double)expf(fminf(a, fminf(b, c)));
+  }
+  acc = warp_sum_d(acc);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    atomicAdd(out, t);
+  }
 }
 
 // ------------------------------------------------------------------ Eq. 9
@@ -373,12 +418,16 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
                               const uint8_t* flags_c, const void* nbr, const float* out8, const float* depth,
                               const void* aux, const float* target, float lambda_ban, const float* gc_weight,
                               int gather, float* scratch, double* acc, float* chunk_scratch, float* loss,
-                              float* gc_load, float* dout8, int32_t* status, void* stream) {
+                              float* gc_load, float* dout8, uint32_t objective, uint32_t n_gauss,
+                              const float* log_scales, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
+  if (objective != PGSAG_OBJ_PG && objective != PGSAG_OBJ_EQ11) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status || !acc || !loss) return PGSAG_ERR_ARG;
   if ((gc_weight == nullptr) != (gc_load == nullptr)) return PGSAG_ERR_ARG;
+  const bool eq11 = objective == PGSAG_OBJ_EQ11;
+  if (eq11 && (!gc_weight || gather || (n_gauss && !log_scales))) return PGSAG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_views * 8 * sizeof(double), s));
+  PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)(n_views + (eq11 ? 1 : 0)) * 8 * sizeof(double), s));
   if (n_chunks) {
     if (!chunks || !px_list || !flags_c || !nbr || !out8 || !depth || !target || !scratch || !dout8 ||
         !chunk_scratch || (gc_weight && !aux))
@@ -389,7 +438,7 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
     const unsigned blocks = pgsag_div_up(n_chunks, kLossThreads / 32);
     k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint4*)chunks, px_list, flags_c,
                                              (const uint4*)nbr, (const float4*)out8, depth, target,
-                                             (const uint4*)aux, gc_weight, scratch, (float4*)chunk_scratch,
+                                             (const uint4*)aux, gc_weight, eq11, scratch, (float4*)chunk_scratch,
                                              (float4*)dout8, status);
     PGSAG_CHECK_LAUNCH();
     k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 8, gc_weight ? 7 : 3, 8,
@@ -402,7 +451,12 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
       PGSAG_CHECK_LAUNCH();
     }
   }
-  k_loss_final<<<1, 32, 0, s>>>(views, n_views, acc, lambda_ban, loss, gc_load, status);
+  if (eq11 && n_gauss) {
+    const unsigned fb = pgsag_div_up(n_gauss, 256) < 148u * 8u ? pgsag_div_up(n_gauss, 256) : 148u * 8u;
+    k_flat_sum<<<fb, 256, 0, s>>>(n_gauss, log_scales, acc + 8 * (size_t)n_views, status);
+    PGSAG_CHECK_LAUNCH();
+  }
+  k_loss_final<<<1, 32, 0, s>>>(views, n_views, acc, lambda_ban, objective, n_gauss, loss, gc_load, status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

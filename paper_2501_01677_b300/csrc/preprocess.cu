@@ -448,7 +448,8 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
                                  const float* __restrict__ grad2d, int accumulate,
                                  float* __restrict__ d_means, float* __restrict__ d_log_scales,
                                  float* __restrict__ d_quats, float* __restrict__ d_opac,
-                                 float* __restrict__ d_sh, const int32_t* status) {
+                                 float* __restrict__ d_sh, const float* __restrict__ dout_scale,
+                                 float flatten_weight, const int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pgsag_view* sv = reinterpret_cast<pgsag_view*>(smem_raw);
   {
@@ -654,6 +655,19 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
   }
 
   if (g < n) {
+    if (flatten_weight != 0.f) {
+      // Eq. 11's flattening term: d(w mean_g min_k exp(ls_gk)) / d ls_gk* = w exp(ls_gk*) / n
+      // at the smallest axis k* (ties: lowest axis)
+      const float l0 = __ldg(log_scales + 3ull * g), l1 = __ldg(log_scales + 3ull * g + 1),
+                  l2 = __ldg(log_scales + 3ull * g + 2);
+      const int k = (l0 <= l1 && l0 <= l2) ? 0 : (l1 <= l2 ? 1 : 2);
+      const float lk = k == 0 ? l0 : (k == 1 ? l1 : l2);
+      const float sc = dout_scale ? __ldg(dout_scale) : 1.f;
+      const float d = flatten_weight * sc * expf(lk) / (float)n;
+      gls[0] += k == 0 ? d : 0.f;
+      gls[1] += k == 1 ? d : 0.f;
+      gls[2] += k == 2 ? d : 0.f;
+    }
     if (accumulate) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -734,7 +748,8 @@ extern "C" int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const 
                                     uint32_t n_views, const pgsag_view* views, const void* bininfo,
                                     const float* grad2d, int accumulate, float* d_means,
                                     float* d_log_scales, float* d_quats, float* d_opacity_logit,
-                                    float* d_sh, int32_t* status, void* stream) {
+                                    float* d_sh, const float* dout_scale, float flatten_weight,
+                                    int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status) return PGSAG_ERR_ARG;
   if (n_gauss == 0) return PGSAG_OK;
@@ -751,7 +766,7 @@ extern "C" int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const 
   k_preprocess_bwd<<<pgsag_div_up(n_gauss, threads), threads, smem, (cudaStream_t)stream>>>(
       n_gauss, means, log_scales, quats, opacity_logit, sh, n_views, views,
       reinterpret_cast<const uint4*>(bininfo), grad2d, accumulate, d_means, d_log_scales, d_quats,
-      d_opacity_logit, d_sh, status);
+      d_opacity_logit, d_sh, dout_scale, flatten_weight, status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

@@ -206,10 +206,12 @@ __device__ __forceinline__ void warp_relevance(const Stage& S, int limit, float4
 }
 
 // Forward outputs of one pixel: {C, D}, {N, A = 1 - T}, the Eq. 4 depth and
-// {T, last blended, count}.  (x, y) is the pixel centre in image coordinates.
-__device__ __forceinline__ void write_pixel(uint64_t gp, float4 cd, float4 nt, uint32_t last, uint32_t cnt, float x,
-                                            float y, const ViewLite& V, float4* __restrict__ out8,
-                                            float* __restrict__ depth, uint4* __restrict__ aux) {
+// {T, last blended, count, soft count}.  (x, y) is the pixel centre in image
+// coordinates.
+__device__ __forceinline__ void write_pixel(uint64_t gp, float4 cd, float4 nt, uint32_t last, uint32_t cnt,
+                                            float soft, float x, float y, const ViewLite& V,
+                                            float4* __restrict__ out8, float* __restrict__ depth,
+                                            uint4* __restrict__ aux) {
   out8[2 * gp + 0] = cd;
   out8[2 * gp + 1] = make_float4(nt.x, nt.y, nt.z, 1.f - nt.w);
   // Eq. 4: ray-plane depth
@@ -217,10 +219,12 @@ __device__ __forceinline__ void write_pixel(uint64_t gp, float4 cd, float4 nt, u
   const float sdot = -(nt.x * rx + nt.y * ry + nt.z);
   const bool valid = cnt > 0 && sdot > kRayDotMin && cd.w > 0.f;
   depth[gp] = valid ? cd.w / sdot : 0.f;
-  aux[gp] = make_uint4(__float_as_uint(nt.w), last, cnt, 0u);
+  aux[gp] = make_uint4(__float_as_uint(nt.w), last, cnt, __float_as_uint(soft));
 }
 
-template <int kWarps>
+// kSoft: also sum the blended alphas per pixel (the soft count g~ of Eq. 9's
+// differentiable form) into aux.w.
+template <int kWarps, bool kSoft>
 __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
     const pgsag_view* __restrict__ views, const float4* __restrict__ rec,
     const uint32_t* __restrict__ dup_pairs, const uint2* __restrict__ ranges,
@@ -251,6 +255,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
       float2 T = f2(1.f), C0 = f2(0.f), C1 = f2(0.f), C2 = f2(0.f), D = f2(0.f), N0 = f2(0.f), N1 = f2(0.f),
              N2 = f2(0.f);
       uint32_t last0 = 0, last1 = 0, cnt0 = 0, cnt1 = 0;
+      float2 Gs = f2(0.f);  // soft count (kSoft)
       bool done0 = !P.has0, done1 = !P.has1;
       bool all_done = done0 && done1;
       for (uint32_t base = ti.rbeg; base < ti.rend; base += kBatch) {
@@ -304,6 +309,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
             N0 = __ffma2_rn(w, f2(q3.x), N0);
             N1 = __ffma2_rn(w, f2(q3.y), N1);
             N2 = __ffma2_rn(w, f2(q3.z), N2);
+            if constexpr (kSoft) Gs = __fadd2_rn(Gs, make_float2(a0 ? alpha.x : 0.f, a1 ? alpha.y : 0.f));
             if (a0) {
               T.x = test.x;
               last0 = base + j;
@@ -324,10 +330,10 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
       }
       if (P.has0)
         write_pixel(P.q0, make_float4(C0.x, C1.x, C2.x, D.x), make_float4(N0.x, N1.x, N2.x, T.x), last0, cnt0,
-                    P.px.x + (float)ox, P.py.x + (float)oy, V, out8, depth, aux);
+                    Gs.x, P.px.x + (float)ox, P.py.x + (float)oy, V, out8, depth, aux);
       if (P.has1)
         write_pixel(P.q1, make_float4(C0.y, C1.y, C2.y, D.y), make_float4(N0.y, N1.y, N2.y, T.y), last1, cnt1,
-                    P.px.y + (float)ox, P.py.y + (float)oy, V, out8, depth, aux);
+                    Gs.y, P.px.y + (float)ox, P.py.y + (float)oy, V, out8, depth, aux);
     }
   }
 }
@@ -384,6 +390,7 @@ struct BwdPix {
   int last0, last1;
   float2 dC0, dC1, dC2, dD, dN0, dN1, dN2, dATf;  // dATf = dL/dA * T_final
   float2 SC0, SC1, SC2, SN0, SN1, SN2, SD;
+  float2 dG;  // dL/d(soft count) (objective Eq. 11)
 };
 
 // Deferred Eq. 8 adjoint (the loss's second pass, run here): dL/dP of the pixel's
@@ -426,8 +433,18 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
                                               uint32_t view, float gscale, const uint4* __restrict__ aux,
                                               const float4* __restrict__ dout8, const float* __restrict__ ddepth,
                                               bool use_ban, const pgsag_ban_gather& ban,
-                                              const float4* __restrict__ out8, float v[9], int& last) {
+                                              const float4* __restrict__ out8, float v[10], int& last,
+                                              bool soft, float gscale_gc) {
   const uint4 ax = __ldg(aux + gp);
+  v[9] = 0.f;
+  if (soft) {
+    // Eq. 9 with the soft count: L_GC = std_i(x_i), x_i = g~_i / w_i over the
+    // view's rendered pixels; dL/dg~_i = (lambda / (n sigma)) (x_i - mean) / w_i,
+    // with {lambda / (n sigma), mean} per view from the loss pass
+    const float2 cm = *reinterpret_cast<const float2*>(ban.acc + 8 * view + 3);
+    const float w = __ldg(ban.gc_weight + gp);
+    v[9] = gscale_gc * cm.x * (__uint_as_float(ax.w) / w - cm.y) / w;
+  }
   const float T = __uint_as_float(ax.x);
   last = ax.z > 0 ? (int)ax.y : -1;
   const float4 g0 = __ldg(dout8 + 2 * gp), g1 = __ldg(dout8 + 2 * gp + 1);
@@ -463,7 +480,9 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
   }
 }
 
-template <int kWarps>
+// kSoft: objective Eq. 11 -- the loss gradients get the (1 - lambda) factor and
+// every blended alpha the soft-count GC-load gradient dL/dg~ of its pixel.
+template <int kWarps, bool kSoft>
 __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     const pgsag_view* __restrict__ views, const float4* __restrict__ rec,
     const uint32_t* __restrict__ dup_pairs, const uint2* __restrict__ ranges,
@@ -482,7 +501,9 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
   __shared__ int s_max;
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float gscale = dout_scale ? __ldg(dout_scale) : 1.f;
+  const float gscale_in = dout_scale ? __ldg(dout_scale) : 1.f;
+  // Eq. 11: the photometric / normal-loss gradients are scaled by (1 - lambda)
+  const float gscale = kSoft ? gscale_in * (1.f - ban.lambda_gc) : gscale_in;
   for (int i = threadIdx.x; i < kBatch; i += kRenderThreads)
     sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t iter = 0;
@@ -500,12 +521,15 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
       const float4 cbox = warp_pixel_box(P);
       BwdPix B;
       {
-        float v0[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f}, v1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+        float v0[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f},
+              v1[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
         B.last0 = B.last1 = -1;
         if (P.has0)
-          load_upstream(P.q0, P.px.x, P.py.x, ox, oy, V, ti.view, gscale, aux, dout8, ddepth, use_ban, ban, out8, v0, B.last0);
+          load_upstream(P.q0, P.px.x, P.py.x, ox, oy, V, ti.view, gscale, aux, dout8, ddepth, use_ban, ban, out8, v0,
+                        B.last0, kSoft, gscale_in);
         if (P.has1)
-          load_upstream(P.q1, P.px.y, P.py.y, ox, oy, V, ti.view, gscale, aux, dout8, ddepth, use_ban, ban, out8, v1, B.last1);
+          load_upstream(P.q1, P.px.y, P.py.y, ox, oy, V, ti.view, gscale, aux, dout8, ddepth, use_ban, ban, out8, v1,
+                        B.last1, kSoft, gscale_in);
         B.dC0 = make_float2(v0[0], v1[0]);
         B.dC1 = make_float2(v0[1], v1[1]);
         B.dC2 = make_float2(v0[2], v1[2]);
@@ -515,6 +539,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
         B.dN2 = make_float2(v0[6], v1[6]);
         B.dATf = make_float2(v0[7], v1[7]);
         B.T = make_float2(v0[8], v1[8]);
+        B.dG = make_float2(v0[9], v1[9]);
         B.SC0 = B.SC1 = B.SC2 = B.SN0 = B.SN1 = B.SN2 = B.SD = f2(0.f);
       }
       const int warp_last = warp_max_i(max(B.last0, B.last1));
@@ -590,7 +615,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
             e = __ffma2_rn(B.SN2, f2(-1.f), f2(q3.z));
             acc = __ffma2_rn(e, B.dN2, acc);
             B.SN2 = __ffma2_rn(am, e, B.SN2);
-            const float2 dal = __ffma2_rn(B.dATf, roma, __fmul2_rn(B.T, acc));
+            float2 dal = __ffma2_rn(B.dATf, roma, __fmul2_rn(B.T, acc));
+            if constexpr (kSoft) dal = __fadd2_rn(dal, B.dG);  // d g~ / d alpha = 1
             g[6] = fmaf(w.y, B.dC0.y, w.x * B.dC0.x);
             g[7] = fmaf(w.y, B.dC1.y, w.x * B.dC1.x);
             g[8] = fmaf(w.y, B.dC2.y, w.x * B.dC2.x);
@@ -671,26 +697,58 @@ static int launch_cfg(const pgsag_sched* sched, uint32_t n_items, const void* ke
   return PGSAG_OK;
 }
 
-extern "C" int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec,
-                                const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
-                                uint32_t n_active, const uint32_t* px_list, const pgsag_sched* sched,
-                                float* out8, float* depth, void* aux, int32_t* status, void* stream) {
-  if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
-  if (!views || !status) return PGSAG_ERR_ARG;
-  if (n_active == 0) return PGSAG_OK;
-  if (!rec || !ranges || !act_tiles || !px_list || !out8 || !depth || !aux) return PGSAG_ERR_ARG;
-  if (((uintptr_t)rec | (uintptr_t)out8 | (uintptr_t)aux | (uintptr_t)act_tiles) & 15u) return PGSAG_ERR_ARG;
+template <bool kSoft>
+static int launch_fwd(const pgsag_sched* sched, uint32_t n_active, const pgsag_view* views, const float* rec,
+                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles, const uint32_t* px_list,
+                      float* out8, float* depth, void* aux, int32_t* status, cudaStream_t st) {
   Sched s;
   unsigned blocks;
   static int occ = 0;
-  int r = launch_cfg(sched, n_active, (const void*)k_render_fwd<PGSAG_FWD_WARPS>, PGSAG_FWD_WARPS * 32, &occ, s,
-                     blocks);
+  int r = launch_cfg(sched, n_active, (const void*)k_render_fwd<PGSAG_FWD_WARPS, kSoft>, PGSAG_FWD_WARPS * 32, &occ,
+                     s, blocks);
   if (r) return r;
-  cudaStream_t st = (cudaStream_t)stream;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
-  k_render_fwd<PGSAG_FWD_WARPS><<<blocks, PGSAG_FWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
-                                                  (const uint4*)act_tiles, n_active, px_list, s, (float4*)out8, depth,
-                                                  (uint4*)aux, status);
+  k_render_fwd<PGSAG_FWD_WARPS, kSoft><<<blocks, PGSAG_FWD_WARPS * 32, 0, st>>>(
+      views, (const float4*)rec, dup_pairs, (const uint2*)ranges, (const uint4*)act_tiles, n_active, px_list, s,
+      (float4*)out8, depth, (uint4*)aux, status);
+  PGSAG_CHECK_LAUNCH();
+  return PGSAG_OK;
+}
+
+extern "C" int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec,
+                                const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
+                                uint32_t n_active, const uint32_t* px_list, const pgsag_sched* sched, uint32_t flags,
+                                float* out8, float* depth, void* aux, int32_t* status, void* stream) {
+  if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
+  if (!views || !status) return PGSAG_ERR_ARG;
+  if (flags & ~PGSAG_RENDER_SOFT_COUNT) return PGSAG_ERR_UNSUPPORTED;
+  if (n_active == 0) return PGSAG_OK;
+  if (!rec || !ranges || !act_tiles || !px_list || !out8 || !depth || !aux) return PGSAG_ERR_ARG;
+  if (((uintptr_t)rec | (uintptr_t)out8 | (uintptr_t)aux | (uintptr_t)act_tiles) & 15u) return PGSAG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (flags & PGSAG_RENDER_SOFT_COUNT)
+    return launch_fwd<true>(sched, n_active, views, rec, dup_pairs, ranges, act_tiles, px_list, out8, depth, aux,
+                            status, st);
+  return launch_fwd<false>(sched, n_active, views, rec, dup_pairs, ranges, act_tiles, px_list, out8, depth, aux,
+                           status, st);
+}
+
+template <bool kSoft>
+static int launch_bwd(const pgsag_sched* sched, uint32_t n_active, const pgsag_view* views, const float* rec,
+                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles, const uint32_t* px_list,
+                      const float* out8, const void* aux, const float* dout8, const float* ddepth,
+                      const pgsag_ban_gather& bg, bool use_ban, const float* dout_scale, float* grad2d,
+                      int32_t* status, cudaStream_t st) {
+  Sched s;
+  unsigned blocks;
+  static int occ = 0;
+  int r = launch_cfg(sched, n_active, (const void*)k_render_bwd<PGSAG_BWD_WARPS, kSoft>, PGSAG_BWD_WARPS * 32, &occ,
+                     s, blocks);
+  if (r) return r;
+  if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
+  k_render_bwd<PGSAG_BWD_WARPS, kSoft><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(
+      views, (const float4*)rec, dup_pairs, (const uint2*)ranges, (const uint4*)act_tiles, n_active, px_list, s,
+      (const float4*)out8, (const uint4*)aux, (const float4*)dout8, ddepth, bg, use_ban, dout_scale, grad2d, status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }
@@ -703,6 +761,8 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
                                 float* grad2d, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status) return PGSAG_ERR_ARG;
+  if (ban && ban->objective != PGSAG_OBJ_PG && ban->objective != PGSAG_OBJ_EQ11) return PGSAG_ERR_UNSUPPORTED;
+  const bool soft = ban && ban->objective == PGSAG_OBJ_EQ11;
   cudaStream_t st = (cudaStream_t)stream;
   if (n_pairs) {
     if (!grad2d || ((uintptr_t)grad2d & 15u)) return PGSAG_ERR_ARG;
@@ -712,21 +772,14 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
   if (!rec || !ranges || !act_tiles || !px_list || !out8 || !aux || !dout8 || !grad2d) return PGSAG_ERR_ARG;
   if (ban && !(ban->flags_c && ban->nbr && ban->scratch && ban->acc)) return PGSAG_ERR_ARG;
   if (ban && ((uintptr_t)ban->nbr & 15u)) return PGSAG_ERR_ARG;
+  if (soft && (!ban->gc_weight || ((uintptr_t)ban->acc & 7u))) return PGSAG_ERR_ARG;
   pgsag_ban_gather bg{};
   if (ban) bg = *ban;
   if (((uintptr_t)rec | (uintptr_t)out8 | (uintptr_t)aux | (uintptr_t)dout8 | (uintptr_t)act_tiles) & 15u)
     return PGSAG_ERR_ARG;
-  Sched s;
-  unsigned blocks;
-  static int occ = 0;
-  int r = launch_cfg(sched, n_active, (const void*)k_render_bwd<PGSAG_BWD_WARPS>, PGSAG_BWD_WARPS * 32, &occ, s,
-                     blocks);
-  if (r) return r;
-  if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
-  k_render_bwd<PGSAG_BWD_WARPS><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(views, (const float4*)rec, dup_pairs, (const uint2*)ranges,
-                                                  (const uint4*)act_tiles, n_active, px_list, s, (const float4*)out8,
-                                                  (const uint4*)aux, (const float4*)dout8, ddepth, bg, ban != nullptr, dout_scale,
-                                                  grad2d, status);
-  PGSAG_CHECK_LAUNCH();
-  return PGSAG_OK;
+  if (soft)
+    return launch_bwd<true>(sched, n_active, views, rec, dup_pairs, ranges, act_tiles, px_list, out8, aux, dout8,
+                            ddepth, bg, true, dout_scale, grad2d, status, st);
+  return launch_bwd<false>(sched, n_active, views, rec, dup_pairs, ranges, act_tiles, px_list, out8, aux, dout8,
+                           ddepth, bg, ban != nullptr, dout_scale, grad2d, status, st);
 }

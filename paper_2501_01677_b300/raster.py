@@ -208,7 +208,8 @@ class Plan:
         self.tile_counts = torch.zeros(max(self.n_active, 1), dtype=i32, device=dev)
         self.k_out = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=i32, device=dev)
-        self.acc_loss = torch.zeros(8 * V, dtype=torch.float64, device=dev)
+        self.acc_loss = torch.zeros(8 * (V + 1), dtype=torch.float64, device=dev)
+        self.objective = "pg"
         self.acc_gc = torch.zeros(3 * V, dtype=torch.float64, device=dev)
         self.chunk_scratch = torch.zeros((max(self.n_chunks, 1), 8), dtype=f32, device=dev)
         self.gc_load = torch.zeros(V, dtype=f32, device=dev)
@@ -281,16 +282,15 @@ class Plan:
     def kernel_launches_per_step(self, with_stats=True) -> int:
         """Number of library kernels one step (step() / RenderLossFn) launches: the
         fused loss sums the GC-load and leaves the Eq. 8 gather to render_bwd."""
-        tile_passes = 0
-        if self.n_active > 1:
-            tile_passes = (int(self.n_active - 1).bit_length() + 7) // 8
         n = 1  # preprocess
-        if self.n_pairs:
-            n += 4 * 3 + 3 + 3 * tile_passes + (1 if self.n_active else 0)
+        if self.n_pairs and self.n_active:
+            n += 7                              # bin: emit, tile scan (3), scatter, per-tile sorts (2)
         if self.sched is not None and getattr(self, "lpt", False) and self.n_active:
             n += 3                              # schedule
         n += 1 if self.n_active else 0          # render_fwd
         n += (2 if self.n_chunks else 0) + 1    # loss pass A (+ GC-load sums), per-view reduce, final
+        if self.objective == "eq11" and self.n_gauss:
+            n += 1                              # flattening-loss sum
         if with_stats:
             n += 1 if self.n_active else 0      # per-tile counts
         n += 1 if self.n_active else 0          # render_bwd
@@ -320,23 +320,38 @@ class Plan:
                                        _ptr(self.dup_pairs), _ptr(self.ranges), _ptr(self.k_out), _ptr(self.status), s),
                     "pgsag_bin")
 
+    def set_objective(self, objective: str):
+        """"pg": the step differentiates L_rgb + lambda_4 L_ban (the GC-load is a
+        value from the integer count).  "eq11": Eq. 10-11 over the locally defined
+        terms, (1 - lambda)(L_rgb + lambda_3 L_s + lambda_4 L_ban) + lambda GC-load
+        with the soft count, all differentiated."""
+        if objective not in ("pg", "eq11"):
+            raise ValueError(objective)
+        self.objective = objective
+
     def render_fwd(self, stream=None):
         s = _stream_ptr(stream)
+        flags = L.RENDER_SOFT_COUNT if self.objective == "eq11" else 0
         with self._ev('render_fwd'):
             L.check(self.lib.pgsag_render_fwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
                                               _ptr(self.ranges), _ptr(self.act_tiles), self.n_active,
-                                              _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.depth),
-                                              _ptr(self.aux), _ptr(self.status), s), "pgsag_render_fwd")
+                                              _ptr(self.px_list), self._sched_arg(), flags, _ptr(self.out8),
+                                              _ptr(self.depth), _ptr(self.aux), _ptr(self.status), s),
+                    "pgsag_render_fwd")
 
     def loss(self, lambda_ban=LAMBDA_BAN, loss_out: Optional[torch.Tensor] = None, stream=None,
-             fused: bool = False):
+             fused: bool = False, P: Optional[GaussianParams] = None):
         """L_rgb + lambda L_ban per view (Eq. 8) and its gradient on the rendered
         channels into dout8.  fused=True also sums the GC-load (Eq. 9) in the same
         pass and leaves the neighbour gather of Eq. 8 to the next render_bwd
-        (which must then be called with ban=True)."""
+        (which must then be called with ban=True).  With the "eq11" objective
+        (fused only) the values follow Eq. 11 and P gives the flattening term."""
         s = _stream_ptr(stream)
         out = self.loss_buf if loss_out is None else loss_out
         self._lambda_ban = float(lambda_ban)
+        eq11 = self.objective == "eq11"
+        if eq11 and not fused:
+            raise ValueError("the eq11 objective needs the fused loss")
         with self._ev('loss'):
             L.check(self.lib.pgsag_loss_ban(self.n_views, _ptr(self.views_dev), self.n_chunks, _ptr(self.chunks),
                                             _ptr(self.act_tiles), _ptr(self.px_list), _ptr(self.flags_c),
@@ -345,6 +360,8 @@ class Plan:
                                             _ptr(self.gc_weight) if fused else None, 0 if fused else 1,
                                             _ptr(self.scratch), _ptr(self.acc_loss), _ptr(self.chunk_scratch),
                                             _ptr(out), _ptr(self.gc_load) if fused else None, _ptr(self.dout8),
+                                            L.OBJ_EQ11 if eq11 else L.OBJ_PG, P.n if (eq11 and P is not None) else 0,
+                                            _ptr(P.log_scales) if (eq11 and P is not None) else None,
                                             _ptr(self.status), s), "pgsag_loss_ban")
         return out
 
@@ -360,8 +377,11 @@ class Plan:
                     "pgsag_tile_stats")
 
     def _ban_gather(self):
+        eq11 = self.objective == "eq11"
         return L.PgsagBanGather(self.flags_c.data_ptr(), self.nbr.data_ptr(), self.scratch.data_ptr(),
-                                self.acc_loss.data_ptr(), float(getattr(self, "_lambda_ban", LAMBDA_BAN)), 0)
+                                self.acc_loss.data_ptr(), float(getattr(self, "_lambda_ban", LAMBDA_BAN)),
+                                L.OBJ_EQ11 if eq11 else L.OBJ_PG, self.gc_weight.data_ptr() if eq11 else None,
+                                L.LAMBDA_GC, 0)
 
     def render_bwd(self, dout8: torch.Tensor, ddepth: Optional[torch.Tensor] = None,
                    dout_scale: Optional[torch.Tensor] = None, stream=None, ban: bool = False):
@@ -376,14 +396,18 @@ class Plan:
                                               _ptr(dout8), _ptr(ddepth), bg, _ptr(dout_scale), self.n_pairs,
                                               _ptr(self.grad2d), _ptr(self.status), s), "pgsag_render_bwd")
 
-    def preprocess_bwd(self, P: GaussianParams, grads: Sequence[torch.Tensor], accumulate=False, stream=None):
+    def preprocess_bwd(self, P: GaussianParams, grads: Sequence[torch.Tensor], accumulate=False, stream=None,
+                       dout_scale: Optional[torch.Tensor] = None):
         s = _stream_ptr(stream)
         gm, gl, gq, go, gs = grads
+        # Eq. 11: the flattening term (1 - lambda) lambda_3 L_s
+        fw = (1.0 - L.LAMBDA_GC) * L.LAMBDA_FLAT if self.objective == "eq11" else 0.0
         with self._ev('preprocess_bwd'):
             L.check(self.lib.pgsag_preprocess_bwd(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats),
                                                   _ptr(P.opacity_logit), _ptr(P.sh), self.n_views, _ptr(self.views_dev),
                                                   _ptr(self.bininfo), _ptr(self.grad2d), 1 if accumulate else 0, _ptr(gm),
-                                                  _ptr(gl), _ptr(gq), _ptr(go), _ptr(gs), _ptr(self.status), s),
+                                                  _ptr(gl), _ptr(gq), _ptr(go), _ptr(gs), _ptr(dout_scale), fw,
+                                                  _ptr(self.status), s),
                     "pgsag_preprocess_bwd")
 
     def forward(self, P: GaussianParams, check: bool = True, stream=None):
@@ -417,7 +441,7 @@ class Plan:
         self.bin(stream)
         self.schedule(stream)
         self.render_fwd(stream)
-        self.loss(lambda_ban, loss_out, stream, fused=True)
+        self.loss(lambda_ban, loss_out, stream, fused=True, P=P)
         self.tile_stats(stream, counts_only=True)
         self.render_bwd(self.dout8, None, None, stream, ban=True)
         self.preprocess_bwd(P, grads, accumulate, stream)
@@ -495,13 +519,15 @@ class Plan:
 
     def images(self, v: int):
         """Dense images of view v: rgb [H,W,3], dist [H,W], normal [H,W,3], alpha
-        [H,W], depth [H,W], n_contrib [H,W] (zero outside the rendered set)."""
+        [H,W], depth [H,W], n_contrib [H,W], final_T, soft_count (sum of the
+        blended alphas; the "eq11" objective only) (zero outside the rendered set)."""
         sl = self.px_slice(v)
         o = self.scatter_image(v, self.out8[sl])
         aux = self.scatter_image(v, self.aux[sl])
         return dict(rgb=o[..., 0:3], dist=o[..., 3], normal=o[..., 4:7], alpha=o[..., 7],
                     depth=self.scatter_image(v, self.depth[sl]), n_contrib=aux[..., 2],
-                    final_T=aux[..., 0].contiguous().view(torch.float32))
+                    final_T=aux[..., 0].contiguous().view(torch.float32),
+                    soft_count=aux[..., 3].contiguous().view(torch.float32))
 
     def flags_image(self, v: int):
         H, W = self.shapes[v]
@@ -515,7 +541,8 @@ def new_param_grads(P: GaussianParams):
 class RenderLossFn(torch.autograd.Function):
     """Fused masked render + loss:  params -> sum over views of
     L_rgb + lambda_4 L_ban  (Eq. 8, Eq. 10 restricted to the L1 photometric and
-    boundary-aware normal terms).  Backward runs the adjoint renderer on the
+    boundary-aware normal terms), or with plan.set_objective("eq11") Eq. 11's
+    (1 - lambda)(L_rgb + lambda_3 L_s + lambda_4 L_ban) + lambda GC-load.  Backward runs the adjoint renderer on the
     gradient the loss kernel produced and the preprocess adjoint."""
 
     @staticmethod
@@ -523,7 +550,7 @@ class RenderLossFn(torch.autograd.Function):
         P = GaussianParams(means, log_scales, quats, opacity_logit, sh)
         plan.forward(P, check=check)
         out = torch.empty(3 * plan.n_views + 1, dtype=torch.float32, device=plan.device)
-        plan.loss(lambda_ban, loss_out=out, fused=True)
+        plan.loss(lambda_ban, loss_out=out, fused=True, P=P)
         plan.tile_stats(counts_only=True)
         ctx.plan = plan
         ctx.P = P
@@ -536,7 +563,7 @@ class RenderLossFn(torch.autograd.Function):
         g = g.contiguous().to(torch.float32)
         plan.render_bwd(plan.dout8, None, g, ban=True)
         grads = new_param_grads(P)
-        plan.preprocess_bwd(P, grads)
+        plan.preprocess_bwd(P, grads, dout_scale=g)
         return (None, None, None) + tuple(grads)
 
 

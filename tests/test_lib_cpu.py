@@ -39,6 +39,12 @@ def test_view_struct_layout(lib):
     assert b"152" in lib.pgsag_build_info()
 
 
+def test_struct_layouts(lib):
+    assert ctypes.sizeof(L.PgsagBanGather) == 56
+    assert ctypes.sizeof(L.PgsagVoteView) == 96
+    assert ctypes.sizeof(L.PgsagSched) == 24
+
+
 def test_status_strings(lib):
     assert lib.pgsag_status_str(0) == b"ok"
     assert b"argument" in lib.pgsag_status_str(-1)
@@ -60,3 +66,21 @@ def test_invalid_arguments_rejected_on_host(lib):
                                 None, None) == -5
     assert lib.pgsag_bin(10, 1, None, 0, None, None, None, None, 0, None, 0, None, None, None, None, None) == -1
     assert lib.pgsag_adam(10, None, None, None, None, 0.1, 0.9, 0.999, 1e-8, 1, None) == -1
+    # unknown render flags / objective
+    assert lib.pgsag_render_fwd(1, ctypes.c_void_p(16), None, None, None, None, 0, None, None, 8, None, None, None,
+                                ctypes.c_void_p(16), None) == -5
+    assert lib.pgsag_loss_ban(1, None, 0, None, None, None, None, None, None, None, None, None, 0.01, None, 0, None,
+                              None, None, None, None, None, 7, 0, None, None, None) == -5
+    # the Eq. 11 objective needs the GC weights and the deferred gather
+    st = ctypes.c_void_p(16)
+    assert lib.pgsag_loss_ban(1, st, 0, None, None, None, None, None, None, None, None, None, 0.01, None, 0, None,
+                              st, None, st, None, None, 1, 0, None, st, None) == -1
+    # voting filter: too many views, missing buffers, bad view table
+    assert lib.pgsag_vote_filter(10, None, 300, None, None, 3, 0, None, None, None, st, None) == -5
+    assert lib.pgsag_vote_filter(10, None, 1, None, None, 3, 0, None, None, None, st, None) == -1
+    v = L.PgsagVoteView()
+    v.width, v.height, v.words_per_row = 100, 10, 3   # 3 words < 100 pixels
+    assert lib.pgsag_vote_filter(10, st, 1, ctypes.byref(v), st, 3, 0, st, st, st, st, None) == -1
+    assert lib.pgsag_vote_pack_mask(100, 10, st, 3, st, None) == -1
+    assert lib.pgsag_vote_compact_workspace_size(0) == 4
+    assert lib.pgsag_vote_compact_workspace_size(4097) == 8

@@ -621,3 +621,124 @@ def vote_workload(n_points: int = 1_000_000, n_views: int = 32, width: int = 547
             t = np.repeat(np.repeat(t, mask_step, 0), mask_step, 1)[:height, :width]
         masks.append(coarse_mask(rm, np.ascontiguousarray(t)))
     return VoteWorkload(pts, onb, cams, masks, tau)
+
+
+# --------------------------------------------------------------------------
+# depth maps for the TSDF workload (Sec. 4.4): building and background depth
+# maps of many views, ray-cast from the box scene
+# --------------------------------------------------------------------------
+
+TSDF_CONFIG_INDEX = 6
+
+
+def raycast_depth(boxes: Sequence[Box], cam: Camera, ground: float = 200.0, step: int = 1):
+    """Camera-z depth of the nearest hit (boxes and the ground square z = 0 of side
+    `ground`) for each pixel centre of a `step` grid, 0 where the ray hits
+    nothing, and whether that nearest hit is a box."""
+    H, W = cam.height, cam.width
+    R = cam.R.astype(np.float64)
+    t = cam.t.astype(np.float64)
+    C = -R.T @ t
+    us = np.arange(0, W, step) + 0.5
+    vs = np.arange(0, H, step) + 0.5
+    uu, vv = np.meshgrid(us, vs)
+    dcam = np.stack([(uu - cam.cx) / cam.fx, (vv - cam.cy) / cam.fy, np.ones_like(uu)], -1)
+    dw = dcam @ R  # R^T d: a hit at C + z dw has camera depth z
+    depth = np.full(uu.shape, np.inf)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        zg = -C[2] / dw[..., 2]
+        gx, gy = C[0] + zg * dw[..., 0], C[1] + zg * dw[..., 1]
+        okg = (zg > 0) & (np.abs(gx) <= ground / 2) & (np.abs(gy) <= ground / 2)
+    depth = np.where(okg, zg, depth)
+    isbox = np.zeros(uu.shape, bool)
+    for b in boxes:
+        lo = np.array([b.x0, b.y0, 0.0])
+        hi = np.array([b.x1, b.y1, b.h])
+        # pixel rectangle of the projected box (whole grid if a corner is behind)
+        corners = np.array([[x, y, z] for x in (b.x0, b.x1) for y in (b.y0, b.y1) for z in (0.0, b.h)])
+        pc = corners @ R.T + t
+        if np.all(pc[:, 2] <= 1e-6):
+            continue
+        if np.any(pc[:, 2] <= 1e-6):
+            iu = np.arange(len(us))
+            iv = np.arange(len(vs))
+        else:
+            px = cam.fx * pc[:, 0] / pc[:, 2] + cam.cx
+            py = cam.fy * pc[:, 1] / pc[:, 2] + cam.cy
+            iu = np.nonzero((us >= px.min() - 2) & (us <= px.max() + 2))[0]
+            iv = np.nonzero((vs >= py.min() - 2) & (vs <= py.max() + 2))[0]
+        if len(iu) == 0 or len(iv) == 0:
+            continue
+        sub = np.ix_(iv, iu)
+        d = dw[sub]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / d
+            t0 = (lo - C) * inv
+            t1 = (hi - C) * inv
+        tmin = np.nanmax(np.minimum(t0, t1), axis=-1)
+        tmax = np.nanmin(np.maximum(t0, t1), axis=-1)
+        cur = depth[sub]
+        hit = (tmax >= np.maximum(tmin, 0.0)) & (tmin > 0) & (tmin < cur)
+        depth[sub] = np.where(hit, tmin, cur)
+        isbox[sub] |= hit
+    depth = np.where(np.isfinite(depth), depth, 0.0)
+    return depth.astype(np.float32), isbox
+
+
+@dataclasses.dataclass
+class TsdfWorkload:
+    cams: List[Camera]
+    building: List[np.ndarray]     # float32 [H,W] building depth maps (0 = none)
+    background: List[np.ndarray]   # float32 [H,W] background depth maps (0 = none)
+    origin: Tuple[float, float, float]
+    voxel: float
+    dims: Tuple[int, int, int]     # nx, ny, nz
+    trunc: float
+
+
+def tsdf_workload(n_views: int = 32, width: int = 2736, height: int = 1824, voxel: float = 0.25,
+                  step: int = 2, band: int = 3, noise: float = 0.01, coverage: float = 0.35) -> TsdfWorkload:
+    """The config-1 building scene (40 boxes, footprints rescaled to ~35% mask
+    coverage in the first view) seen by n_views oblique aerial cameras circling
+    it; per view a building depth map (the ray-cast depth on the building pixels
+    dilated by `band` pixels) and a background depth map (on the pixels outside
+    the building mask eroded by `band`), each with independent N(0, noise) m
+    jitter, so they overlap in a band around every building outline.  The grid
+    covers the 160 x 160 m block up to 50 m at `voxel` m, truncation 4 voxels."""
+    from scipy import ndimage
+    rs, rc, rm, _ = streams(TSDF_CONFIG_INDEX)
+
+    def cams_fn(r):
+        cams = []
+        for j in range(n_views):
+            az = 360.0 * j / max(n_views, 1) + r.uniform(-5.0, 5.0)
+            look = (r.uniform(-30.0, 30.0), r.uniform(-30.0, 30.0), 0.0)
+            cams.append(aerial_camera(width, height, 120.0 + r.uniform(-10.0, 10.0), (45.0, 60.0)[j % 2], az, look))
+        return cams
+
+    scale = 1.0
+    state, cstate = rs.bit_generator.state, rc.bit_generator.state
+    for _ in range(6):
+        rs.bit_generator.state, rc.bit_generator.state = state, cstate
+        boxes = random_boxes(rs, 40, area=160.0, footprint_scale=scale)
+        cams = cams_fn(rc)
+        cov = raycast_box_mask(boxes, cams[0], step=max(1, min(16, width // 64))).mean() if cams else coverage
+        if abs(cov - coverage) <= 0.05:
+            break
+        scale = min(2.0, max(0.25, scale * math.sqrt(coverage / max(cov, 1e-3))))
+    bld, bkg = [], []
+    for c in cams:
+        d, isbox = raycast_depth(boxes, c, 200.0, step)
+        if step > 1:
+            d = np.repeat(np.repeat(d, step, 0), step, 1)[:height, :width]
+            isbox = np.repeat(np.repeat(isbox, step, 0), step, 1)[:height, :width]
+        mb = ndimage.binary_dilation(isbox, iterations=band)
+        mg = ~ndimage.binary_erosion(isbox, iterations=band)
+        has = d > 0
+        b = np.where(mb & has, d + rm.normal(0.0, noise, d.shape), 0.0)
+        g = np.where(mg & has, d + rm.normal(0.0, noise, d.shape), 0.0)
+        bld.append(np.maximum(b, 0.0).astype(np.float32))
+        bkg.append(np.maximum(g, 0.0).astype(np.float32))
+    nx = ny = int(round(160.0 / voxel))
+    nz = int(round(50.0 / voxel))
+    return TsdfWorkload(cams, bld, bkg, (-80.0, -80.0, -1.0), voxel, (nx, ny, nz), 4 * voxel)

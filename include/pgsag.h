@@ -584,6 +584,68 @@ size_t pgsag_vote_compact_workspace_size(uint32_t n_points);
 int pgsag_vote_compact(uint32_t n_points, const uint8_t* reliable, uint32_t* idx, uint32_t* n_out,
                        void* workspace, size_t workspace_bytes, int32_t* status, void* stream);
 
+/*
+ * ---------------------------------------------------------------------------
+ * Depth-map fusion and TSDF integration (Sec. 4.4, "Mesh Extraction and Merge"):
+ * the building and background depth maps of every view are fused by their mean
+ * where they overlap, then integrated into a truncated signed distance function
+ * on a regular voxel grid (the TSDF method, by citation), from which a mesher
+ * extracts the surface (mesh extraction is not part of the library).
+ *
+ * Voxel (i, j, k) (x fastest, linear index i + nx (j + ny k)) has its centre at
+ * origin + ((i, j, k) + 1/2) voxel.  Per view the centre is projected like a
+ * voting-filter point (x_c = R c + t, in front iff z_c > znear, pixel
+ * (floor u, floor v) inside the image); where that pixel holds a depth d (> 0,
+ * finite), sdf = d - z_c; the view is integrated iff sdf >= -trunc, with value
+ * min(1, sdf / trunc) and weight 1.  The TSDF is the weighted mean of the
+ * integrated values; voxels with weight 0 hold 1.  The decisions (in front, inside,
+ * which pixel, valid depth, sdf >= -trunc) are taken in float32 with one correctly
+ * rounded operation per step in the order c = origin + ((i + 1/2) voxel),
+ * x_c = ((R00 c_x + R01 c_y) + R02 c_z) + t0, iz = 1 / z_c, u = fx (x_c iz) + cx,
+ * sdf = d - z_c, so they are reproducible off the GPU.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct pgsag_depth_view {
+  float R[9];              /* world -> camera rotation, row-major: x_c = R x_w + t */
+  float t[3];
+  float fx, fy, cx, cy;
+  float znear;
+  int32_t width, height;   /* > 0                                                   */
+  uint32_t reserved[3];    /* zero                                                  */
+  uint64_t depth_offset;   /* first float of this view's depth map [height, width]  */
+} pgsag_depth_view;        /* 96 bytes */
+
+typedef struct pgsag_tsdf_grid {
+  float origin[3];         /* world position of the grid's low corner               */
+  float voxel;             /* voxel edge length (> 0)                               */
+  uint32_t nx, ny, nz;     /* voxels per axis (nx * ny * nz < 2^32)                 */
+  float trunc;             /* truncation distance (> 0)                             */
+} pgsag_tsdf_grid;         /* 32 bytes */
+
+#define PGSAG_TSDF_MAX_VIEWS 256  /* views per pgsag_tsdf_integrate call */
+
+/*
+ * pgsag_depth_fuse: out[p] = mean of maps[m * n_pix + p] over the maps whose
+ * value there is > 0 and finite; 0 where none is.  maps: float32 [n_maps, n_pix]
+ * (device), 1 <= n_maps <= 8; out: float32 [n_pix] (may not alias maps).
+ */
+int pgsag_depth_fuse(uint32_t n_maps, const float* maps, uint64_t n_pix, float* out, void* stream);
+
+/*
+ * pgsag_tsdf_integrate: integrate n_views <= PGSAG_TSDF_MAX_VIEWS depth maps
+ * into the grid.
+ *   grid, views: HOST structs (copied into the launch; validated: voxel, trunc,
+ *     width, height > 0, grid size < 2^32).
+ *   depth: float32 depth maps (device), view v's at views[v].depth_offset.
+ *   tsdf, weight: float32 [nz, ny, nx] (device).  accumulate = 0: overwritten
+ *     (weight = number of integrated views, tsdf = their mean value, 1 where the
+ *     weight is 0); 1: the new views are merged into the running weighted mean
+ *     (w' = w + n, t' = (t w + sum) / w'; voxels no new view reaches unchanged).
+ */
+int pgsag_tsdf_integrate(const pgsag_tsdf_grid* grid, uint32_t n_views, const pgsag_depth_view* views,
+                         const float* depth, int accumulate, float* tsdf, float* weight, int32_t* status,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

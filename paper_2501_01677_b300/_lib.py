@@ -28,7 +28,9 @@ EXPORTS = (
     "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_tile_stats_noalloc",
     "pgsag_schedule_lpt", "pgsag_adam",
     "pgsag_vote_pack_mask", "pgsag_vote_filter", "pgsag_vote_compact_workspace_size", "pgsag_vote_compact",
+    "pgsag_depth_fuse", "pgsag_tsdf_integrate",
 )
+TSDF_MAX_VIEWS = 256
 VOTE_MAX_VIEWS = 256
 
 
@@ -79,6 +81,26 @@ class PgsagVoteView(ctypes.Structure):
 assert ctypes.sizeof(PgsagVoteView) == 96
 
 
+class PgsagDepthView(ctypes.Structure):
+    """pgsag_depth_view: one camera and depth map of the TSDF integration (Sec. 4.4)."""
+    _fields_ = [
+        ("R", c_float * 9), ("t", c_float * 3),
+        ("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float), ("znear", c_float),
+        ("width", c_int32), ("height", c_int32), ("reserved", c_uint32 * 3), ("depth_offset", c_uint64),
+    ]
+
+
+assert ctypes.sizeof(PgsagDepthView) == 96
+
+
+class PgsagTsdfGrid(ctypes.Structure):
+    _fields_ = [("origin", c_float * 3), ("voxel", c_float), ("nx", c_uint32), ("ny", c_uint32), ("nz", c_uint32),
+                ("trunc", c_float)]
+
+
+assert ctypes.sizeof(PgsagTsdfGrid) == 32
+
+
 _lib = None
 
 
@@ -125,6 +147,9 @@ def load(path: str = LIB_PATH):
          [c_uint32, P, c_uint32, POINTER(PgsagVoteView), P, c_uint32, c_int, P, P, P, P, P])
     _sig(lib, "pgsag_vote_compact_workspace_size", c_size_t, [c_uint32])
     _sig(lib, "pgsag_vote_compact", c_int, [c_uint32, P, P, P, P, c_size_t, P, P])
+    _sig(lib, "pgsag_depth_fuse", c_int, [c_uint32, P, c_uint64, P, P])
+    _sig(lib, "pgsag_tsdf_integrate", c_int,
+         [POINTER(PgsagTsdfGrid), c_uint32, POINTER(PgsagDepthView), P, c_int, P, P, P, P])
     _lib = lib
     return lib
 

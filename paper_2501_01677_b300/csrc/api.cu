@@ -6,6 +6,8 @@
 #define PGSAG_VIEW_BYTES 152
 static_assert(sizeof(pgsag_view) == PGSAG_VIEW_BYTES, "pgsag_view layout");
 static_assert(sizeof(pgsag_vote_view) == 96, "pgsag_vote_view layout");
+static_assert(sizeof(pgsag_depth_view) == 96, "pgsag_depth_view layout");
+static_assert(sizeof(pgsag_tsdf_grid) == 32, "pgsag_tsdf_grid layout");
 
 extern "C" const char* pgsag_status_str(int status) {
   switch (status) {

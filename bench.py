@@ -46,13 +46,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="aerial",
-                    choices=["aerial", "aerial-crop2048", "batched", "capacity", "vote"],
+                    choices=["aerial", "aerial-crop2048", "batched", "capacity", "vote", "tsdf"],
                     help="aerial: the 5472x3648 view; aerial-crop2048: its 2048x2048 window with the most "
                          "mask pixels, all 1.5M Gaussians (a smaller case for profiler captures); batched: 8 "
                          "uneven sub-regions (200k-3M Gaussians) x 4 mixed-resolution views, one graph-captured "
                          "persistent step vs 32 sequential per-view steps; capacity: 12 sub-regions, 20M "
                          "Gaussians, 72 views at 6000x4000 with Adam; vote: the multi-view voting filter, 1M "
-                         "sparse points against 32 coarse masks at 5472x3648")
+                         "sparse points against 32 coarse masks at 5472x3648; tsdf: mean fusion of 32 building / "
+                         "background depth-map pairs at 2736x1824 and their TSDF integration into 640x640x200 voxels")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: fraction of the Gaussians")
     ap.add_argument("--objective", default="pg", choices=["pg", "eq11"],
                     help="aerial workloads: pg = L_rgb + lambda_4 L_ban (GC-load value only); eq11 = Eq. 11 with "
@@ -830,6 +831,138 @@ def vote_bench(args):
         dist.destroy_process_group()
 
 
+TSDF_METRIC = "TSDF integration Gvoxel-views/s (voxels x views / s), 640x640x200 voxels x 32 views @2736x1824"
+TSDF_UNIT = "Gvoxel-views/s"
+
+
+def tsdf_bench(args):
+    """Depth-map fusion and TSDF integration (Sec. 4.4): per step, one fusion
+    launch over the 32 building / background depth-map pairs (2736x1824) and one
+    integration launch of the 32 fused maps into a 640x640x200 grid at 0.25 m
+    (overwrite).  Inputs (two 640 MB map stacks) and the grids (655 MB) are larger
+    than L2."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import pgsag_synth as syn
+    from paper_2501_01677_b300 import tsdf as T
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    w = syn.tsdf_workload()
+    V = len(w.cams)
+    H, W = w.cams[0].height, w.cams[0].width
+    npix = H * W
+    host_maps = np.stack([np.stack(w.building), np.stack(w.background)]).reshape(2, V * npix)
+    maps = torch.from_numpy(host_maps).cuda()
+    fused = torch.empty(V * npix, dtype=torch.float32, device="cuda")
+    nx, ny, nz = w.dims
+    nvox = nx * ny * nz
+    tsdf = torch.empty(nz, ny, nx, dtype=torch.float32, device="cuda")
+    weight = torch.empty_like(tsdf)
+    g = T.grid(w.origin, w.voxel, w.dims, w.trunc)
+    offs = [v * npix for v in range(V)]
+    table = T.depth_views(w.cams, offs)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        T.fuse(maps, out=fused)
+        T.integrate(g, w.cams, fused, offs, tsdf, weight, status=status, table=table)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for e in ev:
+        e[0].record(stream)
+        T.fuse(maps, out=fused)
+        e[1].record(stream)
+        T.integrate(g, w.cams, fused, offs, tsdf, weight, status=status, table=table)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms_step = sum(e[0].elapsed_time(e[2]) for e in ev)
+    ms_fuse = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    ms_int = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    ms, value = aggregate(ms_step, nvox * V / 1e9, args.steps, ws, dist if ws > 1 else None, device="cuda")
+    # end to end: both map stacks from pinned host memory, the TSDF grid back
+    hm = torch.from_numpy(host_maps).pin_memory()
+    ht = torch.empty(nz, ny, nx, dtype=torch.float32, pin_memory=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = min(args.steps, 5)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(n_e2e):
+        maps.copy_(hm, non_blocking=True)
+        step()
+        ht.copy_(tsdf, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e, v_e2e = aggregate(a.elapsed_time(b), nvox * V / 1e9, n_e2e, ws, dist if ws > 1 else None,
+                              device="cuda")
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    pk, pk_src = peaks()
+    alu = measured_alu_peaks()
+    ffma = max(alu["ffma_tflops"], alu["ffma2_tflops"]) if alu else fp32_peak_tflops(2032.0)
+    # per (voxel, view): the projection (25 unfused FP32 operations) and the sdf
+    # (1 sub, 1 div, 1 min, 1 add); per voxel: the centre (6 ops)
+    flops = 29 * nvox * V + 6 * nvox
+    alu_ach = flops / (ms_int / 1e3) / 1e12
+    bytes_int = 4 * V * npix + 8 * nvox      # fused maps read once, tsdf + weight written
+    bytes_fuse = 3 * 4 * V * npix             # two maps read, one written
+    hbm_int = bytes_int / (ms_int / 1e3) / 1e9
+    hbm_fuse = bytes_fuse / (ms_fuse / 1e3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_tsdf", "achieved": alu_ach, "peak": ffma / 2, "unit": "TFLOP/s",
+                "frac": alu_ach / (ffma / 2),
+                "peak_source": "half the FP32 FMA throughput measured in this run (separate mul / add, no FMA)",
+                "algorithmic_flops": flops, "ms_per_launch": ms_int,
+                "hbm": {"achieved": hbm_int, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm_int / pk["hbm_gbs"],
+                        "peak_source": pk_src, "algorithmic_bytes": bytes_int},
+                "fuse": {"kernel": "k_depth_fuse", "bound": "hbm", "ms_per_launch": ms_fuse, "achieved": hbm_fuse,
+                         "peak": pk["hbm_gbs"], "frac": hbm_fuse / pk["hbm_gbs"], "algorithmic_bytes": bytes_fuse},
+                "traffic": read_traffic("k_tsdf", "traffic_tsdf_640x640x200.txt")}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        from oracle import tsdf_oracle as TO
+        fused_o = [TO.fuse_mean([bm, gm]).astype(np.float32) for bm, gm in zip(w.building, w.background)]
+        idx = np.random.default_rng(0).choice(nvox, 2_000_000, replace=False)
+        t0 = time.perf_counter()
+        TO.integrate(w.origin, w.voxel, w.dims, w.trunc, w.cams, fused_o, voxel_index=idx)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": len(idx) * V / 1e9 / t_cpu, "unit": TSDF_UNIT, "cores": 1, "kind": "oracle",
+               "sample": "2,000,000 random voxels of the grid x all 32 views (numpy, one thread; fusion excluded)",
+               "s_per_step": t_cpu}
+    res = {
+        "metric": TSDF_METRIC, "value": value, "unit": TSDF_UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "depth fusion + TSDF: 32 building / background depth-map pairs at %dx%d of the "
+                               "40-building scene, grid %dx%dx%d at %.2f m, truncation %.2f m"
+                               % (W, H, nx, ny, nz, w.voxel, w.trunc),
+                   "views": V, "voxels": nvox, "l2": "inputs larger than L2 (maps 1.28 GB, grids 655 MB)"},
+        "roofline": roofline, "stages_ms": {"fuse": ms_fuse, "integrate": ms_int}, "cpu_baseline": cpu,
+        "e2e": {"value": v_e2e, "unit": TSDF_UNIT, "h2d_bytes_per_step": int(host_maps.nbytes),
+                "d2h_bytes_per_step": 4 * nvox, "ms_per_step": ms_e2e / n_e2e},
+        "gpu_launches": 2 * args.steps, "clocks": ck,
+    }
+    print(json.dumps(res))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -859,5 +992,7 @@ if __name__ == "__main__":
         capacity(a)
     elif a.workload == "vote":
         vote_bench(a)
+    elif a.workload == "tsdf":
+        tsdf_bench(a)
     else:
         ours(a)

@@ -1,12 +1,17 @@
 // Depth-map mean fusion and TSDF integration (Sec. 4.4).
 //
-// Integration is voxel-parallel with every view of a call in one launch: each
-// thread owns kTsdfVPT voxels (consecutive threads take consecutive x, so grid
-// reads and writes are coalesced), keeps their running sums and counts in
-// registers while it sweeps the views in order, and touches the grids once at
-// the end -- one read and one write of tsdf / weight per call instead of one
-// per view.  All CTAs walk the same view sequence at about the same time, so
-// the depth map being read stays in L2.  The camera table is a
+// Integration is voxel-parallel: each thread owns kTsdfVPT voxels (consecutive
+// threads take consecutive x, so grid reads and writes are coalesced), keeps
+// their running sums and counts in registers while it sweeps a chunk of views,
+// and touches the grids once per chunk.  A voxel's samples of one view are
+// spread over the whole depth map (the rays of a column of voxels meet the same
+// pixels), so each map is re-read about as often as voxels project into it; the
+// views are therefore taken in chunks whose maps fit in the L2 together (one
+// launch per chunk, later chunks merged into the running mean): inside a launch
+// the CTAs drift over at most one chunk of views, and a map comes from HBM a few
+// times at most.  On the 32-view bench workload (20 MB maps, 126 MB L2) a
+// single launch over all views read 97 GB from HBM and took 17.3 ms; chunks of
+// 6 / 3 / 1 views take 7.8 / 8.7 / 12.8 ms (more chunks: more grid passes).  The camera table is a
 // __grid_constant__ kernel parameter (constant-cache broadcast).  The
 // projection, the pixel choice and the sdf >= -trunc test are a fixed sequence
 // of correctly rounded float32 operations (reproducible off the GPU).
@@ -17,6 +22,9 @@
 namespace pgsag {
 
 constexpr int kTsdfThreads = 256;
+#ifndef PGSAG_TSDF_L2_DIV
+#define PGSAG_TSDF_L2_DIV 1  // depth maps of one launch: at most L2 / this many bytes
+#endif
 constexpr int kTsdfVPT = 4;  // voxels per thread
 
 template <int kMaxViews>
@@ -24,24 +32,54 @@ struct DepthTable {
   pgsag_depth_view v[kMaxViews];
 };
 
-__global__ void __launch_bounds__(256) k_depth_fuse(uint32_t n_maps, const float* __restrict__ maps, uint64_t n_pix,
-                                                    float* __restrict__ out) {
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pix; p += (uint64_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    uint32_t n = 0;
-    for (uint32_t m = 0; m < n_maps; ++m) {
-      const float d = __ldg(maps + (uint64_t)m * n_pix + p);
-      if (d > 0.f && d < INFINITY) {
-        s += d;
-        ++n;
-      }
-    }
-    out[p] = n ? s / (float)n : 0.f;
+__device__ __forceinline__ void fuse_add(float d, float& s, float& n) {
+  if (d > 0.f && d < INFINITY) {
+    s += d;
+    n += 1.f;
   }
 }
 
+// kVec: 4 pixels per thread and iteration through 16-byte loads and stores (maps
+// and out 16-byte aligned, n_pix a multiple of 4), all maps' loads in flight
+// before the sums.
+template <bool kVec>
+__global__ void __launch_bounds__(256) k_depth_fuse(uint32_t n_maps, const float* __restrict__ maps, uint64_t n_pix,
+                                                    float* __restrict__ out) {
+  if constexpr (kVec) {
+    const uint64_t n4 = n_pix / 4;
+    const float4* m4 = reinterpret_cast<const float4*>(maps);
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n4; p += (uint64_t)gridDim.x * blockDim.x) {
+      float4 v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+        if (m < (int)n_maps) v[m] = __ldg(m4 + (uint64_t)m * n4 + p);
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f), n = s;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        if (m >= (int)n_maps) break;
+        fuse_add(v[m].x, s.x, n.x);
+        fuse_add(v[m].y, s.y, n.y);
+        fuse_add(v[m].z, s.z, n.z);
+        fuse_add(v[m].w, s.w, n.w);
+      }
+      reinterpret_cast<float4*>(out)[p] = make_float4(n.x > 0.f ? s.x / n.x : 0.f, n.y > 0.f ? s.y / n.y : 0.f,
+                                                      n.z > 0.f ? s.z / n.z : 0.f, n.w > 0.f ? s.w / n.w : 0.f);
+    }
+  } else {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pix;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+      float s = 0.f, n = 0.f;
+      for (uint32_t m = 0; m < n_maps; ++m) fuse_add(__ldg(maps + (uint64_t)m * n_pix + p), s, n);
+      out[p] = n > 0.f ? s / n : 0.f;
+    }
+  }
+}
+
+#ifndef PGSAG_TSDF_MINB
+#define PGSAG_TSDF_MINB 1
+#endif
 template <int kMaxViews>
-__global__ void __launch_bounds__(kTsdfThreads) k_tsdf(pgsag_tsdf_grid G, uint32_t n_views,
+__global__ void __launch_bounds__(kTsdfThreads, PGSAG_TSDF_MINB) k_tsdf(pgsag_tsdf_grid G, uint32_t n_views,
                                                        const __grid_constant__ DepthTable<kMaxViews> T,
                                                        const float* __restrict__ depth, int accumulate,
                                                        float* __restrict__ tsdf, float* __restrict__ weight,
@@ -50,7 +88,7 @@ __global__ void __launch_bounds__(kTsdfThreads) k_tsdf(pgsag_tsdf_grid G, uint32
   const uint32_t nvox = G.nx * G.ny * G.nz;
   constexpr uint32_t kGroup = (uint32_t)(kTsdfThreads * kTsdfVPT);
   const uint32_t n_groups = (nvox + kGroup - 1) / kGroup;
-  const float mu = G.trunc, nmu = -G.trunc;
+  const float nmu = -G.trunc, imu = 1.f / G.trunc;  // the value sdf / trunc is taken as sdf * (1 / trunc)
   for (uint32_t grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
     const uint32_t base = grp * kGroup + threadIdx.x;
     float X[kTsdfVPT], Y[kTsdfVPT], Z[kTsdfVPT], sum[kTsdfVPT];
@@ -96,7 +134,7 @@ __global__ void __launch_bounds__(kTsdfThreads) k_tsdf(pgsag_tsdf_grid G, uint32
       for (int k = 0; k < kTsdfVPT; ++k) {
         const float sdf = __fsub_rn(d[k], zc[k]);
         if (in[k] && d[k] > 0.f && d[k] < INFINITY && sdf >= nmu) {
-          sum[k] += fminf(1.f, __fdiv_rn(sdf, mu));
+          sum[k] += fminf(1.f, __fmul_rn(sdf, imu));
           cnt[k] += 1u;
         }
       }
@@ -127,9 +165,14 @@ extern "C" int pgsag_depth_fuse(uint32_t n_maps, const float* maps, uint64_t n_p
   if (n_maps == 0 || n_maps > 8) return PGSAG_ERR_UNSUPPORTED;
   if (n_pix == 0) return PGSAG_OK;
   if (!maps || !out) return PGSAG_ERR_ARG;
-  const uint64_t want = (n_pix + 255) / 256;
+  const bool vec = (n_pix % 4 == 0) && !(((uintptr_t)maps | (uintptr_t)out) & 15u);
+  const uint64_t items = vec ? n_pix / 4 : n_pix;
+  const uint64_t want = (items + 255) / 256;
   const unsigned blocks = (unsigned)(want < 148ull * 16ull ? want : 148ull * 16ull);
-  k_depth_fuse<<<blocks, 256, 0, (cudaStream_t)stream>>>(n_maps, maps, n_pix, out);
+  if (vec)
+    k_depth_fuse<true><<<blocks, 256, 0, (cudaStream_t)stream>>>(n_maps, maps, n_pix, out);
+  else
+    k_depth_fuse<false><<<blocks, 256, 0, (cudaStream_t)stream>>>(n_maps, maps, n_pix, out);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }
@@ -174,6 +217,31 @@ extern "C" int pgsag_tsdf_integrate(const pgsag_tsdf_grid* grid, uint32_t n_view
   for (uint32_t v = 0; v < n_views; ++v)
     if (views[v].width <= 0 || views[v].height <= 0) return PGSAG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  if (n_views <= 32) return launch_tsdf<32>(G, n_views, views, depth, accumulate, tsdf, weight, status, s);
-  return launch_tsdf<PGSAG_TSDF_MAX_VIEWS>(G, n_views, views, depth, accumulate, tsdf, weight, status, s);
+  if (n_views == 0)
+    return launch_tsdf<32>(G, 0, views, depth, accumulate, tsdf, weight, status, s);
+  static int l2 = -1;
+  if (l2 < 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PGSAG_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) return PGSAG_ERR_CUDA;
+  }
+  const uint64_t budget = (uint64_t)(l2 > 0 ? l2 : (64 << 20)) / PGSAG_TSDF_L2_DIV;
+  uint32_t v0 = 0;
+  int acc = accumulate;
+  while (v0 < n_views) {
+    // the longest run of views (at least one, at most 32) whose maps fit the budget
+    uint32_t n = 0;
+    uint64_t bytes = 0;
+    while (v0 + n < n_views && n < 32) {
+      const uint64_t b = 4ull * (uint64_t)views[v0 + n].width * (uint64_t)views[v0 + n].height;
+      if (n > 0 && bytes + b > budget) break;
+      bytes += b;
+      ++n;
+    }
+    const int r = launch_tsdf<32>(G, n, views + v0, depth, acc, tsdf, weight, status, s);
+    if (r) return r;
+    v0 += n;
+    acc = 1;
+  }
+  return PGSAG_OK;
 }

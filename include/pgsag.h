@@ -508,6 +508,28 @@ int pgsag_adam(uint64_t n, float* p, const float* g, float* m, float* v, float l
                float beta2, float eps, int32_t step, void* stream);
 
 /*
+ * pgsag_adam_multi: the same update for up to PGSAG_ADAM_MAX_TENSORS tensors
+ * (each with its own learning rate) in one launch, with the step count in device
+ * memory, so a captured CUDA graph of a training iteration can be replayed as is.
+ *   tensors: HOST array (copied into the launch); p, g, m, v device float32 [n].
+ *   step: device int32 [4]: step[0] is the step count, advanced by one per call
+ *         before the update (start it at 0); step[1], step[2] receive the bias
+ *         corrections of the new step (float bits); step[3] unused.
+ */
+typedef struct pgsag_adam_tensor {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  uint64_t n;
+  float lr;
+  uint32_t reserved;       /* 0 */
+} pgsag_adam_tensor;       /* 48 bytes */
+#define PGSAG_ADAM_MAX_TENSORS 8
+int pgsag_adam_multi(uint32_t n_tensors, const pgsag_adam_tensor* tensors, float beta1, float beta2, float eps,
+                     int32_t* step, int32_t* status, void* stream);
+
+/*
  * ---------------------------------------------------------------------------
  * Reliability-scored multi-view voting filter (Sec. 4.1, Eq. 5-7).  The step
  * before optimisation that refines coarse building masks: every sparse SfM point

@@ -28,7 +28,7 @@ EXPORTS = (
     "pgsag_render_bwd", "pgsag_preprocess_bwd", "pgsag_tile_stats", "pgsag_tile_stats_noalloc",
     "pgsag_schedule_lpt", "pgsag_adam",
     "pgsag_vote_pack_mask", "pgsag_vote_filter", "pgsag_vote_compact_workspace_size", "pgsag_vote_compact",
-    "pgsag_depth_fuse", "pgsag_tsdf_integrate",
+    "pgsag_depth_fuse", "pgsag_tsdf_integrate", "pgsag_adam_multi",
 )
 TSDF_MAX_VIEWS = 256
 VOTE_MAX_VIEWS = 256
@@ -93,6 +93,14 @@ class PgsagDepthView(ctypes.Structure):
 assert ctypes.sizeof(PgsagDepthView) == 96
 
 
+class PgsagAdamTensor(ctypes.Structure):
+    _fields_ = [("p", c_void_p), ("g", c_void_p), ("m", c_void_p), ("v", c_void_p), ("n", c_uint64),
+                ("lr", c_float), ("reserved", c_uint32)]
+
+
+assert ctypes.sizeof(PgsagAdamTensor) == 48
+
+
 class PgsagTsdfGrid(ctypes.Structure):
     _fields_ = [("origin", c_float * 3), ("voxel", c_float), ("nx", c_uint32), ("ny", c_uint32), ("nz", c_uint32),
                 ("trunc", c_float)]
@@ -148,6 +156,7 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_vote_compact_workspace_size", c_size_t, [c_uint32])
     _sig(lib, "pgsag_vote_compact", c_int, [c_uint32, P, P, P, P, c_size_t, P, P])
     _sig(lib, "pgsag_depth_fuse", c_int, [c_uint32, P, c_uint64, P, P])
+    _sig(lib, "pgsag_adam_multi", c_int, [c_uint32, POINTER(PgsagAdamTensor), c_float, c_float, c_float, P, P, P])
     _sig(lib, "pgsag_tsdf_integrate", c_int,
          [POINTER(PgsagTsdfGrid), c_uint32, POINTER(PgsagDepthView), P, c_int, P, P, P, P])
     _lib = lib

@@ -31,6 +31,11 @@ to rounding).  Passages followed:
 * Sec. 4.3, Eq. 9 with a differentiable count: g~_i = sum of the alphas of the
   Gaussians blended into pixel i (the integer count g_i has no gradient; the
   soft count is the surrogate that lets the GC-load term shape the Gaussians).
+* L_rgb with D-SSIM (3DGS by citation, "only the refined building masks are
+  involved"): L_rgb = (1 - 0.2) L1 + 0.2 (1 - SSIM_M), SSIM_M = mean over the mask
+  pixels and the 3 channels of the SSIM map; the SSIM window is 3DGS's 11 x 11
+  Gaussian (sigma 1.5) restricted to the rendered set R and renormalised over it
+  (the rendered image exists on R only), C1 = 0.01^2, C2 = 0.03^2.
 
 Readings of passages where the paper is silent (3DGS constants by citation):
 alpha = min(0.99, o exp(-1/2 d^T Q d)); a Gaussian enters a pixel iff
@@ -66,6 +71,9 @@ W_BOUNDARY = 0.1
 LAMBDA_GC = 0.41
 LAMBDA_BAN = 0.01
 LAMBDA_FLAT = 100.0
+LAMBDA_DSSIM = 0.2          # 3DGS: L_rgb = (1 - 0.2) L1 + 0.2 D-SSIM
+SSIM_C1, SSIM_C2 = 0.01 ** 2, 0.03 ** 2
+SSIM_RADIUS, SSIM_SIGMA = 5, 1.5
 # Validity threshold for Eq. 4 (ray-plane intersection must be in front)
 RAY_DOT_MIN = 1e-8
 # Relative window inside which a float32 threshold decision may legitimately flip
@@ -447,7 +455,7 @@ def dense(vals: torch.Tensor, pu, pv, H, W):
 # losses (Eq. 8, L1 photometric term, Eq. 9)
 # ---------------------------------------------------------------------------
 
-def losses(out, depth, valid, pix, sets, cam: Cam, target: np.ndarray):
+def losses(out, depth, valid, pix, sets, cam: Cam, target: np.ndarray, dssim: bool = False):
     """L_rgb = mean over M of |C - C*|_1 / 3.
 
     L_ban (Eq. 8) = (1/|V|) sum_{i in V} w_i || n_depth,i - n_r,i ||^2 with
@@ -469,6 +477,9 @@ def losses(out, depth, valid, pix, sets, cam: Cam, target: np.ndarray):
     tgt = torch.from_numpy(np.asarray(target, np.float64))
     nM = int(M.sum())
     l_rgb = (C - tgt).abs().sum(-1)[Mt].sum() / (3.0 * max(nM, 1)) if nM else torch.zeros((), dtype=DT) + 0 * C.sum()
+    ssim_m = None
+    if dssim:
+        l_rgb, ssim_m = l_rgb_dssim(C, tgt, M, R)
 
     # back-projected points
     uu = torch.arange(W, dtype=DT)[None, :].expand(H, W)
@@ -500,7 +511,53 @@ def losses(out, depth, valid, pix, sets, cam: Cam, target: np.ndarray):
     else:
         l_ban = torch.zeros((), dtype=DT) + 0 * C.sum()
     total = l_rgb + LAMBDA_BAN * l_ban
-    return dict(l_rgb=l_rgb, l_ban=l_ban, total=total, n_mask=nM, n_valid=nV)
+    return dict(l_rgb=l_rgb, l_ban=l_ban, total=total, n_mask=nM, n_valid=nV, ssim=ssim_m)
+
+
+def ssim_window() -> torch.Tensor:
+    """11 x 11 Gaussian window (sigma 1.5) summing to 1."""
+    r = torch.arange(-SSIM_RADIUS, SSIM_RADIUS + 1, dtype=DT)
+    g = torch.exp(-(r ** 2) / (2.0 * SSIM_SIGMA ** 2))
+    g = g / g.sum()
+    return g[:, None] * g[None, :]
+
+
+def masked_ssim_map(C: torch.Tensor, T: torch.Tensor, R: np.ndarray) -> torch.Tensor:
+    """SSIM per pixel and channel [H, W, 3] with the window restricted to the
+    rendered set R and renormalised: every moment is the weighted mean over the
+    rendered pixels of the window."""
+    G = ssim_window()[None, None]
+    Rt = torch.from_numpy(np.asarray(R, np.float64))
+    pad = SSIM_RADIUS
+
+    def blur(img):  # img [H, W] -> sum_k G(k - i) img(k), zero outside the image
+        return torch.nn.functional.conv2d(img[None, None], G, padding=pad)[0, 0]
+
+    Wsum = blur(Rt)
+    Wd = torch.where(Wsum > 0, Wsum, torch.ones_like(Wsum))
+    out = []
+    for c in range(3):
+        x, y = C[..., c] * Rt, T[..., c] * Rt
+        mx, my = blur(x) / Wd, blur(y) / Wd
+        sxx = blur(x * C[..., c]) / Wd - mx * mx
+        syy = blur(y * T[..., c]) / Wd - my * my
+        sxy = blur(x * T[..., c]) / Wd - mx * my
+        num = (2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)
+        den = (mx * mx + my * my + SSIM_C1) * (sxx + syy + SSIM_C2)
+        out.append(num / den)
+    return torch.stack(out, -1)
+
+
+def l_rgb_dssim(C: torch.Tensor, T: torch.Tensor, M: np.ndarray, R: np.ndarray):
+    """(1 - 0.2) L1 + 0.2 (1 - SSIM_M) over the mask pixels, and SSIM_M."""
+    Mt = torch.from_numpy(M)
+    nM = int(M.sum())
+    if nM == 0:
+        z = torch.zeros((), dtype=DT) + 0 * C.sum()
+        return z, z
+    l1 = (C - T).abs().sum(-1)[Mt].sum() / (3.0 * nM)
+    ssim_m = masked_ssim_map(C, T, R)[Mt].mean()
+    return (1.0 - LAMBDA_DSSIM) * l1 + LAMBDA_DSSIM * (1.0 - ssim_m), ssim_m
 
 
 def luminance_gradient_weight(target: np.ndarray) -> np.ndarray:
@@ -557,14 +614,15 @@ def objective_eq11(l_rgb, l_ban, l_s, l_gc):
 # whole step
 # ---------------------------------------------------------------------------
 
-def step(g, view, need_grad=True, retain_intermediate=False, objective="pg"):
+def step(g, view, need_grad=True, retain_intermediate=False, objective="pg", dssim=False):
     """Forward + loss (+ autograd backward) for one view of a synthetic scene `g`
     (pgsag_synth.Gaussians) and `view` (pgsag_synth.View).  Returns a dict with
     dense images, losses and parameter gradients.
 
     objective "pg": L_rgb + lambda_4 L_ban is differentiated (the GC-load value
     is reported by gc_load, without gradient).  "eq11": objective_eq11 with the
-    flattening loss and the soft-count GC-load, all differentiated."""
+    flattening loss and the soft-count GC-load, all differentiated.  dssim: L_rgb
+    takes the masked D-SSIM term (l_rgb_dssim)."""
     cam = Cam.from_synth(view.cam)
     p = params_from_synth(g, requires_grad=need_grad)
     pr, out, depth, valid, pix, sets = render_view(p, cam, view.mask, np.asarray(g.means, np.float32))
@@ -573,7 +631,7 @@ def step(g, view, need_grad=True, retain_intermediate=False, objective="pg"):
             pr[k].retain_grad()
         for k in ("rgb", "normal", "dist"):
             out[k].retain_grad()
-    L = losses(out, depth, valid, pix, sets, cam, view.target)
+    L = losses(out, depth, valid, pix, sets, cam, view.target, dssim=dssim)
     if objective == "eq11":
         pu, pv = pix
         wts = torch.from_numpy(luminance_gradient_weight(view.target)[pv.numpy(), pu.numpy()])

@@ -489,3 +489,82 @@ def test_eq11_autograd_gradient_matches_central_differences():
     # the soft-count term alone moves opacities: its gradient is not zero
     g_only = O.step(g, v, need_grad=False, objective="eq11")
     assert float(g_only["loss"]["l_gc_soft"]) > 0
+
+
+# ----------------------------------------------------------------- masked D-SSIM
+
+def test_ssim_window_is_normalised_gaussian():
+    G = O.ssim_window().numpy()
+    assert G.shape == (11, 11) and G.sum() == pytest.approx(1.0, rel=1e-14)
+    np.testing.assert_allclose(G, G.T, atol=1e-18)
+    r = np.arange(-5, 6)
+    g = np.exp(-r ** 2 / (2 * 1.5 ** 2))
+    np.testing.assert_allclose(G, np.outer(g, g) / g.sum() ** 2, rtol=1e-13)
+
+
+def test_ssim_identity_and_constant_images_closed_form():
+    rng = np.random.default_rng(0)
+    H, W = 20, 24
+    R = np.ones((H, W), bool)
+    x = torch.tensor(rng.random((H, W, 3)))
+    np.testing.assert_allclose(O.masked_ssim_map(x, x, R).numpy(), 1.0, atol=1e-12)
+    a, b = 0.3, 0.7
+    S = O.masked_ssim_map(torch.full((H, W, 3), a, dtype=torch.float64), torch.full((H, W, 3), b, dtype=torch.float64),
+                          R).numpy()
+    np.testing.assert_allclose(S, (2 * a * b + O.SSIM_C1) / (a * a + b * b + O.SSIM_C1), rtol=1e-12)
+
+
+def test_masked_ssim_matches_direct_windowed_moments():
+    """Weighted moments written out per pixel over the 11 x 11 neighbourhood,
+    restricted to R and the image, the Gaussian weights renormalised."""
+    rng = np.random.default_rng(1)
+    H, W = 17, 19
+    R = rng.random((H, W)) < 0.7
+    x = rng.random((H, W, 3))
+    y = rng.random((H, W, 3))
+    S = O.masked_ssim_map(torch.tensor(x), torch.tensor(y), R).numpy()
+    for (i, j) in [(0, 0), (8, 9), (16, 18), (3, 14), (12, 2)]:
+        for c in range(3):
+            w = []
+            xs, ys = [], []
+            for di in range(-5, 6):
+                for dj in range(-5, 6):
+                    ii, jj = i + di, j + dj
+                    if 0 <= ii < H and 0 <= jj < W and R[ii, jj]:
+                        w.append(math.exp(-(di * di + dj * dj) / (2 * 1.5 ** 2)))
+                        xs.append(x[ii, jj, c])
+                        ys.append(y[ii, jj, c])
+            w = np.array(w) / np.sum(w)
+            xs, ys = np.array(xs), np.array(ys)
+            mx, my = w @ xs, w @ ys
+            vx, vy, cxy = w @ (xs - mx) ** 2, w @ (ys - my) ** 2, w @ ((xs - mx) * (ys - my))
+            want = ((2 * mx * my + O.SSIM_C1) * (2 * cxy + O.SSIM_C2)) / \
+                   ((mx * mx + my * my + O.SSIM_C1) * (vx + vy + O.SSIM_C2))
+            assert S[i, j, c] == pytest.approx(want, rel=1e-10), (i, j, c)
+
+
+def test_l_rgb_dssim_weights_and_gradient_central_differences():
+    rng = np.random.default_rng(2)
+    H, W = 14, 16
+    M = rng.random((H, W)) < 0.5
+    from scipy import ndimage
+    R = ndimage.binary_dilation(M, structure=np.ones((3, 3), bool))
+    C = torch.tensor(rng.random((H, W, 3)), requires_grad=True)
+    T = torch.tensor(rng.random((H, W, 3)))
+    l, s = O.l_rgb_dssim(C, T, M, R)
+    l1 = float((C - T).abs().sum(-1)[torch.from_numpy(M)].sum() / (3 * M.sum()))
+    assert float(l) == pytest.approx(0.8 * l1 + 0.2 * (1 - float(s)), rel=1e-14)
+    l.backward()
+    g = C.grad.numpy()
+    # pixels outside R do not enter the loss
+    assert (g[~R] == 0).all()
+    h = 1e-6
+    for (i, j, c) in [(3, 4, 0), (7, 7, 2), (10, 12, 1), (0, 5, 1)]:
+        if not R[i, j]:
+            continue
+        Cp = C.detach().clone()
+        Cm = C.detach().clone()
+        Cp[i, j, c] += h
+        Cm[i, j, c] -= h
+        fd = (float(O.l_rgb_dssim(Cp, T, M, R)[0]) - float(O.l_rgb_dssim(Cm, T, M, R)[0])) / (2 * h)
+        assert fd == pytest.approx(g[i, j, c], rel=1e-5, abs=1e-9)

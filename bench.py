@@ -57,6 +57,8 @@ def parse():
                          "group training of the 8 sub-regions (10.5M Gaussians), one view per group per iteration, "
                          "graph-replayed iterations with fused Adam")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: fraction of the Gaussians")
+    ap.add_argument("--dssim", action="store_true",
+                    help="aerial workloads: L_rgb with the masked D-SSIM term (0.8 L1 + 0.2 (1 - SSIM))")
     ap.add_argument("--objective", default="pg", choices=["pg", "eq11"],
                     help="aerial workloads: pg = L_rgb + lambda_4 L_ban (GC-load value only); eq11 = Eq. 11 with "
                          "the flattening loss and the soft-count GC-load, all differentiated")
@@ -296,6 +298,8 @@ def ours(args):
     P = raster.GaussianParams.from_numpy(g, requires_grad=True)
     plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, tile=(tw, th))
     plan.set_objective(args.objective)
+    if args.dssim:
+        plan.set_dssim(0.2)
 
     def step(check=False):
         for t in P.tensors():
@@ -486,7 +490,8 @@ def ours(args):
              "stage_model_frac": sum(ab.values()) / sec / 1e9 / pk["hbm_gbs"]}
 
     cpu = None
-    if not args.no_cpu_baseline and ws == 1 and args.workload == "aerial" and args.objective == "pg":
+    if not args.no_cpu_baseline and ws == 1 and args.workload == "aerial" and args.objective == "pg" and \
+            not args.dssim:
         cv, sample = cpu_crop_sample(views)
         times, cores = run_oracle_steps(g, cv, 2)
         t = min(times)
@@ -500,7 +505,7 @@ def ours(args):
         "config": {"workload": WORKLOAD if args.workload == "aerial" else args.workload, "width": v.cam.width, "height": v.cam.height, "n_gaussians": g.n,
                    "mask_pixels": plan.n_mask, "rendered_pixels": plan.n_render, "active_tiles": plan.n_active,
                    "duplicates_K": K_dup, "tile": args.tile, "parallelism": f"replicas x{ws}",
-                   "objective": args.objective,
+                   "objective": args.objective, "dssim": bool(args.dssim),
                    "l2": "inputs larger than L2 (params 354 MB, per-pixel buffers > 2 GB)"},
         "roofline": roofline, "step_roofline": whole,
         "stages_ms": stage_ms, "eager_ms_per_step": ms_eager, "graph": True,

@@ -368,7 +368,27 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
  *            applied by pgsag_render_bwd (pgsag_ban_gather.objective) and
  *            pgsag_preprocess_bwd (flatten_weight).
  *   n_gauss, log_scales  the Gaussians of L_s (objective EQ11; n_gauss may be 0)
+ *   dssim    NULL, or the masked D-SSIM term of L_rgb (pgsag_dssim; act_tiles is
+ *            then read, 16-byte aligned; acc slot 7 of each view receives the
+ *            sum of the SSIM values)
  */
+/*
+ * Masked D-SSIM term of L_rgb (3DGS's photometric loss by citation, restricted
+ * to the building mask): with dssim given, L_rgb = (1 - lambda) L1 +
+ * lambda (1 - SSIM_M), SSIM_M = mean over the mask pixels and the 3 channels of
+ * SSIM with the 11 x 11 Gaussian window (sigma 1.5) restricted to the rendered
+ * set R and renormalised over it, C1 = 0.01^2, C2 = 0.03^2; its gradient is added
+ * to dout8's colour.  The window sums are taken per active tile with a 5-pixel
+ * halo gathered through the dense pixel map pidx.
+ */
+typedef struct pgsag_dssim {
+  const uint32_t* pidx;     /* device, dense pixel -> compact index (pgsag_prep_lists) */
+  float* scratch;           /* device float [9 per compact pixel] (gradient coefficients) */
+  uint32_t n_active_total;  /* entries of act_tiles                                     */
+  int32_t tile_w, tile_h;   /* the tile size every view uses                            */
+  float lambda;             /* D-SSIM weight (3DGS: 0.2)                                */
+} pgsag_dssim;              /* 32 bytes */
+
 #define PGSAG_OBJ_PG 0u
 #define PGSAG_OBJ_EQ11 1u
 #define PGSAG_LAMBDA_GC 0.41f      /* Sec. 4.3, Eq. 11: lambda   */
@@ -379,7 +399,7 @@ int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
                    const void* aux, const float* target, float lambda_ban, const float* gc_weight,
                    int gather, float* scratch, double* acc, float* chunk_scratch, float* loss,
                    float* gc_load, float* dout8, uint32_t objective, uint32_t n_gauss,
-                   const float* log_scales, int32_t* status, void* stream);
+                   const float* log_scales, const pgsag_dssim* dssim, int32_t* status, void* stream);
 
 /*
  * Deferred Eq. 8 adjoint for pgsag_render_bwd.  pgsag_loss_ban with gather = 0

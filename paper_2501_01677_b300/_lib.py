@@ -93,6 +93,16 @@ class PgsagDepthView(ctypes.Structure):
 assert ctypes.sizeof(PgsagDepthView) == 96
 
 
+class PgsagDssim(ctypes.Structure):
+    """pgsag_dssim: the masked D-SSIM term of L_rgb."""
+    _fields_ = [("pidx", c_void_p), ("scratch", c_void_p), ("n_active_total", c_uint32), ("tile_w", c_int32),
+                ("tile_h", c_int32), ("lam", c_float)]
+
+
+assert ctypes.sizeof(PgsagDssim) == 32
+LAMBDA_DSSIM = 0.2
+
+
 class PgsagAdamTensor(ctypes.Structure):
     _fields_ = [("p", c_void_p), ("g", c_void_p), ("m", c_void_p), ("v", c_void_p), ("n", c_uint64),
                 ("lr", c_float), ("reserved", c_uint32)]
@@ -140,7 +150,7 @@ def load(path: str = LIB_PATH):
          [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), c_uint32, P, P, P, P, P])
     _sig(lib, "pgsag_loss_ban", c_int,
          [c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, c_float, P, c_int, P, P, P, P, P, P, c_uint32, c_uint32, P,
-          P, P])
+          POINTER(PgsagDssim), P, P])
     _sig(lib, "pgsag_render_bwd", c_int,
          [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, POINTER(PgsagBanGather), P,
           c_uint32, P, P, P])

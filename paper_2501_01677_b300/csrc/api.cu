@@ -8,6 +8,9 @@ static_assert(sizeof(pgsag_view) == PGSAG_VIEW_BYTES, "pgsag_view layout");
 static_assert(sizeof(pgsag_vote_view) == 96, "pgsag_vote_view layout");
 static_assert(sizeof(pgsag_depth_view) == 96, "pgsag_depth_view layout");
 static_assert(sizeof(pgsag_tsdf_grid) == 32, "pgsag_tsdf_grid layout");
+static_assert(sizeof(pgsag_dssim) == 32, "pgsag_dssim layout");
+static_assert(sizeof(pgsag_adam_tensor) == 48, "pgsag_adam_tensor layout");
+static_assert(sizeof(pgsag_ban_gather) == 56, "pgsag_ban_gather layout");
 
 extern "C" const char* pgsag_status_str(int status) {
   switch (status) {

@@ -139,6 +139,11 @@ __device__ __forceinline__ int warp_max_i(int v) {
   return v;
 }
 
+// Masked D-SSIM passes (ssim.cu), launched by pgsag_loss_ban.
+int launch_dssim(uint32_t n_active, int tw, int th, const pgsag_view* views, const void* act_tiles,
+                 const uint32_t* pidx, const uint8_t* flags_c, const float* out8, const float* target,
+                 float* scratch, double* acc, float lambda, float* dout8, int32_t* status, cudaStream_t s);
+
 }  // namespace pgsag
 
 #define PGSAG_CHECK_LAUNCH()                          \

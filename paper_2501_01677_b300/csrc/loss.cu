@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
     const uint32_t* __restrict__ px_list, const uint8_t* __restrict__ flags_c, const uint4* __restrict__ nbr,
     const float4* __restrict__ out8, const float* __restrict__ depth, const float* __restrict__ target,
     const uint4* __restrict__ aux,
-    const float* __restrict__ gc_weight, bool soft, float* __restrict__ scratch, float4* __restrict__ partial,
+    const float* __restrict__ gc_weight, bool soft, float l1_scale, float* __restrict__ scratch,
+    float4* __restrict__ partial,
     float4* __restrict__ dout8, const int32_t* status) {
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
     float dC[3] = {0.f, 0.f, 0.f}, dNo[3] = {0.f, 0.f, 0.f};
     if (f & PGSAG_PIX_MASK) {
       const uint32_t nm = __ldg(&views[P.view].n_mask);
-      const float inv3m = nm ? 1.f / (3.f * (float)nm) : 0.f;
+      const float inv3m = nm ? l1_scale / (3.f * (float)nm) : 0.f;
       const float C[3] = {o0.x, o0.y, o0.z};
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
@@ -286,9 +287,11 @@ __device__ __forceinline__ float gc_std(double n, double s, double q) {
 // flattening sum in acc[8 n_views] over n_gauss), and slot 3 of each view's
 // accumulators receives {lambda / (n sigma), mean} (two floats), the
 // coefficients of the soft-count gradient dL/dg~_i = c (x_i - mean) / w_i.
+// With D-SSIM (lambda_d > 0) L_rgb = (1 - lambda_d) L1 + lambda_d (1 - SSIM_M),
+// SSIM_M from the sum in slot 7.
 __global__ void k_loss_final(const pgsag_view* __restrict__ views, uint32_t n_views, double* __restrict__ acc,
-                             float lambda_ban, uint32_t objective, uint32_t n_gauss, float* __restrict__ loss,
-                             float* __restrict__ gc_load, const int32_t* status) {
+                             float lambda_ban, uint32_t objective, uint32_t n_gauss, float lambda_d,
+                             float* __restrict__ loss, float* __restrict__ gc_load, const int32_t* status) {
   if (status_bad(status)) return;
   if (threadIdx.x != 0) return;
   const bool eq11 = objective == PGSAG_OBJ_EQ11;
@@ -297,7 +300,9 @@ __global__ void k_loss_final(const pgsag_view* __restrict__ views, uint32_t n_vi
   for (uint32_t v = 0; v < n_views; ++v) {
     double* a = acc + 8 * v;
     const uint32_t nm = views[v].n_mask;
-    const double lr = nm ? a[0] / (3.0 * nm) : 0.0;
+    double lr = nm ? a[0] / (3.0 * nm) : 0.0;
+    if (lambda_d > 0.f && nm)
+      lr = (1.0 - (double)lambda_d) * lr + (double)lambda_d * (1.0 - a[7] / (3.0 * nm));
     const double lb = a[2] > 0.0 ? a[1] / a[2] : 0.0;
     const float gc = gc_load ? gc_std(a[4], a[5], a[6]) : 0.f;
     double lv = lr + (double)lambda_ban * lb;
@@ -419,13 +424,17 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
                               const void* aux, const float* target, float lambda_ban, const float* gc_weight,
                               int gather, float* scratch, double* acc, float* chunk_scratch, float* loss,
                               float* gc_load, float* dout8, uint32_t objective, uint32_t n_gauss,
-                              const float* log_scales, int32_t* status, void* stream) {
+                              const float* log_scales, const pgsag_dssim* dssim, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (objective != PGSAG_OBJ_PG && objective != PGSAG_OBJ_EQ11) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status || !acc || !loss) return PGSAG_ERR_ARG;
   if ((gc_weight == nullptr) != (gc_load == nullptr)) return PGSAG_ERR_ARG;
   const bool eq11 = objective == PGSAG_OBJ_EQ11;
   if (eq11 && (!gc_weight || gather || (n_gauss && !log_scales))) return PGSAG_ERR_ARG;
+  if (dssim && (!dssim->pidx || !dssim->scratch || !act_tiles || ((uintptr_t)act_tiles & 15u) ||
+                !(dssim->lambda >= 0.f && dssim->lambda <= 1.f) || dssim->tile_w <= 0 || dssim->tile_h <= 0))
+    return PGSAG_ERR_ARG;
+  const float lambda_d = dssim ? dssim->lambda : 0.f;
   cudaStream_t s = (cudaStream_t)stream;
   PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)(n_views + (eq11 ? 1 : 0)) * 8 * sizeof(double), s));
   if (n_chunks) {
@@ -438,12 +447,17 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
     const unsigned blocks = pgsag_div_up(n_chunks, kLossThreads / 32);
     k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint4*)chunks, px_list, flags_c,
                                              (const uint4*)nbr, (const float4*)out8, depth, target,
-                                             (const uint4*)aux, gc_weight, eq11, scratch, (float4*)chunk_scratch,
-                                             (float4*)dout8, status);
+                                             (const uint4*)aux, gc_weight, eq11, 1.f - lambda_d, scratch,
+                                             (float4*)chunk_scratch, (float4*)dout8, status);
     PGSAG_CHECK_LAUNCH();
     k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 8, gc_weight ? 7 : 3, 8,
                                                                 acc, status);
     PGSAG_CHECK_LAUNCH();
+    if (dssim && dssim->n_active_total) {
+      const int r = launch_dssim(dssim->n_active_total, dssim->tile_w, dssim->tile_h, views, act_tiles, dssim->pidx,
+                                 flags_c, out8, target, dssim->scratch, acc, dssim->lambda, dout8, status, s);
+      if (r) return r;
+    }
     if (gather) {
       k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint4*)chunks, px_list, flags_c,
                                                (const uint4*)nbr, (const float4*)out8, depth, scratch, acc,
@@ -456,7 +470,8 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
     k_flat_sum<<<fb, 256, 0, s>>>(n_gauss, log_scales, acc + 8 * (size_t)n_views, status);
     PGSAG_CHECK_LAUNCH();
   }
-  k_loss_final<<<1, 32, 0, s>>>(views, n_views, acc, lambda_ban, objective, n_gauss, loss, gc_load, status);
+  k_loss_final<<<1, 32, 0, s>>>(views, n_views, acc, lambda_ban, objective, n_gauss, lambda_d, loss, gc_load,
+                                status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

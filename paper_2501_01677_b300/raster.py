@@ -210,6 +210,8 @@ class Plan:
         self.status = torch.zeros(1, dtype=i32, device=dev)
         self.acc_loss = torch.zeros(8 * (V + 1), dtype=torch.float64, device=dev)
         self.objective = "pg"
+        self.dssim_lambda = 0.0
+        self.ssim_scratch = None
         self.acc_gc = torch.zeros(3 * V, dtype=torch.float64, device=dev)
         self.chunk_scratch = torch.zeros((max(self.n_chunks, 1), 8), dtype=f32, device=dev)
         self.gc_load = torch.zeros(V, dtype=f32, device=dev)
@@ -291,6 +293,8 @@ class Plan:
         n += (2 if self.n_chunks else 0) + 1    # loss pass A (+ GC-load sums), per-view reduce, final
         if self.objective == "eq11" and self.n_gauss:
             n += 1                              # flattening-loss sum
+        if self.dssim_lambda and self.n_active:
+            n += 2                              # D-SSIM window sums and their adjoint
         if with_stats:
             n += 1 if self.n_active else 0      # per-tile counts
         n += 1 if self.n_active else 0          # render_bwd
@@ -329,6 +333,23 @@ class Plan:
             raise ValueError(objective)
         self.objective = objective
 
+    def set_dssim(self, lam: float = L.LAMBDA_DSSIM):
+        """L_rgb = (1 - lam) L1 + lam (1 - SSIM_M) with the masked D-SSIM (3DGS's
+        photometric loss restricted to the building mask); lam = 0 turns it off.
+        Needs the dense pixel map (not released)."""
+        if lam and self.pidx is None:
+            raise ValueError("the D-SSIM term needs the dense pixel map (release_prep_buffers was called)")
+        self.dssim_lambda = float(lam)
+        if lam and self.ssim_scratch is None:
+            self.ssim_scratch = torch.zeros(max(self.n_render, 1) * 9, dtype=torch.float32, device=self.device)
+
+    def _dssim_arg(self):
+        if not self.dssim_lambda:
+            return None
+        tw, th = self.tile
+        return ctypes.byref(L.PgsagDssim(self.pidx.data_ptr(), self.ssim_scratch.data_ptr(), self.n_active, tw, th,
+                                         self.dssim_lambda))
+
     def render_fwd(self, stream=None):
         s = _stream_ptr(stream)
         flags = L.RENDER_SOFT_COUNT if self.objective == "eq11" else 0
@@ -362,7 +383,7 @@ class Plan:
                                             _ptr(out), _ptr(self.gc_load) if fused else None, _ptr(self.dout8),
                                             L.OBJ_EQ11 if eq11 else L.OBJ_PG, P.n if (eq11 and P is not None) else 0,
                                             _ptr(P.log_scales) if (eq11 and P is not None) else None,
-                                            _ptr(self.status), s), "pgsag_loss_ban")
+                                            self._dssim_arg(), _ptr(self.status), s), "pgsag_loss_ban")
         return out
 
     def tile_stats(self, stream=None, counts_only: bool = False):

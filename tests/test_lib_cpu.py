@@ -41,6 +41,10 @@ def test_view_struct_layout(lib):
 
 def test_struct_layouts(lib):
     assert ctypes.sizeof(L.PgsagBanGather) == 56
+    assert ctypes.sizeof(L.PgsagDssim) == 32
+    assert ctypes.sizeof(L.PgsagAdamTensor) == 48
+    assert ctypes.sizeof(L.PgsagDepthView) == 96
+    assert ctypes.sizeof(L.PgsagTsdfGrid) == 32
     assert ctypes.sizeof(L.PgsagVoteView) == 96
     assert ctypes.sizeof(L.PgsagSched) == 24
 
@@ -70,11 +74,15 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.pgsag_render_fwd(1, ctypes.c_void_p(16), None, None, None, None, 0, None, None, 8, None, None, None,
                                 ctypes.c_void_p(16), None) == -5
     assert lib.pgsag_loss_ban(1, None, 0, None, None, None, None, None, None, None, None, None, 0.01, None, 0, None,
-                              None, None, None, None, None, 7, 0, None, None, None) == -5
+                              None, None, None, None, None, 7, 0, None, None, None, None) == -5
     # the Eq. 11 objective needs the GC weights and the deferred gather
     st = ctypes.c_void_p(16)
     assert lib.pgsag_loss_ban(1, st, 0, None, None, None, None, None, None, None, None, None, 0.01, None, 0, None,
-                              st, None, st, None, None, 1, 0, None, st, None) == -1
+                              st, None, st, None, None, 1, 0, None, None, st, None) == -1
+    # D-SSIM needs the pixel map, its scratch and an aligned tile list
+    d = L.PgsagDssim(None, None, 10, 16, 16, 0.2)
+    assert lib.pgsag_loss_ban(1, st, 0, None, None, None, None, None, None, None, None, None, 0.01, None, 1, None,
+                              st, None, st, None, None, 0, 0, None, ctypes.byref(d), st, None) == -1
     # voting filter: too many views, missing buffers, bad view table
     assert lib.pgsag_vote_filter(10, None, 300, None, None, 3, 0, None, None, None, st, None) == -5
     assert lib.pgsag_vote_filter(10, None, 1, None, None, 3, 0, None, None, None, st, None) == -1

@@ -240,6 +240,7 @@ def measured_alu_peaks():
 # duplicate 156 B (emit 12, sort 24, range 8, forward gather 56, adjoint gather
 # 56), per rendered pixel 165 B (forward 44, loss 77, adjoint 44).
 BYTES_PER_PAIR, BYTES_PER_DUP, BYTES_PER_PIXEL = 904, 156, 165
+HBM_NOMINAL_GBS = 7700.0  # B300 HBM3e nominal, for context beside the measured copy bandwidth
 
 
 def read_traffic(kernel: str, summary: str = "traffic_aerial_5472x3648.txt"):
@@ -483,6 +484,7 @@ def ours(args):
     sec = ms / args.steps / 1e3
     whole = {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / sec / 1e9,
              "frac": step_bytes / sec / 1e9 / pk["hbm_gbs"],
+             "frac_of_nominal_7700_gbs": step_bytes / sec / 1e9 / HBM_NOMINAL_GBS,
              "units": {"binned_pairs": n_binned, "duplicates": K_dup, "rendered_pixels": plan.n_render},
              "bytes_per_unit": {"binned_pair": BYTES_PER_PAIR, "duplicate": BYTES_PER_DUP,
                                 "rendered_pixel": BYTES_PER_PIXEL},

@@ -59,7 +59,6 @@ class GroupTrainer:
         self.v = [torch.zeros_like(t) for t in P.tensors()]
         self.step_dev = torch.zeros(4, dtype=torch.int32, device=P.means.device)
         self.status = torch.zeros(1, dtype=torch.int32, device=P.means.device)
-        self.loss_log = torch.zeros(0, dtype=torch.float32, device=P.means.device)
         self.betas, self.eps = betas, eps
         self.table = (L.PgsagAdamTensor * 5)()
         for k, (p, g, mm, vv, lr) in enumerate(zip(P.tensors(), self.grads, self.m, self.v, lrs)):
@@ -125,6 +124,31 @@ class GroupTrainer:
             if record_losses:
                 losses[i:i + 1].copy_(lb[-1:])
         return losses
+
+    # ------------------------------------------------------------------ checkpoints
+    def state_dict(self) -> dict:
+        """Parameters, Adam moments and step count (device tensors cloned to host)."""
+        return {"params": [t.detach().cpu().clone() for t in self.P.tensors()],
+                "m": [t.cpu().clone() for t in self.m], "v": [t.cpu().clone() for t in self.v],
+                "step": self.step_dev.cpu().clone(), "iterations": self.iterations}
+
+    def load_state_dict(self, sd: dict) -> None:
+        """Restore into the existing device buffers (the captured graphs stay valid)."""
+        with torch.no_grad():
+            for dst, src in zip(self.P.tensors(), sd["params"]):
+                dst.copy_(src)
+            for dst, src in zip(self.m, sd["m"]):
+                dst.copy_(src)
+            for dst, src in zip(self.v, sd["v"]):
+                dst.copy_(src)
+            self.step_dev.copy_(sd["step"])
+        self.iterations = int(sd["iterations"])
+
+    def save(self, path: str) -> None:
+        torch.save(self.state_dict(), path)
+
+    def load(self, path: str) -> None:
+        self.load_state_dict(torch.load(path, weights_only=True))
 
     def check_status(self):
         for pl in self.plans:

@@ -435,3 +435,23 @@ def test_neighbour_table_and_chunk_records(config0):
     at = plan.act_tiles[:plan.n_active].cpu().numpy().astype(np.int64)
     t = ch[:, 3]
     assert ((ch[:, 1] >= at[t, 2]) & (ch[:, 1] + ch[:, 2] <= at[t, 2] + at[t, 3])).all()
+
+
+def test_forward_and_sort_bit_stable_across_runs(config0):
+    """No atomics in the forward: the sorted duplicate lists and every forward
+    output are bit-identical when the step is run again."""
+    from paper_2501_01677_b300 import raster
+    g, views, res = config0
+    P = raster.GaussianParams.from_numpy(g)
+    plan = raster.Plan([views[0].cam], [views[0].mask], [views[0].target], g.n)
+    plan.forward(P)
+    torch.cuda.synchronize()
+    K = plan.k_value()
+    dup1 = plan.dup_pairs[:K].clone()
+    out1, aux1, dep1 = plan.out8.clone(), plan.aux.clone(), plan.depth.clone()
+    for _ in range(2):
+        plan.forward(P)
+        torch.cuda.synchronize()
+        assert plan.k_value() == K
+        assert torch.equal(plan.dup_pairs[:K], dup1)
+        assert torch.equal(plan.out8, out1) and torch.equal(plan.aux, aux1) and torch.equal(plan.depth, dep1)

@@ -535,6 +535,10 @@ int pgsag_adam(uint64_t n, float* p, const float* g, float* m, float* v, float l
  *   step: device int32 [4]: step[0] is the step count, advanced by one per call
  *         before the update (start it at 0); step[1], step[2] receive the bias
  *         corrections of the new step (float bits); step[3] unused.
+ *   status: device status word (nonzero: nothing is updated).
+ * Two launches (the step advance, then the update); capturable in a graph.
+ * Errors: PGSAG_ERR_UNSUPPORTED for more than PGSAG_ADAM_MAX_TENSORS tensors,
+ * PGSAG_ERR_ARG for missing pointers.
  */
 typedef struct pgsag_adam_tensor {
   float* p;
@@ -683,6 +687,10 @@ int pgsag_depth_fuse(uint32_t n_maps, const float* maps, uint64_t n_pix, float* 
  *     (weight = number of integrated views, tsdf = their mean value, 1 where the
  *     weight is 0); 1: the new views are merged into the running weighted mean
  *     (w' = w + n, t' = (t w + sum) / w'; voxels no new view reaches unchanged).
+ * The views are integrated in chunks whose depth maps fit in L2 together (one
+ * launch per chunk, later chunks merged into the running mean).
+ * Errors: PGSAG_ERR_UNSUPPORTED for too many views or a grid of 2^32 voxels or
+ * more; PGSAG_ERR_ARG for missing pointers or a bad grid / view.
  */
 int pgsag_tsdf_integrate(const pgsag_tsdf_grid* grid, uint32_t n_views, const pgsag_depth_view* views,
                          const float* depth, int accumulate, float* tsdf, float* weight, int32_t* status,

@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
             bool a0 = !done0 && pw.x >= q1.z;  // alpha >= 1/255
             bool a1 = !done1 && pw.y >= q1.z;
             // warp-uniform: the blend runs for the whole warp with masked weights
-            if (!__any_sync(kFull, a0 || a1)) continue;
+            // (also when no lane enters -- 1% of the events: a vote per event
+            // cost more than it saved)
             const float2 alpha = make_float2(fminf(__fmul_rn(q1.y, __expf(pw.x)), kAlphaMax),
                                              fminf(__fmul_rn(q1.y, __expf(pw.y)), kAlphaMax));
             const float2 test = __fmul2_rn(T, __ffma2_rn(alpha, f2(-1.f), f2(1.f)));  // T (1 - alpha)
@@ -575,9 +576,10 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
           const bool a0 = idx <= B.last0 && pw.x >= q1.z;  // blended by the forward
           const bool a1 = idx <= B.last1 && pw.y >= q1.z;
           // warp-uniform: the whole warp runs the adjoint with masked inputs, so a
-          // lane with no contribution produces zeros (all terms are finite)
-          const uint32_t cm = __ballot_sync(kFull, a0 || a1);
-          if (cm) {
+          // lane with no contribution produces zeros (all terms are finite); run
+          // for every relevant Gaussian (1% have no contributing lane: a vote per
+          // event cost more than it saved)
+          {
             float g[16];
             g[13] = g[14] = g[15] = 0.f;
             const float4 q2 = S.g2[j];

@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
         if (!__any_sync(kFull, !all_done)) continue;
         uint32_t rel[kBatch / 32];
         warp_relevance(S, (int)nb, cbox, lane, rel);
-        // the whole warp walks the relevant Gaussians (warp votes inside); lanes
-        // that are done take no part through their masks
+        // the whole warp walks the relevant Gaussians; lanes that are done take
+        // no part through their masks
 #pragma unroll 1
         for (int c = 0; c < kBatch / 32; ++c) {
           uint32_t m = rel[c];
@@ -321,11 +321,13 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
               last1 = base + j;
               ++cnt1;
             }
-            if (__all_sync(kFull, done0 && done1)) {
-              all_done = true;
-              c = kBatch / 32;
-              break;
-            }
+          }
+          // leave the batch once every pixel of the warp has terminated (checked
+          // per 32 Gaussians: a vote per Gaussian cost more than the Gaussians a
+          // finished warp still walks; terminated lanes take part with zero weight)
+          if (__all_sync(kFull, done0 && done1)) {
+            all_done = true;
+            break;
           }
         }
       }

@@ -271,8 +271,9 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
         uint32_t rel[kBatch / 32];
         warp_relevance(S, (int)nb, cbox, lane, rel);
         // the whole warp walks the relevant Gaussians; lanes that are done take
-        // no part through their masks
-#pragma unroll 1
+        // no part through their masks (the 4 chunks unrolled: rel stays in
+        // registers; 2% faster than a rolled loop here, not in the adjoint)
+#pragma unroll
         for (int c = 0; c < kBatch / 32; ++c) {
           uint32_t m = rel[c];
           while (m) {

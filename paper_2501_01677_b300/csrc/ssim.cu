@@ -44,7 +44,9 @@ __device__ __forceinline__ void ssim_weights(float* s_g) {
 
 // Forward: SSIM of every mask pixel of the tile (summed over channels into the
 // view's accumulator acc[8 v + 7]) and the 9 gradient coefficients per rendered
-// pixel (zero off the mask).
+// pixel (zero off the mask).  The 16 windowed sums travel as 8 pairs through
+// packed two-lane FP32 instructions: (W, xy_2), (x_0, x_1), (y_0, y_1),
+// (x_0^2, x_1^2), (y_0^2, y_1^2), (x_0 y_0, x_1 y_1), (x_2, y_2), (x_2^2, y_2^2).
 __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const pgsag_view* __restrict__ views,
                                                            const uint4* __restrict__ act_tiles,
                                                            const uint32_t* __restrict__ pidx,
@@ -63,52 +65,55 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const pgsag_view* __r
   const int tw = __ldg(&vp->tile_w), th = __ldg(&vp->tile_h);
   const uint64_t pix_base = __ldg((const unsigned long long*)&vp->pix_base);
   const int x0 = (int)(at.y & 0xffffu) * tw, y0 = (int)(at.y >> 16) * th;
-  const int RW = tw + 2 * kSsimR, RH = th + 2 * kSsimR, NR = RW * RH;
-  float* sv = smem;                                  // [7][NR]: r, x0..2, y0..2 (planes: no bank conflicts)
-  float* hs = smem + 7 * NR;                         // [16][RH * tw]
+  // tile sides are multiples of 8, so NR and every plane offset below are even
+  const int RW = tw + 2 * kSsimR, RH = th + 2 * kSsimR, NR = RW * RH, NH = RH * tw;
+  float2* sx = reinterpret_cast<float2*>(smem);           // [NR] (x_0, x_1)
+  float2* sy = sx + NR;                                   // [NR] (y_0, y_1)
+  float2* s2 = sy + NR;                                   // [NR] (x_2, y_2)
+  float* sr = smem + 6 * NR;                              // [NR] indicator of R
+  float2* hs = reinterpret_cast<float2*>(smem + 7 * NR);  // [8][NH] pairs of sums
   ssim_weights(s_g);
   for (int i = threadIdx.x; i < NR; i += kSsimThreads) {
     const int X = x0 - kSsimR + i % RW, Y = y0 - kSsimR + i / RW;
-    float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float2 a = make_float2(0.f, 0.f), b = a, c = a;
+    float r = 0.f;
     if (X >= 0 && X < W && Y >= 0 && Y < H) {
       const uint32_t q = __ldg(pidx + pix_base + (uint64_t)Y * W + X);
       if (q != 0xffffffffu) {
-        const float4 c = __ldg(out8 + 2ull * q);
-        v[0] = 1.f;
-        v[1] = c.x;
-        v[2] = c.y;
-        v[3] = c.z;
-        v[4] = __ldg(target + 3ull * q);
-        v[5] = __ldg(target + 3ull * q + 1);
-        v[6] = __ldg(target + 3ull * q + 2);
+        const float4 col = __ldg(out8 + 2ull * q);
+        r = 1.f;
+        a = make_float2(col.x, col.y);
+        b = make_float2(__ldg(target + 3ull * q), __ldg(target + 3ull * q + 1));
+        c = make_float2(col.z, __ldg(target + 3ull * q + 2));
       }
     }
-#pragma unroll
-    for (int k = 0; k < 7; ++k) sv[k * NR + i] = v[k];
+    sx[i] = a;
+    sy[i] = b;
+    s2[i] = c;
+    sr[i] = r;
   }
   __syncthreads();
-  // horizontal pass: 16 windowed sums for every region row and tile column
-  for (int it = threadIdx.x; it < RH * tw; it += kSsimThreads) {
+  // horizontal pass: the 8 pairs of windowed sums for every region row and tile column
+  for (int it = threadIdx.x; it < NH; it += kSsimThreads) {
     const int ry = it / tw, cx = it % tw;
-    float h[16];
+    float2 h[8];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) h[k] = 0.f;
+    for (int k = 0; k < 8; ++k) h[k] = make_float2(0.f, 0.f);
+    const int i0 = ry * RW + cx;
     for (int d = 0; d <= 2 * kSsimR; ++d) {
-      const float* p = sv + (ry * RW + cx + d);
-      const float g = s_g[d];
-      h[0] += g * p[0];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float x = p[(1 + c) * NR], y = p[(4 + c) * NR];  // zero off R
-        h[1 + 5 * c] += g * x;
-        h[2 + 5 * c] += g * y;
-        h[3 + 5 * c] += g * x * x;
-        h[4 + 5 * c] += g * y * y;
-        h[5 + 5 * c] += g * x * y;
-      }
+      const float2 g = make_float2(s_g[d], s_g[d]);
+      const float2 a = sx[i0 + d], b = sy[i0 + d], c = s2[i0 + d];
+      h[0] = __ffma2_rn(g, make_float2(sr[i0 + d], c.x * c.y), h[0]);
+      h[1] = __ffma2_rn(g, a, h[1]);
+      h[2] = __ffma2_rn(g, b, h[2]);
+      h[3] = __ffma2_rn(g, __fmul2_rn(a, a), h[3]);
+      h[4] = __ffma2_rn(g, __fmul2_rn(b, b), h[4]);
+      h[5] = __ffma2_rn(g, __fmul2_rn(a, b), h[5]);
+      h[6] = __ffma2_rn(g, c, h[6]);
+      h[7] = __ffma2_rn(g, __fmul2_rn(c, c), h[7]);
     }
 #pragma unroll
-    for (int k = 0; k < 16; ++k) hs[k * RH * tw + it] = h[k];
+    for (int k = 0; k < 8; ++k) hs[k * NH + it] = h[k];
   }
   __syncthreads();
   float ssum = 0.f;
@@ -124,21 +129,24 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const pgsag_view* __r
       for (int k = 0; k < 9; ++k) sc[k] = 0.f;
       continue;
     }
-    float v[16];
+    float2 v[8];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = 0.f;
+    for (int k = 0; k < 8; ++k) v[k] = make_float2(0.f, 0.f);
     for (int d = 0; d <= 2 * kSsimR; ++d) {
-      const float* p = hs + (oy + d) * tw + ox;
-      const float g = s_g[d];
+      const float2 g = make_float2(s_g[d], s_g[d]);
+      const float2* p = hs + (oy + d) * tw + ox;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] += g * p[k * RH * tw];
+      for (int k = 0; k < 8; ++k) v[k] = __ffma2_rn(g, p[k * NH], v[k]);
     }
-    const float iw = 1.f / v[0];  // > 0: the pixel itself is rendered
+    const float iw = 1.f / v[0].x;  // > 0: the pixel itself is rendered
+    const float sxs[3] = {v[1].x, v[1].y, v[6].x}, sys[3] = {v[2].x, v[2].y, v[6].y};
+    const float sxx[3] = {v[3].x, v[3].y, v[7].x}, syy[3] = {v[4].x, v[4].y, v[7].y};
+    const float sxy[3] = {v[5].x, v[5].y, v[0].y};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float mx = v[1 + 5 * c] * iw, my = v[2 + 5 * c] * iw;
-      const float vx = v[3 + 5 * c] * iw - mx * mx, vy = v[4 + 5 * c] * iw - my * my;
-      const float cxy = v[5 + 5 * c] * iw - mx * my;
+      const float mx = sxs[c] * iw, my = sys[c] * iw;
+      const float vx = sxx[c] * iw - mx * mx, vy = syy[c] * iw - my * my;
+      const float cxy = sxy[c] * iw - mx * my;
       const float A1 = 2.f * mx * my + kSsimC1, A2 = 2.f * cxy + kSsimC2;
       const float B1 = mx * mx + my * my + kSsimC1, B2 = vx + vy + kSsimC2;
       const float S = (A1 * A2) / (B1 * B2);
@@ -162,7 +170,9 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const pgsag_view* __r
 }
 
 // Backward: dL/dC of every rendered pixel of the tile, added to dout8's colour:
-// scale_v (G * P + 2 x G * Q + y G * Rc), scale_v = -lambda / (3 |M_v|).
+// scale_v (G * P + 2 x G * Q + y G * Rc), scale_v = -lambda / (3 |M_v|).  The 9
+// coefficient images blur as 4 packed pairs (P_0, P_1), (Q_0, Q_1), (Rc_0, Rc_1),
+// (P_2, Q_2) and Rc_2.
 __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const pgsag_view* __restrict__ views,
                                                            const uint4* __restrict__ act_tiles,
                                                            const uint32_t* __restrict__ pidx,
@@ -181,9 +191,11 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const pgsag_view* __r
   const uint32_t nm = __ldg(&vp->n_mask);
   const float scale = nm ? -lambda / (3.f * (float)nm) : 0.f;
   const int x0 = (int)(at.y & 0xffffu) * tw, y0 = (int)(at.y >> 16) * th;
-  const int RW = tw + 2 * kSsimR, RH = th + 2 * kSsimR, NR = RW * RH;
-  float* sv = smem;              // [9][NR]
-  float* hs = smem + 9 * NR;     // [9][RH * tw]
+  const int RW = tw + 2 * kSsimR, RH = th + 2 * kSsimR, NR = RW * RH, NH = RH * tw;
+  float2* sv = reinterpret_cast<float2*>(smem);            // [4][NR] pairs
+  float* s8 = smem + 8 * NR;                               // [NR] Rc_2
+  float2* hs = reinterpret_cast<float2*>(smem + 9 * NR);   // [4][NH]
+  float* h8 = smem + 9 * NR + 8 * NH;                      // [NH]
   ssim_weights(s_g);
   for (int i = threadIdx.x; i < NR; i += kSsimThreads) {
     const int X = x0 - kSsimR + i % RW, Y = y0 - kSsimR + i / RW;
@@ -195,23 +207,30 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const pgsag_view* __r
         for (int k = 0; k < 9; ++k) v[k] = __ldg(scratch + 9ull * q + k);
       }
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sv[k * NR + i] = v[k];
+    // v = {P0, Q0, R0, P1, Q1, R1, P2, Q2, R2}
+    sv[i] = make_float2(v[0], v[3]);
+    sv[NR + i] = make_float2(v[1], v[4]);
+    sv[2 * NR + i] = make_float2(v[2], v[5]);
+    sv[3 * NR + i] = make_float2(v[6], v[7]);
+    s8[i] = v[8];
   }
   __syncthreads();
-  for (int it = threadIdx.x; it < RH * tw; it += kSsimThreads) {
+  for (int it = threadIdx.x; it < NH; it += kSsimThreads) {
     const int ry = it / tw, cx = it % tw;
-    float h[9];
+    float2 h[4];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) h[k] = 0.f;
+    for (int k = 0; k < 4; ++k) h[k] = make_float2(0.f, 0.f);
+    float h1 = 0.f;
+    const int i0 = ry * RW + cx;
     for (int d = 0; d <= 2 * kSsimR; ++d) {
-      const float* p = sv + (ry * RW + cx + d);
-      const float g = s_g[d];
+      const float2 g = make_float2(s_g[d], s_g[d]);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) h[k] += g * p[k * NR];
+      for (int k = 0; k < 4; ++k) h[k] = __ffma2_rn(g, sv[k * NR + i0 + d], h[k]);
+      h1 = fmaf(g.x, s8[i0 + d], h1);
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) hs[k * RH * tw + it] = h[k];
+    for (int k = 0; k < 4; ++k) hs[k * NH + it] = h[k];
+    h8[it] = h1;
   }
   __syncthreads();
   for (int it = threadIdx.x; it < tw * th; it += kSsimThreads) {
@@ -220,22 +239,25 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const pgsag_view* __r
     if (X >= W || Y >= H) continue;
     const uint32_t q = __ldg(pidx + pix_base + (uint64_t)Y * W + X);
     if (q == 0xffffffffu) continue;
-    float b[9];
+    float2 b[4];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) b[k] = 0.f;
+    for (int k = 0; k < 4; ++k) b[k] = make_float2(0.f, 0.f);
+    float b8 = 0.f;
+    const int j0 = oy * tw + ox;
     for (int d = 0; d <= 2 * kSsimR; ++d) {
-      const float* p = hs + (oy + d) * tw + ox;
-      const float g = s_g[d];
+      const float2 g = make_float2(s_g[d], s_g[d]);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) b[k] += g * p[k * RH * tw];
+      for (int k = 0; k < 4; ++k) b[k] = __ffma2_rn(g, hs[k * NH + j0 + d * tw], b[k]);
+      b8 = fmaf(g.x, h8[j0 + d * tw], b8);
     }
+    const float P[3] = {b[0].x, b[0].y, b[3].x}, Q[3] = {b[1].x, b[1].y, b[3].y}, Rc[3] = {b[2].x, b[2].y, b8};
     const float4 c = __ldg(out8 + 2ull * q);
     const float x[3] = {c.x, c.y, c.z};
     float gr[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       const float y = __ldg(target + 3ull * q + ch);
-      gr[ch] = scale * (b[3 * ch] + 2.f * x[ch] * b[3 * ch + 1] + y * b[3 * ch + 2]);
+      gr[ch] = scale * (P[ch] + 2.f * x[ch] * Q[ch] + y * Rc[ch]);
     }
     float4 d = dout8[2ull * q];
     d.x += gr[0];

@@ -4,7 +4,7 @@
 // rendered (mask-dilated) pixels are compacted; each lane takes 2 of them (more
 // rounds for tiles larger than 256 pixels) and evaluates both with packed
 // two-lane FP32 instructions (fma/add/mul .f32x2).  The tile's depth-sorted Gaussians
-// are staged through shared memory in batches of 256 (64-byte records,
+// are staged through shared memory in batches of 128 (64-byte records,
 // coalesced), then each warp walks the batch, skipping -- as a warp-uniform
 // branch -- every Gaussian whose alpha >= 1/255 box misses the bounding box of
 // the warp's pixels.  A pair is rejected before the exponential when the
@@ -20,7 +20,7 @@ namespace pgsag {
 // Launch shape (compile-time; the defaults are the best measured on B300 for the
 // 5472x3648 aerial workload): warps per CTA (one CTA per active tile), Gaussians
 // staged per batch and the number of resident CTAs per SM the register
-// allocation must allow (forward 10, adjoint 7).  Each lane renders 2 pixels.
+// allocation must allow (forward 10, adjoint 9).  Each lane renders 2 pixels.
 #ifndef PGSAG_FWD_WARPS
 #define PGSAG_FWD_WARPS 4
 #endif
@@ -34,7 +34,7 @@ namespace pgsag {
 #define PGSAG_FWD_MINB 10  // resident CTAs per SM the register budget must allow
 #endif
 #ifndef PGSAG_BWD_MINB
-#define PGSAG_BWD_MINB 7
+#define PGSAG_BWD_MINB 9
 #endif
 constexpr int kBatch = PGSAG_BATCH;  // Gaussians staged per batch
 
@@ -245,11 +245,23 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
     if (t >= n_items) break;
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
+    // coordinate origin: the 32-pixel-aligned corner of the 32x32 cell holding
+    // the tile (every supported tile lies in one cell), so offsets round the
+    // same way whatever the tile size
+    const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
+    // the first batch is staged before the pixels are loaded, so that the two
+    // dependent global-load chains overlap; `staged` = S holds the batch at rbeg
+    bool staged = false;
+    if (ti.rbeg < ti.rend) {
+      const uint32_t nb = min((uint32_t)kBatch, ti.rend - ti.rbeg);
+#pragma unroll
+      for (int u = 0; u < kStagePerThread; ++u) {
+        const uint32_t slot = threadIdx.x + u * kRenderThreads;
+        if (slot < nb) stage(ti.rbeg + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, nullptr);
+      }
+      staged = true;
+    }
     for (uint32_t r0 = 0; r0 < ti.npix; r0 += kTilePix) {
-      // coordinate origin: the 32-pixel-aligned corner of the 32x32 cell holding
-      // the tile (every supported tile lies in one cell), so offsets round the
-      // same way whatever the tile size
-      const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
       const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
       float2 T = f2(1.f), C0 = f2(0.f), C1 = f2(0.f), C2 = f2(0.f), D = f2(0.f), N0 = f2(0.f), N1 = f2(0.f),
@@ -259,14 +271,18 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
       bool done0 = !P.has0, done1 = !P.has1;
       bool all_done = done0 && done1;
       for (uint32_t base = ti.rbeg; base < ti.rend; base += kBatch) {
+        // this barrier also publishes an early-staged first batch
         if (!__syncthreads_or(!all_done)) break;
         const uint32_t nb = min((uint32_t)kBatch, ti.rend - base);
+        if (!(staged && base == ti.rbeg)) {
 #pragma unroll
-        for (int u = 0; u < kStagePerThread; ++u) {
-          const uint32_t slot = threadIdx.x + u * kRenderThreads;
-          if (slot < nb) stage(base + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, nullptr);
+          for (int u = 0; u < kStagePerThread; ++u) {
+            const uint32_t slot = threadIdx.x + u * kRenderThreads;
+            if (slot < nb) stage(base + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, nullptr);
+          }
+          staged = base == ti.rbeg;
+          __syncthreads();
         }
-        __syncthreads();
         if (!__any_sync(kFull, !all_done)) continue;
         uint32_t rel[kBatch / 32];
         warp_relevance(S, (int)nb, cbox, lane, rel);
@@ -343,37 +359,44 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
 }
 
 // Reduce 16 per-lane values over the warp; afterwards lane l holds the warp total
-// of value (l >> 1) (lanes l and l^1 hold the same total).  16 shuffles.
+// of value (l >> 1) (lanes l and l^1 hold the same total).  16 shuffles; the
+// additions of the first three levels run in pairs (add.f32x2).
 __device__ __forceinline__ float warp_reduce_scatter16(const float v[16], int lane) {
   float a8[8];
   {
     const bool hi = lane & 16;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float send = hi ? v[i] : v[i + 8];
-      const float keep = hi ? v[i + 8] : v[i];
-      a8[i] = keep + __shfl_xor_sync(kFull, send, 16);
+    for (int i = 0; i < 8; i += 2) {
+      const float2 send = hi ? make_float2(v[i], v[i + 1]) : make_float2(v[i + 8], v[i + 9]);
+      const float2 keep = hi ? make_float2(v[i + 8], v[i + 9]) : make_float2(v[i], v[i + 1]);
+      const float2 got = make_float2(__shfl_xor_sync(kFull, send.x, 16), __shfl_xor_sync(kFull, send.y, 16));
+      const float2 sum = __fadd2_rn(keep, got);
+      a8[i] = sum.x;
+      a8[i + 1] = sum.y;
     }
   }
   float a4[4];
   {
     const bool hi = lane & 8;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float send = hi ? a8[i] : a8[i + 4];
-      const float keep = hi ? a8[i + 4] : a8[i];
-      a4[i] = keep + __shfl_xor_sync(kFull, send, 8);
+    for (int i = 0; i < 4; i += 2) {
+      const float2 send = hi ? make_float2(a8[i], a8[i + 1]) : make_float2(a8[i + 4], a8[i + 5]);
+      const float2 keep = hi ? make_float2(a8[i + 4], a8[i + 5]) : make_float2(a8[i], a8[i + 1]);
+      const float2 got = make_float2(__shfl_xor_sync(kFull, send.x, 8), __shfl_xor_sync(kFull, send.y, 8));
+      const float2 sum = __fadd2_rn(keep, got);
+      a4[i] = sum.x;
+      a4[i + 1] = sum.y;
     }
   }
   float a2[2];
   {
     const bool hi = lane & 4;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float send = hi ? a4[i] : a4[i + 2];
-      const float keep = hi ? a4[i + 2] : a4[i];
-      a2[i] = keep + __shfl_xor_sync(kFull, send, 4);
-    }
+    const float2 send = hi ? make_float2(a4[0], a4[1]) : make_float2(a4[2], a4[3]);
+    const float2 keep = hi ? make_float2(a4[2], a4[3]) : make_float2(a4[0], a4[1]);
+    const float2 got = make_float2(__shfl_xor_sync(kFull, send.x, 4), __shfl_xor_sync(kFull, send.y, 4));
+    const float2 sum = __fadd2_rn(keep, got);
+    a2[0] = sum.x;
+    a2[1] = sum.y;
   }
   float a1;
   {
@@ -385,15 +408,18 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float v[16], int la
   return a1 + __shfl_xor_sync(kFull, a1, 1);
 }
 
-// Adjoint state of the lane's two pixels (x = pixel 0, y = pixel 1).  S* hold the
-// suffix sums S_i = sum_{j>i} x_j a_j prod_{i<l<j} (1 - a_l) of the channels
-// behind the Gaussian being processed; they are advanced eagerly
-// (S <- a x + (1 - a) S) after each contributor.
+// Adjoint state of the lane's two pixels (x = pixel 0, y = pixel 1).  For a
+// blended Gaussian i, dL/dalpha_i needs sum_ch (x_ch,i - S_ch,i) dL/dX_ch with the
+// suffix sums S_ch,i = sum_{j>i} x_ch,j a_j prod_{i<l<j} (1 - a_l) of the 7
+// channels (colour, plane distance, normal) behind it.  The upstream gradients
+// dL/dX_ch are constant along the pixel's list, so only Q = sum_ch S_ch dL/dX_ch
+// is needed, and it obeys the same recurrence as each S_ch:
+// Q <- Q + a (P - Q), P = sum_ch x_ch dL/dX_ch of the Gaussian just passed.
 struct BwdPix {
   float2 T;
   int last0, last1;
   float2 dC0, dC1, dC2, dD, dN0, dN1, dN2, dATf;  // dATf = dL/dA * T_final
-  float2 SC0, SC1, SC2, SN0, SN1, SN2, SD;
+  float2 Q;
   float2 dG;  // dL/d(soft count) (objective Eq. 11)
 };
 
@@ -502,7 +528,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
   __shared__ uint32_t spair[kBatch];
   __shared__ float4 sacc[kBatch][4];
   __shared__ uint32_t s_item;
-  __shared__ int s_max;
+  __shared__ int s_wmax[2][kWarps];
+  uint32_t round = 0;
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float gscale_in = dout_scale ? __ldg(dout_scale) : 1.f;
@@ -516,11 +543,23 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     if (t >= n_items) break;
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
+    // coordinate origin: the 32-pixel-aligned corner of the 32x32 cell holding
+    // the tile (every supported tile lies in one cell), so offsets round the
+    // same way whatever the tile size
+    const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
+    // a list of at most one batch is staged whole before the pixels' upstream
+    // gradients are loaded (the two dependent global-load chains overlap) and
+    // serves every pixel round; slot j holds entry rbeg + j, as in the batch loop
+    const bool one_batch = ti.rend - ti.rbeg <= (uint32_t)kBatch;
+    if (one_batch) {
+      const uint32_t nb = ti.rend - ti.rbeg;
+#pragma unroll
+      for (int u = 0; u < kStagePerThread; ++u) {
+        const uint32_t slot = threadIdx.x + u * kRenderThreads;
+        if (slot < nb) stage(ti.rbeg + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, spair);
+      }
+    }
     for (uint32_t r0 = 0; r0 < ti.npix; r0 += kTilePix) {
-      // coordinate origin: the 32-pixel-aligned corner of the 32x32 cell holding
-      // the tile (every supported tile lies in one cell), so offsets round the
-      // same way whatever the tile size
-      const int ox = ((int)ti.tx * V.tile_w) & ~31, oy = ((int)ti.ty * V.tile_h) & ~31;
       const Pix P = load_pixels(ti, r0, warp, lane, V.width, ox, oy, px_list);
       const float4 cbox = warp_pixel_box(P);
       BwdPix B;
@@ -544,24 +583,30 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
         B.dATf = make_float2(v0[7], v1[7]);
         B.T = make_float2(v0[8], v1[8]);
         B.dG = make_float2(v0[9], v1[9]);
-        B.SC0 = B.SC1 = B.SC2 = B.SN0 = B.SN1 = B.SN2 = B.SD = f2(0.f);
+        B.Q = f2(0.f);
       }
+      // CTA maximum of the last blended entry: one slot per warp, double-buffered
+      // by round so that one barrier suffices (the slots of a round are written
+      // again two rounds later, past this round's barrier and the next one's)
       const int warp_last = warp_max_i(max(B.last0, B.last1));
-      if (threadIdx.x == 0) s_max = -1;
-      __syncthreads();
-      if (lane == 0) atomicMax(&s_max, warp_last);
-      __syncthreads();
-      const int cta_last = s_max;
-      __syncthreads();
+      int* wmax = s_wmax[round & 1];
+      if (lane == 0) wmax[warp] = warp_last;
+      __syncthreads();  // also publishes an early-staged list
+      int cta_last = wmax[0];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) cta_last = max(cta_last, wmax[w]);
+      ++round;
       for (int hi = cta_last; hi >= (int)ti.rbeg; hi -= kBatch) {
         const int lo = max((int)ti.rbeg, hi - kBatch + 1);
         const int nb = hi - lo + 1;
+        if (!one_batch) {
 #pragma unroll
-        for (int u = 0; u < kStagePerThread; ++u) {
-          const int slot = threadIdx.x + u * kRenderThreads;
-          if (slot < nb) stage(lo + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, spair);
+          for (int u = 0; u < kStagePerThread; ++u) {
+            const int slot = threadIdx.x + u * kRenderThreads;
+            if (slot < nb) stage(lo + slot, slot, dup_pairs, rec, (float)ox, (float)oy, S, spair);
+          }
+          __syncthreads();
         }
-        __syncthreads();
         uint32_t rel[kBatch / 32];
         warp_relevance(S, min(nb, warp_last - lo + 1), cbox, lane, rel);
 #pragma unroll 1
@@ -597,29 +642,17 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
             B.T.y = a1 ? Tn.y : B.T.y;
             const float2 am = make_float2(a0 ? alpha.x : 0.f, a1 ? alpha.y : 0.f);
             const float2 w = __fmul2_rn(am, B.T);
-            // dL/dalpha = T sum_ch (x_ch - S_ch) dL/dX_ch + dL/dA T_final / (1 - alpha); the
-            // suffix sums advance past this Gaussian (S <- S + a (x - S); unchanged where a = 0)
-            float2 e = __ffma2_rn(B.SC0, f2(-1.f), f2(q2.x));
-            float2 acc = __fmul2_rn(e, B.dC0);
-            B.SC0 = __ffma2_rn(am, e, B.SC0);
-            e = __ffma2_rn(B.SC1, f2(-1.f), f2(q2.y));
-            acc = __ffma2_rn(e, B.dC1, acc);
-            B.SC1 = __ffma2_rn(am, e, B.SC1);
-            e = __ffma2_rn(B.SC2, f2(-1.f), f2(q2.z));
-            acc = __ffma2_rn(e, B.dC2, acc);
-            B.SC2 = __ffma2_rn(am, e, B.SC2);
-            e = __ffma2_rn(B.SD, f2(-1.f), f2(q2.w));
-            acc = __ffma2_rn(e, B.dD, acc);
-            B.SD = __ffma2_rn(am, e, B.SD);
-            e = __ffma2_rn(B.SN0, f2(-1.f), f2(q3.x));
-            acc = __ffma2_rn(e, B.dN0, acc);
-            B.SN0 = __ffma2_rn(am, e, B.SN0);
-            e = __ffma2_rn(B.SN1, f2(-1.f), f2(q3.y));
-            acc = __ffma2_rn(e, B.dN1, acc);
-            B.SN1 = __ffma2_rn(am, e, B.SN1);
-            e = __ffma2_rn(B.SN2, f2(-1.f), f2(q3.z));
-            acc = __ffma2_rn(e, B.dN2, acc);
-            B.SN2 = __ffma2_rn(am, e, B.SN2);
+            // dL/dalpha = T (P - Q) + dL/dA T_final / (1 - alpha), P = sum_ch x_ch dL/dX_ch;
+            // Q then advances past this Gaussian (unchanged where a = 0)
+            float2 Pc = __fmul2_rn(f2(q2.x), B.dC0);
+            Pc = __ffma2_rn(f2(q2.y), B.dC1, Pc);
+            Pc = __ffma2_rn(f2(q2.z), B.dC2, Pc);
+            Pc = __ffma2_rn(f2(q2.w), B.dD, Pc);
+            Pc = __ffma2_rn(f2(q3.x), B.dN0, Pc);
+            Pc = __ffma2_rn(f2(q3.y), B.dN1, Pc);
+            Pc = __ffma2_rn(f2(q3.z), B.dN2, Pc);
+            const float2 acc = __ffma2_rn(B.Q, f2(-1.f), Pc);
+            B.Q = __ffma2_rn(am, acc, B.Q);
             float2 dal = __ffma2_rn(B.dATf, roma, __fmul2_rn(B.T, acc));
             if constexpr (kSoft) dal = __fadd2_rn(dal, B.dG);  // d g~ / d alpha = 1
             g[6] = fmaf(w.y, B.dC0.y, w.x * B.dC0.x);

@@ -307,6 +307,7 @@ constexpr int kPreThreads = 128;
 #endif
 constexpr int kShStride = 49;
 constexpr size_t kShSlabBytes = (size_t)kPreThreads * kShStride * sizeof(float);
+constexpr int kPreBwdSlice = 2 * kPreThreads;  // Gaussians per adjoint block
 
 __host__ __device__ __forceinline__ size_t views_bytes(uint32_t n_views) {
   return ((size_t)n_views * sizeof(pgsag_view) + 15) & ~(size_t)15;
@@ -438,6 +439,54 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
 // Adjoint of pair_forward + colour, accumulating into the raw-parameter gradients.
 // A Gaussian with no binned pair in any view has zero gradient and reads nothing
 // but its pairs' tile counts.
+// Eq. 11's flattening term of Gaussian g: d(w mean_g min_k exp(ls_gk)) / d ls_gk*
+// = w exp(ls_gk*) / n at the smallest axis k* (ties: lowest axis), added to gls;
+// returns whether the term is on.
+__device__ __forceinline__ bool add_flatten(uint32_t g, const float* __restrict__ log_scales, uint32_t n,
+                                            float flatten_weight, float sc, float gls[3]) {
+  if (flatten_weight == 0.f) return false;
+  const float l0 = __ldg(log_scales + 3ull * g), l1 = __ldg(log_scales + 3ull * g + 1),
+              l2 = __ldg(log_scales + 3ull * g + 2);
+  const int k = (l0 <= l1 && l0 <= l2) ? 0 : (l1 <= l2 ? 1 : 2);
+  const float lk = k == 0 ? l0 : (k == 1 ? l1 : l2);
+  const float d = flatten_weight * sc * expf(lk) / (float)n;
+  gls[0] += k == 0 ? d : 0.f;
+  gls[1] += k == 1 ? d : 0.f;
+  gls[2] += k == 2 ? d : 0.f;
+  return true;
+}
+
+// Gradients of Gaussian g's means, log-scales, quaternion and opacity logit:
+// written, or added to what the buffers hold.
+__device__ __forceinline__ void store_small(uint32_t g, const float gm[3], const float gls[3], const float gq[4],
+                                            float gol, int accumulate, float* __restrict__ d_means,
+                                            float* __restrict__ d_log_scales, float* __restrict__ d_quats,
+                                            float* __restrict__ d_opac) {
+  float4* q4 = reinterpret_cast<float4*>(d_quats) + g;
+  if (accumulate) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      d_means[3ull * g + i] += gm[i];
+      d_log_scales[3ull * g + i] += gls[i];
+    }
+    float4 o = *q4;
+    o.x += gq[0];
+    o.y += gq[1];
+    o.z += gq[2];
+    o.w += gq[3];
+    *q4 = o;
+    d_opac[g] += gol;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      d_means[3ull * g + i] = gm[i];
+      d_log_scales[3ull * g + i] = gls[i];
+    }
+    *q4 = make_float4(gq[0], gq[1], gq[2], gq[3]);
+    d_opac[g] = gol;
+  }
+}
+
 __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_bwd(uint32_t n, const float* __restrict__ means,
                                  const float* __restrict__ log_scales,
                                  const float* __restrict__ quats,
@@ -460,254 +509,259 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
   }
   // dynamic shared memory: [view table | SH gradient slab]
   float* s_gsh = reinterpret_cast<float*>(smem_raw + views_bytes(n_views));
+  __shared__ uint32_t s_list[kPreBwdSlice];        // binned Gaussians of the slice (any order)
+  __shared__ uint32_t s_bits[kPreBwdSlice / 32];   // binned flags of the slice
+  __shared__ uint32_t s_nlist;
   if (status_bad(status)) return;
-  const uint32_t g0 = blockIdx.x * blockDim.x;
-  for (int i = threadIdx.x; i < kPreThreads * kShStride; i += blockDim.x) s_gsh[i] = 0.f;
+  const uint32_t gbase = blockIdx.x * kPreBwdSlice;
+  if (threadIdx.x == 0) s_nlist = 0;
   __syncthreads();
   set_campos(sv, n_views);
   __syncthreads();
-  const uint32_t g = g0 + threadIdx.x;
-  float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gol = 0.f;
-  float* gsh = s_gsh + threadIdx.x * kShStride;
-  bool binned = false;
-  if (g < n) {
-    for (uint32_t vi = 0; vi < n_views && !binned; ++vi) {
-      const pgsag_view& V = sv[vi];
-      if (g >= V.g_begin && g < V.g_end) binned = __ldg(&bininfo[V.pair_base + (g - V.g_begin)].w) != 0u;
+  const float sc = dout_scale ? __ldg(dout_scale) : 1.f;
+  const float zero3[3] = {0.f, 0.f, 0.f}, zero4[4] = {0.f, 0.f, 0.f, 0.f};
+
+  // 1. binned flags; a Gaussian with no binned pair gets its (zero or flattening
+  // only) gradient here, the others go to the list
+#pragma unroll
+  for (int k = 0; k < kPreBwdSlice / kPreThreads; ++k) {
+    const uint32_t li = k * kPreThreads + threadIdx.x, g = gbase + li;
+    bool binned = false;
+    if (g < n) {
+      for (uint32_t vi = 0; vi < n_views && !binned; ++vi) {
+        const pgsag_view& V = sv[vi];
+        if (g >= V.g_begin && g < V.g_end) binned = __ldg(&bininfo[V.pair_base + (g - V.g_begin)].w) != 0u;
+      }
+    }
+    const uint32_t bal = __ballot_sync(kFull, binned);
+    if ((threadIdx.x & 31) == 0) s_bits[li >> 5] = bal;
+    if (binned) {
+      s_list[atomicAdd(&s_nlist, 1u)] = g;
+    } else if (g < n) {
+      float gls[3] = {0.f, 0.f, 0.f};
+      const bool flat = add_flatten(g, log_scales, n, flatten_weight, sc, gls);
+      if (!accumulate || flat) store_small(g, zero3, gls, zero4, 0.f, accumulate, d_means, d_log_scales, d_quats, d_opac);
     }
   }
-  const GaussIn G = binned ? load_gauss(g, means, log_scales, quats, opacity_logit) : GaussIn{};
-  const uint32_t vcount = binned ? n_views : 0u;
+  __syncthreads();
+  const uint32_t nl = s_nlist;
+  if (!accumulate) {
+    // zero SH rows of the Gaussians without a binned pair (coalesced float4)
+    const uint32_t nb = min((uint32_t)kPreBwdSlice, n - gbase);
+    float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * gbase);
+    for (uint32_t i = threadIdx.x; i < nb * 12; i += blockDim.x) {
+      const uint32_t row = i / 12;
+      if (!((s_bits[row >> 5] >> (row & 31)) & 1u)) dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
 
-  for (uint32_t vi = 0; vi < vcount; ++vi) {
-    const pgsag_view& V = sv[vi];
-    if (g < V.g_begin || g >= V.g_end) continue;
-    const uint32_t p = V.pair_base + (g - V.g_begin);
-    if (__ldg(&bininfo[p].w) == 0u) continue;  // culled or off-screen: no contribution
-    PairFwd P;
-    if (!pair_forward(V, G, P)) continue;
-    const float4* G4 = reinterpret_cast<const float4*>(grad2d) + 4ull * p;
-    const float4 g0 = __ldg(G4 + 0), g1 = __ldg(G4 + 1), g2 = __ldg(G4 + 2), g3 = __ldg(G4 + 3);
-    // grad2d = {dmx, dmy, dl11, dl21, dl22, do, dr, dg, db, dd, dnx, dny, dnz}
-    const float dmx = g0.x, dmy = g0.y, dl11 = g0.z, dl21 = g0.w;
-    const float dl22 = g1.x, dop = g1.y;
-    const float drgb[3] = {g1.z, g1.w, g2.x};
-    const float dd = g2.y;
-    float dn[3] = {g2.z, g2.w, g3.x};
+  // 2. the adjoint of every binned pair of the listed Gaussians, one Gaussian per
+  // thread and round (full warps), SH gradients summed in the slab row
+  for (uint32_t base = 0; base < nl; base += kPreThreads) {
+    for (int i = threadIdx.x; i < kPreThreads * kShStride; i += blockDim.x) s_gsh[i] = 0.f;
+    __syncthreads();
+    const uint32_t li = base + threadIdx.x;
+    if (li < nl) {
+      const uint32_t g = s_list[li];
+      float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gol = 0.f;
+      float* gsh = s_gsh + threadIdx.x * kShStride;
+      const GaussIn G = load_gauss(g, means, log_scales, quats, opacity_logit);
+      for (uint32_t vi = 0; vi < n_views; ++vi) {
+        const pgsag_view& V = sv[vi];
+        if (g < V.g_begin || g >= V.g_end) continue;
+        const uint32_t p = V.pair_base + (g - V.g_begin);
+        if (__ldg(&bininfo[p].w) == 0u) continue;  // culled or off-screen: no contribution
+        PairFwd P;
+        if (!pair_forward(V, G, P)) continue;
+        const float4* G4 = reinterpret_cast<const float4*>(grad2d) + 4ull * p;
+        const float4 g0 = __ldg(G4 + 0), g1 = __ldg(G4 + 1), g2 = __ldg(G4 + 2), g3 = __ldg(G4 + 3);
+        // grad2d = {dmx, dmy, dl11, dl21, dl22, do, dr, dg, db, dd, dnx, dny, dnz}
+        const float dmx = g0.x, dmy = g0.y, dl11 = g0.z, dl21 = g0.w;
+        const float dl22 = g1.x, dop = g1.y;
+        const float drgb[3] = {g1.z, g1.w, g2.x};
+        const float dd = g2.y;
+        float dn[3] = {g2.z, g2.w, g3.x};
 
-    float dmc[3] = {0.f, 0.f, 0.f};
-    // opacity
-    gol += dop * P.o * (1.f - P.o);
+        float dmc[3] = {0.f, 0.f, 0.f};
+        // opacity
+        gol += dop * P.o * (1.f - P.o);
 
-    // colour (zero gradient where the colour was clamped at 0)
-    {
-      float dx = G.m[0] - V.reserved0[0], dy = G.m[1] - V.reserved0[1], dz = G.m[2] - V.reserved0[2];
-      const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-      dx *= il;
-      dy *= il;
-      dz *= il;
-      float Y[16];
-      sh_eval(dx, dy, dz, Y);
-      float raw[3];
-      sh_colour(sh, g, Y, raw);
-      float dc[3];
+        // colour (zero gradient where the colour was clamped at 0)
+        {
+          float dx = G.m[0] - V.reserved0[0], dy = G.m[1] - V.reserved0[1], dz = G.m[2] - V.reserved0[2];
+          const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+          dx *= il;
+          dy *= il;
+          dz *= il;
+          float Y[16];
+          sh_eval(dx, dy, dz, Y);
+          float raw[3];
+          sh_colour(sh, g, Y, raw);
+          float dc[3];
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) dc[ch] = raw[ch] < 0.f ? 0.f : drgb[ch];
-      // cw[k] = sum_ch dc[ch] sh[k][ch] (second read of the row, from L1/L2)
-      float cw[16];
+          for (int ch = 0; ch < 3; ++ch) dc[ch] = raw[ch] < 0.f ? 0.f : drgb[ch];
+          // cw[k] = sum_ch dc[ch] sh[k][ch] (second read of the row, from L1/L2)
+          float cw[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) cw[k] = 0.f;
-      {
-        const float4* row = reinterpret_cast<const float4*>(sh + 48ull * g);
+          for (int k = 0; k < 16; ++k) cw[k] = 0.f;
+          {
+            const float4* row = reinterpret_cast<const float4*>(sh + 48ull * g);
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-          const float4 v = __ldg(row + i);
-          const float e[4] = {v.x, v.y, v.z, v.w};
+            for (int i = 0; i < 12; ++i) {
+              const float4 v = __ldg(row + i);
+              const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int f = 4 * i + j;
-            cw[f / 3] += dc[f % 3] * e[j];
+              for (int j = 0; j < 4; ++j) {
+                const int f = 4 * i + j;
+                cw[f / 3] += dc[f % 3] * e[j];
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            gsh[3 * k + 0] += dc[0] * Y[k];
+            gsh[3 * k + 1] += dc[1] * Y[k];
+            gsh[3 * k + 2] += dc[2] * Y[k];
+          }
+          float gx, gy, gz;
+          sh_grad(dx, dy, dz, cw, gx, gy, gz);
+          // dir = v/|v|: d v = (g - dir (dir . g)) / |v|
+          const float dg = dx * gx + dy * gy + dz * gz;
+          gm[0] += (gx - dx * dg) * il;
+          gm[1] += (gy - dy * dg) * il;
+          gm[2] += (gz - dz * dg) * il;
+        }
+
+        // plane distance d = -n_c . mu_c
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dmc[i] -= dd * P.nc[i];
+          dn[i] -= dd * P.mc[i];
+        }
+        // n_c = sign * W n_w, n_w = column `axis` of Rq
+        float dRq[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        {
+          const float s = P.sign;
+          const float dnw0 = s * (V.R[0] * dn[0] + V.R[3] * dn[1] + V.R[6] * dn[2]);
+          const float dnw1 = s * (V.R[1] * dn[0] + V.R[4] * dn[1] + V.R[7] * dn[2]);
+          const float dnw2 = s * (V.R[2] * dn[0] + V.R[5] * dn[1] + V.R[8] * dn[2]);
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            if (P.axis == kk) {
+              dRq[0 * 3 + kk] += dnw0;
+              dRq[1 * 3 + kk] += dnw1;
+              dRq[2 * 3 + kk] += dnw2;
+            }
           }
         }
-      }
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        gsh[3 * k + 0] += dc[0] * Y[k];
-        gsh[3 * k + 1] += dc[1] * Y[k];
-        gsh[3 * k + 2] += dc[2] * Y[k];
-      }
-      float gx, gy, gz;
-      sh_grad(dx, dy, dz, cw, gx, gy, gz);
-      // dir = v/|v|: d v = (g - dir (dir . g)) / |v|
-      const float dg = dx * gx + dy * gy + dz * gz;
-      gm[0] += (gx - dx * dg) * il;
-      gm[1] += (gy - dy * dg) * il;
-      gm[2] += (gz - dz * dg) * il;
-    }
 
-    // plane distance d = -n_c . mu_c
+        // 2D mean
+        const float z = P.mc[2], iz = 1.f / z, iz2 = iz * iz;
+        dmc[0] += dmx * V.fx * iz;
+        dmc[1] += dmy * V.fy * iz;
+        dmc[2] -= dmx * V.fx * P.mc[0] * iz2 + dmy * V.fy * P.mc[1] * iz2;
+
+        // Cholesky factor of the conic -> Sigma' = (a, b, c), det = a c - b^2:
+        // l11 = sqrt(c/det), l21 = -b/sqrt(c det), l22 = c^-1/2
+        const float a = P.a, b = P.b, c = P.c;
+        const float iD = 1.f / P.det, ic = 1.f / c;
+        const float da = -0.5f * c * iD * (dl11 * P.l11 + dl21 * P.l21);
+        const float db = dl11 * P.l11 * b * iD - dl21 * a * P.l11 * iD;
+        const float dcc = dl11 * P.l11 * 0.5f * (ic - a * iD) - dl21 * P.l21 * 0.5f * (ic + a * iD) -
+                          dl22 * 0.5f * P.l22 * ic;
+        // Sigma' = V V^T: dV0 = 2 da V0 + db V1, dV1 = db V0 + 2 dc V1
+        float dV[6];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      dmc[i] -= dd * P.nc[i];
-      dn[i] -= dd * P.mc[i];
-    }
-    // n_c = sign * W n_w, n_w = column `axis` of Rq
-    float dRq[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    {
-      const float s = P.sign;
-      const float dnw0 = s * (V.R[0] * dn[0] + V.R[3] * dn[1] + V.R[6] * dn[2]);
-      const float dnw1 = s * (V.R[1] * dn[0] + V.R[4] * dn[1] + V.R[7] * dn[2]);
-      const float dnw2 = s * (V.R[2] * dn[0] + V.R[5] * dn[1] + V.R[8] * dn[2]);
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        if (P.axis == kk) {
-          dRq[0 * 3 + kk] += dnw0;
-          dRq[1 * 3 + kk] += dnw1;
-          dRq[2 * 3 + kk] += dnw2;
+        for (int k = 0; k < 3; ++k) {
+          dV[k] = 2.f * da * P.V[k] + db * P.V[3 + k];
+          dV[3 + k] = db * P.V[k] + 2.f * dcc * P.V[3 + k];
         }
+        // V = T2 M: dT2 = dV M^T, dM = T2^T dV
+        float dT2[6];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            dT2[i * 3 + j] = dV[i * 3 + 0] * P.M[j * 3 + 0] + dV[i * 3 + 1] * P.M[j * 3 + 1] +
+                             dV[i * 3 + 2] * P.M[j * 3 + 2];
+        float dM[9];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) dM[j * 3 + k] = P.T2[j] * dV[k] + P.T2[3 + j] * dV[3 + k];
+        // T2 = J W: dJ = dT2 W^T (entries J00, J02, J11, J12)
+        const float dJ00 = dT2[0] * V.R[0] + dT2[1] * V.R[1] + dT2[2] * V.R[2];
+        const float dJ02 = dT2[0] * V.R[6] + dT2[1] * V.R[7] + dT2[2] * V.R[8];
+        const float dJ11 = dT2[3] * V.R[3] + dT2[4] * V.R[4] + dT2[5] * V.R[5];
+        const float dJ12 = dT2[3] * V.R[6] + dT2[4] * V.R[7] + dT2[5] * V.R[8];
+        dmc[2] += -dJ00 * V.fx * iz2 - dJ11 * V.fy * iz2;
+        if (!P.clampx) {
+          // J02 = -fx x / z^2
+          dmc[0] += -dJ02 * V.fx * iz2;
+          dmc[2] += dJ02 * 2.f * V.fx * P.mc[0] * iz2 * iz;
+        } else {
+          // J02 = -fx txz / z with txz constant
+          dmc[2] += dJ02 * V.fx * P.txz * iz2;
+        }
+        if (!P.clampy) {
+          dmc[1] += -dJ12 * V.fy * iz2;
+          dmc[2] += dJ12 * 2.f * V.fy * P.mc[1] * iz2 * iz;
+        } else {
+          dmc[2] += dJ12 * V.fy * P.tyz * iz2;
+        }
+        // M = Rq diag(s)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float dsk = dM[0 * 3 + k] * P.Rq[0 * 3 + k] + dM[1 * 3 + k] * P.Rq[1 * 3 + k] +
+                            dM[2 * 3 + k] * P.Rq[2 * 3 + k];
+          gls[k] += dsk * P.s[k];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) dRq[j * 3 + k] += dM[j * 3 + k] * P.s[k];
+        }
+        // Rq(q^) -> q^
+        {
+          const float w = P.qn[0], x = P.qn[1], y = P.qn[2], zq = P.qn[3];
+          const float* Gr = dRq;
+          const float dw = 2.f * (-zq * Gr[1] + y * Gr[2] + zq * Gr[3] - x * Gr[5] - y * Gr[6] + x * Gr[7]);
+          const float dx = 2.f * (y * Gr[1] + zq * Gr[2] + y * Gr[3] - 2.f * x * Gr[4] - w * Gr[5] +
+                                  zq * Gr[6] + w * Gr[7] - 2.f * x * Gr[8]);
+          const float dy = 2.f * (-2.f * y * Gr[0] + x * Gr[1] + w * Gr[2] + x * Gr[3] + zq * Gr[5] -
+                                  w * Gr[6] + zq * Gr[7] - 2.f * y * Gr[8]);
+          const float dz = 2.f * (-2.f * zq * Gr[0] - w * Gr[1] + x * Gr[2] + w * Gr[3] - 2.f * zq * Gr[4] +
+                                  y * Gr[5] + x * Gr[6] + y * Gr[7]);
+          // q^ = q/|q|: dq = (dq^ - q^ (q^ . dq^)) / |q|
+          const float pr = w * dw + x * dx + y * dy + zq * dz;
+          gq[0] += (dw - w * pr) * P.qinv;
+          gq[1] += (dx - x * pr) * P.qinv;
+          gq[2] += (dy - y * pr) * P.qinv;
+          gq[3] += (dz - zq * pr) * P.qinv;
+        }
+        // mu_c = W mu + t
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gm[j] += V.R[0 * 3 + j] * dmc[0] + V.R[1 * 3 + j] * dmc[1] + V.R[2 * 3 + j] * dmc[2];
       }
-    }
 
-    // 2D mean
-    const float z = P.mc[2], iz = 1.f / z, iz2 = iz * iz;
-    dmc[0] += dmx * V.fx * iz;
-    dmc[1] += dmy * V.fy * iz;
-    dmc[2] -= dmx * V.fx * P.mc[0] * iz2 + dmy * V.fy * P.mc[1] * iz2;
-
-    // Cholesky factor of the conic -> Sigma' = (a, b, c), det = a c - b^2:
-    // l11 = sqrt(c/det), l21 = -b/sqrt(c det), l22 = c^-1/2
-    const float a = P.a, b = P.b, c = P.c;
-    const float iD = 1.f / P.det, ic = 1.f / c;
-    const float da = -0.5f * c * iD * (dl11 * P.l11 + dl21 * P.l21);
-    const float db = dl11 * P.l11 * b * iD - dl21 * a * P.l11 * iD;
-    const float dcc = dl11 * P.l11 * 0.5f * (ic - a * iD) - dl21 * P.l21 * 0.5f * (ic + a * iD) -
-                      dl22 * 0.5f * P.l22 * ic;
-    // Sigma' = V V^T: dV0 = 2 da V0 + db V1, dV1 = db V0 + 2 dc V1
-    float dV[6];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      dV[k] = 2.f * da * P.V[k] + db * P.V[3 + k];
-      dV[3 + k] = db * P.V[k] + 2.f * dcc * P.V[3 + k];
+      add_flatten(g, log_scales, n, flatten_weight, sc, gls);
+      store_small(g, gm, gls, gq, gol, accumulate, d_means, d_log_scales, d_quats, d_opac);
     }
-    // V = T2 M: dT2 = dV M^T, dM = T2^T dV
-    float dT2[6];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        dT2[i * 3 + j] = dV[i * 3 + 0] * P.M[j * 3 + 0] + dV[i * 3 + 1] * P.M[j * 3 + 1] +
-                         dV[i * 3 + 2] * P.M[j * 3 + 2];
-    float dM[9];
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) dM[j * 3 + k] = P.T2[j] * dV[k] + P.T2[3 + j] * dV[3 + k];
-    // T2 = J W: dJ = dT2 W^T (entries J00, J02, J11, J12)
-    const float dJ00 = dT2[0] * V.R[0] + dT2[1] * V.R[1] + dT2[2] * V.R[2];
-    const float dJ02 = dT2[0] * V.R[6] + dT2[1] * V.R[7] + dT2[2] * V.R[8];
-    const float dJ11 = dT2[3] * V.R[3] + dT2[4] * V.R[4] + dT2[5] * V.R[5];
-    const float dJ12 = dT2[3] * V.R[6] + dT2[4] * V.R[7] + dT2[5] * V.R[8];
-    dmc[2] += -dJ00 * V.fx * iz2 - dJ11 * V.fy * iz2;
-    if (!P.clampx) {
-      // J02 = -fx x / z^2
-      dmc[0] += -dJ02 * V.fx * iz2;
-      dmc[2] += dJ02 * 2.f * V.fx * P.mc[0] * iz2 * iz;
-    } else {
-      // J02 = -fx txz / z with txz constant
-      dmc[2] += dJ02 * V.fx * P.txz * iz2;
-    }
-    if (!P.clampy) {
-      dmc[1] += -dJ12 * V.fy * iz2;
-      dmc[2] += dJ12 * 2.f * V.fy * P.mc[1] * iz2 * iz;
-    } else {
-      dmc[2] += dJ12 * V.fy * P.tyz * iz2;
-    }
-    // M = Rq diag(s)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float dsk = dM[0 * 3 + k] * P.Rq[0 * 3 + k] + dM[1 * 3 + k] * P.Rq[1 * 3 + k] +
-                        dM[2 * 3 + k] * P.Rq[2 * 3 + k];
-      gls[k] += dsk * P.s[k];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) dRq[j * 3 + k] += dM[j * 3 + k] * P.s[k];
-    }
-    // Rq(q^) -> q^
-    {
-      const float w = P.qn[0], x = P.qn[1], y = P.qn[2], zq = P.qn[3];
-      const float* Gr = dRq;
-      const float dw = 2.f * (-zq * Gr[1] + y * Gr[2] + zq * Gr[3] - x * Gr[5] - y * Gr[6] + x * Gr[7]);
-      const float dx = 2.f * (y * Gr[1] + zq * Gr[2] + y * Gr[3] - 2.f * x * Gr[4] - w * Gr[5] +
-                              zq * Gr[6] + w * Gr[7] - 2.f * x * Gr[8]);
-      const float dy = 2.f * (-2.f * y * Gr[0] + x * Gr[1] + w * Gr[2] + x * Gr[3] + zq * Gr[5] -
-                              w * Gr[6] + zq * Gr[7] - 2.f * y * Gr[8]);
-      const float dz = 2.f * (-2.f * zq * Gr[0] - w * Gr[1] + x * Gr[2] + w * Gr[3] - 2.f * zq * Gr[4] +
-                              y * Gr[5] + x * Gr[6] + y * Gr[7]);
-      // q^ = q/|q|: dq = (dq^ - q^ (q^ . dq^)) / |q|
-      const float pr = w * dw + x * dx + y * dy + zq * dz;
-      gq[0] += (dw - w * pr) * P.qinv;
-      gq[1] += (dx - x * pr) * P.qinv;
-      gq[2] += (dy - y * pr) * P.qinv;
-      gq[3] += (dz - zq * pr) * P.qinv;
-    }
-    // mu_c = W mu + t
-#pragma unroll
-    for (int j = 0; j < 3; ++j) gm[j] += V.R[0 * 3 + j] * dmc[0] + V.R[1 * 3 + j] * dmc[1] + V.R[2 * 3 + j] * dmc[2];
-  }
-
-  if (g < n) {
-    if (flatten_weight != 0.f) {
-      // Eq. 11's flattening term: d(w mean_g min_k exp(ls_gk)) / d ls_gk* = w exp(ls_gk*) / n
-      // at the smallest axis k* (ties: lowest axis)
-      const float l0 = __ldg(log_scales + 3ull * g), l1 = __ldg(log_scales + 3ull * g + 1),
-                  l2 = __ldg(log_scales + 3ull * g + 2);
-      const int k = (l0 <= l1 && l0 <= l2) ? 0 : (l1 <= l2 ? 1 : 2);
-      const float lk = k == 0 ? l0 : (k == 1 ? l1 : l2);
-      const float sc = dout_scale ? __ldg(dout_scale) : 1.f;
-      const float d = flatten_weight * sc * expf(lk) / (float)n;
-      gls[0] += k == 0 ? d : 0.f;
-      gls[1] += k == 1 ? d : 0.f;
-      gls[2] += k == 2 ? d : 0.f;
-    }
-    if (accumulate) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        d_means[3ull * g + i] += gm[i];
-        d_log_scales[3ull * g + i] += gls[i];
+    __syncthreads();
+    // SH gradient rows of this round: coalesced float4 stores, 12 per row
+    const uint32_t nr = min((uint32_t)kPreThreads, nl - base);
+    for (uint32_t i = threadIdx.x; i < nr * 12; i += blockDim.x) {
+      const uint32_t row = i / 12, c4 = i - row * 12;
+      const float* sg = s_gsh + row * kShStride + 4 * c4;
+      float4 v = make_float4(sg[0], sg[1], sg[2], sg[3]);
+      float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * s_list[base + row]) + c4;
+      if (accumulate) {
+        const float4 o = *dst;
+        v.x += o.x;
+        v.y += o.y;
+        v.z += o.z;
+        v.w += o.w;
       }
-      float4* q4 = reinterpret_cast<float4*>(d_quats) + g;
-      float4 o = *q4;
-      o.x += gq[0];
-      o.y += gq[1];
-      o.z += gq[2];
-      o.w += gq[3];
-      *q4 = o;
-      d_opac[g] += gol;
-    } else {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        d_means[3ull * g + i] = gm[i];
-        d_log_scales[3ull * g + i] = gls[i];
-      }
-      reinterpret_cast<float4*>(d_quats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-      d_opac[g] = gol;
+      *dst = v;
     }
-  }
-  // SH gradients: coalesced float4 stores of the block's [nb, 48] slab
-  __syncthreads();
-  const uint32_t nb = min((uint32_t)kPreThreads, n - g0);
-  float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * g0);
-  for (uint32_t i = threadIdx.x; i < nb * 12; i += blockDim.x) {
-    const uint32_t e = 4 * i, row = e / 48, col = e - row * 48;
-    const float* sg = s_gsh + row * kShStride + col;
-    float4 v = make_float4(sg[0], sg[1], sg[2], sg[3]);
-    if (accumulate) {
-      const float4 o = dst[i];
-      v.x += o.x;
-      v.y += o.y;
-      v.z += o.z;
-      v.w += o.w;
-    }
-    dst[i] = v;
+    __syncthreads();
   }
 }
 
@@ -763,7 +817,7 @@ extern "C" int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const 
   const size_t smem = views_bytes(n_views) + kShSlabBytes;
   if (cudaFuncSetAttribute(k_preprocess_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return PGSAG_ERR_CUDA;
-  k_preprocess_bwd<<<pgsag_div_up(n_gauss, threads), threads, smem, (cudaStream_t)stream>>>(
+  k_preprocess_bwd<<<pgsag_div_up(n_gauss, (uint32_t)kPreBwdSlice), threads, smem, (cudaStream_t)stream>>>(
       n_gauss, means, log_scales, quats, opacity_logit, sh, n_views, views,
       reinterpret_cast<const uint4*>(bininfo), grad2d, accumulate, d_means, d_log_scales, d_quats,
       d_opacity_logit, d_sh, dout_scale, flatten_weight, status);

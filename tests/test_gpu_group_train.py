@@ -80,9 +80,16 @@ def test_graph_replayed_iterations_equal_eager_iterations():
     tb.check_status()
     assert all(x is not None for x in ta.graphs)       # every slot captured and replayed
     np.testing.assert_allclose(la, lb, rtol=1e-5)
-    for a, b in zip(A.tensors(), B.tensors()):
-        d = (a - b).abs().max().item()
-        assert d <= 1e-5 * max(1.0, b.abs().max().item()), d
+    # the render adjoint sums gradients with float atomics, so the two runs differ
+    # in the last bits; Adam turns such a difference in a near-zero gradient into
+    # a different step of up to ~3.2 lr (bias-corrected |m| / sqrt(v) <= (1 - b1) /
+    # sqrt(1 - b2)), so a few elements may differ by that much, the rest must not
+    for a, b, lr in zip(A.tensors(), B.tensors(), train.DEFAULT_LRS):
+        diff = (a - b).abs()
+        tol = 1e-5 * max(1.0, b.abs().max().item())
+        frac = (diff > tol).float().mean().item()
+        assert frac <= 1e-3, frac
+        assert diff.max().item() <= 2 * 3.2 * lr * len(order), diff.max().item()
     assert int(ta.step_dev[0].item()) == 9
 
 

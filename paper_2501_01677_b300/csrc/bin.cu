@@ -29,6 +29,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSegMax = 2048;      // keys sorted in shared memory at once by a block (16 KB)
 constexpr int kWarpSegMax = 512;   // longest list a warp sorts on its own (16 keys per lane in registers)
 constexpr int kWarpSortWarps = 8;  // warps per block of the per-warp sort
+#ifndef PGSAG_SORT_MINB
+#define PGSAG_SORT_MINB 3  // resident per-warp sort blocks per SM the register budget must allow
+#endif
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
@@ -368,7 +371,7 @@ __device__ __forceinline__ void warp_sort_list(const uint32_t* __restrict__ in, 
 
 // Step 4a: one warp per active tile sorts lists of up to kWarpSegMax entries
 // in registers; longer lists are appended to `long_list` for k_sort_long.
-__global__ void __launch_bounds__(kWarpSortWarps * 32) k_sort_warp(uint32_t n_active,
+__global__ void __launch_bounds__(kWarpSortWarps * 32, PGSAG_SORT_MINB) k_sort_warp(uint32_t n_active,
                                                                    const uint2* __restrict__ ranges,
                                                                    const uint32_t* __restrict__ dkey,
                                                                    const uint32_t* __restrict__ buf,

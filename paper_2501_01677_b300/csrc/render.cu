@@ -57,9 +57,11 @@ __device__ __forceinline__ TileInfo load_tile(uint32_t t, const uint4* __restric
   return ti;
 }
 
-// Next tile for this CTA: plain grid (one tile per CTA) or a persistent loop over
-// an atomic work counter, optionally through a processing order.  Called by all
-// threads; thread 0 fetches.
+// Next tile for this CTA (adjoint): plain grid (one tile per CTA, known to every thread)
+// or a persistent loop over an atomic work counter (thread 0 fetches, one
+// barrier publishes; the slot alternates between calls so that it is written
+// again only after every thread has passed the next call's barrier), optionally
+// through a processing order.  Called by all threads.
 struct Sched {
   const uint32_t* order;
   uint32_t* counter;
@@ -67,6 +69,27 @@ struct Sched {
 
 __device__ __forceinline__ uint32_t next_tile(const Sched& s, uint32_t& iter, uint32_t n_items,
                                               uint32_t* s_item) {
+  if (!s.counter) {
+    const uint32_t c = iter++ == 0 ? blockIdx.x : n_items;
+    return (c < n_items && s.order) ? __ldg(s.order + c) : c;
+  }
+  uint32_t* slot = s_item + (iter & 1u);
+  if (threadIdx.x == 0) {
+    uint32_t c = atomicAdd(s.counter, 1u);
+    if (c < n_items && s.order) c = __ldg(s.order + c);
+    *slot = c;
+  }
+  __syncthreads();
+  ++iter;
+  return *slot;
+}
+
+// The same with the tile index always broadcast through shared memory by thread
+// 0 (two barriers): the forward uses this form, which keeps the scheduling state
+// out of the other threads' registers (the per-thread form makes the forward
+// spill at its 48-register budget: 0.300 -> 0.324 ms at config 1).
+__device__ __forceinline__ uint32_t next_tile_bcast(const Sched& s, uint32_t& iter, uint32_t n_items,
+                                                    uint32_t* s_item) {
   if (threadIdx.x == 0) {
     uint32_t c;
     if (s.counter)
@@ -241,7 +264,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t iter = 0;
   for (;;) {
-    const uint32_t t = next_tile(sched, iter, n_items, &s_item);
+    const uint32_t t = next_tile_bcast(sched, iter, n_items, &s_item);
     if (t >= n_items) break;
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
@@ -527,7 +550,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
   __shared__ Stage S;
   __shared__ uint32_t spair[kBatch];
   __shared__ float4 sacc[kBatch][4];
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_item[2];
   __shared__ int s_wmax[2][kWarps];
   uint32_t round = 0;
   if (status_bad(status)) return;
@@ -539,7 +562,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t iter = 0;
   for (;;) {
-    const uint32_t t = next_tile(sched, iter, n_items, &s_item);
+    const uint32_t t = next_tile(sched, iter, n_items, s_item);
     if (t >= n_items) break;
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
@@ -699,7 +722,9 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
             }
           }
         }
-        __syncthreads();
+        // the slots are staged and accumulated again only by a following batch of
+        // this round; the next round or tile reaches them past a barrier of its own
+        if (hi - kBatch >= (int)ti.rbeg) __syncthreads();
       }
     }
   }

@@ -194,6 +194,22 @@ def test_results_independent_of_tile_size(config0):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("tile", [(8, 8), (16, 32), (32, 32), (32, 8)])
+def test_gradients_independent_of_tile_size(config0, tile):
+    """The adjoint at every supported tile shape -- tiles of more than 256
+    rendered pixels take several pixel rounds per CTA, each reusing the staged
+    list -- gives the oracle's gradients and, up to the order of the float
+    atomics, the 16x16 tiles' gradients."""
+    g, views, res = config0
+    _, P16 = gpu_run(g, views, tile=(16, 16))
+    _, P = gpu_run(g, views, tile=tile)
+    compare_grads(P, res)
+    for a, b in zip(P.tensors(), P16.tensors()):
+        ga = a.grad.detach().cpu().numpy().astype(np.float64).ravel()
+        gb = b.grad.detach().cpu().numpy().astype(np.float64).ravel()
+        assert rel_l2(ga, gb) < 1e-5
+
+
 def test_batched_views_equal_plain_views():
     """Several views (different resolutions, Gaussian subsets) in one plan give the
     same per-view results as one plan per view; the sort is bit-identical."""

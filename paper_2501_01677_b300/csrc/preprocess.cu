@@ -397,9 +397,12 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
           const EllipseTest et = ellipse_test(P.l11, P.l21, P.l22, -logf(255.f * P.o));
           const int32_t* ta = tile_act + V.tile_base;
           const int rw = x1 - x0 + 1;
+          // every tile of the rectangle is active (the usual case inside the mask):
+          // the activity map need not be read tile by tile
+          const bool all_active = touched == (uint32_t)(rw * (y1 - y0 + 1));
           for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx)
-              if (__ldg(ta + ty * V.tiles_x + tx) >= 0 &&
+              if ((all_active || __ldg(ta + ty * V.tiles_x + tx) >= 0) &&
                   tile_hit(et, mi, ni, mf, nf, tx, ty, V.tile_w, V.tile_h, V.width, V.height))
                 mask |= 1ull << ((ty - y0) * rw + (tx - x0));
           touched = (uint32_t)__popcll(mask);

@@ -500,12 +500,14 @@ extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* v
   if (ws_bytes < w.bytes) return PGSAG_ERR_CAPACITY;
   cudaStream_t s = (cudaStream_t)stream;
   PGSAG_CUDA(cudaMemsetAsync(k_out, 0, sizeof(uint64_t), s));
-  if (n_active_total) {
-    PGSAG_CUDA(cudaMemsetAsync(ranges, 0, (size_t)n_active_total * sizeof(uint2), s));
-    PGSAG_CUDA(cudaMemsetAsync(w.tile_cnt, 0, (size_t)n_active_total * sizeof(uint32_t), s));
+  if (n_pairs == 0 || n_active_total == 0) {
+    // nothing is emitted: every tile's list is empty
+    if (n_active_total) PGSAG_CUDA(cudaMemsetAsync(ranges, 0, (size_t)n_active_total * sizeof(uint2), s));
+    return PGSAG_OK;
   }
+  // (the ranges of every active tile are written by step 2)
+  PGSAG_CUDA(cudaMemsetAsync(w.tile_cnt, 0, (size_t)n_active_total * sizeof(uint32_t), s));
   PGSAG_CUDA(cudaMemsetAsync(w.n_long, 0, sizeof(unsigned long long), s));
-  if (n_pairs == 0 || n_active_total == 0) return PGSAG_OK;
 
   // 1. emission (K accumulates in *k_out)
   k_emit<<<kScanBlocks, kScanThreads, 0, s>>>(n_pairs, (const uint4*)bininfo, views, tile_act,

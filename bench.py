@@ -182,9 +182,10 @@ def algorithmic_bytes(plan, K, n_binned):
         # on mask pixels target 12 + scratch 24
         "loss": 93 * P + 36 * M,
         "tile_stats": 8 * A,
-        # per pixel: list 4 + aux 16 + dout8 32 + out8 32 + neighbour gather (flags 1, index 4, scratch 12);
-        # per duplicate: id 4 + record 64; grad2d zero + write-back 2x64 per pair
-        "render_bwd": 101 * P + 68 * K + 128 * NP,
+        # per pixel: list 4 + aux 16 + dout8 32 + depth 4 (Eq. 4 chain; the Eq. 11 objective reads out8's
+        # 32 instead) + neighbour gather (flags 1, index 4, scratch 12); per duplicate: id 4 + record 64;
+        # grad2d zero + write-back 2x64 per pair
+        "render_bwd": (101 if plan.objective == "eq11" else 73) * P + 68 * K + 128 * NP,
         # gradients written 236 B/G; bininfo 16/pair; binned: params 236 + grad2d 64
         "preprocess_bwd": 236 * N + 16 * NP + 300 * n_binned,
     }
@@ -193,7 +194,7 @@ def algorithmic_bytes(plan, K, n_binned):
 # FP32 work per (pixel, Gaussian) pair: ~10 FLOP to test alpha >= 1/255 (offset,
 # quadratic form); a contributing pair adds ~20 FLOP forward (exp, alpha,
 # transmittance, 7 blended channels) and ~90 backward (transmittance recovery,
-# 7 suffix sums, d alpha, 13 gradient terms).  FMA counts as 2.
+# the suffix term, d alpha, 13 gradient terms).  FMA counts as 2.
 FLOP_TEST, FLOP_FWD_CONTRIB, FLOP_BWD_CONTRIB = 10, 20, 90
 
 

@@ -309,7 +309,8 @@ int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* views,
  *   depth float [1 per compact pixel]
  *   aux   uint4 [1 per compact pixel]: {float bits of final T, index (into dup_pairs) of the
  *         last blended Gaussian, number blended n_contrib, float bits of the soft
- *         count g~ = sum of the blended alphas (PGSAG_RENDER_SOFT_COUNT), else 0}
+ *         count g~ = sum of the blended alphas (PGSAG_RENDER_SOFT_COUNT), else of
+ *         the ray-plane dot s = -N . K^-1 (x+1/2, y+1/2, 1) of Eq. 4}
  * sched may be NULL (one CTA per active tile in index order); with a counter the
  * launch is persistent (ctas_per_sm x SMs CTAs pulling tiles, in `order` if
  * given; ctas_per_sm <= 0: as many as the occupancy allows).
@@ -418,7 +419,11 @@ typedef struct pgsag_ban_gather {
   const float* gc_weight;  /* device, Eq. 9 weights (objective PGSAG_OBJ_EQ11)           */
   float lambda_gc;         /* Eq. 11 lambda (objective PGSAG_OBJ_EQ11)                   */
   uint32_t reserved;       /* 0                                                         */
-} pgsag_ban_gather;       /* 56 bytes */
+  const float* depth;      /* device, nullable: pgsag_render_fwd's depth output; with
+                              objective PGSAG_OBJ_PG the adjoint then takes Eq. 4's
+                              chain rule from it and aux's ray-plane dot instead of
+                              reloading out8                                           */
+} pgsag_ban_gather;       /* 64 bytes */
 
 /*
  * pgsag_render_bwd (Sec. 3.1: the Gaussians' parameters are fitted through the

@@ -59,10 +59,10 @@ class PgsagBanGather(ctypes.Structure):
     for the Eq. 11 objective, the soft-count GC-load gradient)."""
     _fields_ = [("flags_c", c_void_p), ("nbr", c_void_p), ("scratch", c_void_p), ("acc", c_void_p),
                 ("lambda_ban", ctypes.c_float), ("objective", ctypes.c_uint32), ("gc_weight", c_void_p),
-                ("lambda_gc", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+                ("lambda_gc", ctypes.c_float), ("reserved", ctypes.c_uint32), ("depth", c_void_p)]
 
 
-assert ctypes.sizeof(PgsagBanGather) == 56
+assert ctypes.sizeof(PgsagBanGather) == 64
 OBJ_PG, OBJ_EQ11 = 0, 1
 RENDER_SOFT_COUNT = 1
 LAMBDA_GC, LAMBDA_FLAT = 0.41, 100.0

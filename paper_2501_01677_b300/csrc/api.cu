@@ -10,7 +10,7 @@ static_assert(sizeof(pgsag_depth_view) == 96, "pgsag_depth_view layout");
 static_assert(sizeof(pgsag_tsdf_grid) == 32, "pgsag_tsdf_grid layout");
 static_assert(sizeof(pgsag_dssim) == 32, "pgsag_dssim layout");
 static_assert(sizeof(pgsag_adam_tensor) == 48, "pgsag_adam_tensor layout");
-static_assert(sizeof(pgsag_ban_gather) == 56, "pgsag_ban_gather layout");
+static_assert(sizeof(pgsag_ban_gather) == 64, "pgsag_ban_gather layout");
 
 extern "C" const char* pgsag_status_str(int status) {
   switch (status) {

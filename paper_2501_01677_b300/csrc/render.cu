@@ -229,8 +229,9 @@ __device__ __forceinline__ void warp_relevance(const Stage& S, int limit, float4
 }
 
 // Forward outputs of one pixel: {C, D}, {N, A = 1 - T}, the Eq. 4 depth and
-// {T, last blended, count, soft count}.  (x, y) is the pixel centre in image
-// coordinates.
+// {T, last blended, count, soft count (kSoft) or the ray-plane dot s of Eq. 4}.
+// (x, y) is the pixel centre in image coordinates.
+template <bool kSoft>
 __device__ __forceinline__ void write_pixel(uint64_t gp, float4 cd, float4 nt, uint32_t last, uint32_t cnt,
                                             float soft, float x, float y, const ViewLite& V,
                                             float4* __restrict__ out8, float* __restrict__ depth,
@@ -242,7 +243,7 @@ __device__ __forceinline__ void write_pixel(uint64_t gp, float4 cd, float4 nt, u
   const float sdot = -(nt.x * rx + nt.y * ry + nt.z);
   const bool valid = cnt > 0 && sdot > kRayDotMin && cd.w > 0.f;
   depth[gp] = valid ? cd.w / sdot : 0.f;
-  aux[gp] = make_uint4(__float_as_uint(nt.w), last, cnt, __float_as_uint(soft));
+  aux[gp] = make_uint4(__float_as_uint(nt.w), last, cnt, __float_as_uint(kSoft ? soft : sdot));
 }
 
 // kSoft: also sum the blended alphas per pixel (the soft count g~ of Eq. 9's
@@ -372,10 +373,10 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_FWD_MINB) k_render_fwd(
         }
       }
       if (P.has0)
-        write_pixel(P.q0, make_float4(C0.x, C1.x, C2.x, D.x), make_float4(N0.x, N1.x, N2.x, T.x), last0, cnt0,
+        write_pixel<kSoft>(P.q0, make_float4(C0.x, C1.x, C2.x, D.x), make_float4(N0.x, N1.x, N2.x, T.x), last0, cnt0,
                     Gs.x, P.px.x + (float)ox, P.py.x + (float)oy, V, out8, depth, aux);
       if (P.has1)
-        write_pixel(P.q1, make_float4(C0.y, C1.y, C2.y, D.y), make_float4(N0.y, N1.y, N2.y, T.y), last1, cnt1,
+        write_pixel<kSoft>(P.q1, make_float4(C0.y, C1.y, C2.y, D.y), make_float4(N0.y, N1.y, N2.y, T.y), last1, cnt1,
                     Gs.y, P.px.y + (float)ox, P.py.y + (float)oy, V, out8, depth, aux);
     }
   }
@@ -489,6 +490,9 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
                                               const float4* __restrict__ out8, float v[10], int& last,
                                               bool soft, float gscale_gc) {
   const uint4 ax = __ldg(aux + gp);
+  // Eq. 4 chain from the depth output and aux's ray-plane dot (default objective)
+  const bool dep_route = !soft && ban.depth != nullptr;
+  const float dep = dep_route ? __ldg(ban.depth + gp) : 0.f;
   v[9] = 0.f;
   if (soft) {
     // Eq. 9 with the soft count: L_GC = std_i(x_i), x_i = g~_i / w_i over the
@@ -518,7 +522,18 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
   v[8] = T;
   if (ax.z > 0) {
     gd *= gscale;
-    if (gd != 0.f) {
+    if (gd != 0.f && dep_route) {
+      // Depth = D / s > 0 exactly when the pixel is valid; dDepth/dD = 1 / s,
+      // dDepth/dN = D / s^2 r = Depth / s r
+      if (dep > 0.f) {
+        const float is = 1.f / __uint_as_float(ax.w);
+        v[3] += gd * is;
+        const float kk = gd * dep * is;
+        v[4] += kk * rx;
+        v[5] += kk * ry;
+        v[6] += kk;
+      }
+    } else if (gd != 0.f) {
       const float4 o0 = __ldg(out8 + 2 * gp), o1 = __ldg(out8 + 2 * gp + 1);
       const float sdot = -(o1.x * rx + o1.y * ry + o1.z);
       if (sdot > kRayDotMin && o0.w > 0.f) {

@@ -402,7 +402,7 @@ class Plan:
         return L.PgsagBanGather(self.flags_c.data_ptr(), self.nbr.data_ptr(), self.scratch.data_ptr(),
                                 self.acc_loss.data_ptr(), float(getattr(self, "_lambda_ban", LAMBDA_BAN)),
                                 L.OBJ_EQ11 if eq11 else L.OBJ_PG, self.gc_weight.data_ptr() if eq11 else None,
-                                L.LAMBDA_GC, 0)
+                                L.LAMBDA_GC, 0, self.depth.data_ptr())
 
     def render_bwd(self, dout8: torch.Tensor, ddepth: Optional[torch.Tensor] = None,
                    dout_scale: Optional[torch.Tensor] = None, stream=None, ban: bool = False):
@@ -540,15 +540,18 @@ class Plan:
 
     def images(self, v: int):
         """Dense images of view v: rgb [H,W,3], dist [H,W], normal [H,W,3], alpha
-        [H,W], depth [H,W], n_contrib [H,W], final_T, soft_count (sum of the
-        blended alphas; the "eq11" objective only) (zero outside the rendered set)."""
+        [H,W], depth [H,W], n_contrib [H,W], final_T, and soft_count (sum of the
+        blended alphas) under the "eq11" objective or ray_dot (Eq. 4's -N . r)
+        under the default one (zero outside the rendered set)."""
         sl = self.px_slice(v)
         o = self.scatter_image(v, self.out8[sl])
         aux = self.scatter_image(v, self.aux[sl])
-        return dict(rgb=o[..., 0:3], dist=o[..., 3], normal=o[..., 4:7], alpha=o[..., 7],
-                    depth=self.scatter_image(v, self.depth[sl]), n_contrib=aux[..., 2],
-                    final_T=aux[..., 0].contiguous().view(torch.float32),
-                    soft_count=aux[..., 3].contiguous().view(torch.float32))
+        last = aux[..., 3].contiguous().view(torch.float32)
+        out = dict(rgb=o[..., 0:3], dist=o[..., 3], normal=o[..., 4:7], alpha=o[..., 7],
+                   depth=self.scatter_image(v, self.depth[sl]), n_contrib=aux[..., 2],
+                   final_T=aux[..., 0].contiguous().view(torch.float32))
+        out["soft_count" if self.objective == "eq11" else "ray_dot"] = last
+        return out
 
     def flags_image(self, v: int):
         H, W = self.shapes[v]

@@ -40,7 +40,7 @@ def test_view_struct_layout(lib):
 
 
 def test_struct_layouts(lib):
-    assert ctypes.sizeof(L.PgsagBanGather) == 56
+    assert ctypes.sizeof(L.PgsagBanGather) == 64
     assert ctypes.sizeof(L.PgsagDssim) == 32
     assert ctypes.sizeof(L.PgsagAdamTensor) == 48
     assert ctypes.sizeof(L.PgsagDepthView) == 96

@@ -345,7 +345,7 @@ int pgsag_render_fwd(uint32_t n_views, const pgsag_view* views, const float* rec
  *   gather   1: run pass B, dout8 is complete.  0: skip it; dout8 then holds
  *            pass A's values and pgsag_render_bwd must be given a
  *            pgsag_ban_gather built from the same scratch and acc
- *   scratch  float [6 per compact pixel] (only M pixels touched)
+ *   scratch  float [6 per compact pixel] (written for every R pixel: zero off the mask)
  *   acc      double [8 per view]: {sum L1, sum w |n_depth - n|^2, |V|, 0,
  *            |R|, sum g/w, sum (g/w)^2, 0}, overwritten
  *   chunk_scratch  float [8 per chunk] scratch (per-chunk partial sums, reduced
@@ -410,7 +410,7 @@ int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
  * gradient, which saves one pass over the per-pixel arrays.
  */
 typedef struct pgsag_ban_gather {
-  const uint8_t* flags_c;  /* device, compact flags (pgsag_prep_neighbours)             */
+  const uint8_t* flags_c;  /* device, compact flags (pgsag_prep_neighbours; not read)   */
   const void* nbr;         /* device, compact neighbour table (pgsag_prep_neighbours)   */
   const float* scratch;    /* device, loss scratch from pgsag_loss_ban (6 per compact px) */
   const double* acc;       /* device, loss accumulators from pgsag_loss_ban (8 per view) */

@@ -158,6 +158,12 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
         sc[k] = ga[k];
         sc[3 + k] = gb[k];
       }
+    } else {
+      // rendered pixels off the mask have no Eq. 8 term: zero rows, so that a
+      // neighbour's gather needs no flag test
+      float* sc = scratch + 6ull * P.q;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sc[k] = 0.f;
     }
     dout8[2 * P.q] = make_float4(dC[0], dC[1], dC[2], 0.f);
     dout8[2 * P.q + 1] = make_float4(dNo[0], dNo[1], dNo[2], 0.f);
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_b(
   const uint32_t qn[4] = {nb.x, nb.y, nb.z, nb.w};
   bool mk[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) mk[k] = qn[k] != 0xffffffffu && (__ldg(flags_c + qn[k]) & PGSAG_PIX_MASK);
+  for (int k = 0; k < 4; ++k) mk[k] = qn[k] != 0xffffffffu;  // off-mask rows are zero
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (!mk[k]) continue;

@@ -460,14 +460,15 @@ __device__ __forceinline__ float ban_gather(const pgsag_ban_gather& bg, uint32_t
   gn.y *= scale;
   gn.z *= scale;
   // this pixel is P[y+1] of its up neighbour, P[y-1] of the down one, P[x+1] of
-  // the left one, P[x-1] of the right one; only mask neighbours wrote scratch
+  // the left one, P[x-1] of the right one; every rendered neighbour's scratch row
+  // is written by the loss (zero off the mask), so no flag test is needed
   const uint4 nb = __ldg(reinterpret_cast<const uint4*>(bg.nbr) + q);
   const uint32_t qn[4] = {nb.x, nb.y, nb.z, nb.w};
   const float sg[4] = {1.f, -1.f, 1.f, -1.f};
   const int off[4] = {0, 0, 3, 3};
   bool mk[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) mk[k] = qn[k] != 0xffffffffu && (__ldg(bg.flags_c + qn[k]) & PGSAG_PIX_MASK);
+  for (int k = 0; k < 4; ++k) mk[k] = qn[k] != 0xffffffffu;
   float dP0 = 0.f, dP1 = 0.f, dP2 = 0.f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {

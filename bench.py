@@ -171,8 +171,9 @@ def algorithmic_bytes(plan, K, n_binned):
     M = plan.n_mask
     return {
         # means, scales, quats, opacity 44 B/G; per pair: key 4 + bininfo 16;
-        # per binned pair: SH row 192 + rec 64 + tile mask 8
-        "preprocess": 44 * N + 20 * NP + 264 * n_binned,
+        # per binned pair: SH row 192 + rec 64 + tile mask 8 + zeroed grad2d row 64 (read back by the
+        # adjoint's atomics)
+        "preprocess": 44 * N + 20 * NP + 328 * n_binned,
         # bininfo 16 per pair, tile mask 8 per binned pair; per duplicate: emit (tile, pair) 8, scatter reads 8
         # + writes 4, sort reads 4 + depth key 4 + writes 4; per tile: count 4 + range 8
         "bin": 16 * NP + 8 * n_binned + 32 * K + 12 * A,
@@ -183,9 +184,10 @@ def algorithmic_bytes(plan, K, n_binned):
         "loss": 93 * P + 36 * M,
         "tile_stats": 8 * A,
         # per pixel: list 4 + aux 16 + dout8 32 + depth 4 (Eq. 4 chain; the Eq. 11 objective reads out8's
-        # 32 instead) + neighbour gather (flags 1, index 4, scratch 12); per duplicate: id 4 + record 64;
-        # grad2d zero + write-back 2x64 per pair
-        "render_bwd": (101 if plan.objective == "eq11" else 73) * P + 68 * K + 128 * NP,
+        # 32 instead) + neighbour gather (index 4, scratch 12, flags 1 under Eq. 11's out8 route ignored);
+        # per duplicate: id 4 + record 64; grad2d read + write-back 2x64 per binned pair (its zeroing is
+        # the projection's, above)
+        "render_bwd": (101 if plan.objective == "eq11" else 73) * P + 68 * K + 128 * n_binned,
         # gradients written 236 B/G; bininfo 16/pair; binned: params 236 + grad2d 64
         "preprocess_bwd": 236 * N + 16 * NP + 300 * n_binned,
     }

@@ -250,6 +250,9 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, const uint
  *     binned to (popcount = touched); 0 for larger rectangles
  *   rec and tile_mask are written for binned pairs (touched > 0) only; the
  *   other entries keep whatever they held.
+ *   grad2d (nullable, 16-byte aligned) float [16 per pair]: when given, the row
+ *   of every binned pair is zeroed, so that pgsag_render_bwd may be called with
+ *   n_pairs = 0 (only binned rows are accumulated into or read later).
  * n_pairs = sum over views of (g_end - g_begin).
  * This call begins a step: it clears *status before its kernel runs.
  */
@@ -257,7 +260,7 @@ int pgsag_preprocess(uint32_t n_gauss, const float* means, const float* log_scal
                      const float* quats, const float* opacity_logit, const float* sh,
                      uint32_t n_views, const pgsag_view* views, const int32_t* tile_act,
                      const uint32_t* sat, float* rec, uint32_t* depth_key, void* bininfo,
-                     uint64_t* tile_mask, int32_t* status, void* stream);
+                     uint64_t* tile_mask, float* grad2d, int32_t* status, void* stream);
 
 /*
  * pgsag_bin (Sec. 3.1: the projected Gaussians are assigned to the tiles they
@@ -434,7 +437,9 @@ typedef struct pgsag_ban_gather {
  *   grad2d[p*16 + {0..12}] = dL/d{mx, my, l11, l21, l22, o, r, g, b, d, nx, ny, nz}
  * (warp shuffle reduction, shared-memory sum over the CTA's warps, then one
  * float4 atomic add per 4 values per tile).  grad2d (16-byte aligned) is zeroed
- * by this call.  out8, aux, dout8 and ddepth are compact per-pixel arrays
+ * by this call when n_pairs > 0; with n_pairs = 0 it is not cleared and the
+ * rows of the binned pairs must already be zero (pgsag_preprocess given grad2d
+ * clears them).  out8, aux, dout8 and ddepth are compact per-pixel arrays
  * (8, 1, 8, 1 entries per px_list position).  ddepth (nullable) adds a
  * gradient on the depth output, folded into dD and dN through Eq. 4.  ban
  * (nullable, host struct) adds the deferred Eq. 8 gather: dout8 is then the

@@ -143,7 +143,7 @@ def load(path: str = LIB_PATH):
     _sig(lib, "pgsag_prep_lists", c_int, [POINTER(PgsagView), c_uint32, P, P, c_uint32, c_uint32, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_prep_neighbours", c_int, [POINTER(PgsagView), P, c_uint32, c_uint32, P, P, P, P, P])
     _sig(lib, "pgsag_prep_gc_weight", c_int, [POINTER(PgsagView), P, P, c_uint32, c_uint32, P, P, P])
-    _sig(lib, "pgsag_preprocess", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, P, P, P, P, P, P])
+    _sig(lib, "pgsag_preprocess", c_int, [c_uint32, P, P, P, P, P, c_uint32, P, P, P, P, P, P, P, P, P, P])
     _sig(lib, "pgsag_bin_workspace_size", c_size_t, [c_uint32, c_uint32, c_uint64])
     _sig(lib, "pgsag_bin", c_int, [c_uint32, c_uint32, P, c_uint32, P, P, P, P, c_uint64, P, c_size_t, P, P, P, P, P])
     _sig(lib, "pgsag_render_fwd", c_int,

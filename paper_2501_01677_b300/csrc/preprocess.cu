@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
                              const int32_t* __restrict__ tile_act, const uint32_t* __restrict__ sat,
                              float4* __restrict__ rec, uint32_t* __restrict__ dkey,
                              uint4* __restrict__ bininfo, unsigned long long* __restrict__ tmask,
-                             const int32_t* status) {
+                             float4* __restrict__ grad2d, const int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pgsag_view* sv = reinterpret_cast<pgsag_view*>(smem_raw);
   {
@@ -434,6 +434,10 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
     R4[3] = make_float4(P.nc[2], -logf(255.f * P.o), mf, nf);
     dkey[p] = __float_as_uint(P.mc[2]);
     tmask[p] = mask;
+    if (grad2d) {  // the adjoint accumulates into this row
+      float4* G2 = grad2d + 4ull * p;
+      G2[0] = G2[1] = G2[2] = G2[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     bininfo[p] = make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16), vi,
                             touched);
   }
@@ -778,7 +782,7 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
                                 const float* quats, const float* opacity_logit, const float* sh,
                                 uint32_t n_views, const pgsag_view* views, const int32_t* tile_act,
                                 const uint32_t* sat, float* rec, uint32_t* depth_key, void* bininfo,
-                                uint64_t* tile_mask, int32_t* status, void* stream) {
+                                uint64_t* tile_mask, float* grad2d, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !sat || !tile_act || !status) return PGSAG_ERR_ARG;
   if (n_gauss == 0) return cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream) == cudaSuccess ? PGSAG_OK : PGSAG_ERR_CUDA;
@@ -786,6 +790,7 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
     return PGSAG_ERR_ARG;
   if (!aligned16(quats) || !aligned16(sh) || !aligned16(rec) || !aligned16(bininfo) || ((uintptr_t)tile_mask & 7u))
     return PGSAG_ERR_ARG;
+  if (grad2d && !aligned16(grad2d)) return PGSAG_ERR_ARG;
   PGSAG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream));
   const unsigned threads = kPreThreads;
   const size_t smem = views_bytes(n_views);
@@ -795,7 +800,7 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
   k_preprocess<<<pgsag_div_up(n_gauss, threads), threads, smem, (cudaStream_t)stream>>>(
       n_gauss, means, log_scales, quats, opacity_logit, sh, n_views, views, tile_act, sat,
       reinterpret_cast<float4*>(rec), depth_key, reinterpret_cast<uint4*>(bininfo),
-      reinterpret_cast<unsigned long long*>(tile_mask), status);
+      reinterpret_cast<unsigned long long*>(tile_mask), reinterpret_cast<float4*>(grad2d), status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }

@@ -313,7 +313,10 @@ class Plan:
             L.check(self.lib.pgsag_preprocess(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats), _ptr(P.opacity_logit),
                                               _ptr(P.sh), self.n_views, _ptr(self.views_dev), _ptr(self.tile_act),
                                               _ptr(self.sat), _ptr(self.rec), _ptr(self.dkey), _ptr(self.bininfo),
-                                              _ptr(self.tile_mask), _ptr(self.status), s), "pgsag_preprocess")
+                                              _ptr(self.tile_mask), _ptr(self.grad2d), _ptr(self.status), s),
+                    "pgsag_preprocess")
+        # the binned pairs' rows of grad2d are zero until the next render adjoint
+        self._grad2d_clear = True
 
     def bin(self, stream=None):
         s = _stream_ptr(stream)
@@ -410,11 +413,14 @@ class Plan:
         and the deferred Eq. 8 gather runs in this kernel's prologue."""
         s = _stream_ptr(stream)
         bg = ctypes.byref(self._ban_gather()) if ban else None
+        # after a projection the binned rows are already zero: no full clear
+        n_clear = 0 if getattr(self, "_grad2d_clear", False) else self.n_pairs
+        self._grad2d_clear = False
         with self._ev('render_bwd'):
             L.check(self.lib.pgsag_render_bwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),
                                               _ptr(self.ranges), _ptr(self.act_tiles), self.n_active,
                                               _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.aux),
-                                              _ptr(dout8), _ptr(ddepth), bg, _ptr(dout_scale), self.n_pairs,
+                                              _ptr(dout8), _ptr(ddepth), bg, _ptr(dout_scale), n_clear,
                                               _ptr(self.grad2d), _ptr(self.status), s), "pgsag_render_bwd")
 
     def preprocess_bwd(self, P: GaussianParams, grads: Sequence[torch.Tensor], accumulate=False, stream=None,

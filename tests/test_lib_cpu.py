@@ -67,7 +67,7 @@ def test_bin_workspace_size_grows_with_sizes(lib):
 def test_invalid_arguments_rejected_on_host(lib):
     # argument errors are detected before any device work
     assert lib.pgsag_preprocess(10, None, None, None, None, None, 0, None, None, None, None, None, None, None,
-                                None, None) == -5
+                                None, None, None) == -5
     assert lib.pgsag_bin(10, 1, None, 0, None, None, None, None, 0, None, 0, None, None, None, None, None) == -1
     assert lib.pgsag_adam(10, None, None, None, None, 0.1, 0.9, 0.999, 1e-8, 1, None) == -1
     # unknown render flags / objective

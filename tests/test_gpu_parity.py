@@ -210,6 +210,29 @@ def test_gradients_independent_of_tile_size(config0, tile):
         assert rel_l2(ga, gb) < 1e-5
 
 
+def test_repeated_adjoint_after_one_forward(config0):
+    """The projection clears the binned pairs' gradient rows, so the first render
+    adjoint after it skips the full clear; a second adjoint on the same forward
+    must clear them itself and give the same per-pair gradients (up to the order
+    of the float atomics), not twice them."""
+    from paper_2501_01677_b300 import raster
+    g, views, _ = config0
+    P = raster.GaussianParams.from_numpy(g)
+    plan = raster.Plan([v.cam for v in views], [v.mask for v in views], [v.target for v in views], g.n)
+    plan.forward(P)
+    plan.loss(O.LAMBDA_BAN, fused=True, P=P)
+    plan.render_bwd(plan.dout8, ban=True)
+    torch.cuda.synchronize()
+    binned = plan.bininfo[:, 3].cpu().numpy() > 0
+    first = plan.grad2d.cpu().numpy()[binned]
+    plan.render_bwd(plan.dout8, ban=True)
+    torch.cuda.synchronize()
+    plan.check_status()
+    second = plan.grad2d.cpu().numpy()[binned]
+    assert np.abs(first).max() > 0
+    assert rel_l2(second.ravel().astype(np.float64), first.ravel().astype(np.float64)) < 1e-5
+
+
 def test_batched_views_equal_plain_views():
     """Several views (different resolutions, Gaussian subsets) in one plan give the
     same per-view results as one plan per view; the sort is bit-identical."""

@@ -413,7 +413,7 @@ int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_t n_chunks,
  * gradient, which saves one pass over the per-pixel arrays.
  */
 typedef struct pgsag_ban_gather {
-  const uint8_t* flags_c;  /* device, compact flags (pgsag_prep_neighbours; not read)   */
+  const uint8_t* flags_c;  /* compact flags (pgsag_prep_neighbours); not read, nullable */
   const void* nbr;         /* device, compact neighbour table (pgsag_prep_neighbours)   */
   const float* scratch;    /* device, loss scratch from pgsag_loss_ban (6 per compact px) */
   const double* acc;       /* device, loss accumulators from pgsag_loss_ban (8 per view) */

@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) k_view_reduce(const pgsag_view* __restric
 // differences used this pixel, map it to D and N through Eq. 4, scale.
 __global__ void __launch_bounds__(kLossThreads) k_loss_b(
     const pgsag_view* __restrict__ views, uint32_t n_chunks, const uint4* __restrict__ chunks,
-    const uint32_t* __restrict__ px_list, const uint8_t* __restrict__ flags_c, const uint4* __restrict__ nbr,
+    const uint32_t* __restrict__ px_list, const uint4* __restrict__ nbr,
     const float4* __restrict__ out8, const float* __restrict__ depth, const float* __restrict__ scratch,
     const double* __restrict__ acc,
     float lambda_ban, float4* __restrict__ dout8, const int32_t* status) {
@@ -468,7 +468,7 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
       if (r) return r;
     }
     if (gather) {
-      k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint4*)chunks, px_list, flags_c,
+      k_loss_b<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint4*)chunks, px_list,
                                                (const uint4*)nbr, (const float4*)out8, depth, scratch, acc,
                                                lambda_ban, (float4*)dout8, status);
       PGSAG_CHECK_LAUNCH();

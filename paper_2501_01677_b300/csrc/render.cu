@@ -849,7 +849,7 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
   }
   if (n_active == 0) return PGSAG_OK;
   if (!rec || !ranges || !act_tiles || !px_list || !out8 || !aux || !dout8 || !grad2d) return PGSAG_ERR_ARG;
-  if (ban && !(ban->flags_c && ban->nbr && ban->scratch && ban->acc)) return PGSAG_ERR_ARG;
+  if (ban && !(ban->nbr && ban->scratch && ban->acc)) return PGSAG_ERR_ARG;
   if (ban && ((uintptr_t)ban->nbr & 15u)) return PGSAG_ERR_ARG;
   if (soft && (!ban->gc_weight || ((uintptr_t)ban->acc & 7u))) return PGSAG_ERR_ARG;
   pgsag_ban_gather bg{};

@@ -203,6 +203,7 @@ class Plan:
         self.bininfo = torch.empty((npairs, 4), dtype=i32, device=dev)
         self.tile_mask = torch.empty(npairs, dtype=torch.int64, device=dev)
         self.grad2d = torch.empty((npairs, 16), dtype=f32, device=dev)
+        self._grad2d_clear = False  # True between a projection and the next render adjoint
         # ---- per-tile / per-view
         self.ranges = torch.zeros((max(self.n_active, 1), 2), dtype=i32, device=dev)
         self.tile_counts = torch.zeros(max(self.n_active, 1), dtype=i32, device=dev)
@@ -414,7 +415,7 @@ class Plan:
         s = _stream_ptr(stream)
         bg = ctypes.byref(self._ban_gather()) if ban else None
         # after a projection the binned rows are already zero: no full clear
-        n_clear = 0 if getattr(self, "_grad2d_clear", False) else self.n_pairs
+        n_clear = 0 if self._grad2d_clear else self.n_pairs
         self._grad2d_clear = False
         with self._ev('render_bwd'):
             L.check(self.lib.pgsag_render_bwd(self.n_views, _ptr(self.views_dev), _ptr(self.rec), _ptr(self.dup_pairs),

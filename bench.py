@@ -27,6 +27,12 @@ import sys
 import tempfile
 import time
 
+
+def _load_json(path):
+    with open(path) as f:
+        return json.load(f)
+
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -279,7 +285,7 @@ def aggregate(ms_local: float, units_local: float, steps: int, world: int, dist_
 
 def peaks():
     try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+        return _load_json(os.path.join(ROOT, "MEASURED_PEAKS.json")), "measured"
     except Exception:
         return {"hbm_gbs": 6400.0}, "fallback"
 

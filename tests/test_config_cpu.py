@@ -11,7 +11,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def test_paper_constants_match_the_golden_fixture():
-    g = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        g = json.load(f)
     c = PgsagConfig()
     assert c.boundary_weight == g["boundary_weight"]["value"]
     assert c.lambda_gc == g["lambda_gc"]["value"]

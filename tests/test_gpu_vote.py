@@ -11,6 +11,12 @@ import torch
 import pgsag_synth as syn
 from oracle import vote_oracle as VO
 
+
+def _load_json(path):
+    with open(path) as f:
+        return json.load(f)
+
+
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -58,7 +64,7 @@ def test_pack_mask_bits_ragged_rows():
 
 
 def test_hand_worked_example():
-    g = json.load(open(os.path.join(GOLDEN, "vote_example.json")))
+    g = _load_json(os.path.join(GOLDEN, "vote_example.json"))
     cams = [SimpleNamespace(R=np.eye(3, dtype=np.float32), t=np.asarray(v["t"], np.float32), fx=2.0, fy=2.0,
                             cx=2.0, cy=2.0, znear=0.2, width=4, height=4) for v in g["views"]]
     masks = [np.asarray(v["mask"], np.uint8) for v in g["views"]]

@@ -12,13 +12,19 @@ import torch
 import pgsag_synth as syn
 from oracle import pgsag_oracle as O
 
+
+def _load_json(path):
+    with open(path) as f:
+        return json.load(f)
+
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 # ----------------------------------------------------------------- constants
 
 def test_paper_constants_golden():
-    g = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
+    g = _load_json(os.path.join(GOLDEN, "paper_constants.json"))
     assert O.W_BOUNDARY == g["boundary_weight"]["value"]
     assert O.LAMBDA_GC == g["lambda_gc"]["value"]
     assert O.LAMBDA_BAN == g["lambda_4_ban"]["value"]

@@ -14,11 +14,17 @@ from scipy.spatial.transform import Rotation
 import pgsag_synth as syn
 from oracle import vote_oracle as VO
 
+
+def _load_json(path):
+    with open(path) as f:
+        return json.load(f)
+
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def example():
-    g = json.load(open(os.path.join(GOLDEN, "vote_example.json")))
+    g = _load_json(os.path.join(GOLDEN, "vote_example.json"))
     cams = [SimpleNamespace(R=np.eye(3, dtype=np.float32), t=np.asarray(v["t"], np.float32), fx=2.0, fy=2.0,
                             cx=2.0, cy=2.0, znear=0.2, width=4, height=4) for v in g["views"]]
     masks = [np.asarray(v["mask"], np.uint8) for v in g["views"]]

@@ -399,7 +399,7 @@ def test_autograd_gradient_matches_central_differences(seed):
             x0 = base[idx]
             lp = _loss_at(g, v, name, idx, x0 + h)
             lm = _loss_at(g, v, name, idx, x0 - h)
-            l0 = float(res["loss"]["total"])
+            l0 = float(res["loss"]["total"].detach())
             fwd, bwd = (lp - l0) / h, (l0 - lm) / h
             if abs(fwd - bwd) > 1e-3 * max(abs(fwd), abs(bwd), 1e-6):
                 continue
@@ -478,7 +478,7 @@ def test_eq11_autograd_gradient_matches_central_differences():
     rng = np.random.default_rng(7)
     h = 1e-6
     checked = 0
-    l0 = float(res["loss"]["total"])
+    l0 = float(res["loss"]["total"].detach())
     for name in ("means", "log_scales", "quats", "opacity_logit", "sh"):
         base = res["params"][name].detach().reshape(-1).numpy()
         gr = res["grads"][name].reshape(-1).numpy()
@@ -558,8 +558,8 @@ def test_l_rgb_dssim_weights_and_gradient_central_differences():
     C = torch.tensor(rng.random((H, W, 3)), requires_grad=True)
     T = torch.tensor(rng.random((H, W, 3)))
     l, s = O.l_rgb_dssim(C, T, M, R)
-    l1 = float((C - T).abs().sum(-1)[torch.from_numpy(M)].sum() / (3 * M.sum()))
-    assert float(l) == pytest.approx(0.8 * l1 + 0.2 * (1 - float(s)), rel=1e-14)
+    l1 = float((C.detach() - T).abs().sum(-1)[torch.from_numpy(M)].sum() / (3 * M.sum()))
+    assert float(l.detach()) == pytest.approx(0.8 * l1 + 0.2 * (1 - float(s.detach())), rel=1e-14)
     l.backward()
     g = C.grad.numpy()
     # pixels outside R do not enter the loss

@@ -508,6 +508,14 @@ def ours(args):
         t = min(times)
         cpu = {"value": float(cv.mask.sum()) / 1e6 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": sample, "s_per_step": t}
+        # the same oracle step on one host thread (its single-core figure)
+        nt = torch.get_num_threads()
+        torch.set_num_threads(1)
+        try:
+            t1 = min(run_oracle_steps(g, cv, 1)[0])
+        finally:
+            torch.set_num_threads(nt)
+        cpu["single_core"] = {"value": float(cv.mask.sum()) / 1e6 / t1, "s_per_step": t1}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

@@ -22,7 +22,11 @@
 
 namespace pgsag {
 
-constexpr int kScanBlocks = 592;   // 4 blocks per SM on 148 SMs
+#ifndef PGSAG_SCAN_BLOCKS
+#define PGSAG_SCAN_BLOCKS 592  // 4 blocks per SM on 148 SMs
+#endif
+constexpr int kScanBlocks = PGSAG_SCAN_BLOCKS;
+static_assert(kScanBlocks >= 1 && kScanBlocks <= 1024, "k_scan_partials scans one partial per thread of one 1024-thread block");
 constexpr int kScanThreads = 256;
 constexpr int kEmitChunk = 1024;   // pairs gathered per block round in the emission
 constexpr int kSortThreads = 256;

@@ -8,11 +8,14 @@
 // coalesced), then each warp walks the batch, skipping -- as a warp-uniform
 // branch -- every Gaussian whose alpha >= 1/255 box misses the bounding box of
 // the warp's pixels.  A pair is rejected before the exponential when the
-// exponent is below the Gaussian's threshold -ln(255 o) (alpha < 1/255).  The forward stops a batch loop when every warp of the
-// CTA has terminated (__syncthreads_or).  The adjoint re-walks the list back to
-// front from the CTA's last blended Gaussian, recovers T by division, reduces
-// each Gaussian's 13 gradient values across the warp with 16 shuffles, sums the
-// warps in shared memory and issues one float4 atomic per 4 values per tile.
+// exponent is below the Gaussian's threshold -ln(255 o) (alpha < 1/255).  The
+// forward stops a batch loop when every warp of the CTA has terminated
+// (__syncthreads_or).  The adjoint re-walks the list back to front from the
+// CTA's last blended Gaussian, recovers T by division, carries one suffix
+// scalar per pixel (see BwdPix), reduces each Gaussian's 13 gradient values
+// across the warp with 16 shuffles, sums the warps in shared memory and issues
+// one float4 atomic per 4 values per tile; its prologue does the loss's
+// deferred Eq. 8 gather and the Eq. 4 chain from the depth output.
 #include "common.cuh"
 
 namespace pgsag {

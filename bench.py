@@ -189,11 +189,11 @@ def algorithmic_bytes(plan, K, n_binned):
         # on mask pixels target 12 + scratch 24
         "loss": 93 * P + 36 * M,
         "tile_stats": 8 * A,
-        # per pixel: list 4 + aux 16 + dout8 32 + depth 4 (Eq. 4 chain; the Eq. 11 objective reads out8's
-        # 32 instead) + neighbour gather (index 4, scratch 12, flags 1 under Eq. 11's out8 route ignored);
+        # per pixel: list 4 + aux 16 + dout8 32 + depth 4 (Eq. 4 chain; the Eq. 11 objective also reads
+        # the 16-byte normal half of out8) + neighbour gather (index 4, scratch 12);
         # per duplicate: id 4 + record 64; grad2d read + write-back 2x64 per binned pair (its zeroing is
         # the projection's, above)
-        "render_bwd": (101 if plan.objective == "eq11" else 73) * P + 68 * K + 128 * n_binned,
+        "render_bwd": (89 if plan.objective == "eq11" else 73) * P + 68 * K + 128 * n_binned,
         # gradients written 236 B/G; bininfo 16/pair; binned: params 236 + grad2d 64
         "preprocess_bwd": 236 * N + 16 * NP + 300 * n_binned,
     }

@@ -422,10 +422,11 @@ typedef struct pgsag_ban_gather {
   const float* gc_weight;  /* device, Eq. 9 weights (objective PGSAG_OBJ_EQ11)           */
   float lambda_gc;         /* Eq. 11 lambda (objective PGSAG_OBJ_EQ11)                   */
   uint32_t reserved;       /* 0                                                         */
-  const float* depth;      /* device, nullable: pgsag_render_fwd's depth output; with
-                              objective PGSAG_OBJ_PG the adjoint then takes Eq. 4's
-                              chain rule from it and aux's ray-plane dot instead of
-                              reloading out8                                           */
+  const float* depth;      /* device, nullable: pgsag_render_fwd's depth output; the
+                              adjoint then takes Eq. 4's chain rule from it and the
+                              ray-plane dot (aux's fourth word under PGSAG_OBJ_PG, the
+                              rendered normal under PGSAG_OBJ_EQ11) instead of
+                              reloading all of out8                                    */
 } pgsag_ban_gather;       /* 64 bytes */
 
 /*

@@ -494,9 +494,12 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
                                               const float4* __restrict__ out8, float v[10], int& last,
                                               bool soft, float gscale_gc) {
   const uint4 ax = __ldg(aux + gp);
-  // Eq. 4 chain from the depth output and aux's ray-plane dot (default objective)
-  const bool dep_route = !soft && ban.depth != nullptr;
+  // Eq. 4 chain from the depth output and the ray-plane dot s: aux.w holds s
+  // under the default objective; under Eq. 11 (aux.w = soft count) s comes from
+  // the rendered normal, the second half of the pixel's out8 record
+  const bool dep_route = ban.depth != nullptr;
   const float dep = dep_route ? __ldg(ban.depth + gp) : 0.f;
+  const float4 nrm = (dep_route && soft) ? __ldg(out8 + 2 * gp + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
   v[9] = 0.f;
   if (soft) {
     // Eq. 9 with the soft count: L_GC = std_i(x_i), x_i = g~_i / w_i over the
@@ -530,7 +533,7 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
       // Depth = D / s > 0 exactly when the pixel is valid; dDepth/dD = 1 / s,
       // dDepth/dN = D / s^2 r = Depth / s r
       if (dep > 0.f) {
-        const float is = 1.f / __uint_as_float(ax.w);
+        const float is = 1.f / (soft ? -(nrm.x * rx + nrm.y * ry + nrm.z) : __uint_as_float(ax.w));
         v[3] += gd * is;
         const float kk = gd * dep * is;
         v[4] += kk * rx;

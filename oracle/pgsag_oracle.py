@@ -504,7 +504,9 @@ def losses(out, depth, valid, pix, sets, cam: Cam, target: np.ndarray, dssim: bo
     nd = cr / crn[:, None]
     Nv = N[cvt, cut]
     nr = Nv / torch.linalg.norm(Nv, dim=-1, keepdim=True)
-    w = torch.where(torch.from_numpy(E[cvt.numpy(), cut.numpy()]), W_BOUNDARY, 1.0).to(DT)
+    # weight built in float64 (a Python-scalar torch.where would round 0.1 to float32)
+    w = torch.where(torch.from_numpy(E[cvt.numpy(), cut.numpy()]), torch.tensor(W_BOUNDARY, dtype=DT),
+                    torch.tensor(1.0, dtype=DT))
     nV = int(cvt.shape[0])
     if nV:
         l_ban = (w * ((nd - nr) ** 2).sum(-1)).sum() / nV

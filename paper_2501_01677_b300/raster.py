@@ -69,7 +69,10 @@ class Plan:
       first forward (one host synchronisation) and grows it on overflow.
 
     Outputs of forward() live in this plan's buffers and stay valid until the
-    next forward on the same plan; backward must run before that.
+    next forward on the same plan; backward must run before that.  One plan
+    therefore holds one forward in flight: the autograd Functions record the
+    plan's forward count and their backward raises if another forward ran on
+    the same plan in between (use one plan per concurrently live graph).
     """
 
     def __init__(self, cams, masks, targets, n_gauss: int, g_ranges: Optional[Sequence[Tuple[int, int]]] = None,
@@ -221,6 +224,7 @@ class Plan:
         self.sched_order = None
         self.sched_counter = torch.zeros(1, dtype=i32, device=dev)
         self.stage_events = None  # list -> (name, start event, end event) per step call
+        self.forward_count = 0  # projections run on this plan (each starts a new forward)
         self._auto_capacity = capacity is None
         self._alloc_capacity(int(capacity) if capacity is not None else max(4 * self.n_pairs, 1 << 16))
 
@@ -310,6 +314,7 @@ class Plan:
 
     def preprocess(self, P: GaussianParams, stream=None):
         s = _stream_ptr(stream)
+        self.forward_count += 1
         with self._ev('preprocess'):
             L.check(self.lib.pgsag_preprocess(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats), _ptr(P.opacity_logit),
                                               _ptr(P.sh), self.n_views, _ptr(self.views_dev), _ptr(self.tile_act),
@@ -566,7 +571,26 @@ class Plan:
 
 
 def new_param_grads(P: GaussianParams):
+    """Gradient buffers for pgsag_preprocess_bwd, which overwrites every element
+    (uninitialised: a step whose device status is set skips its kernels, so its
+    gradients are meaningful only once the status reads zero)."""
     return [torch.empty_like(t) for t in P.tensors()]
+
+
+def _check_same_forward(ctx):
+    if ctx.plan.forward_count != ctx.forward_count:
+        raise RuntimeError("another forward ran on this Plan after the one being differentiated: its buffers "
+                           "(outputs, upstream gradients, projected records) now hold the newer forward; "
+                           "use one Plan per live autograd graph")
+
+
+def _finish_backward(ctx):
+    """check=True: read the device status once (one host synchronisation) and
+    raise if any kernel of the step flagged an error, since the kernels then
+    skipped their work and the gradients are not valid.  check=False (CUDA-graph
+    capture): the caller must call plan.check_status() before using them."""
+    if ctx.check:
+        ctx.plan.check_status()
 
 
 class RenderLossFn(torch.autograd.Function):
@@ -574,7 +598,12 @@ class RenderLossFn(torch.autograd.Function):
     L_rgb + lambda_4 L_ban  (Eq. 8, Eq. 10 restricted to the L1 photometric and
     boundary-aware normal terms), or with plan.set_objective("eq11") Eq. 11's
     (1 - lambda)(L_rgb + lambda_3 L_s + lambda_4 L_ban) + lambda GC-load.  Backward runs the adjoint renderer on the
-    gradient the loss kernel produced and the preprocess adjoint."""
+    gradient the loss kernel produced and the preprocess adjoint.
+
+    The plan's buffers carry the state between forward and backward, so no other
+    forward may run on the plan before this one's backward (it raises if one
+    did).  With check=False the step never synchronises the host; the gradients
+    are then valid only once plan.check_status() reports no device error."""
 
     @staticmethod
     def forward(ctx, plan: Plan, lambda_ban: float, check: bool, means, log_scales, quats, opacity_logit, sh):
@@ -586,22 +615,31 @@ class RenderLossFn(torch.autograd.Function):
         ctx.plan = plan
         ctx.P = P
         ctx.per_view = out
+        ctx.check = bool(check)
+        ctx.forward_count = plan.forward_count
         return out[3 * plan.n_views]
 
     @staticmethod
     def backward(ctx, g):
         plan, P = ctx.plan, ctx.P
+        _check_same_forward(ctx)
         g = g.contiguous().to(torch.float32)
         plan.render_bwd(plan.dout8, None, g, ban=True)
         grads = new_param_grads(P)
         plan.preprocess_bwd(P, grads, dout_scale=g)
+        _finish_backward(ctx)
         return (None, None, None) + tuple(grads)
 
 
 class RenderFn(torch.autograd.Function):
     """Differentiable masked renderer: params -> (out8 [n_render, 8] = {rgb, dist,
     normal, alpha}, depth [n_render]) for all views' rendered pixels (Eq. 1-4),
-    row q holding the pixel plan.px_list[q] (view by plan.px_slice)."""
+    row q holding the pixel plan.px_list[q] (view by plan.px_slice).
+
+    The returned tensors are the plan's own output buffers (no copy): the next
+    forward on the same plan overwrites them, and backward raises if such a
+    forward ran before it.  With check=False the gradients are valid only once
+    plan.check_status() reports no device error."""
 
     @staticmethod
     def forward(ctx, plan: Plan, check: bool, means, log_scales, quats, opacity_logit, sh):
@@ -609,11 +647,14 @@ class RenderFn(torch.autograd.Function):
         plan.forward(P, check=check)
         ctx.plan = plan
         ctx.P = P
+        ctx.check = bool(check)
+        ctx.forward_count = plan.forward_count
         return plan.out8.detach(), plan.depth.detach()
 
     @staticmethod
     def backward(ctx, g_out8, g_depth):
         plan, P = ctx.plan, ctx.P
+        _check_same_forward(ctx)
         if g_out8 is None:
             g_out8 = torch.zeros_like(plan.out8)
         g_out8 = g_out8.contiguous()
@@ -622,6 +663,7 @@ class RenderFn(torch.autograd.Function):
         plan.render_bwd(g_out8, g_depth, None)
         grads = new_param_grads(P)
         plan.preprocess_bwd(P, grads)
+        _finish_backward(ctx)
         return (None, None) + tuple(grads)
 
 

@@ -102,6 +102,7 @@ def test_fullsize_sampled_gaussian_gradients(aerial):
     cand = np.nonzero(ok_rect.numpy() & (area > 20) & (area < 400) & (u0 >= 0) & (v0 >= 0) & (u1 < W) & (v1 < H))[0]
     rng.shuffle(cand)
     checked = 0
+    refs, gots = {k: [] for k in NAMES}, {k: [] for k in NAMES}
     for gi in cand:
         if checked >= 8:
             break
@@ -135,9 +136,17 @@ def test_fullsize_sampled_gaussian_gradients(aerial):
         got = np.concatenate([gpu[k][gi].ravel().astype(np.float64) for k in NAMES])
         if np.linalg.norm(ref) == 0:
             continue
-        assert rel_l2(got, ref) < 2e-3, (gi, rel_l2(got, ref))
+        print("gaussian", int(gi), "rel-L2", rel_l2(got, ref))
+        assert rel_l2(got, ref) <= 1e-3, (gi, rel_l2(got, ref))
+        for k in NAMES:
+            refs[k].append(p1[k].grad.numpy().ravel())
+            gots[k].append(gpu[k][gi].ravel().astype(np.float64))
         checked += 1
     assert checked >= 6
+    # per parameter tensor over the sampled Gaussians (the gradient tolerance's own form)
+    per = {k: rel_l2(np.concatenate(gots[k]), np.concatenate(refs[k])) for k in NAMES}
+    print("per-tensor rel-L2 over the sample:", per)
+    assert max(per.values()) <= 1e-3, per
 
 
 def test_fullsize_loss_directional_derivative_sh(aerial):

@@ -520,7 +520,13 @@ int pgsag_schedule_lpt(uint32_t n_active_total, const void* ranges, const void* 
  *     pixels); larger inputs return PGSAG_ERR_CAPACITY and enqueue nothing.
  *   - The first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress (that device must be current); make this first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the process: after a
+ *     cudaDeviceReset (or anything else that destroys and re-creates the
+ *     device's primary context) it is stale, and this entry point must not be
+ *     called again on that device.
+ *   - Every view's chunk range [chunk_base, chunk_base + n_chunks) in the
+ *     device view table must lie inside [0, n_chunks); a view table that does
+ *     not agree sets PGSAG_DEV_BOUNDS in *status and the view is skipped.
  *   - Calls share the array: calls that overlap on the GPU (other streams or
  *     host threads on the same device) race and give wrong results.
  *   - Allocates nothing (no cudaMalloc / cudaFree, no allocating library call).

@@ -184,15 +184,21 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
 
 // Grid (blocks, views): each block sums a slice of the view's per-chunk partials
 // (pstride floats per chunk, the first ncomp <= 8 used) in double and adds them
-// into acc[stride * v + 0 .. ncomp) (acc zeroed before).
+// into acc[stride * v + 0 .. ncomp) (acc zeroed before).  n_rows = partial rows
+// available: a view whose chunk range leaves them sets PGSAG_DEV_BOUNDS and is
+// skipped.
 __global__ void __launch_bounds__(256) k_view_reduce(const pgsag_view* __restrict__ views,
                                                      const float* __restrict__ partial, int pstride, int ncomp,
-                                                     int stride, double* __restrict__ acc,
-                                                     const int32_t* status) {
+                                                     int stride, double* __restrict__ acc, uint32_t n_rows,
+                                                     int32_t* status) {
   __shared__ double sh[8][8];
   if (status_bad(status)) return;
   const pgsag_view* V = views + blockIdx.y;
   const uint32_t b = __ldg(&V->chunk_base), n = __ldg(&V->n_chunks);
+  if ((uint64_t)b + n > n_rows) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) status_set(status, PGSAG_DEV_BOUNDS);
+    return;
+  }
   const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
   const uint32_t lo = min(n, blockIdx.x * per), hi = min(n, lo + per);
   if (lo >= hi) return;
@@ -460,7 +466,7 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
                                              (float4*)chunk_scratch, (float4*)dout8, status);
     PGSAG_CHECK_LAUNCH();
     k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 8, gc_weight ? 7 : 3, 8,
-                                                                acc, status);
+                                                                acc, n_chunks, status);
     PGSAG_CHECK_LAUNCH();
     if (dssim && dssim->n_active_total) {
       const int r = launch_dssim(dssim->n_active_total, dssim->tile_w, dssim->tile_h, views, act_tiles, dssim->pidx,
@@ -510,7 +516,8 @@ extern "C" int pgsag_tile_stats(uint32_t n_views, const pgsag_view* views, uint3
         views, n_chunks, (const uint4*)chunks, px_list, (const uint4*)aux, gc_weight,
         (float4*)chunk_scratch, status);
     PGSAG_CHECK_LAUNCH();
-    k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 4, 3, 3, acc, status);
+    k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 4, 3, 3, acc, n_chunks,
+                                                                status);
     PGSAG_CHECK_LAUNCH();
   }
   k_gc_final<<<pgsag_div_up(n_views, 128), 128, 0, s>>>(n_views, acc, gc_load, status);
@@ -544,10 +551,12 @@ extern "C" int pgsag_prep_gc_weight(const pgsag_view* view, const float* target,
 // library holds it (kNoAllocScratchBytes) until the process exits.  Host code
 // cannot use its name as a device address, so its address is looked up once per
 // device with cudaGetSymbolAddress, on that device's first call (with the device
-// current).  Make that first call before any stream capture.  All calls share
-// the array and it keeps the last call's contents: the accumulators are cleared
-// at the start of every call, and calls that overlap on the GPU (different
-// streams, or host threads on the same device) race on it.
+// current).  Make that first call before any stream capture.  The address is
+// kept for the process, so it is stale after a cudaDeviceReset (the entry point
+// must not be called on that device again).  All calls share the array and it
+// keeps the last call's contents: the accumulators are cleared at the start of
+// every call, and calls that overlap on the GPU (different streams, or host
+// threads on the same device) race on it.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr uint32_t kNoAllocMaxChunks = PGSAG_NOALLOC_MAX_CHUNKS;

@@ -72,6 +72,9 @@ def parse():
                     help="batched workload: use the launch shape the autotuner chose on B300 (16x16 tiles, "
                          "occupancy-deep persistent queue, index order) instead of tuning")
     ap.add_argument("--retune", action="store_true", help="batched workload: ignore the autotune cache")
+    ap.add_argument("--ncu-region", default="none", choices=["none", "plain"],
+                    help="batched workload: run one more eager plain step between cudaProfilerStart/Stop, for "
+                         "ncu --profile-from-start off (a launch list of one plain step)")
     ap.add_argument("--no-batched", action="store_true",
                     help="aerial workload: leave out the batched-vs-plain sub-record (8 sub-regions, 32 views)")
     return ap.parse_args()
@@ -662,14 +665,34 @@ def run_batched(args, tune: bool, steps: int, warmup: int):
     grads_plain = raster.new_param_grads(P)
 
     def plain_step():
+        # each plan covers its sub-region's Gaussian span only: the first view of
+        # a sub-region writes the span's gradients, its other views add to them
+        seen = set()
         for i, pl in enumerate(plans):
-            pl.step(P, grads_plain, accumulate=i > 0)
+            pl.step(P, grads_plain, accumulate=owner[i] in seen)
+            seen.add(owner[i])
 
     for _ in range(warmup):
         plain_step()
     ms_plain = timed(plain_step, steps)
     for pl in plans:
         pl.check_status()
+    # per-stage split of one eager plain step (CUDA events around each stage call)
+    for pl in plans:
+        pl.stage_events = []
+    plain_step()
+    torch.cuda.synchronize()
+    stages_plain = {}
+    for pl in plans:
+        for name, a, b in pl.stage_events:
+            stages_plain[name] = stages_plain.get(name, 0.0) + a.elapsed_time(b)
+        pl.stage_events = None
+    if getattr(args, "ncu_region", "none") == "plain":
+        # one eager plain step between cudaProfilerStart/Stop (ncu --profile-from-start off)
+        torch.cuda.profiler.start()
+        plain_step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     n_mask = sum(pl.n_mask for pl in plans)
     launches_plain = sum(pl.kernel_launches_per_step() for pl in plans)
     del plans
@@ -686,6 +709,15 @@ def run_batched(args, tune: bool, steps: int, warmup: int):
     ms_batched = timed(graph.replay, steps)
     ck = clocks.stop()
     plan.check_status()
+    # per-stage split of one eager batched step
+    plan.stage_events = []
+    plan.step(P, grads)
+    torch.cuda.synchronize()
+    stages_batched = {}
+    for name, a, b in plan.stage_events:
+        stages_batched[name] = stages_batched.get(name, 0.0) + a.elapsed_time(b)
+    plan.stage_events = None
+    plan.check_status()
     assert plan.n_mask == n_mask
     diff = max(float((a - b).abs().max() / (b.abs().max() + 1e-30)) for a, b in zip(grads, grads_plain))
     return {
@@ -694,6 +726,7 @@ def run_batched(args, tune: bool, steps: int, warmup: int):
         "ms_plain": ms_plain, "ms_batched": ms_batched, "ratio": ms_plain / ms_batched,
         "launches_plain": launches_plain, "launches_batched": plan.kernel_launches_per_step(),
         "shape": shape, "table": table, "t_tune": t_tune, "clocks": ck, "grad_diff": diff,
+        "stages_plain": stages_plain, "stages_batched": stages_batched,
     }
 
 
@@ -710,6 +743,7 @@ def batched_summary(r, tuned: bool) -> dict:
             "launch_shape": {"tile": f"{sh.tile_w}x{sh.tile_h}", "ctas_per_sm": sh.ctas_per_sm, "lpt": sh.lpt,
                              "source": "autotuned in this run" if tuned else "the autotuner's choice on B300"},
             "gpu_launches_per_step": {"plain": r["launches_plain"], "batched": r["launches_batched"]},
+            "eager_stages_ms": {"plain": r["stages_plain"], "batched": r["stages_batched"]},
             "grad_max_rel_diff_batched_vs_plain": r["grad_diff"], "clocks": r["clocks"]}
 
 

@@ -63,7 +63,10 @@ class Plan:
     masks: uint8 [H,W] building masks (host numpy or device tensors)
     targets: float32 [H,W,3] photometric targets
     g_ranges: per view (g_begin, g_end) into the shared Gaussian arrays; default
-      every view renders all n_gauss Gaussians
+      every view renders all n_gauss Gaussians.  The plan's calls cover only the
+      span [min g_begin, max g_end) of the arrays (offset pointers): a plan of one
+      sub-region of a large shared array does not touch the other Gaussians; its
+      gradients outside the span are left as they are (see new_grads)
     tile: (tile_w, tile_h), each in {8, 16, 32}
     capacity: maximum number of (tile, Gaussian) duplicates; None sizes it on the
       first forward (one host synchronisation) and grows it on overflow.
@@ -89,6 +92,11 @@ class Plan:
         views = (L.PgsagView * V)()
         pix_base = tile_base = sat_base = pair_base = 0
         self.shapes = []
+        spans = [(g_ranges[v] if g_ranges is not None else (0, self.n_gauss)) for v in range(V)]
+        self.g_lo = min(int(a) for a, _ in spans) if V else 0
+        self.g_hi = max(int(b) for _, b in spans) if V else 0
+        if not (0 <= self.g_lo <= self.g_hi <= self.n_gauss):
+            raise ValueError("bad Gaussian range")
         for v, cam in enumerate(cams):
             vw = views[v]
             R = np.asarray(cam.R, np.float32).reshape(9)
@@ -102,10 +110,10 @@ class Plan:
             W, H = int(cam.width), int(cam.height)
             vw.width, vw.height, vw.tile_w, vw.tile_h = W, H, tw, th
             vw.tiles_x, vw.tiles_y = (W + tw - 1) // tw, (H + th - 1) // th
-            gb, ge = g_ranges[v] if g_ranges is not None else (0, self.n_gauss)
+            gb, ge = spans[v]
             if not (0 <= gb <= ge <= self.n_gauss):
                 raise ValueError("bad Gaussian range")
-            vw.g_begin, vw.g_end = gb, ge
+            vw.g_begin, vw.g_end = gb - self.g_lo, ge - self.g_lo  # relative to the span
             vw.pair_base = pair_base
             vw.tile_base = tile_base
             vw.sat_base = sat_base
@@ -312,12 +320,31 @@ class Plan:
     def k_value(self) -> int:
         return int(self.k_out.item())
 
+    def _span(self, P: GaussianParams):
+        """(n, pointers of means, log_scales, quats, opacity_logit, sh) of the
+        plan's Gaussian span of P's arrays (or of gradient arrays shaped like
+        them)."""
+        if P.n != self.n_gauss:
+            raise ValueError(f"the plan was built for {self.n_gauss} Gaussians, got {P.n}")
+        lo = self.g_lo
+        ptrs = [ctypes.c_void_p(t.data_ptr() + lo * (t.numel() // max(P.n, 1)) * t.element_size())
+                for t in P.tensors()]
+        return (self.g_hi - lo, *ptrs)
+
+    def new_grads(self, P: GaussianParams):
+        """Gradient buffers for this plan's preprocess_bwd (accumulate=False):
+        uninitialised when the plan's span covers all of P (every row is then
+        written), zeros otherwise (rows outside the span are not touched)."""
+        if (self.g_lo, self.g_hi) == (0, P.n):
+            return new_param_grads(P)
+        return [torch.zeros_like(t) for t in P.tensors()]
+
     def preprocess(self, P: GaussianParams, stream=None):
         s = _stream_ptr(stream)
         self.forward_count += 1
         with self._ev('preprocess'):
-            L.check(self.lib.pgsag_preprocess(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats), _ptr(P.opacity_logit),
-                                              _ptr(P.sh), self.n_views, _ptr(self.views_dev), _ptr(self.tile_act),
+            n, means, log_scales, quats, opacity_logit, sh = self._span(P)
+            L.check(self.lib.pgsag_preprocess(n, means, log_scales, quats, opacity_logit, sh, self.n_views, _ptr(self.views_dev), _ptr(self.tile_act),
                                               _ptr(self.sat), _ptr(self.rec), _ptr(self.dkey), _ptr(self.bininfo),
                                               _ptr(self.tile_mask), _ptr(self.grad2d), _ptr(self.status), s),
                     "pgsag_preprocess")
@@ -390,8 +417,9 @@ class Plan:
                                             _ptr(self.gc_weight) if fused else None, 0 if fused else 1,
                                             _ptr(self.scratch), _ptr(self.acc_loss), _ptr(self.chunk_scratch),
                                             _ptr(out), _ptr(self.gc_load) if fused else None, _ptr(self.dout8),
-                                            L.OBJ_EQ11 if eq11 else L.OBJ_PG, P.n if (eq11 and P is not None) else 0,
-                                            _ptr(P.log_scales) if (eq11 and P is not None) else None,
+                                            L.OBJ_EQ11 if eq11 else L.OBJ_PG,
+                                            self.g_hi - self.g_lo if (eq11 and P is not None) else 0,
+                                            self._span(P)[2] if (eq11 and P is not None) else None,
                                             self._dssim_arg(), _ptr(self.status), s), "pgsag_loss_ban")
         return out
 
@@ -436,10 +464,11 @@ class Plan:
         # Eq. 11: the flattening term (1 - lambda) lambda_3 L_s
         fw = (1.0 - L.LAMBDA_GC) * L.LAMBDA_FLAT if self.objective == "eq11" else 0.0
         with self._ev('preprocess_bwd'):
-            L.check(self.lib.pgsag_preprocess_bwd(P.n, _ptr(P.means), _ptr(P.log_scales), _ptr(P.quats),
-                                                  _ptr(P.opacity_logit), _ptr(P.sh), self.n_views, _ptr(self.views_dev),
-                                                  _ptr(self.bininfo), _ptr(self.grad2d), 1 if accumulate else 0, _ptr(gm),
-                                                  _ptr(gl), _ptr(gq), _ptr(go), _ptr(gs), _ptr(dout_scale), fw,
+            n, means, log_scales, quats, opacity_logit, sh = self._span(P)
+            _, gm, gl, gq, go, gs = self._span(GaussianParams(gm, gl, gq, go, gs))
+            L.check(self.lib.pgsag_preprocess_bwd(n, means, log_scales, quats, opacity_logit, sh, self.n_views,
+                                                  _ptr(self.views_dev), _ptr(self.bininfo), _ptr(self.grad2d),
+                                                  1 if accumulate else 0, gm, gl, gq, go, gs, _ptr(dout_scale), fw,
                                                   _ptr(self.status), s),
                     "pgsag_preprocess_bwd")
 
@@ -625,7 +654,7 @@ class RenderLossFn(torch.autograd.Function):
         _check_same_forward(ctx)
         g = g.contiguous().to(torch.float32)
         plan.render_bwd(plan.dout8, None, g, ban=True)
-        grads = new_param_grads(P)
+        grads = plan.new_grads(P)
         plan.preprocess_bwd(P, grads, dout_scale=g)
         _finish_backward(ctx)
         return (None, None, None) + tuple(grads)
@@ -661,7 +690,7 @@ class RenderFn(torch.autograd.Function):
         if g_depth is not None:
             g_depth = g_depth.contiguous()
         plan.render_bwd(g_out8, g_depth, None)
-        grads = new_param_grads(P)
+        grads = plan.new_grads(P)
         plan.preprocess_bwd(P, grads)
         _finish_backward(ctx)
         return (None, None) + tuple(grads)

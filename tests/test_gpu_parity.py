@@ -494,3 +494,27 @@ def test_forward_and_sort_bit_stable_across_runs(config0):
         assert plan.k_value() == K
         assert torch.equal(plan.dup_pairs[:K], dup1)
         assert torch.equal(plan.out8, out1) and torch.equal(plan.aux, aux1) and torch.equal(plan.depth, dep1)
+
+
+def test_plan_over_a_gaussian_span_equals_plan_over_the_slice():
+    """A plan whose views render the range [a, b) of a larger Gaussian array works
+    on that span only (offset pointers): outputs bitwise those of a plan over the
+    sliced arrays, gradients equal on the span and zero outside it."""
+    from paper_2501_01677_b300 import raster
+    g, v = syn.tiny_scene(12, n=300, width=64, height=48)
+    a, b = 70, 230
+    sub = g.subset(np.arange(a, b))
+    plan_s, P_s = gpu_run(sub, [v])
+    P = raster.GaussianParams.from_numpy(g, requires_grad=True)
+    plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, g_ranges=[(a, b)])
+    assert (plan.g_lo, plan.g_hi) == (a, b)
+    loss = raster.render_loss(plan, P)
+    loss.backward()
+    torch.cuda.synchronize()
+    plan.check_status()
+    assert np.array_equal(plan.out8.cpu().numpy(), plan_s.out8.cpu().numpy())
+    assert np.array_equal(plan.aux.cpu().numpy(), plan_s.aux.cpu().numpy())
+    for t, ts in zip(P.tensors(), P_s.tensors()):
+        gr = t.grad.cpu().numpy()
+        assert rel_l2(gr[a:b].ravel().astype(np.float64), ts.grad.cpu().numpy().ravel().astype(np.float64)) < 1e-6
+        assert float(np.abs(gr[:a]).max(initial=0.0)) == 0.0 and float(np.abs(gr[b:]).max(initial=0.0)) == 0.0

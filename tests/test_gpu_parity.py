@@ -496,17 +496,23 @@ def test_forward_and_sort_bit_stable_across_runs(config0):
         assert torch.equal(plan.out8, out1) and torch.equal(plan.aux, aux1) and torch.equal(plan.depth, dep1)
 
 
-def test_plan_over_a_gaussian_span_equals_plan_over_the_slice():
+@pytest.mark.parametrize("objective", ["pg", "eq11"])
+def test_plan_over_a_gaussian_span_equals_plan_over_the_slice(objective):
     """A plan whose views render the range [a, b) of a larger Gaussian array works
     on that span only (offset pointers): outputs bitwise those of a plan over the
-    sliced arrays, gradients equal on the span and zero outside it."""
+    sliced arrays, gradients equal on the span and zero outside it (under Eq. 11
+    the flattening term is the mean over the span's Gaussians)."""
     from paper_2501_01677_b300 import raster
     g, v = syn.tiny_scene(12, n=300, width=64, height=48)
     a, b = 70, 230
     sub = g.subset(np.arange(a, b))
-    plan_s, P_s = gpu_run(sub, [v])
+    P_s = raster.GaussianParams.from_numpy(sub, requires_grad=True)
+    plan_s = raster.Plan([v.cam], [v.mask], [v.target], sub.n)
+    plan_s.set_objective(objective)
+    raster.render_loss(plan_s, P_s).backward()
     P = raster.GaussianParams.from_numpy(g, requires_grad=True)
     plan = raster.Plan([v.cam], [v.mask], [v.target], g.n, g_ranges=[(a, b)])
+    plan.set_objective(objective)
     assert (plan.g_lo, plan.g_hi) == (a, b)
     loss = raster.render_loss(plan, P)
     loss.backward()
@@ -518,3 +524,35 @@ def test_plan_over_a_gaussian_span_equals_plan_over_the_slice():
         gr = t.grad.cpu().numpy()
         assert rel_l2(gr[a:b].ravel().astype(np.float64), ts.grad.cpu().numpy().ravel().astype(np.float64)) < 1e-6
         assert float(np.abs(gr[:a]).max(initial=0.0)) == 0.0 and float(np.abs(gr[b:]).max(initial=0.0)) == 0.0
+
+
+def test_backward_after_another_forward_on_the_plan_raises():
+    """The plan's buffers carry a forward's state to its backward; a second
+    forward on the same plan in between is detected."""
+    from paper_2501_01677_b300 import raster
+    g, v = syn.tiny_scene(13, n=64, width=40, height=32)
+    P = raster.GaussianParams.from_numpy(g, requires_grad=True)
+    plan = raster.Plan([v.cam], [v.mask], [v.target], g.n)
+    loss = raster.render_loss(plan, P)
+    plan.forward(raster.GaussianParams(*[t.detach() for t in P.tensors()]))
+    with pytest.raises(RuntimeError, match="another forward"):
+        loss.backward()
+    out8, depth = raster.render(plan, P)
+    raster.render_loss(plan, raster.GaussianParams(*[t.detach().clone().requires_grad_(True) for t in P.tensors()]))
+    with pytest.raises(RuntimeError, match="another forward"):
+        out8.sum().backward()
+
+
+def test_backward_with_check_raises_on_device_status():
+    """With check=True the backward reads the device status once: a step whose
+    kernels found an error (here a status planted before the adjoint) raises
+    instead of returning gradients the skipped kernels never wrote."""
+    from paper_2501_01677_b300 import _lib as L
+    from paper_2501_01677_b300 import raster
+    g, v = syn.tiny_scene(14, n=64, width=40, height=32)
+    P = raster.GaussianParams.from_numpy(g, requires_grad=True)
+    plan = raster.Plan([v.cam], [v.mask], [v.target], g.n)
+    loss = raster.render_loss(plan, P, check=True)
+    plan.status.fill_(L.PGSAG_DEV_BOUNDS)
+    with pytest.raises(L.PgsagError):
+        loss.backward()

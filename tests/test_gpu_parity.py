@@ -556,3 +556,28 @@ def test_backward_with_check_raises_on_device_status():
     plan.status.fill_(L.PGSAG_DEV_BOUNDS)
     with pytest.raises(L.PgsagError):
         loss.backward()
+
+
+def test_persistent_lpt_multiview_step_matches_oracle_per_view():
+    """Two views of one scene (different masks and targets) in one plan with the
+    persistent longest-first render queue: the summed loss and gradients equal
+    the sums of the oracle's per-view losses and gradients."""
+    from paper_2501_01677_b300 import raster
+    g, v = syn.tiny_scene(9, n=200, width=72, height=64)
+    v2 = syn.View(v.cam, np.ascontiguousarray(v.mask[:, ::-1]), np.ascontiguousarray(v.target[:, ::-1]))
+    views = [v, v2]
+    P = raster.GaussianParams.from_numpy(g, requires_grad=True)
+    plan = raster.Plan([x.cam for x in views], [x.mask for x in views], [x.target for x in views], g.n)
+    plan.forward(raster.GaussianParams(*[t.detach() for t in P.tensors()]))  # sizes the capacity
+    plan.use_persistent_schedule(ctas_per_sm=0, lpt=True)
+    loss = raster.render_loss(plan, P)
+    loss.backward()
+    torch.cuda.synchronize()
+    plan.check_status()
+    refs = [oracle_run(g, x) for x in views]
+    want = sum(float(r["loss"]["total"].detach()) for r in refs)
+    assert float(loss.detach()) == pytest.approx(want, rel=1e-5)
+    for name, t in zip(("means", "log_scales", "quats", "opacity_logit", "sh"), P.tensors()):
+        ref = sum(r["grads"][name].numpy() for r in refs)
+        err = rel_l2(t.grad.cpu().numpy().ravel().astype(np.float64), ref.ravel())
+        assert err <= GRAD_TOL, (name, err)

@@ -99,10 +99,10 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
       const int W = P.V.width, H = P.V.height;
       const float dep = __ldg(depth + P.q);
       bool inV = P.x >= 1 && P.x <= W - 2 && P.y >= 1 && P.y <= H - 2 && dep > 0.f;
-      float Pn[4][3];  // y-1, y+1, x-1, x+1
+      // central differences of the back-projected points P = Depth r, r = ((x + 1/2 - cx) / fx,
+      // (y + 1/2 - cy) / fy, 1): a = P[y+1] - P[y-1], b = P[x+1] - P[x-1]
+      float a[3] = {0.f, 0.f, 0.f}, b[3] = {0.f, 0.f, 0.f};
       if (inV) {
-        const int nx[4] = {P.x, P.x, P.x - 1, P.x + 1};
-        const int ny[4] = {P.y - 1, P.y + 1, P.y, P.y};
         // up, down, left, right neighbours (~0: not rendered)
         const uint4 nb = __ldg(nbr + P.q);
         const uint32_t qn[4] = {nb.x, nb.y, nb.z, nb.w};
@@ -110,20 +110,25 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
 #pragma unroll
         for (int k = 0; k < 4; ++k) dq[k] = qn[k] != 0xffffffffu ? __ldg(depth + qn[k]) : 0.f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const bool rk = qn[k] != 0xffffffffu;
-          const float d = dq[k];
-          inV = inV && rk && d > 0.f;
-          float r[3];
-          ray(P.V, nx[k], ny[k], r);
-          Pn[k][0] = d * r[0];
-          Pn[k][1] = d * r[1];
-          Pn[k][2] = d * r[2];
-        }
+        for (int k = 0; k < 4; ++k) inV = inV && qn[k] != 0xffffffffu && dq[k] > 0.f;
+        // d1 r1 - d0 r0 = (d1 - d0) r1 + d0 (r1 - r0): the depth difference is exact
+        // for depths within a factor 2 of each other and the two rays differ by two
+        // pixel pitches along one axis, so the difference carries no cancellation
+        // (forming d1 r1 and d0 r0 first loses ~depth / footprint ulps: ~1e3 at
+        // aerial range)
+        float r[3], rd[3], rr[3];
+        ray(P.V, P.x, P.y, r);
+        ray(P.V, P.x, P.y + 1, rd);
+        ray(P.V, P.x + 1, P.y, rr);
+        const float dv = dq[1] - dq[0], du = dq[3] - dq[2];
+        a[0] = dv * r[0];
+        a[1] = fmaf(dv, rd[1], dq[0] * (2.f / P.V.fy));
+        a[2] = dv;
+        b[0] = fmaf(du, rr[0], dq[2] * (2.f / P.V.fx));
+        b[1] = du * r[1];
+        b[2] = du;
       }
       if (inV) {
-        const float a[3] = {Pn[1][0] - Pn[0][0], Pn[1][1] - Pn[0][1], Pn[1][2] - Pn[0][2]};
-        const float b[3] = {Pn[3][0] - Pn[2][0], Pn[3][1] - Pn[2][1], Pn[3][2] - Pn[2][2]};
         const float cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
         const float cn = sqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
         const float Nn = sqrtf(o1.x * o1.x + o1.y * o1.y + o1.z * o1.z);

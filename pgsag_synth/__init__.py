@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Sequence, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -526,6 +526,54 @@ def hashed_uniform(index: np.ndarray, channel: int, seed: int = 0) -> np.ndarray
         x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
         x = x ^ (x >> np.uint64(31))
     return ((x >> np.uint64(40)).astype(np.float64) / float(1 << 24) * 2.0 - 1.0).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# stand-in rendered channels (inputs of the loss pass alone)
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class RenderedChannels:
+    """Dense [H,W] float32 stand-ins for what a render hands the loss: colour,
+    blended plane distance, blended (not unit) normal, alpha, camera depth
+    (0 = nothing rendered) and the blended count.  Drawn directly, so a test can
+    give the loss kernels and the oracle's loss the same values."""
+    rgb: np.ndarray        # [H,W,3]
+    dist: np.ndarray       # [H,W]   > 0 where depth > 0
+    normal: np.ndarray     # [H,W,3] facing the camera (z component < 0)
+    alpha: np.ndarray      # [H,W]
+    depth: np.ndarray      # [H,W]
+    n_contrib: np.ndarray  # [H,W] int32, 0 exactly where depth = 0
+
+
+def rendered_channels(cam: Camera, boxes: Optional[Sequence[Box]] = None, seed: int = 0) -> RenderedChannels:
+    """Depth: the ray-cast box scene when `boxes` are given, else two tilted
+    planes with a step between them; a disc of unrendered pixels (depth 0) either
+    way.  Normals: a smooth field (x, y components in [-0.32, 0.32], z = -1)
+    with 1% noise, scaled by alpha in [0.6, 1]; colour uniform in [0, 1]."""
+    ss = np.random.SeedSequence([BASE_SEED, 11, seed])
+    rng = np.random.Generator(np.random.PCG64(ss))
+    H, W = cam.height, cam.width
+    vv, uu = np.mgrid[0:H, 0:W].astype(np.float64)
+    if boxes is not None:
+        depth = raycast_depth(boxes, cam)[0].astype(np.float64)
+    else:
+        a, b = rng.uniform(-2.0, 2.0, 2)
+        depth = 8.0 + a * (uu / W - 0.5) + b * (vv / H - 0.5)
+        depth = np.where(uu > rng.uniform(0.3, 0.7) * W, depth + 0.5, depth)
+    cu, cv, rad = rng.uniform(0.2, 0.8) * W, rng.uniform(0.2, 0.8) * H, 0.08 * min(H, W)
+    depth = np.where((uu - cu) ** 2 + (vv - cv) ** 2 < rad * rad, 0.0, depth)
+    on = depth > 0
+    p1, p2 = rng.uniform(0.0, 2.0 * math.pi, 2)
+    nx = 0.3 * np.sin(2.0 * math.pi * 3.0 * uu / W + p1) + 0.02 * rng.uniform(-1.0, 1.0, (H, W))
+    ny = 0.3 * np.cos(2.0 * math.pi * 2.0 * vv / H + p2) + 0.02 * rng.uniform(-1.0, 1.0, (H, W))
+    alpha = np.where(on, rng.uniform(0.6, 1.0, (H, W)), 0.0)
+    normal = np.stack([nx, ny, -np.ones((H, W))], -1) * alpha[..., None]
+    dist = np.where(on, depth * rng.uniform(0.6, 1.0, (H, W)), 0.0)
+    n_contrib = np.where(on, rng.integers(1, 40, (H, W)), 0).astype(np.int32)
+    f32 = np.float32
+    return RenderedChannels(rng.random((H, W, 3)).astype(f32), dist.astype(f32), normal.astype(f32),
+                            alpha.astype(f32), depth.astype(f32), n_contrib)
 
 
 # --------------------------------------------------------------------------

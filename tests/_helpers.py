@@ -134,3 +134,61 @@ def compare_grads(P, res, tol=GRAD_TOL):
     for k, e in errs.items():
         assert e <= tol, errs
     return errs
+
+
+
+def loss_pass_vs_oracle(plan, v, view, ch, lambda_ban=O.LAMBDA_BAN):
+    """The loss pass alone (pgsag_loss_ban with its own gather, so dout8 is the
+    complete dL/d(rendered channels)) against the oracle's L_rgb + lambda L_ban
+    (Sec. 4.2 Eq. 8) and its autograd gradient, on the stand-in rendered
+    channels `ch` (pgsag_synth.rendered_channels) written into view v's compact
+    rows; the oracle takes the same float32 values in float64, on its own
+    render set R.  Eq. 8 reads the depth values as given; their gradient reaches
+    the plane distance and the normal through Eq. 4 (Depth = D / (-N . r)),
+    differentiated at the given D and N.  Compared element by element over every
+    rendered pixel.  Returns {loss relative errors, gradient rel-L2 per channel
+    group, render-set and validity checks, alpha-channel gradient maximum}."""
+    sl = plan.px_slice(v)
+    H, W = plan.shapes[v]
+    lin = plan.px_index(v).cpu().numpy()
+    rows8 = np.concatenate([ch.rgb.reshape(-1, 3), ch.dist.reshape(-1, 1), ch.normal.reshape(-1, 3),
+                            ch.alpha.reshape(-1, 1)], 1)[lin]
+    plan.out8[sl] = torch.from_numpy(np.ascontiguousarray(rows8)).cuda()
+    plan.depth[sl] = torch.from_numpy(ch.depth.reshape(-1)[lin]).cuda()
+    plan.aux[sl, 2] = torch.from_numpy(ch.n_contrib.reshape(-1)[lin]).cuda()
+    plan.loss(lambda_ban)
+    torch.cuda.synchronize()
+    plan.check_status()
+    d8 = np.zeros((H * W, 8))
+    d8[lin] = plan.dout8[sl].double().cpu().numpy()
+    lb = plan.loss_buf.cpu().numpy().astype(np.float64)
+    # the oracle's own render set and pixel order
+    sets = O.mask_sets(view.mask)
+    pv_np, pu_np = np.nonzero(sets[2])
+    pu, pv = torch.from_numpy(pu_np), torch.from_numpy(pv_np)
+    lin_o = pv_np * W + pu_np
+
+    def leaf(a, k):
+        return torch.from_numpy(a.reshape(H * W, k)[lin_o].astype(np.float64)).squeeze(-1).requires_grad_(True)
+
+    rgb, dist, normal = leaf(ch.rgb, 3), leaf(ch.dist, 1), leaf(ch.normal, 3)
+    out = dict(rgb=rgb, dist=dist, normal=normal, n_contrib=torch.from_numpy(ch.n_contrib.reshape(-1)[lin_o]))
+    cam = O.Cam.from_synth(view.cam)
+    chain, valid = O.unbiased_depth(out, cam, pu, pv)
+    given = torch.from_numpy(ch.depth.reshape(-1)[lin_o].astype(np.float64))
+    depth = torch.where(valid, given + (chain - chain.detach()), torch.zeros_like(given))
+    lv = O.losses(out, depth, valid, (pu, pv), sets, cam, view.target)
+    total = lv["l_rgb"] + lambda_ban * lv["l_ban"]
+    total.backward()
+    ref = dict(rgb=rgb.grad.numpy(), dist=dist.grad.numpy(), normal=normal.grad.numpy())
+    got = dict(rgb=d8[lin_o, 0:3], dist=d8[lin_o, 3], normal=d8[lin_o, 4:7])
+    errs = {"grad_" + k: rel_l2(got[k].ravel(), ref[k].ravel()) for k in ref}
+    want = (float(lv["l_rgb"].detach()), float(lv["l_ban"].detach()), float(total.detach()))
+    for i, (name, w) in enumerate(zip(("l_rgb", "l_ban", "total"), want)):
+        errs[name] = abs(lb[3 * v + i] - w) / abs(w) if w != 0 else abs(lb[3 * v + i])
+    errs["render_set_equal"] = bool(np.array_equal(np.sort(lin), lin_o))
+    errs["valid_is_depth_positive"] = bool(np.array_equal(valid.numpy(), given.numpy() > 0))
+    errs["alpha_grad_max"] = float(np.abs(d8[:, 7]).max())
+    errs["n_valid"] = int(lv["n_valid"])
+    errs["n_mask"] = int(lv["n_mask"])
+    return errs

@@ -4,14 +4,16 @@ rendered pixels against the oracle evaluated pixel by pixel; per-Gaussian
 gradients of <G, outputs> for a hashed upstream field G on sampled Gaussians
 (the oracle differentiates each one over its footprint); and the directional
 derivative of the fused loss along a random SH direction (colour only, so no
-alpha threshold moves) against its float64-accumulated central difference."""
+alpha threshold moves) against its float64-accumulated central difference; and
+the loss pass alone on every rendered pixel, on stand-in rendered channels, against
+the oracle's loss and its gradient."""
 import numpy as np
 import pytest
 import torch
 
 import pgsag_synth as syn
 from oracle import pgsag_oracle as O
-from tests._helpers import FWD_TOL, rel_l2
+from tests._helpers import FWD_TOL, GRAD_TOL, loss_pass_vs_oracle, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -27,7 +29,7 @@ def aerial():
     cam = O.Cam.from_synth(v.cam)
     pr = O.project(O.params_from_synth(g), cam, g.means)
     pr = {k: (t.detach() if torch.is_tensor(t) else t) for k, t in pr.items()}
-    return g, v, plan, cam, pr
+    return g, v, plan, cam, pr, boxes
 
 
 def _oracle_pixels(pr, cam, pu, pv):
@@ -39,7 +41,7 @@ def _oracle_pixels(pr, cam, pu, pv):
 
 def test_fullsize_forward_sampled_pixels(aerial):
     from paper_2501_01677_b300 import raster
-    g, v, plan, cam, pr = aerial
+    g, v, plan, cam, pr, boxes = aerial
     P = raster.GaussianParams.from_numpy(g)
     plan.forward(P)
     torch.cuda.synchronize()
@@ -76,7 +78,7 @@ def test_fullsize_sampled_gaussian_gradients(aerial):
     parameters: CUDA (whole image) vs oracle (the Gaussian's footprint, every
     Gaussian overlapping it, autograd through the sampled one)."""
     from paper_2501_01677_b300 import raster
-    g, v, plan, cam, pr = aerial
+    g, v, plan, cam, pr, boxes = aerial
     H, W = cam.height, cam.width
 
     def G8(lin):  # upstream gradient field, a function of the linear pixel index
@@ -156,7 +158,7 @@ def test_fullsize_loss_directional_derivative_sh(aerial):
     fraction (~1e-3), and the signal has no cancellation (unlike a random
     direction, whose derivative is a small residual of random-sign terms)."""
     from paper_2501_01677_b300 import raster
-    g, v, plan, cam, pr = aerial
+    g, v, plan, cam, pr, boxes = aerial
     P = raster.GaussianParams.from_numpy(g, requires_grad=True)
     loss = raster.render_loss(plan, P)
     loss.backward()
@@ -176,3 +178,20 @@ def test_fullsize_loss_directional_derivative_sh(aerial):
     fd = (L(eps) - L(-eps)) / (2 * eps)
     an = float(grad_sh.double().abs().sum())
     assert abs(fd - an) <= 2e-3 * an, (fd, an)
+
+
+def test_fullsize_loss_pass_every_pixel(aerial):
+    """The loss pass at full size on stand-in rendered channels (the ray-cast
+    depth of the scene's buildings and ground, with an unrendered disc): loss
+    values and the complete upstream gradient of every rendered pixel against
+    the oracle's Eq. 8 / L1 autograd on the same values."""
+    g, v, plan, cam, pr, boxes = aerial
+    errs = loss_pass_vs_oracle(plan, 0, v, syn.rendered_channels(v.cam, boxes, seed=1))
+    print("full-size loss pass vs oracle:", errs)
+    assert errs["render_set_equal"] and errs["valid_is_depth_positive"], errs
+    assert errs["n_valid"] > 1_000_000
+    assert errs["alpha_grad_max"] == 0.0, errs
+    assert errs["l_rgb"] <= 1e-5, errs
+    assert errs["l_ban"] <= 1e-4 and errs["total"] <= 1e-4, errs
+    for k in ("grad_rgb", "grad_dist", "grad_normal"):
+        assert errs[k] <= GRAD_TOL, errs

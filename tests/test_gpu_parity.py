@@ -7,7 +7,8 @@ import torch
 
 import pgsag_synth as syn
 from oracle import pgsag_oracle as O
-from tests._helpers import (FWD_TOL, GRAD_TOL, compare_forward, compare_grads, gpu_run, oracle_run, rel_l2)
+from tests._helpers import (FWD_TOL, GRAD_TOL, compare_forward, compare_grads, gpu_run, loss_pass_vs_oracle,
+                            oracle_run, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +39,42 @@ def test_config0_loss_and_gradients(config0):
     assert lb[3] == pytest.approx(float(lv["total"].detach()), rel=1e-4)
     errs = compare_grads(P, res)
     print("config0 gradient rel-L2", errs)
+
+
+def _assert_loss_pass(errs):
+    """Same rendered channels on both sides, so only float32 arithmetic separates
+    them: the L1 sum to 1e-5 (per-pixel rounding plus the float32 chunk sums),
+    the Eq. 8 mean to 1e-4 (central differences of back-projected points cancel),
+    the gradient groups to the gradient tolerance; validity (Eq. 4) and the zero
+    alpha-channel gradient exactly."""
+    print("loss pass vs oracle:", errs)
+    assert errs["render_set_equal"] and errs["valid_is_depth_positive"], errs
+    assert errs["n_valid"] > 0
+    assert errs["alpha_grad_max"] == 0.0, errs
+    assert errs["l_rgb"] <= 1e-5, errs
+    assert errs["l_ban"] <= 1e-4 and errs["total"] <= 1e-4, errs
+    for k in ("grad_rgb", "grad_dist", "grad_normal"):
+        assert errs[k] <= GRAD_TOL, errs
+
+
+def test_config0_loss_pass_matches_oracle_on_same_channels(config0):
+    """pgsag_loss_ban alone, on stand-in rendered channels (two tilted planes
+    with a step and an unrendered disc): the three loss values and the complete
+    upstream gradient (L1 sign term, Eq. 8 own-normal term, Eq. 8 neighbour
+    gather mapped through Eq. 4) against the oracle's autograd."""
+    g, views, _ = config0
+    plan, P = gpu_run(g, views, grad=False)
+    _assert_loss_pass(loss_pass_vs_oracle(plan, 0, views[0], syn.rendered_channels(views[0].cam, None, seed=0)))
+
+
+def test_loss_pass_second_view_of_a_ragged_two_view_plan():
+    """Odd image sizes (ragged chunks and tiles) and the second view's rows of a
+    two-view plan (non-zero compact and chunk bases)."""
+    g, v = syn.tiny_scene(4, n=300, width=83, height=61, coverage=0.6)
+    v2 = syn.View(v.cam, np.ascontiguousarray(v.mask[::-1, :]), np.ascontiguousarray(v.target[::-1, :]))
+    plan, P = gpu_run(g, [v, v2], grad=False)
+    for i, view in enumerate((v, v2)):
+        _assert_loss_pass(loss_pass_vs_oracle(plan, i, view, syn.rendered_channels(view.cam, None, seed=3 + i)))
 
 
 def test_config0_preprocess_parity(config0):

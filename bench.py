@@ -347,21 +347,26 @@ def ours(args):
     K_dup = plan.k_value()
     stream = torch.cuda.current_stream()
 
-    # eager autograd steps with per-stage events (the split; events cost a little)
+    # eager autograd steps with per-stage events (the split; events cost a little).
+    # A host slower than the GPU would leave launch gaps between a stage's two
+    # events, so the stream is first held by a bounded spin kernel (torch's
+    # cycle-count sleep) for longer than the host takes to enqueue the steps.
+    n_stage = max(1, min(args.steps, 5))
+    host_ms = host_enqueue_ms(step)
     plan.stage_events = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
+    hold_stream(host_ms * n_stage)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(n_stage):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_eager = e0.elapsed_time(e1) / args.steps
+    ms_eager = e0.elapsed_time(e1) / n_stage
     stage_ms = {}
     for name, a, b in plan.stage_events:
         stage_ms[name] = stage_ms.get(name, 0.0) + a.elapsed_time(b)
     plan.stage_events = None
-    stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
+    stage_ms = {k: v / n_stage for k, v in stage_ms.items()}
     plan.check_status()
 
     # the same autograd step (forward through the autograd.Function, backward,
@@ -677,9 +682,28 @@ def run_batched(args, tune: bool, steps: int, warmup: int):
     ms_plain = timed(plain_step, steps)
     for pl in plans:
         pl.check_status()
+    # the same per-view launches captured as one CUDA graph: the plain form's GPU
+    # cost without the host's launch overhead
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        plain_step()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph_plain = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_plain):
+        plain_step()
+    for _ in range(warmup):
+        graph_plain.replay()
+    ms_plain_graph = timed(graph_plain.replay, steps)
+    del graph_plain
+    for pl in plans:
+        pl.check_status()
     # per-stage split of one eager plain step (CUDA events around each stage call)
+    host_ms = host_enqueue_ms(plain_step)
     for pl in plans:
         pl.stage_events = []
+    hold_stream(host_ms)
     plain_step()
     torch.cuda.synchronize()
     stages_plain = {}
@@ -710,7 +734,9 @@ def run_batched(args, tune: bool, steps: int, warmup: int):
     ck = clocks.stop()
     plan.check_status()
     # per-stage split of one eager batched step
+    host_ms = host_enqueue_ms(lambda: plan.step(P, grads))
     plan.stage_events = []
+    hold_stream(host_ms)
     plan.step(P, grads)
     torch.cuda.synchronize()
     stages_batched = {}
@@ -724,10 +750,33 @@ def run_batched(args, tune: bool, steps: int, warmup: int):
         "n_gauss": g.n, "views": len(views), "mask_pixels": n_mask, "pairs": plan.n_pairs,
         "duplicates_K": plan.k_value(), "active_tiles": plan.n_active,
         "ms_plain": ms_plain, "ms_batched": ms_batched, "ratio": ms_plain / ms_batched,
+        "ms_plain_graph": ms_plain_graph, "ratio_vs_plain_graph": ms_plain_graph / ms_batched,
         "launches_plain": launches_plain, "launches_batched": plan.kernel_launches_per_step(),
         "shape": shape, "table": table, "t_tune": t_tune, "clocks": ck, "grad_diff": diff,
         "stages_plain": stages_plain, "stages_batched": stages_batched,
     }
+
+
+def host_enqueue_ms(fn) -> float:
+    """Host time to enqueue fn()'s GPU work, taken while the stream is held by a
+    bounded spin kernel (torch's cycle-count sleep, ~0.3 s) so the GPU cannot
+    drain the queue meanwhile."""
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda._sleep(int(0.3 * 2.0e9))
+    t = time.perf_counter()
+    fn()
+    ms = (time.perf_counter() - t) * 1e3
+    torch.cuda.synchronize()
+    return ms
+
+
+def hold_stream(host_ms: float):
+    """Hold the current stream (bounded cycle-count spin, ~2 GHz clock) for about
+    four times the host time needed to enqueue what follows, so per-stage CUDA
+    events record GPU time only, not host launch gaps of a slow host."""
+    import torch
+    torch.cuda._sleep(int((4.0 * host_ms + 5.0) * 2.0e6))
 
 
 def batched_summary(r, tuned: bool) -> dict:
@@ -739,6 +788,8 @@ def batched_summary(r, tuned: bool) -> dict:
             "plain_value": r["mask_pixels"] / 1e6 / (r["ms_plain"] / 1e3), "unit": UNIT,
             "mask_pixels": r["mask_pixels"],
             "plain": "32 per-view plans run one after the other on one stream (same kernels, no graph)",
+            "plain_graph_ms": r["ms_plain_graph"], "ratio_vs_plain_graph": r["ratio_vs_plain_graph"],
+            "plain_graph": "the same 32 per-view plans' launches captured as one CUDA graph (no host overhead)",
             "batched": "one plan over the 32 views, persistent render launches, one CUDA-graph replay",
             "launch_shape": {"tile": f"{sh.tile_w}x{sh.tile_h}", "ctas_per_sm": sh.ctas_per_sm, "lpt": sh.lpt,
                              "source": "autotuned in this run" if tuned else "the autotuner's choice on B300"},

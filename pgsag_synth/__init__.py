@@ -544,13 +544,15 @@ class RenderedChannels:
     alpha: np.ndarray      # [H,W]
     depth: np.ndarray      # [H,W]
     n_contrib: np.ndarray  # [H,W] int32, 0 exactly where depth = 0
+    soft_count: np.ndarray  # [H,W] float32 in [0.3, 1] x n_contrib (a sum of blended alphas)
 
 
 def rendered_channels(cam: Camera, boxes: Optional[Sequence[Box]] = None, seed: int = 0) -> RenderedChannels:
     """Depth: the ray-cast box scene when `boxes` are given, else two tilted
     planes with a step between them; a disc of unrendered pixels (depth 0) either
     way.  Normals: a smooth field (x, y components in [-0.32, 0.32], z = -1)
-    with 1% noise, scaled by alpha in [0.6, 1]; colour uniform in [0, 1]."""
+    with 1% noise, scaled by alpha in [0.6, 1]; colour uniform in [0, 1];
+    counts uniform in 1..39 where rendered, the soft count 0.3-1 times the count."""
     ss = np.random.SeedSequence([BASE_SEED, 11, seed])
     rng = np.random.Generator(np.random.PCG64(ss))
     H, W = cam.height, cam.width
@@ -571,9 +573,10 @@ def rendered_channels(cam: Camera, boxes: Optional[Sequence[Box]] = None, seed: 
     normal = np.stack([nx, ny, -np.ones((H, W))], -1) * alpha[..., None]
     dist = np.where(on, depth * rng.uniform(0.6, 1.0, (H, W)), 0.0)
     n_contrib = np.where(on, rng.integers(1, 40, (H, W)), 0).astype(np.int32)
+    soft = n_contrib * rng.uniform(0.3, 1.0, (H, W))
     f32 = np.float32
     return RenderedChannels(rng.random((H, W, 3)).astype(f32), dist.astype(f32), normal.astype(f32),
-                            alpha.astype(f32), depth.astype(f32), n_contrib)
+                            alpha.astype(f32), depth.astype(f32), n_contrib, soft.astype(f32))
 
 
 # --------------------------------------------------------------------------

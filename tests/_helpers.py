@@ -137,6 +137,23 @@ def compare_grads(P, res, tol=GRAD_TOL):
 
 
 
+def write_stand_in(plan, v, ch):
+    """Write the stand-in rendered channels `ch` (pgsag_synth.rendered_channels)
+    into view v's compact rows of the plan's render outputs: out8, depth, the
+    count (aux word 2) and, under the Eq. 11 objective, the soft count (aux word
+    3).  Returns the rows' linear pixel indices."""
+    sl = plan.px_slice(v)
+    lin = plan.px_index(v).cpu().numpy()
+    rows8 = np.concatenate([ch.rgb.reshape(-1, 3), ch.dist.reshape(-1, 1), ch.normal.reshape(-1, 3),
+                            ch.alpha.reshape(-1, 1)], 1)[lin]
+    plan.out8[sl] = torch.from_numpy(np.ascontiguousarray(rows8)).cuda()
+    plan.depth[sl] = torch.from_numpy(ch.depth.reshape(-1)[lin]).cuda()
+    plan.aux[sl, 2] = torch.from_numpy(ch.n_contrib.reshape(-1)[lin]).cuda()
+    if plan.objective == "eq11":
+        plan.aux[sl, 3] = torch.from_numpy(ch.soft_count.reshape(-1)[lin].view(np.int32)).cuda()
+    return lin
+
+
 def loss_pass_vs_oracle(plan, v, view, ch, lambda_ban=O.LAMBDA_BAN):
     """The loss pass alone (pgsag_loss_ban with its own gather, so dout8 is the
     complete dL/d(rendered channels)) against the oracle's L_rgb + lambda L_ban
@@ -150,12 +167,7 @@ def loss_pass_vs_oracle(plan, v, view, ch, lambda_ban=O.LAMBDA_BAN):
     group, render-set and validity checks, alpha-channel gradient maximum}."""
     sl = plan.px_slice(v)
     H, W = plan.shapes[v]
-    lin = plan.px_index(v).cpu().numpy()
-    rows8 = np.concatenate([ch.rgb.reshape(-1, 3), ch.dist.reshape(-1, 1), ch.normal.reshape(-1, 3),
-                            ch.alpha.reshape(-1, 1)], 1)[lin]
-    plan.out8[sl] = torch.from_numpy(np.ascontiguousarray(rows8)).cuda()
-    plan.depth[sl] = torch.from_numpy(ch.depth.reshape(-1)[lin]).cuda()
-    plan.aux[sl, 2] = torch.from_numpy(ch.n_contrib.reshape(-1)[lin]).cuda()
+    lin = write_stand_in(plan, v, ch)
     plan.loss(lambda_ban)
     torch.cuda.synchronize()
     plan.check_status()

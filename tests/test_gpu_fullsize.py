@@ -13,7 +13,7 @@ import torch
 
 import pgsag_synth as syn
 from oracle import pgsag_oracle as O
-from tests._helpers import FWD_TOL, GRAD_TOL, loss_pass_vs_oracle, rel_l2
+from tests._helpers import FWD_TOL, GRAD_TOL, loss_pass_vs_oracle, rel_l2, write_stand_in
 
 pytestmark = pytest.mark.gpu
 
@@ -195,3 +195,43 @@ def test_fullsize_loss_pass_every_pixel(aerial):
     assert errs["l_ban"] <= 1e-4 and errs["total"] <= 1e-4, errs
     for k in ("grad_rgb", "grad_dist", "grad_normal"):
         assert errs[k] <= GRAD_TOL, errs
+
+
+@pytest.mark.parametrize("objective", ["pg", "eq11"])
+def test_fullsize_gc_load_on_stand_in_counts(aerial, objective):
+    """Eq. 9 at full size on stand-in per-pixel counts (the integer count under
+    the default objective, the soft count under Eq. 11): the Sobel weight of
+    every rendered pixel, the GC-load value and, under Eq. 11, the per-view
+    coefficients {lambda / (n sigma), mean} of the soft-count gradient, against
+    the oracle."""
+    g, v, plan, cam, pr, boxes = aerial
+    ch = syn.rendered_channels(v.cam, boxes, seed=2)
+    plan.set_objective(objective)
+    try:
+        lin = write_stand_in(plan, 0, ch)
+        plan.loss(O.LAMBDA_BAN, fused=True)
+        torch.cuda.synchronize()
+        plan.check_status()
+        M, E, R = O.mask_sets(v.mask)
+        w = O.luminance_gradient_weight(v.target)
+        wg = plan.gc_weight[plan.px_slice(0)].cpu().numpy().astype(np.float64)
+        wo = w.reshape(-1)[lin]
+        werr = float(np.abs(wg - wo).max() / wo.max())
+        got = float(plan.gc_load[0].cpu())
+        if objective == "pg":
+            want = O.gc_load(ch.n_contrib, w, R)
+        else:
+            soft = torch.from_numpy(ch.soft_count[R].astype(np.float64))
+            want = float(O.gc_load_soft(soft, torch.from_numpy(w[R])))
+        print(objective, "weights max err / max", werr, "GC-load", got, want)
+        assert werr <= 1e-6
+        assert abs(got - want) <= 1e-5 * want
+        if objective == "eq11":
+            x = ch.soft_count[R].astype(np.float64) / w[R]
+            cm = plan.acc_loss[3:4].cpu().numpy().view(np.float32)  # {lambda / (n sigma), mean}
+            want_c = O.LAMBDA_GC / (x.size * x.std())
+            print("coefficients", cm, want_c, x.mean())
+            assert abs(cm[0] - want_c) <= 1e-5 * want_c
+            assert abs(cm[1] - x.mean()) <= 1e-5 * x.mean()
+    finally:
+        plan.set_objective("pg")

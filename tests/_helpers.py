@@ -204,3 +204,51 @@ def loss_pass_vs_oracle(plan, v, view, ch, lambda_ban=O.LAMBDA_BAN):
     errs["n_valid"] = int(lv["n_valid"])
     errs["n_mask"] = int(lv["n_mask"])
     return errs
+
+
+def check_projection(plan, pr):
+    """Projection records of every binned pair of the plan's first view against
+    the oracle's projection pr (Sec. 3.1, Eq. 2-3): the 2D mean (integer part +
+    fraction, compensated) within 2e-6 px, the Cholesky factor of the conic
+    within 1e-5 of its scale, opacity, colour, plane distance, the flattened
+    normal (off flip-ambiguous Gaussians) and the float32 depth key bit for bit.
+    Returns the number of pairs checked."""
+    rec = plan.rec.cpu().numpy()
+    bi = plan.bininfo.cpu().numpy()
+    n = pr["visible"].shape[0]
+    rec, bi = rec[:n], bi[:n]
+    vis = pr["visible"].numpy() & (bi[:, 3] > 0)
+    m2 = pr["mean2d"].detach().numpy()
+    q = pr["conic"].detach().numpy()
+    # 2D mean = integer part + fraction (compensated evaluation): the integer part
+    # is the float32 value s = f x/z + c rounded to an integer, and the fraction
+    # also carries the compensation terms (the rounding errors of f x/z and of
+    # the sum, each within an ulp of |f x/z| <= |s| + |c|), so |fraction| <= 1/2
+    # + a few ulps of (|s| + image size)
+    H, W = plan.shapes[0]
+    for j, fj in ((0, 14), (1, 15)):
+        ip, fp = rec[vis, j], rec[vis, fj]
+        assert (ip == np.rint(ip)).all()
+        excess = (np.abs(fp) - 0.5) / np.spacing(np.abs(ip) + np.float32(max(W, H)))
+        k = int(np.argmax(excess))
+        assert excess[k] <= 4.0, (j, float(excess[k]), float(ip[k]), float(fp[k]))
+    mean = np.stack([rec[:, 0].astype(np.float64) + rec[:, 14], rec[:, 1].astype(np.float64) + rec[:, 15]], 1)
+    err_mean = float(np.abs(mean[vis] - m2[vis]).max())
+    assert err_mean < 2e-6, err_mean
+    # the record holds the Cholesky factor of the conic: Q = L L^T
+    l11 = np.sqrt(q[:, 0])
+    l21 = q[:, 1] / l11
+    l22 = np.sqrt(q[:, 2] - l21 * l21)
+    for j, ref in ((2, l11), (3, l21), (4, l22)):
+        scale = np.maximum(np.maximum(np.abs(l11), np.abs(l22))[vis], 1e-12)
+        assert (np.abs(rec[vis, j] - ref[vis]) / scale).max() < 1e-5
+    np.testing.assert_allclose(rec[vis, 5], pr["opacity"].detach().numpy()[vis], rtol=1e-5)
+    np.testing.assert_allclose(rec[vis, 6:9], pr["rgb"].detach().numpy()[vis], rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(rec[vis, 9], pr["dist"].detach().numpy()[vis], rtol=1e-4, atol=1e-5)
+    amb = pr["flip_ambiguous"].numpy()
+    ok = vis & ~amb
+    np.testing.assert_allclose(rec[ok, 10:13], pr["normal"].detach().numpy()[ok], atol=1e-5)
+    # depth key is bit-identical to the oracle's float32 key
+    assert (plan.dkey.cpu().numpy()[:n].view(np.float32)[vis] == pr["key"].numpy()[vis]).all()
+    print("projection: pairs checked", int(vis.sum()), "max 2D-mean error", err_mean)
+    return int(vis.sum())

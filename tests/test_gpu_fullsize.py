@@ -13,7 +13,7 @@ import torch
 
 import pgsag_synth as syn
 from oracle import pgsag_oracle as O
-from tests._helpers import FWD_TOL, GRAD_TOL, loss_pass_vs_oracle, rel_l2, write_stand_in
+from tests._helpers import FWD_TOL, GRAD_TOL, check_projection, loss_pass_vs_oracle, rel_l2, write_stand_in
 
 pytestmark = pytest.mark.gpu
 
@@ -235,3 +235,14 @@ def test_fullsize_gc_load_on_stand_in_counts(aerial, objective):
             assert abs(cm[1] - x.mean()) <= 1e-5 * x.mean()
     finally:
         plan.set_objective("pg")
+
+
+def test_fullsize_projection_every_binned_pair(aerial):
+    """Projection at full size: the record of every binned (view, Gaussian) pair
+    (~0.6M of the 1.5M) against the oracle's projection of all 1.5M Gaussians."""
+    from paper_2501_01677_b300 import raster
+    g, v, plan, cam, pr, boxes = aerial
+    plan.forward(raster.GaussianParams.from_numpy(g))
+    torch.cuda.synchronize()
+    plan.check_status()
+    assert check_projection(plan, pr) > 500_000

@@ -252,3 +252,66 @@ def check_projection(plan, pr):
     assert (plan.dkey.cpu().numpy()[:n].view(np.float32)[vis] == pr["key"].numpy()[vis]).all()
     print("projection: pairs checked", int(vis.sum()), "max 2D-mean error", err_mean)
     return int(vis.sum())
+
+
+def check_binning(plan, pr, R, n_sample=None, seed=0):
+    """The duplicate lists of the plan's first view (tile size 16x16): ranges
+    partition [0, K) in tile order and equal the tile counts; each tile's list
+    is in strictly ascending (depth key, pair) order; each pair has `touched`
+    duplicates, all inside its tile rectangle; and binning is conservative: every
+    (active tile, Gaussian) with a rendered pixel where the oracle finds
+    alpha >= 1/255 is a duplicate.  The last check takes every Gaussian
+    (n_sample None) or a seeded sample of n_sample Gaussians, whose bounding-box
+    pixels are evaluated one by one.  Returns (K, the duplicate set)."""
+    K = plan.k_value()
+    dup = plan.dup_pairs[:K].cpu().numpy().astype(np.int64)
+    rg = plan.ranges.cpu().numpy().astype(np.int64)[:plan.n_active]
+    key = plan.dkey.cpu().numpy().view(np.uint32).astype(np.int64)
+    bi = plan.bininfo.cpu().numpy().astype(np.int64)
+    at = plan.act_tiles.cpu().numpy().astype(np.int64)[:plan.n_active]
+    ln = rg[:, 1] - rg[:, 0]
+    assert ln.sum() == K and (ln >= 0).all()
+    nz = ln > 0
+    assert (rg[nz, 0] == np.concatenate([[0], np.cumsum(ln)[:-1]])[nz]).all()
+    assert (plan.tile_counts.cpu().numpy()[:plan.n_active] == ln).all()
+    tile_of = np.repeat(np.arange(plan.n_active), ln)
+    same = tile_of[1:] == tile_of[:-1]
+    k0, k1 = key[dup[:-1]], key[dup[1:]]
+    assert (((k0 < k1) | ((k0 == k1) & (dup[:-1] < dup[1:])))[same]).all()
+    assert (np.bincount(dup, minlength=len(bi)) == bi[:, 3]).all()
+    tx, ty = at[tile_of, 1] & 0xFFFF, at[tile_of, 1] >> 16
+    x0, y0, x1, y1 = bi[dup, 0] & 0xFFFF, bi[dup, 0] >> 16, bi[dup, 1] & 0xFFFF, bi[dup, 1] >> 16
+    assert ((tx >= x0) & (tx <= x1) & (ty >= y0) & (ty <= y1)).all()
+    H, W = plan.shapes[0]
+    tiles_x = (W + 15) // 16
+    ta = plan.tile_act.cpu().numpy()
+    have = set(zip(tile_of.tolist(), dup.tolist()))
+    assert len(have) == K
+    m2, q, o = pr["mean2d"].detach().numpy(), pr["conic"].detach().numpy(), pr["opacity"].detach().numpy()
+    if n_sample is None:
+        lin, gid = O.candidate_pairs(pr, W, H)
+        u, v, gid = (lin % W).numpy(), (lin // W).numpy(), gid.numpy()
+    else:
+        ok, u0, u1, v0, v1 = O._ellipse_bbox(pr, pr["visible"])
+        ok = ok.numpy()
+        u0, u1 = np.clip(u0.numpy(), 0, W - 1).astype(np.int64), np.clip(u1.numpy(), 0, W - 1).astype(np.int64)
+        v0, v1 = np.clip(v0.numpy(), 0, H - 1).astype(np.int64), np.clip(v1.numpy(), 0, H - 1).astype(np.int64)
+        cand = np.nonzero(ok & (u1 >= u0) & (v1 >= v0))[0]
+        rng = np.random.default_rng(seed)
+        gs = rng.choice(cand, size=min(n_sample, len(cand)), replace=False)
+        w_, h_ = u1[gs] - u0[gs] + 1, v1[gs] - v0[gs] + 1
+        gs, w_, h_ = gs[w_ * h_ <= 65536], w_[w_ * h_ <= 65536], h_[w_ * h_ <= 65536]
+        npx = w_ * h_
+        gid = np.repeat(gs, npx)
+        off = np.arange(npx.sum()) - np.repeat(np.cumsum(npx) - npx, npx)
+        u = u0[gid] + off % np.repeat(w_, npx)
+        v = v0[gid] + off // np.repeat(w_, npx)
+    keep = R[v, u]
+    u, v, gid = u[keep], v[keep], gid[keep]
+    dx, dy = u + 0.5 - m2[gid, 0], v + 0.5 - m2[gid, 1]
+    a = o[gid] * np.exp(-0.5 * (q[gid, 0] * dx * dx + 2 * q[gid, 1] * dx * dy + q[gid, 2] * dy * dy))
+    ent = a >= 1 / 255 * (1 + 1e-4)
+    need = set(zip(ta[(v[ent] // 16) * tiles_x + u[ent] // 16].tolist(), gid[ent].tolist()))
+    assert need <= have, len(need - have)
+    print("binning: duplicates", K, "(tile, Gaussian) pairs the oracle requires", len(need))
+    return K, have

@@ -13,7 +13,8 @@ import torch
 
 import pgsag_synth as syn
 from oracle import pgsag_oracle as O
-from tests._helpers import FWD_TOL, GRAD_TOL, check_projection, loss_pass_vs_oracle, rel_l2, write_stand_in
+from tests._helpers import (FWD_TOL, GRAD_TOL, check_binning, check_projection, loss_pass_vs_oracle, rel_l2,
+                            write_stand_in)
 
 pytestmark = pytest.mark.gpu
 
@@ -246,3 +247,20 @@ def test_fullsize_projection_every_binned_pair(aerial):
     torch.cuda.synchronize()
     plan.check_status()
     assert check_projection(plan, pr) > 500_000
+
+
+def test_fullsize_binning_sorted_and_conservative(aerial):
+    """Binning at full size: every one of the ~1.56M duplicates in its tile's
+    list in strict (depth key, pair) order, counts and rectangles consistent,
+    and, for 20,000 sampled Gaussians evaluated pixel by pixel over their
+    bounding boxes, every (active tile, Gaussian) with an entering rendered pixel
+    binned."""
+    from paper_2501_01677_b300 import raster
+    g, v, plan, cam, pr, boxes = aerial
+    plan.forward(raster.GaussianParams.from_numpy(g))
+    plan.tile_stats(counts_only=True)
+    torch.cuda.synchronize()
+    plan.check_status()
+    M, E, R = O.mask_sets(v.mask)
+    K, have = check_binning(plan, pr, R, n_sample=20_000, seed=3)
+    assert K > 1_000_000

@@ -7,7 +7,8 @@ import torch
 
 import pgsag_synth as syn
 from oracle import pgsag_oracle as O
-from tests._helpers import (FWD_TOL, GRAD_TOL, check_projection, compare_forward, compare_grads, gpu_run,
+from tests._helpers import (FWD_TOL, GRAD_TOL, check_binning, check_projection, compare_forward, compare_grads,
+                            gpu_run,
                             loss_pass_vs_oracle, oracle_run, rel_l2)
 
 pytestmark = pytest.mark.gpu
@@ -122,44 +123,10 @@ def test_config0_bin_sort_and_binning(config0):
     the oracle finds alpha >= 1/255 (binning is conservative)."""
     g, views, res = config0
     plan, P = gpu_run(g, views, grad=False)
-    K = plan.k_value()
-    dup = plan.dup_pairs[:K].cpu().numpy().astype(np.int64)
-    rg = plan.ranges.cpu().numpy().astype(np.int64)[:plan.n_active]
-    key = plan.dkey.cpu().numpy().view(np.uint32).astype(np.int64)
-    bi = plan.bininfo.cpu().numpy().astype(np.int64)
-    at = plan.act_tiles.cpu().numpy().astype(np.int64)[:plan.n_active]
-    # ranges partition [0, K) in tile order
-    ln = rg[:, 1] - rg[:, 0]
-    assert ln.sum() == K and (ln >= 0).all()
-    nz = ln > 0
-    assert (rg[nz, 0] == np.concatenate([[0], np.cumsum(ln)[:-1]])[nz]).all()
-    assert (plan.tile_counts.cpu().numpy()[:plan.n_active] == ln).all()
-    tile_of = np.repeat(np.arange(plan.n_active), ln)
-    # order inside each tile: (key, pair) strictly increasing
-    same = tile_of[1:] == tile_of[:-1]
-    k0, k1 = key[dup[:-1]], key[dup[1:]]
-    assert (((k0 < k1) | ((k0 == k1) & (dup[:-1] < dup[1:])))[same]).all()
-    # per-pair duplicate count equals touched; tiles inside the rectangle
-    assert (np.bincount(dup, minlength=len(bi)) == bi[:, 3]).all()
-    tx, ty = at[tile_of, 1] & 0xFFFF, at[tile_of, 1] >> 16
-    x0, y0, x1, y1 = bi[dup, 0] & 0xFFFF, bi[dup, 0] >> 16, bi[dup, 1] & 0xFFFF, bi[dup, 1] >> 16
-    assert ((tx >= x0) & (tx <= x1) & (ty >= y0) & (ty <= y1)).all()
-    # conservative: oracle alpha >= 1/255 on rendered pixels implies the duplicate exists
-    pr = res["proj"]
     M, E, R = res["sets"]
-    lin, gid = O.candidate_pairs(pr, 256, 256)
-    u, v, gid = (lin % 256).numpy(), (lin // 256).numpy(), gid.numpy()
-    keep = R[v, u]
-    u, v, gid = u[keep], v[keep], gid[keep]
-    m2, q, o = pr["mean2d"].detach().numpy(), pr["conic"].detach().numpy(), pr["opacity"].detach().numpy()
-    dx, dy = u + 0.5 - m2[gid, 0], v + 0.5 - m2[gid, 1]
-    a = o[gid] * np.exp(-0.5 * (q[gid, 0] * dx * dx + 2 * q[gid, 1] * dx * dy + q[gid, 2] * dy * dy))
-    ent = a >= 1 / 255 * (1 + 1e-4)
+    K, have = check_binning(plan, res["proj"], R)
+    bi = plan.bininfo.cpu().numpy().astype(np.int64)
     ta = plan.tile_act.cpu().numpy()
-    need = set(zip(ta[(v[ent] // 16) * 16 + u[ent] // 16].tolist(), gid[ent].tolist()))
-    have = set(zip(tile_of.tolist(), dup.tolist()))
-    assert need <= have
-    assert len(have) == K
     # the exact test prunes the axis-aligned rule
     aabb = 0
     for p in np.nonzero(bi[:, 3] > 0)[0]:

@@ -542,7 +542,7 @@ def ours(args):
                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "peak_source": pk_src, "traffic": traffic,
                     "algorithmic_bytes": ab[dom]}
     # whole step against HBM: compulsory bytes from the per-unit figures and the
-    # measured units.  Two readings of "visible Gaussian": (a) the survey's unit,
+    # measured units.  Two readings of "visible Gaussian" (the per-unit figure's unit): (a)
     # a Gaussian whose centre lies in the view frustum (in front of the near plane,
     # projecting inside the image), counted on the host; (b) a (view, Gaussian)
     # pair the projection bins to at least one active tile (the pairs every later

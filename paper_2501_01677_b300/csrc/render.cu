@@ -612,12 +612,23 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
         float v0[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f},
               v1[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
         B.last0 = B.last1 = -1;
-        if (P.has0)
-          load_upstream(P.q0, P.px.x, P.py.x, ox, oy, V, ti.view, gscale, aux, dout8, ddepth, use_ban, ban, out8, v0,
-                        B.last0, kSoft, gscale_in);
-        if (P.has1)
-          load_upstream(P.q1, P.px.y, P.py.y, ox, oy, V, ti.view, gscale, aux, dout8, ddepth, use_ban, ban, out8, v1,
-                        B.last1, kSoft, gscale_in);
+        {
+          // both pixels' loads in one basic block (a missing pixel reads the tile's
+          // first row and its results are discarded)
+          float w0[10], w1[10];
+          int l0, l1;
+          load_upstream(P.has0 ? P.q0 : ti.px_first, P.px.x, P.py.x, ox, oy, V, ti.view, gscale, aux, dout8, ddepth,
+                        use_ban, ban, out8, w0, l0, kSoft, gscale_in);
+          load_upstream(P.has1 ? P.q1 : ti.px_first, P.px.y, P.py.y, ox, oy, V, ti.view, gscale, aux, dout8, ddepth,
+                        use_ban, ban, out8, w1, l1, kSoft, gscale_in);
+#pragma unroll
+          for (int k = 0; k < 10; ++k) {
+            v0[k] = P.has0 ? w0[k] : v0[k];
+            v1[k] = P.has1 ? w1[k] : v1[k];
+          }
+          B.last0 = P.has0 ? l0 : -1;
+          B.last1 = P.has1 ? l1 : -1;
+        }
         B.dC0 = make_float2(v0[0], v1[0]);
         B.dC1 = make_float2(v0[1], v1[1]);
         B.dC2 = make_float2(v0[2], v1[2]);

@@ -365,6 +365,13 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
     unsigned long long mask = 0ull;  // tiles binned to, bit (ty - y0) * width + (tx - x0) of the rect
     float mi = 0.f, mf = 0.f, ni = 0.f, nf = 0.f;
     if (vis) {
+      // the SH row (192 B) is read only if the pair is binned; ask L2 for it now
+      // so that the read after the tile test finds it there
+      {
+        const float* row = sh + 48ull * g;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(row + 32));
+      }
       {
         float xh, xl, yh, yl, zh, zl;
         dot3_comp(V.R + 0, G.m, V.t[0], xh, xl);

@@ -75,6 +75,9 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
   const PixCtx P = pix_ctx(c, lane, chunks, px_list, views);
   float l1 = 0.f, lb = 0.f, nv = 0.f, gn = 0.f, gx = 0.f;
   if (P.has) {
+    // the flags and outputs are loaded before the Eq. 9 division waits on the count
+    const uint8_t f = __ldg(flags_c + P.q);
+    const float4 o0 = __ldg(out8 + 2 * P.q), o1 = __ldg(out8 + 2 * P.q + 1);
     if (gc_weight != nullptr) {
       // Eq. 9 term of this rendered pixel: g / w (g = Gaussians blended, or the
       // soft count g~ = sum of their alphas)
@@ -82,8 +85,6 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
       gx = g / __ldg(gc_weight + P.q);
       gn = 1.f;
     }
-    const uint8_t f = __ldg(flags_c + P.q);
-    const float4 o0 = __ldg(out8 + 2 * P.q), o1 = __ldg(out8 + 2 * P.q + 1);
     float dC[3] = {0.f, 0.f, 0.f}, dNo[3] = {0.f, 0.f, 0.f};
     if (f & PGSAG_PIX_MASK) {
       const uint32_t nm = __ldg(&views[P.view].n_mask);

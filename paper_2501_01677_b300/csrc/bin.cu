@@ -159,6 +159,11 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(uint32_t n, const uint4* 
       const uint32_t j = r + threadIdx.x;
       const uint32_t p = j < m ? s_list[j] : 0u;
       const uint4 bi = j < m ? __ldg(&bininfo[p]) : make_uint4(0, 0, 0, 0);
+      // the tile mask and the view's tiling are requested before the block scan
+      const unsigned long long mk0 = j < m ? __ldg(tmask + p) : 0ull;
+      const pgsag_view* V = views + bi.z;
+      const int tiles_x = j < m ? __ldg(&V->tiles_x) : 0;
+      const uint32_t tbase = j < m ? __ldg(&V->tile_base) : 0u;
       uint32_t total;
       const uint32_t off = block_excl_scan(bi.w, total, sh);
       if (threadIdx.x == 0) s_base = atomicAdd(k_total, (unsigned long long)total);
@@ -167,9 +172,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(uint32_t n, const uint4* 
       __syncthreads();
       if (threadIdx.x == 0 && base + total > capacity) status_set(status, PGSAG_DEV_CAPACITY);
       if (bi.w) {
-        const pgsag_view* V = views + bi.z;
-        const int tiles_x = __ldg(&V->tiles_x);
-        const int32_t* ta = tile_act + __ldg(&V->tile_base);
+        const int32_t* ta = tile_act + tbase;
         const uint32_t x0 = bi.x & 0xffffu, y0 = bi.x >> 16, x1 = bi.y & 0xffffu, y1 = bi.y >> 16;
         const uint32_t rw = x1 - x0 + 1;
         const bool exact = rw * (y1 - y0 + 1) <= (uint32_t)kExactTileMax;
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(uint32_t n, const uint4* 
         };
         if (exact) {
           // the tiles the projection's exact test accepted, one bit each
-          for (unsigned long long mk = __ldg(tmask + p); mk; mk &= mk - 1) {
+          for (unsigned long long mk = mk0; mk; mk &= mk - 1) {
             const uint32_t b = (uint32_t)__ffsll((long long)mk) - 1u;
             const uint32_t ty = y0 + b / rw, tx = x0 + b % rw;
             put(__ldg(ta + (size_t)ty * tiles_x + tx));
@@ -239,6 +242,7 @@ __global__ void k_scatter(const uint64_t* __restrict__ k_dev, uint64_t cap, uint
   const uint32_t n = (uint32_t)umin64(*k_dev, cap);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const uint32_t a = __ldg(tile_keys + k);
+    const uint32_t pv = __ldg(pair_vals + k);  // requested with the key, not after the atomic
     if (a >= n_active) {
       status_set(status, PGSAG_DEV_BOUNDS);
       continue;
@@ -249,7 +253,7 @@ __global__ void k_scatter(const uint64_t* __restrict__ k_dev, uint64_t cap, uint
       status_set(status, PGSAG_DEV_BOUNDS);
       continue;
     }
-    out[r.x + left - 1u] = __ldg(pair_vals + k);
+    out[r.x + left - 1u] = pv;
   }
 }
 

@@ -31,10 +31,10 @@ constexpr int kScanThreads = 256;
 constexpr int kEmitChunk = 1024;   // pairs gathered per block round in the emission
 constexpr int kSortThreads = 256;
 constexpr int kSegMax = 2048;      // keys sorted in shared memory at once by a block (16 KB)
-constexpr int kWarpSegMax = 512;   // longest list a warp sorts on its own (16 keys per lane in registers)
+constexpr int kWarpSegMax = 256;   // longest list a warp sorts on its own (8 keys per lane in registers)
 constexpr int kWarpSortWarps = 8;  // warps per block of the per-warp sort
 #ifndef PGSAG_SORT_MINB
-#define PGSAG_SORT_MINB 3  // resident per-warp sort blocks per SM the register budget must allow
+#define PGSAG_SORT_MINB 6  // resident per-warp sort blocks per SM the register budget must allow
 #endif
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kWarpSortWarps * 32, PGSAG_SORT_MINB) k_sort_w
                                                                    uint32_t* __restrict__ long_list,
                                                                    unsigned long long* __restrict__ n_long,
                                                                    const int32_t* status) {
-  static_assert(kWarpSegMax == 32 * 16, "the register sort covers up to 16 keys per lane");
+  static_assert(kWarpSegMax == 32 * 8, "the register sort covers up to 8 keys per lane");
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t a = blockIdx.x * kWarpSortWarps + warp; a < n_active; a += gridDim.x * kWarpSortWarps) {
@@ -402,8 +402,7 @@ __global__ void __launch_bounds__(kWarpSortWarps * 32, PGSAG_SORT_MINB) k_sort_w
     if (n <= 32) warp_sort_list<1>(in, n, o, dkey, lane);
     else if (n <= 64) warp_sort_list<2>(in, n, o, dkey, lane);
     else if (n <= 128) warp_sort_list<4>(in, n, o, dkey, lane);
-    else if (n <= 256) warp_sort_list<8>(in, n, o, dkey, lane);
-    else if (n <= (uint32_t)kWarpSegMax) warp_sort_list<16>(in, n, o, dkey, lane);
+    else if (n <= (uint32_t)kWarpSegMax) warp_sort_list<8>(in, n, o, dkey, lane);
     else if (lane == 0) long_list[atomicAdd(n_long, 1ull)] = a;
   }
 }

@@ -34,7 +34,7 @@ namespace pgsag {
 #define PGSAG_BATCH 128
 #endif
 #ifndef PGSAG_FWD_MINB
-#define PGSAG_FWD_MINB 10  // resident CTAs per SM the register budget must allow
+#define PGSAG_FWD_MINB 9  // resident CTAs per SM the register budget must allow (56 registers)
 #endif
 #ifndef PGSAG_BWD_MINB
 #define PGSAG_BWD_MINB 9

@@ -73,6 +73,18 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
   if (c >= n_chunks) return;
   const PixCtx P = pix_ctx(c, lane, chunks, px_list, views);
+  {
+    // the chunk's target (3 lines), neighbour-table (4 lines) and depth (1 line)
+    // rows are read only after the flag and depth tests: ask L2 for them now
+    // (only lines that start inside the chunk's rows)
+    const uint32_t n = __popc(__ballot_sync(0xffffffffu, P.has));
+    const uint64_t q0 = P.q - (uint64_t)lane;
+    const char* a = nullptr;
+    if (lane < 3 && 128u * lane < 12u * n) a = reinterpret_cast<const char*>(target + 3 * q0) + 128 * lane;
+    else if (lane >= 3 && lane < 7 && 128u * (lane - 3) < 16u * n) a = reinterpret_cast<const char*>(nbr + q0) + 128 * (lane - 3);
+    else if (lane == 7 && n > 0) a = reinterpret_cast<const char*>(depth + q0);
+    if (a) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+  }
   float l1 = 0.f, lb = 0.f, nv = 0.f, gn = 0.f, gx = 0.f;
   if (P.has) {
     // the flags and outputs are loaded before the Eq. 9 division waits on the count

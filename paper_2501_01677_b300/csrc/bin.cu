@@ -26,6 +26,9 @@ namespace pgsag {
 #define PGSAG_SCAN_BLOCKS 592  // 4 blocks per SM on 148 SMs
 #endif
 constexpr int kScanBlocks = PGSAG_SCAN_BLOCKS;
+// the emission and the scatter wait on dependent loads and atomics: 20 blocks
+// per SM in flight (grid-stride beyond that; blocks without work exit at once)
+constexpr int kWideBlocks = 148 * 20;
 static_assert(kScanBlocks >= 1 && kScanBlocks <= 1024, "k_scan_partials scans one partial per thread of one 1024-thread block");
 constexpr int kScanThreads = 256;
 constexpr int kEmitChunk = 1024;   // pairs gathered per block round in the emission
@@ -517,7 +520,7 @@ extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* v
   PGSAG_CUDA(cudaMemsetAsync(w.n_long, 0, sizeof(unsigned long long), s));
 
   // 1. emission (K accumulates in *k_out)
-  k_emit<<<kScanBlocks, kScanThreads, 0, s>>>(n_pairs, (const uint4*)bininfo, views, tile_act,
+  k_emit<<<kWideBlocks, kScanThreads, 0, s>>>(n_pairs, (const uint4*)bininfo, views, tile_act,
                                               (const unsigned long long*)tile_mask, n_active_total, capacity, (unsigned long long*)k_out, w.tile_keys,
                                               w.pair_vals, w.tile_cnt, status);
   PGSAG_CHECK_LAUNCH();
@@ -530,7 +533,7 @@ extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* v
                                                      status);
   PGSAG_CHECK_LAUNCH();
   // 3. scatter into the tiles' ranges; 4. per-tile sort into dup_pairs
-  k_scatter<<<kScanBlocks, 256, 0, s>>>(k_out, capacity, n_active_total, w.tile_keys, w.pair_vals,
+  k_scatter<<<kWideBlocks, 256, 0, s>>>(k_out, capacity, n_active_total, w.tile_keys, w.pair_vals,
                                         (const uint2*)ranges, w.tile_cnt, w.buf, status);
   PGSAG_CHECK_LAUNCH();
   const uint32_t warp_blocks = (n_active_total + kWarpSortWarps - 1) / kWarpSortWarps;

@@ -254,7 +254,9 @@ int pgsag_prep_gc_weight(const pgsag_view* view, const float* target, const uint
  *   of every binned pair is zeroed, so that pgsag_render_bwd may be called with
  *   n_pairs = 0 (only binned rows are accumulated into or read later).
  * n_pairs = sum over views of (g_end - g_begin).
- * This call begins a step: it clears *status before its kernel runs.
+ * This call begins a step: it clears *status (its kernel, which sets no flag,
+ * does it; with n_gauss = 0 a memset does), so every later call of the step
+ * sees only the flags raised after it.
  */
 int pgsag_preprocess(uint32_t n_gauss, const float* means, const float* log_scales,
                      const float* quats, const float* opacity_logit, const float* sh,

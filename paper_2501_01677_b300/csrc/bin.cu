@@ -135,6 +135,18 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint64_t* __restrict__ p
 // kScanThreads of them reserves its output with one atomic on *k_total, and
 // every duplicate is written as (active tile, pair) and counted per tile.
 // Duplicates beyond `capacity` are not written (the capacity flag is set).
+// The binning's counters: per-tile counts, the long-list count and K (one
+// launch instead of three memsets).
+__global__ void k_bin_clear(uint32_t n_active, uint32_t* __restrict__ tile_cnt, unsigned long long* __restrict__ n_long,
+                            unsigned long long* __restrict__ k_total) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_active) tile_cnt[i] = 0u;
+  if (i == 0) {
+    *n_long = 0ull;
+    *k_total = 0ull;
+  }
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_emit(uint32_t n, const uint4* __restrict__ bininfo,
                                                        const pgsag_view* __restrict__ views,
                                                        const int32_t* __restrict__ tile_act,
@@ -509,15 +521,16 @@ extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* v
   const BinWs w = carve(ws, n_active_total, capacity);
   if (ws_bytes < w.bytes) return PGSAG_ERR_CAPACITY;
   cudaStream_t s = (cudaStream_t)stream;
-  PGSAG_CUDA(cudaMemsetAsync(k_out, 0, sizeof(uint64_t), s));
   if (n_pairs == 0 || n_active_total == 0) {
+    PGSAG_CUDA(cudaMemsetAsync(k_out, 0, sizeof(uint64_t), s));
     // nothing is emitted: every tile's list is empty
     if (n_active_total) PGSAG_CUDA(cudaMemsetAsync(ranges, 0, (size_t)n_active_total * sizeof(uint2), s));
     return PGSAG_OK;
   }
   // (the ranges of every active tile are written by step 2)
-  PGSAG_CUDA(cudaMemsetAsync(w.tile_cnt, 0, (size_t)n_active_total * sizeof(uint32_t), s));
-  PGSAG_CUDA(cudaMemsetAsync(w.n_long, 0, sizeof(unsigned long long), s));
+  k_bin_clear<<<pgsag_div_up(n_active_total, 256u), 256, 0, s>>>(n_active_total, w.tile_cnt, w.n_long,
+                                                                  (unsigned long long*)k_out);
+  PGSAG_CHECK_LAUNCH();
 
   // 1. emission (K accumulates in *k_out)
   k_emit<<<kWideBlocks, kScanThreads, 0, s>>>(n_pairs, (const uint4*)bininfo, views, tile_act,

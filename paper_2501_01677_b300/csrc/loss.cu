@@ -67,7 +67,11 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
     const uint4* __restrict__ aux,
     const float* __restrict__ gc_weight, bool soft, float l1_scale, float* __restrict__ scratch,
     float4* __restrict__ partial,
-    float4* __restrict__ dout8, const int32_t* status) {
+    float4* __restrict__ dout8, double* __restrict__ acc, uint32_t n_acc, const int32_t* status) {
+  // the per-view accumulators the reduction after this pass adds into (a memset
+  // node costs more than these few stores)
+  if (blockIdx.x == 0)
+    for (uint32_t i = threadIdx.x; i < n_acc; i += blockDim.x) acc[i] = 0.0;
   if (status_bad(status)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t c = blockIdx.x * (kLossThreads / 32) + (threadIdx.x >> 5);
@@ -469,7 +473,8 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
     return PGSAG_ERR_ARG;
   const float lambda_d = dssim ? dssim->lambda : 0.f;
   cudaStream_t s = (cudaStream_t)stream;
-  PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)(n_views + (eq11 ? 1 : 0)) * 8 * sizeof(double), s));
+  const uint32_t n_acc = (n_views + (eq11 ? 1u : 0u)) * 8u;
+  if (n_chunks == 0) PGSAG_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_acc * sizeof(double), s));
   if (n_chunks) {
     if (!chunks || !px_list || !flags_c || !nbr || !out8 || !depth || !target || !scratch || !dout8 ||
         !chunk_scratch || (gc_weight && !aux))
@@ -481,7 +486,7 @@ extern "C" int pgsag_loss_ban(uint32_t n_views, const pgsag_view* views, uint32_
     k_loss_a<<<blocks, kLossThreads, 0, s>>>(views, n_chunks, (const uint4*)chunks, px_list, flags_c,
                                              (const uint4*)nbr, (const float4*)out8, depth, target,
                                              (const uint4*)aux, gc_weight, eq11, 1.f - lambda_d, scratch,
-                                             (float4*)chunk_scratch, (float4*)dout8, status);
+                                             (float4*)chunk_scratch, (float4*)dout8, acc, n_acc, status);
     PGSAG_CHECK_LAUNCH();
     k_view_reduce<<<dim3(kReduceBlocks, n_views), 256, 0, s>>>(views, chunk_scratch, 8, gc_weight ? 7 : 3, 8,
                                                                 acc, n_chunks, status);

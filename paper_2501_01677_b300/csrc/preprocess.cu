@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
                              const int32_t* __restrict__ tile_act, const uint32_t* __restrict__ sat,
                              float4* __restrict__ rec, uint32_t* __restrict__ dkey,
                              uint4* __restrict__ bininfo, unsigned long long* __restrict__ tmask,
-                             float4* __restrict__ grad2d, const int32_t* status) {
+                             float4* __restrict__ grad2d, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pgsag_view* sv = reinterpret_cast<pgsag_view*>(smem_raw);
   {
@@ -346,7 +346,9 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_MINB) k_preprocess(uint
     uint32_t* dst = reinterpret_cast<uint32_t*>(smem_raw);
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   }
-  if (status_bad(status)) return;
+  // the step's device status starts here: this kernel sets no flag, so the
+  // reset (one store) needs no memset node before it
+  if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
   __syncthreads();
   set_campos(sv, n_views);
   __syncthreads();
@@ -798,7 +800,6 @@ extern "C" int pgsag_preprocess(uint32_t n_gauss, const float* means, const floa
   if (!aligned16(quats) || !aligned16(sh) || !aligned16(rec) || !aligned16(bininfo) || ((uintptr_t)tile_mask & 7u))
     return PGSAG_ERR_ARG;
   if (grad2d && !aligned16(grad2d)) return PGSAG_ERR_ARG;
-  PGSAG_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), (cudaStream_t)stream));
   const unsigned threads = kPreThreads;
   const size_t smem = views_bytes(n_views);
   if (smem > 48 * 1024 &&

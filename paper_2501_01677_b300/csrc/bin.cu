@@ -29,7 +29,7 @@ constexpr int kScanBlocks = PGSAG_SCAN_BLOCKS;
 // the emission and the scatter wait on dependent loads and atomics: 20 blocks
 // per SM in flight (grid-stride beyond that; blocks without work exit at once)
 constexpr int kWideBlocks = 148 * 20;
-static_assert(kScanBlocks >= 1 && kScanBlocks <= 1024, "k_scan_partials scans one partial per thread of one 1024-thread block");
+static_assert(kScanBlocks >= 1 && kScanBlocks <= 1024, "k_tile_ranges sums the block sums before its own");
 constexpr int kScanThreads = 256;
 constexpr int kEmitChunk = 1024;   // pairs gathered per block round in the emission
 constexpr int kSortThreads = 256;
@@ -93,48 +93,6 @@ __global__ void __launch_bounds__(kScanThreads) k_block_sums(uint32_t n, const u
   }
 }
 
-// One block: exclusive scan (in place) of nb <= 1024 block sums; the total goes
-// to *total_out when given, and with check_cap a total above `capacity` sets
-// the capacity flag (nothing is emitted then: later kernels see the status).
-__global__ void __launch_bounds__(1024) k_scan_partials(uint64_t* __restrict__ partial, uint32_t nb,
-                                                        uint64_t* __restrict__ total_out, uint64_t capacity,
-                                                        int check_cap, int32_t* status) {
-  __shared__ unsigned long long wsum[32];
-  if (status_bad(status)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned long long s = threadIdx.x < nb ? partial[threadIdx.x] : 0ull;
-  unsigned long long x = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned long long w = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(kFull, w, o);
-      if (lane >= o) w += y;
-    }
-    wsum[lane] = w;
-  }
-  __syncthreads();
-  const unsigned long long pre = x - s + (warp > 0 ? wsum[warp - 1] : 0ull);
-  if (threadIdx.x < nb) partial[threadIdx.x] = pre;
-  if (threadIdx.x == 1023) {
-    const unsigned long long total = pre + s;
-    if (total_out) *total_out = total;
-    if (check_cap && total > capacity) status_set(status, PGSAG_DEV_CAPACITY);
-  }
-}
-
-// Step 1: emission.  Blocks stride over kEmitChunk-pair slices; the binned
-// pairs of a slice are gathered in shared memory, each round of up to
-// kScanThreads of them reserves its output with one atomic on *k_total, and
-// every duplicate is written as (active tile, pair) and counted per tile.
-// Duplicates beyond `capacity` are not written (the capacity flag is set).
 // The binning's counters: per-tile counts, the long-list count and K (one
 // launch instead of three memsets).
 __global__ void k_bin_clear(uint32_t n_active, uint32_t* __restrict__ tile_cnt, unsigned long long* __restrict__ n_long,
@@ -147,6 +105,11 @@ __global__ void k_bin_clear(uint32_t n_active, uint32_t* __restrict__ tile_cnt, 
   }
 }
 
+// Step 1: emission.  Blocks stride over kEmitChunk-pair slices; the binned
+// pairs of a slice are gathered in shared memory, each round of up to
+// kScanThreads of them reserves its output with one atomic on *k_total, and
+// every duplicate is written as (active tile, pair) and counted per tile.
+// Duplicates beyond `capacity` are not written (the capacity flag is set).
 __global__ void __launch_bounds__(kScanThreads) k_emit(uint32_t n, const uint4* __restrict__ bininfo,
                                                        const pgsag_view* __restrict__ views,
                                                        const int32_t* __restrict__ tile_act,
@@ -233,10 +196,22 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_ranges(uint32_t n_active,
                                                               const uint64_t* __restrict__ partial,
                                                               uint2* __restrict__ ranges, const int32_t* status) {
   __shared__ uint32_t sh[kScanThreads / 32];
+  __shared__ unsigned long long s_pre[kScanThreads / 32];
   if (status_bad(status)) return;
   uint32_t lo, hi;
   block_range(n_active, blockIdx.x, gridDim.x, lo, hi);
-  uint32_t carry = (uint32_t)partial[blockIdx.x];
+  // this block's offset: the sum of the block sums before it (at most a few
+  // hundred L2-resident values; no separate scan launch)
+  unsigned long long pre = 0;
+  for (uint32_t b = threadIdx.x; b < blockIdx.x; b += kScanThreads) pre += __ldg(partial + b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(kFull, pre, o);
+  if ((threadIdx.x & 31) == 0) s_pre[threadIdx.x >> 5] = pre;
+  __syncthreads();
+  pre = 0;
+#pragma unroll
+  for (int w = 0; w < kScanThreads / 32; ++w) pre += s_pre[w];
+  uint32_t carry = (uint32_t)pre;
   for (uint32_t base = lo; base < hi; base += kScanThreads) {
     const uint32_t a = base + threadIdx.x;
     const uint32_t c = a < hi ? __ldg(cnt + a) : 0u;
@@ -539,8 +514,6 @@ extern "C" int pgsag_bin(uint32_t n_pairs, uint32_t n_views, const pgsag_view* v
   PGSAG_CHECK_LAUNCH();
   // 2. per-tile ranges
   k_block_sums<<<kScanBlocks, kScanThreads, 0, s>>>(n_active_total, w.tile_cnt, 1, w.tile_partial, status);
-  PGSAG_CHECK_LAUNCH();
-  k_scan_partials<<<1, 1024, 0, s>>>(w.tile_partial, kScanBlocks, nullptr, 0, 0, status);
   PGSAG_CHECK_LAUNCH();
   k_tile_ranges<<<kScanBlocks, kScanThreads, 0, s>>>(n_active_total, w.tile_cnt, w.tile_partial, (uint2*)ranges,
                                                      status);

@@ -299,7 +299,7 @@ class Plan:
         fused loss sums the GC-load and leaves the Eq. 8 gather to render_bwd."""
         n = 1  # preprocess
         if self.n_pairs and self.n_active:
-            n += 8                              # bin: counter clear, emit, tile scan (3), scatter, sorts (2)
+            n += 7                              # bin: counter clear, emit, tile scan (2), scatter, sorts (2)
         if self.sched is not None and getattr(self, "lpt", False) and self.n_active:
             n += 3                              # schedule
         n += 1 if self.n_active else 0          # render_fwd

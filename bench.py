@@ -198,10 +198,11 @@ def algorithmic_bytes(plan, K, n_binned):
         # per pixel: list 4 + aux 16 + dout8 32 + depth 4 (Eq. 4 chain; the Eq. 11 objective also reads
         # the 16-byte normal half of out8) + neighbour gather (index 4, scratch 12);
         # per duplicate: id 4 + record 64; grad2d read + write-back 2x64 per binned pair (its zeroing is
-        # the projection's, above)
-        "render_bwd": (89 if plan.objective == "eq11" else 73) * P + 68 * K + 128 * n_binned,
-        # gradients written 236 B/G; bininfo 16/pair; binned: params 236 + grad2d 64
-        "preprocess_bwd": 236 * N + 16 * NP + 300 * n_binned,
+        # the projection's, above); the step's gradient buffers cleared on the side, 236 B/G
+        "render_bwd": (89 if plan.objective == "eq11" else 73) * P + 68 * K + 128 * n_binned + 236 * N,
+        # gradient rows of the Gaussians with a binned pair written, 236 B (the others keep the clear's
+        # zeros); bininfo 16/pair; binned: params 236 + grad2d 64
+        "preprocess_bwd": 16 * NP + 536 * n_binned,
     }
 
 

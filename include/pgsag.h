@@ -448,13 +448,25 @@ typedef struct pgsag_ban_gather {
  * (nullable, host struct) adds the deferred Eq. 8 gather: dout8 is then the
  * output of pgsag_loss_ban with gather = 0.  dout_scale (nullable, device float[1])
  * multiplies the whole upstream gradient (chain rule from a scalar loss).
+ * clear (nullable, host struct) names buffers that this call sets to zero on
+ * the side: every CTA stores zeros over its share of them (streaming stores
+ * that drain while it renders; the call is ALU-bound and leaves most of the
+ * memory bandwidth unused).  It is meant for the raw-parameter gradients of
+ * the step, so that pgsag_preprocess_bwd with accumulate = 2 writes only the
+ * rows of the Gaussians that have a binned pair.  The cleared buffers must not
+ * overlap any input or output of this call.
  */
+#define PGSAG_CLEAR_MAX 5
+typedef struct pgsag_clear {
+  float* ptr[PGSAG_CLEAR_MAX];   /* device, 16-byte aligned; NULL where n is 0   */
+  uint64_t n[PGSAG_CLEAR_MAX];   /* floats to set to zero from ptr[i]            */
+} pgsag_clear;                   /* 80 bytes */
 int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec,
                      const uint32_t* dup_pairs, const void* ranges, const void* act_tiles,
                      uint32_t n_active_total, const uint32_t* px_list, const pgsag_sched* sched,
                      const float* out8, const void* aux, const float* dout8, const float* ddepth,
                      const pgsag_ban_gather* ban, const float* dout_scale, uint32_t n_pairs, float* grad2d,
-                     int32_t* status, void* stream);
+                     const pgsag_clear* clear, int32_t* status, void* stream);
 
 /*
  * pgsag_preprocess_bwd: chain rule from grad2d to the raw parameters (the
@@ -464,7 +476,10 @@ int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec
  * over that list).  The argmin axis, the normal flip, the Jacobian clamp and
  * the colour clamp are locally constant.  accumulate = 0 overwrites the
  * outputs, 1 adds to them (the outputs of a Gaussian with no binned pair and no
- * flattening term are then left as they are: its gradient is zero).
+ * flattening term are then left as they are: its gradient is zero), 2 takes
+ * outputs that already hold zeros (pgsag_render_bwd's clear): the rows of the
+ * Gaussians with a binned pair are overwritten, the others are written only
+ * where the flattening term is on.
  * flatten_weight != 0 adds the gradient of flatten_weight * L_s, L_s = mean over
  * the n_gauss Gaussians of min(exp(log_scales)) (Eq. 11's flattening term; its
  * weight there is (1 - lambda) lambda_3), scaled by *dout_scale if dout_scale is

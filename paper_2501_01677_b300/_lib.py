@@ -63,6 +63,15 @@ class PgsagBanGather(ctypes.Structure):
 
 
 assert ctypes.sizeof(PgsagBanGather) == 64
+CLEAR_MAX = 5
+
+
+class PgsagClear(ctypes.Structure):
+    """pgsag_clear: float buffers the render adjoint sets to zero on the side."""
+    _fields_ = [("ptr", c_void_p * CLEAR_MAX), ("n", c_uint64 * CLEAR_MAX)]
+
+
+assert ctypes.sizeof(PgsagClear) == 80
 OBJ_PG, OBJ_EQ11 = 0, 1
 RENDER_SOFT_COUNT = 1
 LAMBDA_GC, LAMBDA_FLAT = 0.41, 100.0
@@ -153,7 +162,7 @@ def load(path: str = LIB_PATH):
           POINTER(PgsagDssim), P, P])
     _sig(lib, "pgsag_render_bwd", c_int,
          [c_uint32, P, P, P, P, P, c_uint32, P, POINTER(PgsagSched), P, P, P, P, POINTER(PgsagBanGather), P,
-          c_uint32, P, P, P])
+          c_uint32, P, POINTER(PgsagClear), P, P])
     _sig(lib, "pgsag_preprocess_bwd", c_int,
          [c_uint32, P, P, P, P, P, c_uint32, P, P, P, c_int, P, P, P, P, P, P, c_float, P, P])
     _sig(lib, "pgsag_tile_stats", c_int, [c_uint32, P, c_uint32, P, c_uint32, P, P, P, P, P, P, P, P, P, P, P])

@@ -556,12 +556,14 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
     } else if (g < n) {
       float gls[3] = {0.f, 0.f, 0.f};
       const bool flat = add_flatten(g, log_scales, n, flatten_weight, sc, gls);
-      if (!accumulate || flat) store_small(g, zero3, gls, zero4, 0.f, accumulate, d_means, d_log_scales, d_quats, d_opac);
+      // accumulate = 2: the row holds zeros already (written only for a flattening term)
+      if (accumulate == 0 || flat)
+        store_small(g, zero3, gls, zero4, 0.f, accumulate == 1, d_means, d_log_scales, d_quats, d_opac);
     }
   }
   __syncthreads();
   const uint32_t nl = s_nlist;
-  if (!accumulate) {
+  if (accumulate == 0) {
     // zero SH rows of the Gaussians without a binned pair (coalesced float4)
     const uint32_t nb = min((uint32_t)kPreBwdSlice, n - gbase);
     float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * gbase);
@@ -758,7 +760,7 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
       }
 
       add_flatten(g, log_scales, n, flatten_weight, sc, gls);
-      store_small(g, gm, gls, gq, gol, accumulate, d_means, d_log_scales, d_quats, d_opac);
+      store_small(g, gm, gls, gq, gol, accumulate == 1, d_means, d_log_scales, d_quats, d_opac);
     }
     __syncthreads();
     // SH gradient rows of this round: coalesced float4 stores, 12 per row
@@ -768,7 +770,7 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
       const float* sg = s_gsh + row * kShStride + 4 * c4;
       float4 v = make_float4(sg[0], sg[1], sg[2], sg[3]);
       float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * s_list[base + row]) + c4;
-      if (accumulate) {
+      if (accumulate == 1) {
         const float4 o = *dst;
         v.x += o.x;
         v.y += o.y;
@@ -821,7 +823,7 @@ extern "C" int pgsag_preprocess_bwd(uint32_t n_gauss, const float* means, const 
                                     float* d_sh, const float* dout_scale, float flatten_weight,
                                     int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
-  if (!views || !status) return PGSAG_ERR_ARG;
+  if (!views || !status || accumulate < 0 || accumulate > 2) return PGSAG_ERR_ARG;
   if (n_gauss == 0) return PGSAG_OK;
   if (!means || !log_scales || !quats || !opacity_logit || !sh || !bininfo || !grad2d || !d_means ||
       !d_log_scales || !d_quats || !d_opacity_logit || !d_sh)

@@ -557,6 +557,42 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
 
 // kSoft: objective Eq. 11 -- the loss gradients get the (1 - lambda) factor and
 // every blended alpha the soft-count GC-load gradient dL/dg~ of its pixel.
+// Buffers the adjoint's CTAs set to zero on the side (pgsag_clear): the float4
+// body of each buffer is cut into one share per CTA; the at most 3 trailing
+// floats of a buffer are cleared by CTA 0.
+struct ClearJob {
+  float4* p[PGSAG_CLEAR_MAX];
+  uint64_t n4[PGSAG_CLEAR_MAX];  // float4 units of the body
+  float* tail[PGSAG_CLEAR_MAX];
+  uint32_t n_tail[PGSAG_CLEAR_MAX];
+  uint64_t total;  // sum of n4
+};
+
+// Streaming stores (evict-first in L2): they drain while the CTA renders and
+// leave the lists and records the adjoint re-reads in L2.
+__device__ __forceinline__ void clear_share(const ClearJob& cj) {
+  if (blockIdx.x == 0 && threadIdx.x < 3) {
+#pragma unroll
+    for (int i = 0; i < PGSAG_CLEAR_MAX; ++i)
+      if (threadIdx.x < cj.n_tail[i]) cj.tail[i][threadIdx.x] = 0.f;
+  }
+  const uint64_t per = (cj.total + gridDim.x - 1) / gridDim.x;
+  uint64_t lo = (uint64_t)blockIdx.x * per;
+  const uint64_t hi = min(cj.total, lo + per);
+  uint64_t off = 0;
+#pragma unroll
+  for (int i = 0; i < PGSAG_CLEAR_MAX; ++i) {
+    const uint64_t end = off + cj.n4[i];
+    if (lo < hi && lo < end) {
+      const uint64_t b = min(hi, end) - off;
+      for (uint64_t k = lo - off + threadIdx.x; k < b; k += blockDim.x)
+        __stcs(cj.p[i] + k, make_float4(0.f, 0.f, 0.f, 0.f));
+      lo = min(hi, end);
+    }
+    off = end;
+  }
+}
+
 template <int kWarps, bool kSoft>
 __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     const pgsag_view* __restrict__ views, const float4* __restrict__ rec,
@@ -564,7 +600,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     const uint4* __restrict__ act_tiles, uint32_t n_items, const uint32_t* __restrict__ px_list,
     Sched sched, const float4* __restrict__ out8, const uint4* __restrict__ aux,
     const float4* __restrict__ dout8, const float* __restrict__ ddepth, const pgsag_ban_gather ban, bool use_ban,
-    const float* __restrict__ dout_scale, float* __restrict__ grad2d, const int32_t* status) {
+    const float* __restrict__ dout_scale, float* __restrict__ grad2d, const ClearJob clear,
+    const int32_t* status) {
   constexpr int kRenderThreads = kWarps * 32;
   constexpr int kTilePix = kRenderThreads * 2;
   constexpr int kStagePerThread = kBatch / kRenderThreads;
@@ -576,6 +613,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
   __shared__ int s_wmax[2][kWarps];
   uint32_t round = 0;
   if (status_bad(status)) return;
+  if (clear.total | clear.n_tail[0] | clear.n_tail[1] | clear.n_tail[2] | clear.n_tail[3] | clear.n_tail[4])
+    clear_share(clear);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float gscale_in = dout_scale ? __ldg(dout_scale) : 1.f;
   // Eq. 11: the photometric / normal-loss gradients are scaled by (1 - lambda)
@@ -834,7 +873,7 @@ static int launch_bwd(const pgsag_sched* sched, uint32_t n_active, const pgsag_v
                       const uint32_t* dup_pairs, const void* ranges, const void* act_tiles, const uint32_t* px_list,
                       const float* out8, const void* aux, const float* dout8, const float* ddepth,
                       const pgsag_ban_gather& bg, bool use_ban, const float* dout_scale, float* grad2d,
-                      int32_t* status, cudaStream_t st) {
+                      const ClearJob& cj, int32_t* status, cudaStream_t st) {
   Sched s;
   unsigned blocks;
   static int occ = 0;
@@ -844,7 +883,8 @@ static int launch_bwd(const pgsag_sched* sched, uint32_t n_active, const pgsag_v
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
   k_render_bwd<PGSAG_BWD_WARPS, kSoft><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(
       views, (const float4*)rec, dup_pairs, (const uint2*)ranges, (const uint4*)act_tiles, n_active, px_list, s,
-      (const float4*)out8, (const uint4*)aux, (const float4*)dout8, ddepth, bg, use_ban, dout_scale, grad2d, status);
+      (const float4*)out8, (const uint4*)aux, (const float4*)dout8, ddepth, bg, use_ban, dout_scale, grad2d, cj,
+      status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
 }
@@ -854,17 +894,36 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
                                 uint32_t n_active, const uint32_t* px_list, const pgsag_sched* sched,
                                 const float* out8, const void* aux, const float* dout8, const float* ddepth,
                                 const pgsag_ban_gather* ban, const float* dout_scale, uint32_t n_pairs,
-                                float* grad2d, int32_t* status, void* stream) {
+                                float* grad2d, const pgsag_clear* clear, int32_t* status, void* stream) {
   if (n_views == 0 || n_views > PGSAG_MAX_VIEWS) return PGSAG_ERR_UNSUPPORTED;
   if (!views || !status) return PGSAG_ERR_ARG;
   if (ban && ban->objective != PGSAG_OBJ_PG && ban->objective != PGSAG_OBJ_EQ11) return PGSAG_ERR_UNSUPPORTED;
   const bool soft = ban && ban->objective == PGSAG_OBJ_EQ11;
   cudaStream_t st = (cudaStream_t)stream;
+  ClearJob cj{};
+  if (clear) {
+    for (int i = 0; i < PGSAG_CLEAR_MAX; ++i) {
+      const uint64_t n = clear->n[i];
+      if (n == 0) continue;
+      if (!clear->ptr[i] || ((uintptr_t)clear->ptr[i] & 15u)) return PGSAG_ERR_ARG;
+      cj.p[i] = reinterpret_cast<float4*>(clear->ptr[i]);
+      cj.n4[i] = n / 4;
+      cj.tail[i] = clear->ptr[i] + 4 * (n / 4);
+      cj.n_tail[i] = (uint32_t)(n % 4);
+      cj.total += n / 4;
+    }
+  }
   if (n_pairs) {
     if (!grad2d || ((uintptr_t)grad2d & 15u)) return PGSAG_ERR_ARG;
     PGSAG_CUDA(cudaMemsetAsync(grad2d, 0, (size_t)n_pairs * PGSAG_GRAD2D_FLOATS * sizeof(float), st));
   }
-  if (n_active == 0) return PGSAG_OK;
+  if (n_active == 0) {
+    // no CTA runs: the buffers to clear are cleared here
+    if (clear)
+      for (int i = 0; i < PGSAG_CLEAR_MAX; ++i)
+        if (clear->n[i]) PGSAG_CUDA(cudaMemsetAsync(clear->ptr[i], 0, clear->n[i] * sizeof(float), st));
+    return PGSAG_OK;
+  }
   if (!rec || !ranges || !act_tiles || !px_list || !out8 || !aux || !dout8 || !grad2d) return PGSAG_ERR_ARG;
   if (ban && !(ban->nbr && ban->scratch && ban->acc)) return PGSAG_ERR_ARG;
   if (ban && ((uintptr_t)ban->nbr & 15u)) return PGSAG_ERR_ARG;
@@ -875,7 +934,7 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
     return PGSAG_ERR_ARG;
   if (soft)
     return launch_bwd<true>(sched, n_active, views, rec, dup_pairs, ranges, act_tiles, px_list, out8, aux, dout8,
-                            ddepth, bg, true, dout_scale, grad2d, status, st);
+                            ddepth, bg, true, dout_scale, grad2d, cj, status, st);
   return launch_bwd<false>(sched, n_active, views, rec, dup_pairs, ranges, act_tiles, px_list, out8, aux, dout8,
-                           ddepth, bg, ban != nullptr, dout_scale, grad2d, status, st);
+                           ddepth, bg, ban != nullptr, dout_scale, grad2d, cj, status, st);
 }

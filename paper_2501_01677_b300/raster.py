@@ -339,6 +339,23 @@ class Plan:
             return new_param_grads(P)
         return [torch.zeros_like(t) for t in P.tensors()]
 
+    def clearable(self, grads: Sequence[torch.Tensor]):
+        """grads if the render adjoint can clear them for preprocess_bwd(cleared=True)
+        (the plan's span covers every row and each buffer starts on 16 bytes), else
+        None (preprocess_bwd then overwrites every row of the span itself)."""
+        if (self.g_lo, self.g_hi) != (0, self.n_gauss) or any(t.data_ptr() % 16 for t in grads):
+            return None
+        return grads
+
+    def backward_grads(self, P: GaussianParams):
+        """(grads, clear, cleared) for an autograd backward: the buffers, what the
+        render adjoint must clear, and whether preprocess_bwd may take them as
+        zeros (new_grads returns zero-filled buffers for a partial span)."""
+        grads = self.new_grads(P)
+        full = (self.g_lo, self.g_hi) == (0, P.n)
+        clear = self.clearable(grads) if full else None
+        return grads, clear, (clear is not None) or not full
+
     def preprocess(self, P: GaussianParams, stream=None):
         s = _stream_ptr(stream)
         self.forward_count += 1
@@ -442,11 +459,21 @@ class Plan:
                                 L.LAMBDA_GC, 0, self.depth.data_ptr())
 
     def render_bwd(self, dout8: torch.Tensor, ddepth: Optional[torch.Tensor] = None,
-                   dout_scale: Optional[torch.Tensor] = None, stream=None, ban: bool = False):
+                   dout_scale: Optional[torch.Tensor] = None, stream=None, ban: bool = False,
+                   clear: Optional[Sequence[torch.Tensor]] = None):
         """Adjoint render into grad2d.  ban=True: dout8 comes from loss(fused=True)
-        and the deferred Eq. 8 gather runs in this kernel's prologue."""
+        and the deferred Eq. 8 gather runs in this kernel's prologue.  clear: the
+        raw-parameter gradient buffers of this step (shaped like P's tensors),
+        whose rows in the plan's span the kernel sets to zero on the side, for a
+        following preprocess_bwd(cleared=True)."""
         s = _stream_ptr(stream)
         bg = ctypes.byref(self._ban_gather()) if ban else None
+        cl = None
+        if clear is not None:
+            n, *ptrs = self._span(GaussianParams(*clear))
+            per_row = [t.numel() // max(self.n_gauss, 1) for t in clear]
+            cl = ctypes.byref(L.PgsagClear((ctypes.c_void_p * L.CLEAR_MAX)(*[p.value for p in ptrs]),
+                                           (ctypes.c_uint64 * L.CLEAR_MAX)(*[n * r for r in per_row])))
         # after a projection the binned rows are already zero: no full clear
         n_clear = 0 if self._grad2d_clear else self.n_pairs
         self._grad2d_clear = False
@@ -455,11 +482,16 @@ class Plan:
                                               _ptr(self.ranges), _ptr(self.act_tiles), self.n_active,
                                               _ptr(self.px_list), self._sched_arg(), _ptr(self.out8), _ptr(self.aux),
                                               _ptr(dout8), _ptr(ddepth), bg, _ptr(dout_scale), n_clear,
-                                              _ptr(self.grad2d), _ptr(self.status), s), "pgsag_render_bwd")
+                                              _ptr(self.grad2d), cl, _ptr(self.status), s), "pgsag_render_bwd")
 
     def preprocess_bwd(self, P: GaussianParams, grads: Sequence[torch.Tensor], accumulate=False, stream=None,
-                       dout_scale: Optional[torch.Tensor] = None):
+                       dout_scale: Optional[torch.Tensor] = None, cleared: bool = False):
+        """Chain rule into the raw-parameter gradients `grads`: overwritten, added
+        to (accumulate=True), or, with cleared=True, taken as zeros already (a
+        render_bwd(clear=grads) or zero-filled buffers) so that only the rows of
+        the Gaussians with a binned pair are written."""
         s = _stream_ptr(stream)
+        mode = 1 if accumulate else (2 if cleared else 0)
         gm, gl, gq, go, gs = grads
         # Eq. 11: the flattening term (1 - lambda) lambda_3 L_s
         fw = (1.0 - L.LAMBDA_GC) * L.LAMBDA_FLAT if self.objective == "eq11" else 0.0
@@ -468,7 +500,7 @@ class Plan:
             _, gm, gl, gq, go, gs = self._span(GaussianParams(gm, gl, gq, go, gs))
             L.check(self.lib.pgsag_preprocess_bwd(n, means, log_scales, quats, opacity_logit, sh, self.n_views,
                                                   _ptr(self.views_dev), _ptr(self.bininfo), _ptr(self.grad2d),
-                                                  1 if accumulate else 0, gm, gl, gq, go, gs, _ptr(dout_scale), fw,
+                                                  mode, gm, gl, gq, go, gs, _ptr(dout_scale), fw,
                                                   _ptr(self.status), s),
                     "pgsag_preprocess_bwd")
 
@@ -505,8 +537,9 @@ class Plan:
         self.render_fwd(stream)
         self.loss(lambda_ban, loss_out, stream, fused=True, P=P)
         self.tile_stats(stream, counts_only=True)
-        self.render_bwd(self.dout8, None, None, stream, ban=True)
-        self.preprocess_bwd(P, grads, accumulate, stream)
+        clear = None if accumulate else self.clearable(grads)
+        self.render_bwd(self.dout8, None, None, stream, ban=True, clear=clear)
+        self.preprocess_bwd(P, grads, accumulate, stream, cleared=clear is not None)
 
     def capture(self, P: GaussianParams, grads: Sequence[torch.Tensor], lambda_ban: float = LAMBDA_BAN):
         """CUDA graph of one whole step (see step); replay() runs it."""
@@ -653,9 +686,9 @@ class RenderLossFn(torch.autograd.Function):
         plan, P = ctx.plan, ctx.P
         _check_same_forward(ctx)
         g = g.contiguous().to(torch.float32)
-        plan.render_bwd(plan.dout8, None, g, ban=True)
-        grads = plan.new_grads(P)
-        plan.preprocess_bwd(P, grads, dout_scale=g)
+        grads, clear, cleared = plan.backward_grads(P)
+        plan.render_bwd(plan.dout8, None, g, ban=True, clear=clear)
+        plan.preprocess_bwd(P, grads, dout_scale=g, cleared=cleared)
         _finish_backward(ctx)
         return (None, None, None) + tuple(grads)
 
@@ -689,9 +722,9 @@ class RenderFn(torch.autograd.Function):
         g_out8 = g_out8.contiguous()
         if g_depth is not None:
             g_depth = g_depth.contiguous()
-        plan.render_bwd(g_out8, g_depth, None)
-        grads = plan.new_grads(P)
-        plan.preprocess_bwd(P, grads)
+        grads, clear, cleared = plan.backward_grads(P)
+        plan.render_bwd(g_out8, g_depth, None, clear=clear)
+        plan.preprocess_bwd(P, grads, cleared=cleared)
         _finish_backward(ctx)
         return (None, None) + tuple(grads)
 

@@ -213,6 +213,43 @@ def test_repeated_adjoint_after_one_forward(config0):
     assert rel_l2(second.ravel().astype(np.float64), first.ravel().astype(np.float64)) < 1e-5
 
 
+@pytest.mark.parametrize("objective", ["pg", "eq11"])
+def test_gradient_rows_cleared_by_the_render_adjoint(objective):
+    """The step's render adjoint clears the raw-parameter gradient buffers on the
+    side (pgsag_clear: float4 bodies split over its CTAs, 1-3 trailing floats),
+    and the projection adjoint over those zeros (accumulate = 2) writes only the
+    Gaussians with a binned pair and the flattening term.  Buffers filled with
+    NaN before the step end up bitwise equal to the mode that writes every row
+    (accumulate = 0, same grad2d): no row is left uncleared or written twice."""
+    from paper_2501_01677_b300 import raster
+    n = 1001  # means / log-scales 3003 floats, opacity 1001: trailing floats
+    g, v = syn.tiny_scene(21, n=n, width=83, height=61, coverage=0.4)
+    g.means[:150, 2] = -3.0  # behind the camera: never binned
+    P = raster.GaussianParams.from_numpy(g)
+    plan = raster.Plan([v.cam], [v.mask], [v.target], g.n)
+    plan.set_objective(objective)
+    plan.forward(P)
+    nan = [torch.full_like(t, float("nan")) for t in P.tensors()]
+    assert plan.clearable(nan) is not None
+    plan.step(P, nan)
+    ref = [torch.full_like(t, float("nan")) for t in P.tensors()]
+    plan.preprocess_bwd(P, ref)
+    torch.cuda.synchronize()
+    plan.check_status()
+    binned = plan.bininfo[:, 3].cpu().numpy() > 0
+    assert binned.sum() > 0 and not binned[:150].any()
+    for a, b in zip(nan, ref):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        assert np.isfinite(a).all()
+        assert np.array_equal(a, b)
+        rows = a.reshape(n, -1)
+        assert np.abs(rows[binned]).max() > 0
+    if objective == "pg":
+        assert all(float(np.abs(t.cpu().numpy().reshape(n, -1)[~binned]).max()) == 0.0 for t in nan)
+    else:  # the flattening term reaches every Gaussian's smallest log-scale
+        assert np.abs(nan[1].cpu().numpy()[~binned]).max() > 0
+
+
 def test_batched_views_equal_plain_views():
     """Several views (different resolutions, Gaussian subsets) in one plan give the
     same per-view results as one plan per view; the sort is bit-identical."""

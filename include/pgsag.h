@@ -471,8 +471,8 @@ int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const float* rec
 /*
  * pgsag_preprocess_bwd: chain rule from grad2d to the raw parameters (the
  * adjoint of pgsag_preprocess), summed over the views that render each Gaussian
- * (no atomics: one thread per Gaussian loops over its views; a block lists the
- * Gaussians of its slice that have a binned pair and runs the per-pair work
+ * (no atomics: one thread per Gaussian loops over its views; each warp lists
+ * the Gaussians of its 64 that have a binned pair and runs the per-pair work
  * over that list).  The argmin axis, the normal flip, the Jacobian clamp and
  * the colour clamp are locally constant.  accumulate = 0 overwrites the
  * outputs, 1 adds to them (the outputs of a Gaussian with no binned pair and no

@@ -525,23 +525,29 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
   }
   // dynamic shared memory: [view table | SH gradient slab]
   float* s_gsh = reinterpret_cast<float*>(smem_raw + views_bytes(n_views));
-  __shared__ uint32_t s_list[kPreBwdSlice];        // binned Gaussians of the slice (any order)
-  __shared__ uint32_t s_bits[kPreBwdSlice / 32];   // binned flags of the slice
-  __shared__ uint32_t s_nlist;
+  // Each warp works on its own 64 consecutive Gaussians of the block's slice,
+  // with its own list and its own 32 rows of the slab: no block barrier after
+  // the view table is set up.
+  constexpr int kPreWarps = kPreThreads / 32;
+  constexpr int kPerWarp = kPreBwdSlice / kPreWarps;
+  static_assert(kPerWarp == 64, "two Gaussians of a warp's share per lane");
+  __shared__ uint32_t s_list[kPreWarps][kPerWarp];  // each warp's Gaussians with a binned pair, ascending
   if (status_bad(status)) return;
-  const uint32_t gbase = blockIdx.x * kPreBwdSlice;
-  if (threadIdx.x == 0) s_nlist = 0;
   __syncthreads();
   set_campos(sv, n_views);
   __syncthreads();
   const float sc = dout_scale ? __ldg(dout_scale) : 1.f;
   const float zero3[3] = {0.f, 0.f, 0.f}, zero4[4] = {0.f, 0.f, 0.f, 0.f};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t wbase = blockIdx.x * kPreBwdSlice + warp * kPerWarp;
+  uint32_t* wl = s_list[warp];
 
   // 1. binned flags; a Gaussian with no binned pair gets its (zero or flattening
-  // only) gradient here, the others go to the list
+  // only) gradient here, the others go to the warp's list
+  uint32_t nl = 0, bits0 = 0, bits1 = 0;
 #pragma unroll
-  for (int k = 0; k < kPreBwdSlice / kPreThreads; ++k) {
-    const uint32_t li = k * kPreThreads + threadIdx.x, g = gbase + li;
+  for (int k = 0; k < 2; ++k) {
+    const uint32_t g = wbase + k * 32 + lane;
     bool binned = false;
     if (g < n) {
       for (uint32_t vi = 0; vi < n_views && !binned; ++vi) {
@@ -550,9 +556,9 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
       }
     }
     const uint32_t bal = __ballot_sync(kFull, binned);
-    if ((threadIdx.x & 31) == 0) s_bits[li >> 5] = bal;
+    (k == 0 ? bits0 : bits1) = bal;
     if (binned) {
-      s_list[atomicAdd(&s_nlist, 1u)] = g;
+      wl[nl + __popc(bal & ((1u << lane) - 1u))] = g;
     } else if (g < n) {
       float gls[3] = {0.f, 0.f, 0.f};
       const bool flat = add_flatten(g, log_scales, n, flatten_weight, sc, gls);
@@ -560,29 +566,38 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
       if (accumulate == 0 || flat)
         store_small(g, zero3, gls, zero4, 0.f, accumulate == 1, d_means, d_log_scales, d_quats, d_opac);
     }
+    nl += __popc(bal);
   }
-  __syncthreads();
-  const uint32_t nl = s_nlist;
-  if (accumulate == 0) {
+  if (accumulate == 0 && wbase < n) {
     // zero SH rows of the Gaussians without a binned pair (coalesced float4)
-    const uint32_t nb = min((uint32_t)kPreBwdSlice, n - gbase);
-    float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * gbase);
-    for (uint32_t i = threadIdx.x; i < nb * 12; i += blockDim.x) {
+    const uint32_t nb = min((uint32_t)kPerWarp, n - wbase);
+    float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * wbase);
+    for (uint32_t i = lane; i < nb * 12; i += 32) {
       const uint32_t row = i / 12;
-      if (!((s_bits[row >> 5] >> (row & 31)) & 1u)) dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!(((row < 32 ? bits0 : bits1) >> (row & 31)) & 1u)) dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+  // the list length goes through shared memory: held in a register across the
+  // per-Gaussian work below it costs some 290 B of spills per thread
+  __shared__ uint32_t s_nl[kPreWarps];
+  if (lane == 0) s_nl[warp] = nl;
+  __syncwarp();
+  nl = s_nl[warp];
 
   // 2. the adjoint of every binned pair of the listed Gaussians, one Gaussian per
-  // thread and round (full warps), SH gradients summed in the slab row
-  for (uint32_t base = 0; base < nl; base += kPreThreads) {
-    for (int i = threadIdx.x; i < kPreThreads * kShStride; i += blockDim.x) s_gsh[i] = 0.f;
-    __syncthreads();
-    const uint32_t li = base + threadIdx.x;
+  // lane and round, SH gradients summed in the lane's slab row
+  for (uint32_t base = 0; base < nl; base += 32) {
+    // the warp's 32 slab rows zeroed together before a warp barrier (a lane that
+    // zeroes its own row lets the compiler hold the row's sums in registers:
+    // 56 B of spills per thread)
+    for (uint32_t i = threadIdx.x & 31; i < 32 * kShStride; i += 32)
+      s_gsh[(threadIdx.x & ~31u) * kShStride + i] = 0.f;
+    __syncwarp();
+    const uint32_t li = base + (threadIdx.x & 31);
     if (li < nl) {
-      const uint32_t g = s_list[li];
-      float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gol = 0.f;
       float* gsh = s_gsh + threadIdx.x * kShStride;
+      const uint32_t g = s_list[threadIdx.x >> 5][li];
+      float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gol = 0.f;
       const GaussIn G = load_gauss(g, means, log_scales, quats, opacity_logit);
       for (uint32_t vi = 0; vi < n_views; ++vi) {
         const pgsag_view& V = sv[vi];
@@ -762,14 +777,14 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
       add_flatten(g, log_scales, n, flatten_weight, sc, gls);
       store_small(g, gm, gls, gq, gol, accumulate == 1, d_means, d_log_scales, d_quats, d_opac);
     }
-    __syncthreads();
+    __syncwarp();
     // SH gradient rows of this round: coalesced float4 stores, 12 per row
-    const uint32_t nr = min((uint32_t)kPreThreads, nl - base);
-    for (uint32_t i = threadIdx.x; i < nr * 12; i += blockDim.x) {
+    const uint32_t nr = min(32u, nl - base);
+    for (uint32_t i = threadIdx.x & 31; i < nr * 12; i += 32) {
       const uint32_t row = i / 12, c4 = i - row * 12;
-      const float* sg = s_gsh + row * kShStride + 4 * c4;
+      const float* sg = s_gsh + ((threadIdx.x & ~31u) + row) * kShStride + 4 * c4;
       float4 v = make_float4(sg[0], sg[1], sg[2], sg[3]);
-      float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * s_list[base + row]) + c4;
+      float4* dst = reinterpret_cast<float4*>(d_sh + 48ull * s_list[threadIdx.x >> 5][base + row]) + c4;
       if (accumulate == 1) {
         const float4 o = *dst;
         v.x += o.x;
@@ -779,7 +794,7 @@ __global__ void __launch_bounds__(kPreThreads, PGSAG_PRE_BWD_MINB) k_preprocess_
       }
       *dst = v;
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 

@@ -557,15 +557,17 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
 
 // kSoft: objective Eq. 11 -- the loss gradients get the (1 - lambda) factor and
 // every blended alpha the soft-count GC-load gradient dL/dg~ of its pixel.
-// Buffers the adjoint's CTAs set to zero on the side (pgsag_clear): the float4
-// body of each buffer is cut into one share per CTA; the at most 3 trailing
-// floats of a buffer are cleared by CTA 0.
+// Buffers the adjoint's CTAs set to zero on the side (pgsag_clear): their
+// float4 bodies, laid end to end (buffer i holds units [start[i], start[i+1])),
+// are cut into one share of `per` units per CTA (32-bit: the host checks the
+// range); the at most 3 trailing floats of a buffer are cleared by CTA 0.
 struct ClearJob {
   float4* p[PGSAG_CLEAR_MAX];
-  uint64_t n4[PGSAG_CLEAR_MAX];  // float4 units of the body
+  uint32_t start[PGSAG_CLEAR_MAX + 1];
+  uint32_t per;
   float* tail[PGSAG_CLEAR_MAX];
   uint32_t n_tail[PGSAG_CLEAR_MAX];
-  uint64_t total;  // sum of n4
+  bool on;
 };
 
 // Streaming stores (evict-first in L2): they drain while the CTA renders and
@@ -576,20 +578,12 @@ __device__ __forceinline__ void clear_share(const ClearJob& cj) {
     for (int i = 0; i < PGSAG_CLEAR_MAX; ++i)
       if (threadIdx.x < cj.n_tail[i]) cj.tail[i][threadIdx.x] = 0.f;
   }
-  const uint64_t per = (cj.total + gridDim.x - 1) / gridDim.x;
-  uint64_t lo = (uint64_t)blockIdx.x * per;
-  const uint64_t hi = min(cj.total, lo + per);
-  uint64_t off = 0;
+  const uint32_t lo = blockIdx.x * cj.per, hi = min(cj.start[PGSAG_CLEAR_MAX], lo + cj.per);
 #pragma unroll
   for (int i = 0; i < PGSAG_CLEAR_MAX; ++i) {
-    const uint64_t end = off + cj.n4[i];
-    if (lo < hi && lo < end) {
-      const uint64_t b = min(hi, end) - off;
-      for (uint64_t k = lo - off + threadIdx.x; k < b; k += blockDim.x)
-        __stcs(cj.p[i] + k, make_float4(0.f, 0.f, 0.f, 0.f));
-      lo = min(hi, end);
-    }
-    off = end;
+    const uint32_t b = min(hi, cj.start[i + 1]);
+    for (uint32_t k = max(lo, cj.start[i]) + threadIdx.x; k < b; k += blockDim.x)
+      __stcs(cj.p[i] + (k - cj.start[i]), make_float4(0.f, 0.f, 0.f, 0.f));
   }
 }
 
@@ -613,8 +607,7 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
   __shared__ int s_wmax[2][kWarps];
   uint32_t round = 0;
   if (status_bad(status)) return;
-  if (clear.total | clear.n_tail[0] | clear.n_tail[1] | clear.n_tail[2] | clear.n_tail[3] | clear.n_tail[4])
-    clear_share(clear);
+  if (clear.on) clear_share(clear);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float gscale_in = dout_scale ? __ldg(dout_scale) : 1.f;
   // Eq. 11: the photometric / normal-loss gradients are scaled by (1 - lambda)
@@ -881,9 +874,11 @@ static int launch_bwd(const pgsag_sched* sched, uint32_t n_active, const pgsag_v
                      s, blocks);
   if (r) return r;
   if (s.counter) PGSAG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(uint32_t), st));
+  ClearJob job = cj;
+  job.per = (uint32_t)(((uint64_t)job.start[PGSAG_CLEAR_MAX] + blocks - 1) / blocks);
   k_render_bwd<PGSAG_BWD_WARPS, kSoft><<<blocks, PGSAG_BWD_WARPS * 32, 0, st>>>(
       views, (const float4*)rec, dup_pairs, (const uint2*)ranges, (const uint4*)act_tiles, n_active, px_list, s,
-      (const float4*)out8, (const uint4*)aux, (const float4*)dout8, ddepth, bg, use_ban, dout_scale, grad2d, cj,
+      (const float4*)out8, (const uint4*)aux, (const float4*)dout8, ddepth, bg, use_ban, dout_scale, grad2d, job,
       status);
   PGSAG_CHECK_LAUNCH();
   return PGSAG_OK;
@@ -901,28 +896,39 @@ extern "C" int pgsag_render_bwd(uint32_t n_views, const pgsag_view* views, const
   const bool soft = ban && ban->objective == PGSAG_OBJ_EQ11;
   cudaStream_t st = (cudaStream_t)stream;
   ClearJob cj{};
+  bool clear_by_memset = false;
   if (clear) {
+    uint64_t total = 0;
     for (int i = 0; i < PGSAG_CLEAR_MAX; ++i) {
       const uint64_t n = clear->n[i];
+      cj.start[i] = (uint32_t)total;
       if (n == 0) continue;
       if (!clear->ptr[i] || ((uintptr_t)clear->ptr[i] & 15u)) return PGSAG_ERR_ARG;
       cj.p[i] = reinterpret_cast<float4*>(clear->ptr[i]);
-      cj.n4[i] = n / 4;
       cj.tail[i] = clear->ptr[i] + 4 * (n / 4);
       cj.n_tail[i] = (uint32_t)(n % 4);
-      cj.total += n / 4;
+      cj.on = true;
+      total += n / 4;
+    }
+    // shares are indexed in 32 bits (with a CTA's share added): beyond 2^31
+    // float4 units (32 GiB) the buffers are cleared by memsets instead
+    if (total >= (1ull << 31)) {
+      clear_by_memset = true;
+      cj = ClearJob{};
+    } else {
+      cj.start[PGSAG_CLEAR_MAX] = (uint32_t)total;
     }
   }
   if (n_pairs) {
     if (!grad2d || ((uintptr_t)grad2d & 15u)) return PGSAG_ERR_ARG;
     PGSAG_CUDA(cudaMemsetAsync(grad2d, 0, (size_t)n_pairs * PGSAG_GRAD2D_FLOATS * sizeof(float), st));
   }
-  if (n_active == 0) {
-    // no CTA runs: the buffers to clear are cleared here
+  if (n_active == 0 || clear_by_memset) {
+    // no CTA runs (or the buffers are too large for its shares): memsets
     if (clear)
       for (int i = 0; i < PGSAG_CLEAR_MAX; ++i)
         if (clear->n[i]) PGSAG_CUDA(cudaMemsetAsync(clear->ptr[i], 0, clear->n[i] * sizeof(float), st));
-    return PGSAG_OK;
+    if (n_active == 0) return PGSAG_OK;
   }
   if (!rec || !ranges || !act_tiles || !px_list || !out8 || !aux || !dout8 || !grad2d) return PGSAG_ERR_ARG;
   if (ban && !(ban->nbr && ban->scratch && ban->acc)) return PGSAG_ERR_ARG;

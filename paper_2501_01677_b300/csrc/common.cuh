@@ -133,10 +133,18 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
 }
-__device__ __forceinline__ int warp_max_i(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
-  return v;
+__device__ __forceinline__ int warp_max_i(int v) { return __reduce_max_sync(kFull, v); }
+// Warp-wide float minimum / maximum in one instruction (redux.sync .f32,
+// Blackwell); exact, so every lane obtains the same value a shuffle tree would.
+__device__ __forceinline__ float warp_min_f(float v) {
+  float r;
+  asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+  float r;
+  asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
 }
 
 // Masked D-SSIM passes (ssim.cu), launched by pgsag_loss_ban.

@@ -162,14 +162,7 @@ __device__ __forceinline__ float4 warp_pixel_box(const Pix& P) {
     y0 = fminf(y0, P.py.y);
     y1 = fmaxf(y1, P.py.y);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    x0 = fminf(x0, __shfl_xor_sync(kFull, x0, o));
-    x1 = fmaxf(x1, __shfl_xor_sync(kFull, x1, o));
-    y0 = fminf(y0, __shfl_xor_sync(kFull, y0, o));
-    y1 = fmaxf(y1, __shfl_xor_sync(kFull, y1, o));
-  }
-  return make_float4(x0, x1, y0, y1);
+  return make_float4(warp_min_f(x0), warp_max_f(x1), warp_min_f(y0), warp_max_f(y1));
 }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }

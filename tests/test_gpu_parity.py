@@ -250,6 +250,38 @@ def test_gradient_rows_cleared_by_the_render_adjoint(objective):
         assert np.abs(nan[1].cpu().numpy()[~binned]).max() > 0
 
 
+def test_maximum_view_count():
+    """PGSAG_MAX_VIEWS (256) views in one plan, each with its own principal point
+    and mask: the view table fills 39 KB of the projection's shared memory and,
+    with the SH slab, takes the projection adjoint past the 48 KB default.  Each
+    sampled view renders bitwise as in a plan of its own, and the gradient of
+    the 256-view loss equals the sum over four 64-view plans (float atomics
+    order aside)."""
+    n_max = 256
+    g, v = syn.tiny_scene(8, n=300, width=24, height=20, coverage=0.7)
+    c = v.cam
+    views = []
+    for k in range(n_max):
+        cam = syn.Camera(c.R, c.t, c.fx, c.fy, c.cx + 0.7 * (k % 9 - 4), c.cy + 0.6 * (k // 9 % 7 - 3),
+                         c.width, c.height, c.znear)
+        views.append(syn.View(cam, np.ascontiguousarray(np.roll(v.mask, k, axis=1)),
+                              np.ascontiguousarray(np.roll(v.target, k, axis=1))))
+    plan, P = gpu_run(g, views)
+    assert plan.n_views == n_max
+    for k in (0, 131, n_max - 1):
+        one, _ = gpu_run(g, [views[k]], grad=False)
+        a, b = plan.images(k), one.images(0)
+        for ch in ("rgb", "dist", "normal", "alpha", "n_contrib", "depth"):
+            assert np.array_equal(a[ch].cpu().numpy(), b[ch].cpu().numpy()), (k, ch)
+    parts = [gpu_run(g, views[i:i + 64])[1] for i in range(0, n_max, 64)]
+    for name, t, *ts in zip(("means", "log_scales", "quats", "opacity_logit", "sh"), P.tensors(),
+                            *[q.tensors() for q in parts]):
+        ref = sum(x.grad.detach().cpu().numpy().astype(np.float64) for x in ts).ravel()
+        got = t.grad.detach().cpu().numpy().astype(np.float64).ravel()
+        assert np.abs(ref).max() > 0
+        assert rel_l2(got, ref) < 1e-5, name
+
+
 def test_batched_views_equal_plain_views():
     """Several views (different resolutions, Gaussian subsets) in one plan give the
     same per-view results as one plan per view; the sort is bit-identical."""

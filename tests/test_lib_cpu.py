@@ -42,6 +42,7 @@ def test_view_struct_layout(lib):
 
 def test_struct_layouts(lib):
     assert ctypes.sizeof(L.PgsagBanGather) == 64
+    assert ctypes.sizeof(L.PgsagClear) == 80
     assert ctypes.sizeof(L.PgsagDssim) == 32
     assert ctypes.sizeof(L.PgsagAdamTensor) == 48
     assert ctypes.sizeof(L.PgsagDepthView) == 96
@@ -92,4 +93,32 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.pgsag_vote_filter(10, st, 1, ctypes.byref(v), st, 3, 0, st, st, st, st, None) == -1
     assert lib.pgsag_vote_pack_mask(100, 10, st, 3, st, None) == -1
     assert lib.pgsag_vote_compact_workspace_size(0) == 4
+
+
+def test_adjoint_clear_and_accumulate_modes_checked_on_host(lib):
+    """The render adjoint's side clear takes 16-byte aligned buffers and the
+    projection adjoint's accumulate modes 0-2; a view count beyond
+    PGSAG_MAX_VIEWS is refused; all before any device work."""
+    st = ctypes.c_void_p(16)
+
+    def render_bwd(n_views, clear):
+        return lib.pgsag_render_bwd(n_views, st, None, None, None, None, 0, None, None, None, None, None, None, None,
+                                    None, 0, None, clear, st, None)
+
+    def clear_of(ptr, n):
+        c = L.PgsagClear()
+        c.ptr[0], c.n[0] = ptr, n
+        return ctypes.byref(c)
+    assert render_bwd(1, clear_of(24, 8)) == -1          # not 16-byte aligned
+    assert render_bwd(1, clear_of(None, 8)) == -1        # null buffer with floats to clear
+    assert render_bwd(L.MAX_VIEWS + 1, None) == -5
+    args = [10, st, st, st, st, st, 1, st, st, st, None, st, st, st, st, st, None, 0.0, st, None]
+    for bad in (-1, 3):
+        a = list(args)
+        a[10] = bad
+        assert lib.pgsag_preprocess_bwd(*a) == -1
+    a = list(args)
+    a[6] = L.MAX_VIEWS + 1
+    a[10] = 0
+    assert lib.pgsag_preprocess_bwd(*a) == -5
     assert lib.pgsag_vote_compact_workspace_size(4097) == 8

@@ -26,6 +26,7 @@ __device__ __forceinline__ void status_set(int32_t* st, unsigned flag) {
 // Camera / view fields needed per chunk, read from the device view table.
 struct ViewLite {
   float fx, fy, cx, cy;
+  float ifx, ify;  // 1 / fx, 1 / fy: a pixel's ray (u + 1/2 - cx) / fx is taken as (u + 1/2 - cx) * ifx
   int width, height, tile_w, tile_h;
   uint64_t pix_base;
 };
@@ -35,6 +36,8 @@ __device__ __forceinline__ ViewLite load_view_lite(const pgsag_view* v) {
   r.fy = __ldg(&v->fy);
   r.cx = __ldg(&v->cx);
   r.cy = __ldg(&v->cy);
+  r.ifx = 1.f / r.fx;
+  r.ify = 1.f / r.fy;
   r.width = __ldg(&v->width);
   r.height = __ldg(&v->height);
   r.tile_w = __ldg(&v->tile_w);

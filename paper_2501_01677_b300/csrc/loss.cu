@@ -51,8 +51,8 @@ __device__ __forceinline__ PixCtx pix_ctx(uint32_t c, int lane, const uint4* __r
 }
 
 __device__ __forceinline__ void ray(const ViewLite& V, int x, int y, float r[3]) {
-  r[0] = ((float)x + 0.5f - V.cx) / V.fx;
-  r[1] = ((float)y + 0.5f - V.cy) / V.fy;
+  r[0] = ((float)x + 0.5f - V.cx) * V.ifx;
+  r[1] = ((float)y + 0.5f - V.cy) * V.ify;
   r[2] = 1.f;
 }
 
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
         ray(P.V, P.x + 1, P.y, rr);
         const float dv = dq[1] - dq[0], du = dq[3] - dq[2];
         a[0] = dv * r[0];
-        a[1] = fmaf(dv, rd[1], dq[0] * (2.f / P.V.fy));
+        a[1] = fmaf(dv, rd[1], dq[0] * (2.f * P.V.ify));
         a[2] = dv;
-        b[0] = fmaf(du, rr[0], dq[2] * (2.f / P.V.fx));
+        b[0] = fmaf(du, rr[0], dq[2] * (2.f * P.V.ifx));
         b[1] = du * r[1];
         b[2] = du;
       }

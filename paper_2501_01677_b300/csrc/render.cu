@@ -235,7 +235,7 @@ __device__ __forceinline__ void write_pixel(uint64_t gp, float4 cd, float4 nt, u
   out8[2 * gp + 0] = cd;
   out8[2 * gp + 1] = make_float4(nt.x, nt.y, nt.z, 1.f - nt.w);
   // Eq. 4: ray-plane depth
-  const float rx = (x - V.cx) / V.fx, ry = (y - V.cy) / V.fy;
+  const float rx = (x - V.cx) * V.ifx, ry = (y - V.cy) * V.ify;
   const float sdot = -(nt.x * rx + nt.y * ry + nt.z);
   const bool valid = cnt > 0 && sdot > kRayDotMin && cd.w > 0.f;
   depth[gp] = valid ? cd.w / sdot : 0.f;
@@ -505,7 +505,7 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
   const float T = __uint_as_float(ax.x);
   last = ax.z > 0 ? (int)ax.y : -1;
   const float4 g0 = __ldg(dout8 + 2 * gp), g1 = __ldg(dout8 + 2 * gp + 1);
-  const float rx = (px + (float)ox - V.cx) / V.fx, ry = (py + (float)oy - V.cy) / V.fy;
+  const float rx = (px + (float)ox - V.cx) * V.ifx, ry = (py + (float)oy - V.cy) * V.ify;
   float3 gn = make_float3(g1.x, g1.y, g1.z);
   float gd = ddepth != nullptr ? __ldg(ddepth + gp) : 0.f;
   if (use_ban) {

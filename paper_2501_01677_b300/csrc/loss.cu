@@ -10,6 +10,7 @@
 // (loss, own-pixel gradient, neighbour scratch, optionally the GC-load sums)
 // is followed either by pass B here or by the same gather in the render
 // adjoint's prologue.
+#include <float.h>
 #include <mutex>
 
 #include "common.cuh"
@@ -147,10 +148,12 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
       }
       if (inV) {
         const float cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-        const float cn = sqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-        const float Nn = sqrtf(o1.x * o1.x + o1.y * o1.y + o1.z * o1.z);
-        if (cn > 0.f && Nn > 0.f) {
-          const float icn = 1.f / cn, iNn = 1.f / Nn;
+        // unit vectors by reciprocal square roots of the squared norms (a norm
+        // this side of the smallest normal float is taken as zero)
+        const float c2 = cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2];
+        const float n2 = o1.x * o1.x + o1.y * o1.y + o1.z * o1.z;
+        if (c2 >= FLT_MIN && n2 >= FLT_MIN) {
+          const float icn = rsqrtf(c2), iNn = rsqrtf(n2);
           const float nd[3] = {cr[0] * icn, cr[1] * icn, cr[2] * icn};
           const float nr[3] = {o1.x * iNn, o1.y * iNn, o1.z * iNn};
           const float w = (f & PGSAG_PIX_EDGE) ? kWBoundary : 1.f;

@@ -446,12 +446,16 @@ struct BwdPix {
 // Deferred Eq. 8 adjoint (the loss's second pass, run here): dL/dP of the pixel's
 // back-projected point P = Depth r, gathered from the 4 neighbours whose central
 // differences used it (their dL/da, dL/db in the loss scratch), as dL/dDepth;
-// the rendered-normal gradient from the loss is scaled by lambda / |V|.
+// the rendered-normal gradient from the loss is scaled by lambda / |V|
+// (`scale`, ban_scale of the pixel's view).
 // Returns dL/dDepth; scales gn (dL/dN) in place.  q: the pixel's compact index.
-__device__ __forceinline__ float ban_gather(const pgsag_ban_gather& bg, uint32_t view, uint64_t q, float rx, float ry,
-                                            float3& gn) {
+__device__ __forceinline__ float ban_scale(const pgsag_ban_gather& bg, uint32_t view) {
   const double nV = bg.acc[8 * view + 2];
-  const float scale = nV > 0.0 ? (float)((double)bg.lambda_ban / nV) : 0.f;
+  return nV > 0.0 ? (float)((double)bg.lambda_ban / nV) : 0.f;
+}
+
+__device__ __forceinline__ float ban_gather(const pgsag_ban_gather& bg, float scale, uint64_t q, float rx, float ry,
+                                            float3& gn) {
   gn.x *= scale;
   gn.y *= scale;
   gn.z *= scale;
@@ -483,7 +487,7 @@ __device__ __forceinline__ float ban_gather(const pgsag_ban_gather& bg, uint32_t
 __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, int ox, int oy, const ViewLite& V,
                                               uint32_t view, float gscale, const uint4* __restrict__ aux,
                                               const float4* __restrict__ dout8, const float* __restrict__ ddepth,
-                                              bool use_ban, const pgsag_ban_gather& ban,
+                                              bool use_ban, const pgsag_ban_gather& ban, float bscale,
                                               const float4* __restrict__ out8, float v[10], int& last,
                                               bool soft, float gscale_gc) {
   const uint4 ax = __ldg(aux + gp);
@@ -509,7 +513,7 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
   float3 gn = make_float3(g1.x, g1.y, g1.z);
   float gd = ddepth != nullptr ? __ldg(ddepth + gp) : 0.f;
   if (use_ban) {
-    gd += ban_gather(ban, view, gp, rx, ry, gn);
+    gd += ban_gather(ban, bscale, gp, rx, ry, gn);
   }
   v[0] = gscale * g0.x;
   v[1] = gscale * g0.y;
@@ -524,9 +528,11 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
     gd *= gscale;
     if (gd != 0.f && dep_route) {
       // Depth = D / s > 0 exactly when the pixel is valid; dDepth/dD = 1 / s,
-      // dDepth/dN = D / s^2 r = Depth / s r
+      // dDepth/dN = D / s^2 r = Depth / s r (1 / s by the fast reciprocal:
+      // s is in (1e-8, 2] on a valid pixel, and the exact division's
+      // multi-instruction sequence cost the adjoint 8 us)
       if (dep > 0.f) {
-        const float is = 1.f / (soft ? -(nrm.x * rx + nrm.y * ry + nrm.z) : __uint_as_float(ax.w));
+        const float is = __fdividef(1.f, soft ? -(nrm.x * rx + nrm.y * ry + nrm.z) : __uint_as_float(ax.w));
         v[3] += gd * is;
         const float kk = gd * dep * is;
         v[4] += kk * rx;
@@ -537,7 +543,7 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
       const float4 o0 = __ldg(out8 + 2 * gp), o1 = __ldg(out8 + 2 * gp + 1);
       const float sdot = -(o1.x * rx + o1.y * ry + o1.z);
       if (sdot > kRayDotMin && o0.w > 0.f) {
-        const float is = 1.f / sdot;
+        const float is = __fdividef(1.f, sdot);
         v[3] += gd * is;
         const float kk = gd * o0.w * is * is;
         v[4] += kk * rx;
@@ -613,6 +619,8 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
     if (t >= n_items) break;
     const TileInfo ti = load_tile(t, act_tiles, ranges);
     const ViewLite V = load_view_lite(views + ti.view);
+    // the Eq. 8 scale lambda / |V| of the tile's view (once per tile, not per pixel)
+    const float bscale = use_ban ? ban_scale(ban, ti.view) : 0.f;
     // coordinate origin: the 32-pixel-aligned corner of the 32x32 cell holding
     // the tile (every supported tile lies in one cell), so offsets round the
     // same way whatever the tile size
@@ -643,9 +651,9 @@ __global__ void __launch_bounds__(kWarps * 32, PGSAG_BWD_MINB) k_render_bwd(
           float w0[10], w1[10];
           int l0, l1;
           load_upstream(P.has0 ? P.q0 : ti.px_first, P.px.x, P.py.x, ox, oy, V, ti.view, gscale, aux, dout8, ddepth,
-                        use_ban, ban, out8, w0, l0, kSoft, gscale_in);
+                        use_ban, ban, bscale, out8, w0, l0, kSoft, gscale_in);
           load_upstream(P.has1 ? P.q1 : ti.px_first, P.px.y, P.py.y, ox, oy, V, ti.view, gscale, aux, dout8, ddepth,
-                        use_ban, ban, out8, w1, l1, kSoft, gscale_in);
+                        use_ban, ban, bscale, out8, w1, l1, kSoft, gscale_in);
 #pragma unroll
           for (int k = 0; k < 10; ++k) {
             v0[k] = P.has0 ? w0[k] : v0[k];

@@ -99,13 +99,13 @@ __global__ void __launch_bounds__(kLossThreads, PGSAG_LOSS_MINB) k_loss_a(
       // Eq. 9 term of this rendered pixel: g / w (g = Gaussians blended, or the
       // soft count g~ = sum of their alphas)
       const float g = soft ? __uint_as_float(__ldg(&aux[P.q].w)) : (float)__ldg(&aux[P.q].z);
-      gx = g / __ldg(gc_weight + P.q);
+      gx = __fdividef(g, __ldg(gc_weight + P.q));  // w >= 1
       gn = 1.f;
     }
     float dC[3] = {0.f, 0.f, 0.f}, dNo[3] = {0.f, 0.f, 0.f};
     if (f & PGSAG_PIX_MASK) {
       const uint32_t nm = __ldg(&views[P.view].n_mask);
-      const float inv3m = nm ? l1_scale / (3.f * (float)nm) : 0.f;
+      const float inv3m = nm ? __fdividef(l1_scale, 3.f * (float)nm) : 0.f;
       const float C[3] = {o0.x, o0.y, o0.z};
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {

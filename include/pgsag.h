@@ -276,7 +276,7 @@ int pgsag_preprocess(uint32_t n_gauss, const float* means, const float* log_scal
  *   2. exclusive scan of the tile counts -> ranges, in active-tile order;
  *   3. scatter of the duplicates into their tiles' ranges;
  *   4. per tile, sort of the range by the 64-bit key (depth_key << 32 | pair):
- *      a warp in registers for lists of up to 512, else a block in shared
+ *      a warp in registers for lists of up to 256, else a block in shared
  *      memory (chunks of 2048 merged in global memory).
  * The result equals a sort of K keys (tile, depth, index) and is bit-exact and
  * deterministic (the sort key is unique).

@@ -469,9 +469,9 @@ def test_autotuner_picks_a_shape_and_caches_it(tmp_path, monkeypatch):
     plan.check_status()
 
 
-@pytest.mark.parametrize("n,seed,kmin", [(1500, 11, 513), (5000, 16, 4097), (9000, 14, 8193)])
+@pytest.mark.parametrize("n,seed,kmin", [(400, 20, 257), (1500, 11, 513), (5000, 16, 4097), (9000, 14, 8193)])
 def test_long_tile_lists_sorted_through_merges(n, seed, kmin):
-    """Tile lists longer than a warp sorts on its own (512 entries) go to the
+    """Tile lists longer than a warp sorts on its own (256 entries) go to the
     block sort: one shared-memory pass up to 2048 entries, beyond that sorted
     chunks merged in global memory (an even and an odd number of merge
     rounds).  The list is still in strictly ascending (depth key, pair) order

@@ -503,8 +503,8 @@ __device__ __forceinline__ void load_upstream(uint64_t gp, float px, float py, i
     // view's rendered pixels; dL/dg~_i = (lambda / (n sigma)) (x_i - mean) / w_i,
     // with {lambda / (n sigma), mean} per view from the loss pass
     const float2 cm = *reinterpret_cast<const float2*>(ban.acc + 8 * view + 3);
-    const float w = __ldg(ban.gc_weight + gp);
-    v[9] = gscale_gc * cm.x * (__uint_as_float(ax.w) / w - cm.y) / w;
+    const float iw = __fdividef(1.f, __ldg(ban.gc_weight + gp));  // w >= 1
+    v[9] = gscale_gc * cm.x * (__uint_as_float(ax.w) * iw - cm.y) * iw;
   }
   const float T = __uint_as_float(ax.x);
   last = ax.z > 0 ? (int)ax.y : -1;

@@ -122,3 +122,33 @@ def test_adjoint_clear_and_accumulate_modes_checked_on_host(lib):
     a[10] = 0
     assert lib.pgsag_preprocess_bwd(*a) == -5
     assert lib.pgsag_vote_compact_workspace_size(4097) == 8
+
+
+def test_autograd_backward_asks_for_the_clear_only_where_it_can():
+    """The autograd backward hands the render adjoint the gradient buffers to
+    clear only when the plan spans every Gaussian and each buffer starts on 16
+    bytes (the C ABI's alignment); a plan over a span gets zero-filled buffers
+    instead, which the projection adjoint may also take as zeros."""
+    import torch
+    from paper_2501_01677_b300 import raster
+    n = 10
+    P = raster.GaussianParams(torch.zeros(n, 3), torch.zeros(n, 3), torch.zeros(n, 4), torch.zeros(n),
+                              torch.zeros(n, 16, 3))
+
+    def plan(lo, hi):
+        p = raster.Plan.__new__(raster.Plan)  # host logic only: no device buffers
+        p.g_lo, p.g_hi, p.n_gauss = lo, hi, n
+        return p
+    full, part = plan(0, n), plan(2, 7)
+    grads = [torch.zeros_like(t) for t in P.tensors()]
+    assert full.clearable(grads) is grads
+    assert part.clearable(grads) is None
+    shifted = [torch.zeros(t.numel() + 1)[1:].view(t.shape) for t in P.tensors()]  # 4 bytes past an allocation
+    assert all(t.data_ptr() % 16 == 4 for t in shifted)
+    assert full.clearable(shifted) is None
+    g, clear, cleared = full.backward_grads(P)
+    assert clear is g and cleared
+    assert [t.shape for t in g] == [t.shape for t in P.tensors()]
+    g, clear, cleared = part.backward_grads(P)
+    assert clear is None and cleared
+    assert all(float(t.abs().max()) == 0.0 for t in g)
